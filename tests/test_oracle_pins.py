@@ -1,0 +1,442 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle (oracle/ifctn_oracle.c) against an independent
+formulation: brute-force sums over every rank tuple (eq. iFCTN), the FCTN
+contraction of cherry cores built by Def. 1 (eq. FCTN), the explicit
+sub-network matrix of Prop. 1, transposition invariance (Prop. 3), printed
+numbers (Tables 5 and 6), textbook special cases (rank-1 CP, N=2 proximal ALS),
+explicit dense least-squares systems for the block updates (eq. updateG),
+the monotone decrease of Lemma 2 and the planted fixed point.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_16358_gb300 import inputs as inp
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def _problem(dims, edge, seed, dist="normal"):
+    N = len(dims)
+    R = inp.rank_matrix(N, edge)
+    G = inp.gaussian_factors(dims, R, seed) if dist == "normal" else inp.uniform_factors(dims, R, seed)
+    return R, G
+
+
+def _bruteforce_ifctn(dims, R, G):
+    """eq. (iFCTN) literally: for every entry, sum over every tuple of rank
+    indices r_{k,l} (k<l) of the product of all N(N-1) cherry-factor entries."""
+    N = len(dims)
+    F = inp.unpack_factors(G, dims, R)
+    pairs = [(k, l) for k in range(N) for l in range(k + 1, N)]
+    ranges = [range(int(R[k][l])) for k, l in pairs]
+    out = np.zeros(dims)
+    for idx in itertools.product(*[range(d) for d in dims]):
+        tot = 0.0
+        for rt in itertools.product(*ranges):
+            r = {}
+            for (k, l), rv in zip(pairs, rt):
+                r[(k, l)] = r[(l, k)] = rv
+            prod = 1.0
+            for k in range(N):
+                for l in range(N):
+                    if l != k:
+                        prod *= F[(k, l)][r[(k, l)], idx[k]]
+            tot += prod
+        out[idx] = tot
+    return out
+
+
+def _khatri_rao(A, B):
+    """Column-wise Kronecker product of Sec. 2.1: c_{(i-1)n+j,l} = a_{il} b_{jl}."""
+    m, r = A.shape
+    n, r2 = B.shape
+    assert r == r2
+    return (A[:, None, :] * B[None, :, :]).reshape(m * n, r)
+
+
+def _fold_littleendian(M, shape, k):
+    """Inverse of the mode-k unfolding of Sec. 2.1 (first remaining index fastest)."""
+    rest = [shape[m] for m in range(len(shape)) if m != k]
+    T = M.reshape([shape[k]] + rest, order="F")
+    return np.moveaxis(T, 0, k)
+
+
+def _unfold_littleendian(T, k):
+    return np.moveaxis(T, k, 0).reshape(T.shape[k], -1, order="F")
+
+
+def _cherry_core(dims, R, F, k):
+    """Def. 1: core whose mode-k unfolding is (M_N kr ... kr M_{k+1} kr M_{k-1} kr ... kr M_1)^T
+    with M_m = G_{k,m}; modes (R_{1,k},...,I_k,...,R_{k,N})."""
+    N = len(dims)
+    order = [m for m in range(N - 1, -1, -1) if m != k]
+    # Def. 1 writes M_m in R^{R_m x I_k}; the KR product of Sec. 2.1 pairs the
+    # columns (index i_k), so the product's row index runs over the rank tuple.
+    C = F[(k, order[0])]
+    for m in order[1:]:
+        C = _khatri_rao(C, F[(k, m)])  # rows: rank tuple, first listed factor slowest
+    # C is (prod R) x I_k = (G_(k))^T
+    shape = [int(R[k][m]) if m != k else int(dims[k]) for m in range(N)]
+    return _fold_littleendian(C.T, shape, k)
+
+
+def _fctn_contract(dims, cores):
+    """eq. (FCTN): sum over every rank index of the product of the N cores."""
+    N = len(dims)
+    letters = iter("abcdefghijklmnopqrstuvwxyz")
+    pair_letter = {}
+    for k in range(N):
+        for l in range(k + 1, N):
+            pair_letter[(k, l)] = pair_letter[(l, k)] = next(letters)
+    idx_letter = [next(letters) for _ in range(N)]
+    subs = []
+    for k in range(N):
+        subs.append("".join(idx_letter[k] if m == k else pair_letter[(k, m)] for m in range(N)))
+    return np.einsum(",".join(subs) + "->" + "".join(idx_letter), *cores)
+
+
+# ---------------------------------------------------------------------------
+# reconstruction, eq. (iFCTN)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,edge,seed", [
+    ((3, 4, 2), {(0, 1): 2, (0, 2): 3, (1, 2): 1}, 11),
+    ((2, 3, 2, 3), {(0, 1): 2, (0, 2): 1, (0, 3): 2, (1, 2): 2, (1, 3): 1, (2, 3): 2}, 12),
+    ((4, 3), {(0, 1): 3}, 13),
+])
+def test_reconstruct_matches_bruteforce_rank_sum(dims, edge, seed):
+    R, G = _problem(dims, edge, seed)
+    ref = _bruteforce_ifctn(dims, R, G)
+    got = oracle.reconstruct(dims, R, G)
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("dims,edge,seed", [
+    ((3, 4, 2), {(0, 1): 2, (0, 2): 3, (1, 2): 2}, 21),
+    ((2, 3, 4, 2), {(0, 1): 2, (0, 2): 3, (0, 3): 1, (1, 2): 2, (1, 3): 3, (2, 3): 2}, 22),
+])
+def test_reconstruct_equals_fctn_of_cherry_cores(dims, edge, seed):
+    """Def. 1 cores (KR-structured, little-endian unfolding) contracted by eq. (FCTN)."""
+    R, G = _problem(dims, edge, seed)
+    F = inp.unpack_factors(G, dims, R)
+    cores = [_cherry_core(dims, R, F, k) for k in range(len(dims))]
+    # the entry of core k at rank tuple r and index i_k is prod_m G_{k,m}(r_m, i_k)
+    k = 1
+    rr = [0] * len(dims)
+    rr[k] = 1
+    expect = np.prod([F[(k, m)][0, 1] for m in range(len(dims)) if m != k])
+    assert np.isclose(cores[k][tuple(rr)], expect)
+    ref = _fctn_contract(dims, cores)
+    got = oracle.reconstruct(dims, R, G)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-13 * np.abs(ref).max())
+
+
+def test_three_way_remark_formula():
+    """The N = 3 remark of Sec. 3: explicit triple sum over r12, r13, r23."""
+    dims = (4, 3, 5)
+    R, G = _problem(dims, {(0, 1): 3, (0, 2): 2, (1, 2): 4}, 31)
+    F = inp.unpack_factors(G, dims, R)
+    ref = np.einsum("ai,bi,aj,cj,bk,ck->ijk", F[(0, 1)], F[(0, 2)], F[(1, 0)], F[(1, 2)],
+                    F[(2, 0)], F[(2, 1)])
+    np.testing.assert_allclose(oracle.reconstruct(dims, R, G), ref, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_prop1_subnetwork_unfolding(k):
+    """Prop. 1: (X_(k))^T = Z_k (G_(k))^T, Z_k = diag(vec S_k) (kron_{i=N..1, i!=k} G_{i,k}^T),
+    S_k the broadcast product of G_{i,j}^T G_{j,i} over pairs without k."""
+    dims = (3, 2, 4, 3)
+    edge = {(0, 1): 2, (0, 2): 3, (0, 3): 2, (1, 2): 1, (1, 3): 2, (2, 3): 3}
+    R, G = _problem(dims, edge, 40 + k)
+    N = len(dims)
+    F = inp.unpack_factors(G, dims, R)
+    rest = [m for m in range(N) if m != k]
+    S = np.ones([dims[m] for m in rest])
+    for a_, i in enumerate(rest):
+        for b_, j in enumerate(rest):
+            if b_ <= a_:
+                continue
+            Wij = F[(i, j)].T @ F[(j, i)]
+            shp = [1] * len(rest)
+            shp[a_], shp[b_] = dims[i], dims[j]
+            S = S * Wij.reshape(shp)
+    K = None
+    for i in range(N - 1, -1, -1):
+        if i == k:
+            continue
+        K = F[(i, k)].T if K is None else np.kron(K, F[(i, k)].T)
+    Z = S.reshape(-1, order="F")[:, None] * K
+    core = _cherry_core(dims, R, F, k)
+    Gk = _unfold_littleendian(core, k)  # I_k x prod R
+    X = oracle.reconstruct(dims, R, G)
+    np.testing.assert_allclose(Z @ Gk.T, _unfold_littleendian(X, k).T, rtol=1e-12, atol=1e-13)
+
+
+def test_prop3_transposition_invariance():
+    dims = (3, 4, 2, 5)
+    edge = {(0, 1): 2, (0, 2): 3, (0, 3): 1, (1, 2): 2, (1, 3): 3, (2, 3): 2}
+    R, G = _problem(dims, edge, 51)
+    F = inp.unpack_factors(G, dims, R)
+    X = oracle.reconstruct(dims, R, G)
+    for n in [(2, 0, 3, 1), (3, 2, 1, 0), (1, 0, 2, 3)]:
+        dn = tuple(dims[m] for m in n)
+        Rn = np.zeros((4, 4), dtype=np.int32)
+        for a in range(4):
+            for b in range(4):
+                if a != b:
+                    Rn[a, b] = R[n[a], n[b]]
+        Gn = np.concatenate([F[(n[k], n[l])].ravel() for k in range(4) for l in range(4) if l != k])
+        np.testing.assert_allclose(oracle.reconstruct(dn, Rn, Gn), np.transpose(X, n),
+                                   rtol=1e-13, atol=1e-14)
+
+
+def test_rank_one_is_cp_outer_product():
+    dims = (3, 4, 5, 2)
+    R, G = _problem(dims, 1, 61)
+    F = inp.unpack_factors(G, dims, R)
+    u = [np.prod([F[(k, l)][0] for l in range(4) if l != k], axis=0) for k in range(4)]
+    ref = np.einsum("i,j,k,l->ijkl", *u)
+    np.testing.assert_allclose(oracle.reconstruct(dims, R, G), ref, rtol=1e-13, atol=1e-15)
+
+
+def test_table5_parameter_count():
+    (row,) = _golden("table5_parameter_count.txt")
+    I1, I2, I3, r12, r13, r23, n_ifctn, n_fctn = map(int, row)
+    R = inp.rank_matrix(3, {(0, 1): r12, (0, 2): r13, (1, 2): r23})
+    assert oracle.param_count((I1, I2, I3), R) == n_ifctn
+    assert inp.factor_size((I1, I2, I3), R) == n_ifctn
+    # an FCTN core k holds I_k * prod_{l != k} R_{k,l} entries (eq. FCTN)
+    fctn = sum(d * np.prod([R[k][l] for l in range(3) if l != k]) for k, d in enumerate((I1, I2, I3)))
+    assert fctn == n_fctn
+
+
+def test_table6_observed_rows_pin_metric_conventions():
+    """RSE of the zero-filled observation = sqrt(missing fraction) and constant
+    RMSE over missing entries: the printed Observed rows of Table 6."""
+    rows = _golden("table6_observed_rows.txt")
+    shape = (214, 61, 144)  # Guangzhou traffic tensor shape (Sec. 5.3)
+    xt = 0.5 + 0.1 * inp.normal(77, int(np.prod(shape))).reshape(shape)
+    rmses = []
+    for _, miss, rse_printed, _rmse_printed in rows:
+        miss = float(miss)
+        mask = inp.uniform_mask(shape, 1.0 - miss, 78)
+        Xobs = oracle.init_x(xt, mask)
+        rse, rmse = oracle.metrics(xt, Xobs, mask)
+        assert abs(rse - float(rse_printed)) < 1.5e-3, (miss, rse, rse_printed)
+        rmses.append(rmse)
+    assert max(rmses) - min(rmses) < 2e-3 * max(rmses)
+
+
+# ---------------------------------------------------------------------------
+# block update, eq. (updateG)
+# ---------------------------------------------------------------------------
+
+def _explicit_A(dims, R, G, k, i, j):
+    """Dense coefficient matrix of column j of G_{k,i}: the model is linear in
+    that column, so column r of A is the slice i_k = j of the reconstruction
+    with the column set to e_r (computed by the FCTN route, not the oracle)."""
+    F = inp.unpack_factors(G.copy(), dims, R)
+    cols = []
+    for r in range(int(R[k][i])):
+        Gm = G.copy()
+        Fm = inp.unpack_factors(Gm, dims, R)
+        Fm[(k, i)][:, j] = 0.0
+        Fm[(k, i)][r, j] = 1.0
+        cores = [_cherry_core(dims, R, Fm, m) for m in range(len(dims))]
+        Xr = _fctn_contract(dims, cores)
+        cols.append(np.take(Xr, j, axis=k).ravel())
+    del F
+    return np.stack(cols, axis=1)
+
+
+@pytest.mark.parametrize("k,i,j", [(0, 1, 2), (1, 0, 0), (2, 1, 3), (3, 0, 1), (1, 3, 2)])
+def test_block_system_equals_dense_normal_equations(k, i, j):
+    dims = (3, 4, 5, 2)
+    edge = {(0, 1): 2, (0, 2): 3, (0, 3): 2, (1, 2): 2, (1, 3): 3, (2, 3): 1}
+    R, G = _problem(dims, edge, 70 + k)
+    X = inp.normal(71, int(np.prod(dims))).reshape(dims)
+    A = _explicit_A(dims, R, G, k, i, j)
+    x = np.take(X, j, axis=k).ravel()
+    H, b = oracle.block_system(dims, R, G, X, k, i, j)
+    np.testing.assert_allclose(H, A.T @ A, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(b, A.T @ x, rtol=1e-12, atol=1e-12)
+
+
+def _numpy_sweep(dims, R, rho, G, X, mask):
+    """Algorithm 1, one sweep, from explicit dense systems (tiny sizes only)."""
+    N = len(dims)
+    G = G.copy()
+    X = X.copy()
+    for k in range(N):
+        for i in range(N):
+            if i == k:
+                continue
+            F = inp.unpack_factors(G, dims, R)
+            newcols = []
+            for j in range(dims[k]):
+                A = _explicit_A(dims, R, G, k, i, j)
+                x = np.take(X, j, axis=k).ravel()
+                n = A.shape[1]
+                g = np.linalg.solve(A.T @ A + rho * np.eye(n), A.T @ x + rho * F[(k, i)][:, j])
+                newcols.append(g)
+            F[(k, i)][:, :] = np.stack(newcols, axis=1)
+    cores = [_cherry_core(dims, R, inp.unpack_factors(G, dims, R), m) for m in range(N)]
+    rec = _fctn_contract(dims, cores)
+    Xn = np.where(mask.astype(bool), X, (rec + rho * X) / (1 + rho))
+    return G, Xn
+
+
+def test_sweep_equals_dense_gauss_seidel_pam():
+    dims = (3, 2, 4)
+    R, G0 = _problem(dims, {(0, 1): 2, (0, 2): 1, (1, 2): 2}, 81)
+    xt = inp.normal(82, int(np.prod(dims))).reshape(dims)
+    mask = inp.uniform_mask(dims, 0.6, 83)
+    X0 = oracle.init_x(xt, mask)
+    Gref, Xref = _numpy_sweep(dims, R, 0.3, G0, X0, mask)
+    G = G0.copy()
+    X = X0.copy()
+    oracle.sweep(dims, R, 0.3, G, X, mask)
+    np.testing.assert_allclose(G, Gref, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(X, Xref, rtol=1e-10, atol=1e-12)
+
+
+def test_two_way_case_is_proximal_als():
+    """N = 2: X = G_{1,2}^T G_{2,1}; each block is textbook proximal ALS."""
+    dims = (6, 5)
+    R, G = _problem(dims, 3, 91)
+    F = inp.unpack_factors(G, dims, R)
+    A0, B0 = F[(0, 1)].copy(), F[(1, 0)].copy()
+    X = inp.normal(92, 30).reshape(dims)
+    mask = np.ones(dims, dtype=np.uint8)
+    rho = 0.2
+    A1 = np.linalg.solve(B0 @ B0.T + rho * np.eye(3), B0 @ X.T + rho * A0)
+    B1 = np.linalg.solve(A1 @ A1.T + rho * np.eye(3), A1 @ X + rho * B0)
+    Gw = G.copy()
+    Xw = X.copy()
+    oracle.sweep(dims, R, rho, Gw, Xw, mask)
+    Fw = inp.unpack_factors(Gw, dims, R)
+    np.testing.assert_allclose(Fw[(0, 1)], A1, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(Fw[(1, 0)], B1, rtol=1e-12, atol=1e-13)
+    np.testing.assert_array_equal(Xw, X)  # fully observed: X is never changed
+
+
+def test_cholesky_solver():
+    rng = inp.normal(93, 64).reshape(8, 8)
+    H = rng @ rng.T + 0.5 * np.eye(8)
+    b = inp.normal(94, 8)
+    np.testing.assert_allclose(oracle.cholesky_solve(H, b), np.linalg.solve(H, b), rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# whole sweeps: Lemma 2, stationarity, fixed point
+# ---------------------------------------------------------------------------
+
+def test_sufficient_decrease_lemma2_every_sweep():
+    dims = (8, 7, 6)
+    R, Gt = _problem(dims, {(0, 1): 2, (0, 2): 3, (1, 2): 2}, 101)
+    xt = oracle.reconstruct(dims, R, Gt)
+    mask = inp.uniform_mask(dims, 0.4, 102)
+    rho = 0.1
+    G = inp.uniform_factors(dims, R, 103)
+    X = oracle.init_x(xt, mask)
+    F = oracle.objective(dims, R, G, X)
+    for _ in range(8):
+        G0, X0 = G.copy(), X.copy()
+        oracle.sweep(dims, R, rho, G, X, mask)
+        F1 = oracle.objective(dims, R, G, X)
+        step = np.sum((G - G0) ** 2) + np.sum((X - X0) ** 2)
+        assert F - F1 >= 0.5 * rho * step - 1e-12 * max(F, 1.0), (F, F1, step)
+        F = F1
+
+
+def test_first_order_conditions_hold_after_block():
+    """First-order condition of each block (appendix, proof of Lemma 3):
+    A^T(A g - x) + rho (g - g_old) = 0 for the updated column."""
+    dims = (4, 3, 5)
+    R, G0 = _problem(dims, {(0, 1): 2, (0, 2): 3, (1, 2): 2}, 111)
+    X = inp.normal(112, 60).reshape(dims)
+    mask = np.zeros(dims, dtype=np.uint8)
+    rho = 0.25
+    G = G0.copy()
+    oracle.sweep(dims, R, rho, G, X.copy(), mask)
+    # block (0,1) is the first block, computed from the initial state
+    F0 = inp.unpack_factors(G0, dims, R)
+    Fn = inp.unpack_factors(G, dims, R)
+    for j in range(dims[0]):
+        Gs = G0.copy()
+        A = _explicit_A(dims, R, Gs, 0, 1, j)
+        x = np.take(X, j, axis=0).ravel()
+        g, g0 = Fn[(0, 1)][:, j], F0[(0, 1)][:, j]
+        grad = A.T @ (A @ g - x) + rho * (g - g0)
+        scale = np.linalg.norm(A.T @ x) + rho * np.linalg.norm(g0)
+        assert np.linalg.norm(grad) <= 1e-12 * scale
+
+
+def test_planted_truth_is_fixed_point_under_full_observation():
+    dims = (6, 5, 4, 3)
+    R, Gt = _problem(dims, 2, 121)
+    xt = oracle.reconstruct(dims, R, Gt)
+    mask = np.ones(dims, dtype=np.uint8)
+    G, X = Gt.copy(), xt.copy()
+    st = oracle.sweep(dims, R, 0.1, G, X, mask)
+    np.testing.assert_allclose(G, Gt, rtol=1e-11, atol=1e-12)
+    np.testing.assert_array_equal(X, xt)
+    assert st["objective"] <= 1e-20 * np.sum(xt ** 2)
+
+
+def test_perturbed_planted_start_converges_monotonically():
+    dims = (7, 6, 5)
+    R, Gt = _problem(dims, 2, 131)
+    xt = oracle.reconstruct(dims, R, Gt)
+    mask = np.ones(dims, dtype=np.uint8)
+    G = Gt + 1e-3 * inp.normal(132, Gt.size)
+    X = xt.copy()
+    log = oracle.complete(dims, R, 0.1, G, X, mask, max_sweeps=30)
+    obj = [s["objective"] for s in log]
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(obj, obj[1:]))
+    assert obj[-1] < 1e-3 * obj[0]
+
+
+def test_observed_entries_unchanged_and_update_closed_form():
+    dims = (5, 4, 6)
+    R, G = _problem(dims, 2, 141)
+    xt = inp.normal(142, 120).reshape(dims)
+    mask = inp.uniform_mask(dims, 0.5, 143)
+    X = oracle.init_x(xt, mask)
+    X0 = X.copy()
+    G1 = G.copy()
+    oracle.sweep(dims, R, 0.1, G1, X, mask)
+    rec = oracle.reconstruct(dims, R, G1)
+    obs = mask.astype(bool)
+    np.testing.assert_array_equal(X[obs], X0[obs])
+    np.testing.assert_allclose(X[~obs], (rec[~obs] + 0.1 * X0[~obs]) / 1.1, rtol=1e-14, atol=1e-15)
+    np.testing.assert_array_equal(X0[~obs], 0.0)  # X^0 = P_Omega(O)
+
+
+def test_thread_count_does_not_change_results():
+    dims = (9, 8, 7)
+    R, G = _problem(dims, 3, 151)
+    xt = inp.normal(152, int(np.prod(dims))).reshape(dims)
+    mask = inp.uniform_mask(dims, 0.3, 153)
+    outs = []
+    for nt in (1, 4):
+        Gw, Xw = G.copy(), oracle.init_x(xt, mask)
+        oracle.sweep(dims, R, 0.1, Gw, Xw, mask, nthreads=nt)
+        outs.append((Gw, Xw))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
