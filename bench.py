@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the iFCTN PAM sweep on one GB300 (or N replicas, one per GPU).
+
+Workload (default): the multispectral-image shaped problem, 256 x 256 x 31
+FP32 in [0,1], planted iFCTN with all ranks 6 plus N(0, 0.01^2) noise, 10%
+uniformly observed, rho = 0.1, 100 sweeps per job, mixed precision.  One
+"step" is one whole completion job (100 PAM sweeps) starting from the job's
+initial state, which is restored from device-resident copies before the step;
+L2 is flushed (a 256 MiB write) before every timed step.  The metric is PAM
+sweeps per second over the whole job (all ranks).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (the reference arm of this benchmark).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PAM sweeps/s"
+UNIT = "sweeps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="msi256x256x31_r6")
+    ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64"])
+    ap.add_argument("--quick", action="store_true", help="skip the FP64-path, time-to-RSE and e2e extras")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampling during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload inputs (planted with the library's own reconstruction)
+# ---------------------------------------------------------------------------
+def make_inputs(w, b, inp):
+    dims, R = w.dims, w.R
+    Gt = inp.gaussian_factors(dims, R, inp.planted_factor_seed(w))
+    P = int(np.prod(dims))
+    prob = b.make_problem(dims, R, rho=w.rho, max_sweeps=0, tol=0.0, precision=b.FP64)
+    ctx = b.create(prob, np.zeros(P), np.zeros(P, dtype=np.uint8), Gt)
+    planted = b.reconstruct(ctx, np.empty(dims, dtype=np.float64))
+    b.destroy(ctx)
+    xt, mask, _ = inp.workload_inputs(w, planted)
+    return xt, mask
+
+
+def time_steps(b, torch, ctx, stream, X0_dev, G0_dev, sweeps, steps, warmup, flush):
+    times = []
+    for it in range(warmup + steps):
+        b.set_factors(ctx, G0_dev)
+        b.set_x(ctx, X0_dev)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            b.sweep_async(ctx, sweeps)
+            e.record(stream)
+        stream.synchronize()
+        if it >= warmup:
+            times.append(s.elapsed_time(e) / 1000.0)
+    st = b.sweep(ctx, 0)  # surfaces any device-side failure
+    return times, st
+
+
+def stage_times(b, torch, ctx, stream, N, reps=20):
+    """Average device time per launch of each stage kernel (CUDA events on the
+    context's stream)."""
+    out = {}
+    for stage, name in ((0, "contract"), (1, "gram"), (2, "solve"), (3, "xupdate")):
+        modes = range(N) if stage != 3 else [0]
+        for k in modes:
+            for _ in range(3):
+                b.launch_stage(ctx, stage, k)
+            with torch.cuda.stream(stream):
+                s = torch.cuda.Event(enable_timing=True)
+                e = torch.cuda.Event(enable_timing=True)
+                s.record(stream)
+                for _ in range(reps):
+                    b.launch_stage(ctx, stage, k)
+                e.record(stream)
+            stream.synchronize()
+            out[f"{name}{k}" if stage != 3 else name] = s.elapsed_time(e) / reps / 1000.0
+    return out
+
+
+def rse_curve(b, ctx, xt, sweeps):
+    b.set_truth(ctx, xt, log=True)
+    b.sweep(ctx, sweeps)
+    log = b.get_log(ctx)
+    return [r["rse"] for r in log[-sweeps:]]
+
+
+def cpu_baseline(w, budget_s=12.0):
+    import oracle
+    from paper_2511_16358_gb300 import inputs as inp
+    dims, R = w.dims, w.R
+    planted = oracle.reconstruct(dims, R, inp.gaussian_factors(dims, R, inp.planted_factor_seed(w)))
+    xt, mask, G0 = inp.workload_inputs(w, planted)
+    X = oracle.init_x(xt, mask)
+    rec = oracle.reconstruct(dims, R, G0)
+    N = len(dims)
+    G = G0 * (np.linalg.norm(X) / np.sqrt(w.p_observed) / np.linalg.norm(rec)) ** (1.0 / (N * (N - 1)))
+    cores = os.cpu_count() or 1
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.sweep(dims, R, w.rho, G, X, mask, nthreads=cores)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= 200:
+            break
+    return {"value": n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} FP64 oracle sweeps of {w.name} on {cores} host threads ({el:.1f} s)"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2511_16358_gb300 import inputs as inp
+    dims, R = w.dims, w.R
+    planted = oracle.reconstruct(dims, R, inp.gaussian_factors(dims, R, inp.planted_factor_seed(w)))
+    xt, mask, G0 = inp.workload_inputs(w, planted)
+    X = oracle.init_x(xt, mask)
+    rec = oracle.reconstruct(dims, R, G0)
+    N = len(dims)
+    G = G0 * (np.linalg.norm(X) / np.sqrt(w.p_observed) / np.linalg.norm(rec)) ** (1.0 / (N * (N - 1)))
+    cores = os.cpu_count() or 1
+    per = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.sweep(dims, R, w.rho, G, X, mask, nthreads=cores)
+        if it >= args.warmup:
+            per.append(time.perf_counter() - t0)
+    tot = sum(per)
+    v = len(per) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(per),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "dims": list(dims), "sweeps_per_step": 1,
+                                             "implementation": "FP64 CPU oracle (C, OpenMP)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"1 oracle sweep of {w.name} per step, {cores} host threads"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    from paper_2511_16358_gb300 import inputs as inp
+    w = inp.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2511_16358_gb300 import binding as b
+
+    prec = b.MIXED if (args.precision or w.precision) == "mixed" else b.FP64
+    dt = b.tensor_dtype(prec)
+    sweeps = w.sweeps
+    xt, mask = make_inputs(w, b, inp)
+    P = xt.size
+    dims = w.dims
+    N = len(dims)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+
+    def new_ctx(precision, n):
+        return b.create(b.make_problem(dims, w.R, rho=w.rho, max_sweeps=n, tol=0.0, precision=precision,
+                                       seed=4000 + w.seed_base),
+                        xt.astype(b.tensor_dtype(precision)), mask, None, stream.cuda_stream)
+
+    ctx = new_ctx(prec, sweeps)
+    G0 = torch.empty(inp.factor_size(dims, w.R), dtype=torch.float64, device="cuda")
+    b.get_factors(ctx, G0)
+    X0 = torch.empty(dims, dtype=torch.float32 if dt == np.float32 else torch.float64, device="cuda")
+    b.get_x(ctx, X0)
+    kps = b.kernels_per_sweep(ctx)
+
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times, st_last = time_steps(b, torch, ctx, stream, X0, G0, sweeps, args.steps, args.warmup, flush)
+    ck = clocks.stop()
+    torch.cuda.synchronize()
+    tot = sum(times)
+    if dist:
+        t = torch.tensor([tot], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    value = world * args.steps * sweeps / tot
+
+    extras = {}
+    # per-stage device times (separate context: stages mutate the state)
+    pctx = new_ctx(prec, sweeps)
+    stt = stage_times(b, torch, pctx, stream, N)
+    b.destroy(pctx)
+    sz = np.dtype(dt).itemsize
+    per_sweep = {}
+    for key, v in stt.items():
+        base = key.rstrip("0123456789")
+        per_sweep[base] = per_sweep.get(base, 0.0) + v
+    dominant = max(per_sweep, key=per_sweep.get)
+    contract_t = sum(v for kk, v in stt.items() if kk.startswith("contract")) / N
+    alg_bytes = P * sz  # one read of X per contraction launch
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = alg_bytes / contract_t / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_contract (mode-k streaming contraction)",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "stage_seconds_per_launch": stt, "stage_share_per_sweep": {
+                    k: v / sum(per_sweep.values()) for k, v in per_sweep.items()},
+                "dominant_stage": dominant}
+
+    if not args.quick and rank == 0:
+        # plain FP64 GPU path on the same job
+        if prec == b.MIXED:
+            c64 = new_ctx(b.FP64, sweeps)
+            G064 = torch.empty_like(G0)
+            b.get_factors(c64, G064)
+            X064 = torch.empty(dims, dtype=torch.float64, device="cuda")
+            b.get_x(c64, X064)
+            t64, _ = time_steps(b, torch, c64, stream, X064, G064, sweeps, max(1, min(args.steps, 3)), 1, flush)
+            v64 = sweeps * len(t64) / sum(t64)
+            extras["fp64_path"] = {"value": v64, "unit": UNIT, "speedup_mixed_over_fp64": value / world / v64}
+            # time-to-RSE: RSE* = FP64 RSE after the job's sweeps x (1 + 1e-3)
+            b.set_factors(c64, G064)
+            b.set_x(c64, X064)
+            r64 = rse_curve(b, c64, xt.astype(np.float64), sweeps)
+            b.set_factors(ctx, G0)
+            b.set_x(ctx, X0)
+            r32 = rse_curve(b, ctx, xt.astype(np.float32), sweeps)
+            target = r64[-1] * (1 + 1e-3)
+            s32 = next((i + 1 for i, r in enumerate(r32) if r <= target), None)
+            s64 = next((i + 1 for i, r in enumerate(r64) if r <= target), None)
+            extras["time_to_rse"] = {
+                "rse_target": target, "rse_fp64_final": r64[-1], "rse_mixed_final": r32[-1],
+                "sweeps_mixed": s32, "sweeps_fp64": s64,
+                "seconds_mixed": (s32 / (value / world)) if s32 else None,
+                "seconds_fp64": (s64 / v64) if s64 else None}
+            b.destroy(c64)
+        # end to end through the public API with host buffers
+        import torch as _t
+        obs_h = _t.from_numpy(xt.astype(dt)).pin_memory()
+        mask_h = _t.from_numpy(mask.astype(np.uint8)).pin_memory()
+        out_h = _t.empty(dims, dtype=obs_h.dtype).pin_memory()
+        e2e = []
+        for it in range(2 + args.steps):
+            t0 = time.perf_counter()
+            c = b.create(b.make_problem(dims, w.R, rho=w.rho, max_sweeps=sweeps, tol=0.0, precision=prec,
+                                        seed=4000 + w.seed_base), obs_h, mask_h, None, None)
+            b.complete(c, out_h)
+            b.destroy(c)
+            if it >= 2:
+                e2e.append(time.perf_counter() - t0)
+        extras["e2e"] = {"value": sweeps * len(e2e) / sum(e2e), "unit": UNIT,
+                         "h2d_bytes_per_step": int(P * (sz + 1)), "d2h_bytes_per_step": int(P * sz)}
+        extras["cpu_baseline"] = cpu_baseline(w)
+    b.destroy(ctx)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == b.MIXED else "f64",
+                "data": "synthetic",
+                "config": {"workload": w.name, "dims": list(dims), "ranks": int(w.R[0][1]),
+                           "observed": w.p_observed, "sweeps_per_step": sweeps,
+                           "precision": "mixed (FP32 tensor/contractions, FP64 solves)" if prec == b.MIXED else "fp64",
+                           "l2": "flushed (256 MiB write) before every timed step",
+                           "parallelism": f"replicas x{world}"},
+                "gpu_launches": kps * sweeps * args.steps,
+                "clocks": ck, "roofline": roofline}
+        line.update(extras)
+        line.setdefault("e2e", None)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * ifctn.h -- C ABI of the GB300 (sm_103a) iFCTN tensor-completion library.
+ *
+ * The library runs the proximal alternating minimisation (PAM) solver of
+ * iFCTN-TC (Gan & Cui, "iFCTN: an intra-block Fully-Connected Tensor Network
+ * Decomposition for Tensor Completion"): Sec. 4.1 eq. (iFCTN-TC) is the model,
+ * Sec. 4.2 eq. (updateG) the factor blocks, eq. (updateX) the tensor block,
+ * Algorithm 1 the loop.  All arithmetic runs in the library's CUDA kernels.
+ *
+ * Conventions (every entry point):
+ *   - Dense tensors are C order (last index fastest), I_1 x ... x I_N,
+ *     2 <= N <= 4.
+ *   - Cherry factor G_{k,l} (k != l, Sec. 3 eq. (cherry_factor_set)) is an
+ *     R_{k,l} x I_k row-major matrix.  A "packed factor array" holds the
+ *     blocks in the order k = 0..N-1, then l = 0..N-1 (l != k), as FP64.
+ *   - ranks[k*4+l] is the symmetric iFCTN-rank matrix R (Def. 2); entries
+ *     with k,l < N, k != l must satisfy 1 <= R_{k,l} <= 8; others are ignored.
+ *   - The observation mask holds one byte per tensor entry, nonzero =
+ *     observed (the sample set Omega).
+ *   - Tensor buffers are FP64 when the problem's precision is IFCTN_FP64 and
+ *     FP32 when it is IFCTN_MIXED.  Factor buffers are always FP64.
+ *   - Every pointer argument may be host memory (pageable or pinned) or device
+ *     memory of the current device; the library detects which.  It copies
+ *     inputs into memory it owns; the caller keeps ownership of its buffers.
+ *   - No function throws.  Each returns an ifctn_status and, on failure,
+ *     records a message readable with ifctn_last_error() (per thread).
+ *   - A context is not thread-safe; a server is (submit/poll from any thread).
+ */
+#ifndef IFCTN_H
+#define IFCTN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IFCTN_OK = 0,
+    IFCTN_EINVAL = 1,     /* bad argument: shape, rank, rho, null pointer */
+    IFCTN_ENOMEM = 2,     /* device allocation failed or budget too small */
+    IFCTN_ECUDA = 3,      /* a CUDA call failed */
+    IFCTN_ENOTSPD = 4,    /* a proximal normal-equation matrix lost positive definiteness */
+    IFCTN_EBUSY = 5,      /* server queue full */
+    IFCTN_ENOTREADY = 6,  /* poll: job not finished yet (timeout 0) */
+    IFCTN_ETIMEOUT = 7,   /* poll timed out, or a bounded device wait gave up */
+    IFCTN_ENOTFOUND = 8   /* unknown ticket */
+} ifctn_status;
+
+typedef enum {
+    IFCTN_FP64 = 0,   /* tensor, contractions, solves, reductions all FP64 */
+    IFCTN_MIXED = 1   /* FP32 tensor and contractions (FP32 accumulate);
+                         FP64 factor master copy, normal-equation right-hand
+                         sides, Cholesky solves and cross-block reductions */
+} ifctn_precision;
+
+/* Algorithm 1's inputs (Sec. 4.2): order N, sizes, iFCTN ranks, proximal
+   weight rho, t_max, epsilon, plus the arithmetic mode and the seed of the
+   default initial factors. */
+typedef struct {
+    int32_t order;          /* N, 2..4 */
+    int64_t dims[4];        /* I_k >= 1 for k < N */
+    int32_t ranks[16];      /* R[k*4+l], symmetric, 1..8 off the diagonal */
+    double rho;             /* proximal weight, > 0 (paper default 0.1) */
+    int32_t max_sweeps;     /* t_max >= 0 (paper default 1000) */
+    double tol;             /* epsilon of the relative-change test; 0 = run all sweeps */
+    int32_t precision;      /* ifctn_precision */
+    uint64_t seed;          /* seed of G^(0) when no initial factors are given */
+} ifctn_problem;
+
+/* Per-sweep record.  rel_change = ||X^{s+1}-X^s||_F / ||X^s||_F (the stop test
+   of Algorithm 1); objective = 1/2 ||X^{s+1} - iFCTN(G^{s+1})||_F^2 (Sec. 4.1);
+   rse = ||X_true - X||_F / ||X_true||_F and rmse = sqrt(mean over missing
+   entries of (X_true - X)^2) (Sec. 5) when a ground truth was registered with
+   ifctn_set_truth and metric logging is on, else NaN. */
+typedef struct {
+    int32_t sweeps_done;
+    int32_t converged;
+    double rel_change;
+    double objective;
+    double rse;
+    double rmse;
+} ifctn_stats;
+
+typedef struct ifctn_ctx ifctn_ctx;
+typedef struct ifctn_server ifctn_server;
+
+/* Creates a solver context for one completion problem.
+   obs: the observation O (tensor dtype, see conventions); entries outside
+   Omega are ignored.  mask: one byte per entry.  X^(0) = P_Omega(O) with zeros
+   elsewhere (Algorithm 1, initialisation).  init_factors: packed FP64 G^(0),
+   or NULL for the default: seeded U(0,1) entries rescaled by one common
+   factor so that ||iFCTN(G^0)||_F = ||P_Omega(O)||_F / sqrt(|Omega|/P).
+   cuda_stream: a cudaStream_t to run on, or NULL for a stream owned by the
+   context.  On success *out receives the context (free with ifctn_destroy). */
+ifctn_status ifctn_create(const ifctn_problem* prob, const void* obs, const uint8_t* mask,
+                          const double* init_factors, void* cuda_stream, ifctn_ctx** out);
+
+/* Runs n sweeps of Algorithm 1 (eq. (updateG) for every block in the order
+   k = 1..N, i != k ascending, each block with the latest other factors; then
+   eq. (updateX)), ignoring tol.  Blocks until done.  out (nullable) receives
+   the record of the last sweep. */
+ifctn_status ifctn_sweep(ifctn_ctx* ctx, int32_t n, ifctn_stats* out);
+
+/* Enqueues n sweeps (tol ignored) on the context's stream and returns without
+   waiting, so that callers can pipeline or time them with their own events on
+   that stream.  Device-side failures are reported by the next synchronous call
+   (e.g. ifctn_sweep(ctx, 0, &stats)). */
+ifctn_status ifctn_sweep_async(ifctn_ctx* ctx, int32_t n);
+
+/* Algorithm 1 from the current state: sweeps until rel_change < tol (tol > 0)
+   or until max_sweeps sweeps have run in this call.  out_X (nullable) receives
+   the recovered tensor; out (nullable) the last record. */
+ifctn_status ifctn_complete(ifctn_ctx* ctx, void* out_X, ifctn_stats* out);
+
+/* Writes iFCTN(G) of the current factors (eq. (iFCTN), Def. 2) into out
+   (tensor dtype, P entries). */
+ifctn_status ifctn_reconstruct(ifctn_ctx* ctx, void* out);
+
+/* Checkpoint / resume: the PAM state is (G, X) (Sec. 4.2). */
+ifctn_status ifctn_get_factors(ifctn_ctx* ctx, double* out);
+ifctn_status ifctn_set_factors(ifctn_ctx* ctx, const double* in);
+ifctn_status ifctn_get_x(ifctn_ctx* ctx, void* out);
+ifctn_status ifctn_set_x(ifctn_ctx* ctx, const void* in);
+
+/* Registers a ground-truth tensor (tensor dtype) for RSE/RMSE and turns
+   per-sweep metric logging on (log != 0) or off. */
+ifctn_status ifctn_set_truth(ifctn_ctx* ctx, const void* xtrue, int32_t log);
+
+/* Copies up to max per-sweep records (oldest first, of the sweeps run since
+   creation, capped at the last 4096) into out; *n receives the count. */
+ifctn_status ifctn_get_log(ifctn_ctx* ctx, ifctn_stats* out, int32_t max, int32_t* n);
+
+/* Stage-level access for verification: the mode-k regrouped quantities of
+   Prop. 1 at the current state, M_k = X_(k) Z_k (I_k x Q_k, row-major) and
+   K_k = Z_k^T Z_k (Q_k x Q_k), Q_k = prod_{m != k} R_{k,m}, rank index in C
+   order over the modes m != k ascending.  FP64 host or device buffers. */
+ifctn_status ifctn_mode_system(ifctn_ctx* ctx, int32_t k, double* Mk, double* Kk);
+
+/* Enqueues one launch of a single stage of the sweep on the context's stream,
+   without waiting (for per-kernel timing with CUDA events).  stage:
+     0 = the HBM-streaming mode-k contraction (partials of M_k),
+     1 = the mode-k Gram chain (K_k), 2 = the mode-k proximal solves (updates
+     the factors), 3 = the fused reconstruct + masked X update (updates X).
+   k is ignored by stage 3. */
+ifctn_status ifctn_launch_stage(ifctn_ctx* ctx, int32_t stage, int32_t k);
+
+/* Number of kernel launches one sweep issues (for launch accounting). */
+int32_t ifctn_kernels_per_sweep(const ifctn_ctx* ctx);
+
+void ifctn_destroy(ifctn_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+   Serving: continuous batching of completion jobs on one GPU.
+   A server owns a device-memory budget and up to max_slots resident jobs.
+   ifctn_submit copies the job's inputs to pinned host memory and queues it;
+   a scheduler thread admits queued jobs in arrival order as slots and budget
+   free up, runs the resident jobs' sweeps interleaved on separate CUDA streams
+   (so their kernels overlap on the device), and copies each result to pinned
+   host memory when its job finishes.  Every job runs exactly the kernels it
+   would run alone, so its result does not depend on the mix.
+   --------------------------------------------------------------------------- */
+ifctn_status ifctn_server_create(size_t hbm_budget_bytes, int32_t max_slots, ifctn_server** out);
+
+/* Queues one job (same inputs as ifctn_create; obs/mask/init are copied
+   before return).  *ticket receives the job id.  Fails with IFCTN_ENOMEM if
+   the job alone exceeds the budget. */
+ifctn_status ifctn_submit(ifctn_server* srv, const ifctn_problem* prob, const void* obs,
+                          const uint8_t* mask, const double* init_factors, uint64_t* ticket);
+
+/* Waits up to timeout_us microseconds (0 = do not wait, <0 = forever) for the
+   job.  On IFCTN_OK the result was copied to out_X (nullable; tensor dtype)
+   and out (nullable), and the ticket is released.  IFCTN_ENOTREADY (timeout 0)
+   or IFCTN_ETIMEOUT leave the job untouched. */
+ifctn_status ifctn_poll(ifctn_server* srv, uint64_t ticket, void* out_X, ifctn_stats* out,
+                        int64_t timeout_us);
+
+/* Server counters: jobs queued, resident, done; device bytes in use;
+   latency (submit to completion, seconds) of the i-th completed job. */
+typedef struct {
+    int64_t queued, resident, completed;
+    int64_t bytes_in_use;
+    int64_t peak_resident;
+} ifctn_server_info;
+ifctn_status ifctn_server_info_get(ifctn_server* srv, ifctn_server_info* out);
+ifctn_status ifctn_server_latency(ifctn_server* srv, uint64_t ticket, double* seconds);
+
+void ifctn_server_destroy(ifctn_server* srv);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* ifctn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IFCTN_H */

@@ -1,0 +1,945 @@
+// ifctn_api.cu -- host runtime and C ABI of the iFCTN library.
+//
+// A context owns every device buffer of one completion problem, plans the
+// launch geometry of each mode once, and captures one PAM sweep (Algorithm 1,
+// one pass of its loop) into a CUDA graph that is replayed per sweep.  The
+// Gram chain of mode k runs on a side branch of the graph, concurrently with
+// the HBM-streaming contraction of the same mode.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ifctn.h"
+#include "ifctn_api_internal.h"
+#include "ifctn_launch.h"
+
+namespace ifctn {
+
+thread_local std::string g_last_error;
+
+void set_error(const std::string& m) { g_last_error = m; }
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+            return IFCTN_ECUDA;                                                                    \
+        }                                                                                          \
+    } while (0)
+
+namespace {
+
+constexpr int STAGE_BYTES = 32 * 1024;
+constexpr int NSTAGES = 3;
+constexpr int SMEM_LIMIT = 220 * 1024;
+constexpr int LOG_CAP = 4096;
+
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+inline int cdiv(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
+
+// Split [0, len) into n nearly equal chunks; returns chunk c's [lo, hi).
+inline void chunk(int len, int n, int c, int& lo, int& hi) {
+    lo = static_cast<int>(static_cast<long long>(len) * c / n);
+    hi = static_cast<int>(static_cast<long long>(len) * (c + 1) / n);
+}
+
+}  // namespace
+
+ifctn_status build_shape(const ifctn_problem* p, Shape& s) {
+    if (!p) {
+        set_error("null problem");
+        return IFCTN_EINVAL;
+    }
+    memset(&s, 0, sizeof(s));
+    s.N = p->order;
+    if (s.N < 2 || s.N > 4) {
+        set_error("order must be 2..4");
+        return IFCTN_EINVAL;
+    }
+    s.P = 1;
+    for (int k = 0; k < s.N; ++k) {
+        if (p->dims[k] < 1 || p->dims[k] > (1 << 30)) {
+            set_error("dims must be >= 1");
+            return IFCTN_EINVAL;
+        }
+        s.I[k] = static_cast<int>(p->dims[k]);
+        s.P *= p->dims[k];
+    }
+    for (int k = 0; k < s.N; ++k)
+        for (int l = 0; l < s.N; ++l) {
+            if (k == l) continue;
+            const int r = p->ranks[k * 4 + l];
+            if (r < 1 || r > RMAX || r != p->ranks[l * 4 + k]) {
+                set_error("ranks must be symmetric and in 1..8");
+                return IFCTN_EINVAL;
+            }
+            s.R[k][l] = r;
+        }
+    if (!(p->rho > 0.0) || !std::isfinite(p->rho)) {
+        set_error("rho must be > 0");
+        return IFCTN_EINVAL;
+    }
+    if (p->max_sweeps < 0 || p->tol < 0) {
+        set_error("max_sweeps and tol must be >= 0");
+        return IFCTN_EINVAL;
+    }
+    if (p->precision != IFCTN_FP64 && p->precision != IFCTN_MIXED) {
+        set_error("unknown precision");
+        return IFCTN_EINVAL;
+    }
+    long long off = 0;
+    for (int k = 0; k < s.N; ++k)
+        for (int l = 0; l < s.N; ++l) {
+            if (k == l) continue;
+            s.goff[k][l] = static_cast<int>(off);
+            off += static_cast<long long>(s.R[k][l]) * s.I[k];
+        }
+    s.gsize = static_cast<int>(off);
+    off = 0;
+    for (int p2 = 0; p2 < s.N; ++p2)
+        for (int q = p2 + 1; q < s.N; ++q) {
+            s.woff[p2][q] = static_cast<int>(off);
+            off += static_cast<long long>(s.I[p2]) * s.I[q];
+        }
+    if (off > (1LL << 31)) {
+        set_error("pair matrices too large");
+        return IFCTN_EINVAL;
+    }
+    s.wsize = static_cast<int>(off);
+    s.IA = s.I[s.N - 2];
+    s.IB = s.I[s.N - 1];
+    s.nF = 1;
+    for (int m = 0; m < s.N - 2; ++m) s.nF *= s.I[m];
+    return IFCTN_OK;
+}
+
+int mode_q(const Shape& s, int k) {
+    int q = 1;
+    for (int m = 0; m < s.N; ++m)
+        if (m != k) q *= s.R[k][m];
+    return q;
+}
+
+// Launch geometry of the mode-k contraction and its work units.
+ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>& units) {
+    ContractPlan pl;
+    memset(&pl, 0, sizeof(pl));
+    const int N = s.N, Am = N - 2, Bm = N - 1, IA = s.IA, IB = s.IB;
+    const int target = 4 * num_sms();
+    pl.Q = mode_q(s, k);
+    pl.nstages = NSTAGES;
+    units.clear();
+    auto add = [&](int f0, int fstride, int ns, int key, int a0, int a1, int b0, int b1, int slot) {
+        UnitDesc u;
+        memset(&u, 0, sizeof(u));
+        u.f0 = f0;
+        u.fstride = fstride;
+        u.ns = ns;
+        u.key = key;
+        u.a0 = a0;
+        u.a1 = a1;
+        u.b0 = b0;
+        u.b1 = b1;
+        u.slot = slot;
+        units.push_back(u);
+    };
+    if (k == Bm) {  // COL
+        pl.kcase = CASE_COL;
+        pl.R1 = s.R[k][Am];
+        if (N == 4) {
+            pl.l2 = 1;
+            pl.dmode = 0;
+        } else if (N == 3) {
+            pl.l2 = 0;
+            pl.dmode = -1;
+        } else {
+            pl.l2 = -1;
+            pl.dmode = -1;
+        }
+        pl.Rl2 = pl.l2 >= 0 ? s.R[k][pl.l2] : 1;
+        pl.Qp = pl.Rl2 * pl.R1;
+        const int TB = std::min(IB, 256);
+        const int nbch = cdiv(IB, TB);
+        const int gmax = std::max(1, 256 / TB);
+        int maxns = 1;
+        if (N == 4) {
+            const int I0 = s.I[0], I1 = s.I[1];
+            const int nsmin = gmax;
+            int nC = std::max(1, std::min(cdiv(target, static_cast<long long>(I0) * nbch), std::max(1, I1 / nsmin)));
+            for (int i0 = 0; i0 < I0; ++i0)
+                for (int c = 0; c < nC; ++c)
+                    for (int bc = 0; bc < nbch; ++bc) {
+                        int lo, hi, b0, b1;
+                        chunk(I1, nC, c, lo, hi);
+                        chunk(IB, nbch, bc, b0, b1);
+                        add(i0 * I1 + lo, 1, hi - lo, i0, 0, IA, b0, b1, 0);
+                        maxns = std::max(maxns, hi - lo);
+                    }
+        } else if (N == 3) {
+            const int I0 = s.I[0];
+            const int nsmin = std::max(gmax, cdiv(4LL * pl.Qp, IA));
+            int nC = std::max(1, std::min(cdiv(target, nbch), std::max(1, I0 / nsmin)));
+            for (int c = 0; c < nC; ++c)
+                for (int bc = 0; bc < nbch; ++bc) {
+                    int lo, hi, b0, b1;
+                    chunk(I0, nC, c, lo, hi);
+                    chunk(IB, nbch, bc, b0, b1);
+                    add(lo, 1, hi - lo, -1, 0, IA, b0, b1, 0);
+                    maxns = std::max(maxns, hi - lo);
+                }
+        } else {
+            const int nAC = std::max(1, std::min(cdiv(target, nbch), cdiv(IA, 64)));
+            for (int ac = 0; ac < nAC; ++ac)
+                for (int bc = 0; bc < nbch; ++bc) {
+                    int a0, a1, b0, b1;
+                    chunk(IA, nAC, ac, a0, a1);
+                    chunk(IB, nbch, bc, b0, b1);
+                    add(0, 1, 1, -1, a0, a1, b0, b1, 0);
+                }
+        }
+        int G = std::max(1, std::min(gmax, maxns));
+        for (;;) {
+            int TAc = std::max(1, std::min(IA, STAGE_BYTES / (G * IB * sz)));
+            const int nthr = round_up(TB * G, 32);
+            const int sub = round_up(TAc * IB + 32 / sz, 16 / sz);
+            const long long smem = 128 + static_cast<long long>(NSTAGES) * G * sub * sz +
+                                   static_cast<long long>(G) * TAc * (pl.R1 | 1) * sz +
+                                   static_cast<long long>(nthr) * pl.Qp * sz;
+            if (smem <= SMEM_LIMIT || G == 1) {
+                pl.TA = TB;
+                pl.TAc = TAc;
+                pl.G = G;
+                pl.nthreads = nthr;
+                pl.sub_elems = sub;
+                pl.smem = static_cast<int>(smem);
+                break;
+            }
+            --G;
+        }
+        pl.nrow = IB;
+        pl.nunits = static_cast<int>(units.size());
+        pl.part_elems = static_cast<long long>(pl.nunits) * IB * pl.Qp;
+        return pl;
+    }
+    // ROW kinds
+    pl.R1 = s.R[k][Bm];
+    const bool isF = k < Am;
+    pl.kcase = isF ? CASE_F : CASE_A;
+    if (isF) {
+        pl.RA = s.R[k][Am];
+        pl.dmode = -1;
+        if (N == 4) {
+            pl.l2 = 1 - k;
+            pl.Rl2 = s.R[k][pl.l2];
+        } else {
+            pl.l2 = -1;
+            pl.Rl2 = 1;
+        }
+        pl.Qp = pl.Q;
+    } else {
+        if (N == 4) {
+            pl.l2 = 1;
+            pl.dmode = 0;
+        } else if (N == 3) {
+            pl.l2 = 0;
+            pl.dmode = -1;
+        } else {
+            pl.l2 = -1;
+            pl.dmode = -1;
+        }
+        pl.Rl2 = pl.l2 >= 0 ? s.R[k][pl.l2] : 1;
+        pl.Qp = pl.Rl2 * pl.R1;
+    }
+    const int rows_cap = std::max(1, STAGE_BYTES / (IB * sz));
+    const int TA = std::min(std::min(IA, rows_cap), 256);
+    const int gmax = std::max(1, std::min(256 / TA, STAGE_BYTES / (TA * IB * sz)));
+    int maxns = 1;
+    if (isF && N == 4) {
+        const int o = 1 - k, Io = s.I[o], Ik = s.I[k], I1 = s.I[1];
+        int nOC = std::max(1, std::min(cdiv(target, Ik), std::max(1, Io / gmax)));
+        for (int j = 0; j < Ik; ++j)
+            for (int oc = 0; oc < nOC; ++oc) {
+                int lo, hi;
+                chunk(Io, nOC, oc, lo, hi);
+                if (k == 0)
+                    add(j * I1 + lo, 1, hi - lo, j, 0, IA, 0, IB, oc);
+                else
+                    add(lo * I1 + j, I1, hi - lo, j, 0, IA, 0, IB, oc);
+                maxns = std::max(maxns, hi - lo);
+            }
+        pl.nslot = nOC;
+        pl.part_elems = static_cast<long long>(Ik) * nOC * pl.Q;
+    } else if (isF) {  // N = 3, k = 0: one slab per output row
+        for (int j = 0; j < s.I[0]; ++j) add(j, 1, 1, j, 0, IA, 0, IB, 0);
+        pl.nslot = 1;
+        pl.part_elems = static_cast<long long>(s.I[0]) * pl.Q;
+    } else if (N == 4) {
+        const int I0 = s.I[0], I1 = s.I[1];
+        const int nsmin = std::max(gmax, cdiv(4LL * pl.Qp, IB));
+        int nC = std::max(1, std::min(cdiv(target, I0), std::max(1, I1 / nsmin)));
+        for (int i0 = 0; i0 < I0; ++i0)
+            for (int c = 0; c < nC; ++c) {
+                int lo, hi;
+                chunk(I1, nC, c, lo, hi);
+                add(i0 * I1 + lo, 1, hi - lo, i0, 0, IA, 0, IB, 0);
+                maxns = std::max(maxns, hi - lo);
+            }
+    } else if (N == 3) {
+        const int I0 = s.I[0];
+        const int nsmin = std::max(gmax, cdiv(4LL * pl.Qp, IB));
+        int nC = std::max(1, std::min(target, std::max(1, I0 / nsmin)));
+        for (int c = 0; c < nC; ++c) {
+            int lo, hi;
+            chunk(I0, nC, c, lo, hi);
+            add(lo, 1, hi - lo, -1, 0, IA, 0, IB, 0);
+            maxns = std::max(maxns, hi - lo);
+        }
+    } else {  // N = 2: one slab, split into row chunks of TA
+        const int nAC = cdiv(IA, TA);
+        for (int ac = 0; ac < nAC; ++ac) {
+            int a0 = ac * TA, a1 = std::min(IA, a0 + TA);
+            add(0, 1, 1, -1, a0, a1, 0, IB, 0);
+        }
+    }
+    if (!isF) pl.part_elems = static_cast<long long>(units.size()) * IA * pl.Qp;
+    int G = std::max(1, std::min(gmax, maxns));
+    for (;;) {
+        const int nthr = round_up(TA * G, 32);
+        const int nwarp = nthr / 32;
+        const int sub = round_up(TA * IB + 32 / sz, 16 / sz);
+        long long smem = 128 + static_cast<long long>(NSTAGES) * G * sub * sz +
+                         static_cast<long long>(G) * IB * (pl.R1 | 1) * sz;
+        if (isF)
+            smem += static_cast<long long>(TA) * IB * sz + static_cast<long long>(nwarp + 1) * pl.Q * sz;
+        else
+            smem += static_cast<long long>(nthr) * pl.Qp * sz;
+        if (smem <= SMEM_LIMIT || G == 1) {
+            pl.TA = TA;
+            pl.G = G;
+            pl.nthreads = nthr;
+            pl.sub_elems = sub;
+            pl.smem = static_cast<int>(smem);
+            break;
+        }
+        --G;
+    }
+    pl.skew = (IB % 2 == 0) ? 1 : 0;
+    pl.nrow = IA;
+    pl.nunits = static_cast<int>(units.size());
+    return pl;
+}
+
+}  // namespace ifctn
+
+using namespace ifctn;
+
+namespace {
+
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    cudaError_t alloc(size_t count) {
+        n = count;
+        return cudaMalloc(reinterpret_cast<void**>(&p), std::max<size_t>(count, 1) * sizeof(T) + 64);
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+    }
+};
+
+}  // namespace
+
+struct ifctn_ctx {
+    virtual ~ifctn_ctx() {}
+    virtual ifctn_status sweep(int n, ifctn_stats* out) = 0;
+    virtual ifctn_status complete(void* out_X, ifctn_stats* out) = 0;
+    virtual ifctn_status reconstruct(void* out) = 0;
+    virtual ifctn_status get_factors(double* out) = 0;
+    virtual ifctn_status set_factors(const double* in) = 0;
+    virtual ifctn_status get_x(void* out) = 0;
+    virtual ifctn_status set_x(const void* in) = 0;
+    virtual ifctn_status set_truth(const void* xt, int log) = 0;
+    virtual ifctn_status get_log(ifctn_stats* out, int max, int* n) = 0;
+    virtual ifctn_status mode_system(int k, double* Mk, double* Kk) = 0;
+    virtual int kernels_per_sweep() const = 0;
+    virtual size_t device_bytes() const = 0;
+    virtual ifctn_status enqueue(int n, double tol, bool reset) = 0;
+    virtual ifctn_status launch_stage(int stage, int k) = 0;
+    virtual cudaStream_t stream() const = 0;
+};
+
+namespace ifctn {
+
+template <typename T>
+struct Engine : ifctn_ctx {
+    Shape sh;
+    ifctn_problem prob;
+    cudaStream_t st = nullptr, side = nullptr;
+    bool own_stream = false;
+    cudaEvent_t ev_fork[MAXN] = {}, ev_join[MAXN] = {};
+    DevBuf<T> X, Xt, Gt, W, Kk, t1, t2, part, tmpT;
+    DevBuf<double> Gd, Mk[MAXN], xpart, mpart, scal, tmpD, tol;
+    DevBuf<uint32_t> maskbits;
+    DevBuf<UnitDesc> units;
+    DevBuf<SweepStat> log;
+    DevBuf<int> ints;  // [0] counter, [1] done, [2] flags
+    ContractPlan plan[MAXN];
+    int unit_off[MAXN] = {};
+    int xblocks = 0;
+    long long nmiss = 0, nobs = 0;
+    bool truth = false, logm = false;
+    cudaGraphExec_t gexec = nullptr;
+    int launches = 0;
+    size_t bytes = 0;
+
+    int* counter() { return ints.p; }
+    int* done() { return ints.p + 1; }
+    int* flags() { return ints.p + 2; }
+
+    ~Engine() override {
+        if (st) cudaStreamSynchronize(st);
+        if (gexec) cudaGraphExecDestroy(gexec);
+        for (int k = 0; k < MAXN; ++k) {
+            if (ev_fork[k]) cudaEventDestroy(ev_fork[k]);
+            if (ev_join[k]) cudaEventDestroy(ev_join[k]);
+            Mk[k].release();
+        }
+        X.release(); Xt.release(); Gt.release(); W.release(); Kk.release(); t1.release(); t2.release();
+        part.release(); tmpT.release(); Gd.release(); xpart.release(); mpart.release(); scal.release();
+        tmpD.release(); tol.release(); maskbits.release(); units.release(); log.release(); ints.release();
+        if (side) cudaStreamDestroy(side);
+        if (own_stream && st) cudaStreamDestroy(st);
+    }
+
+    size_t device_bytes() const override { return bytes; }
+
+    template <typename U>
+    cudaError_t alloc(DevBuf<U>& b, size_t n) {
+        bytes += n * sizeof(U) + 64;
+        return b.alloc(n);
+    }
+
+    ifctn_status init(const ifctn_problem* p, const void* obs, const uint8_t* mask, const double* init_f,
+                      void* stream) {
+        prob = *p;
+        ifctn_status rs = build_shape(p, sh);
+        if (rs != IFCTN_OK) return rs;
+        if (!obs || !mask) {
+            set_error("obs and mask are required");
+            return IFCTN_EINVAL;
+        }
+        if (stream) {
+            st = static_cast<cudaStream_t>(stream);
+        } else {
+            CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            own_stream = true;
+        }
+        CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        for (int k = 0; k < MAXN; ++k) {
+            CK(cudaEventCreateWithFlags(&ev_fork[k], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&ev_join[k], cudaEventDisableTiming));
+        }
+        const int sz = sizeof(T);
+        std::vector<UnitDesc> all;
+        long long maxpart = 1, maxt1 = 1, maxt2 = 1, maxK = 1;
+        for (int k = 0; k < sh.N; ++k) {
+            std::vector<UnitDesc> u;
+            plan[k] = plan_contract(sh, k, sz, u);
+            if (plan[k].smem > SMEM_LIMIT) {
+                set_error("tensor shape needs more shared memory than available");
+                return IFCTN_EINVAL;
+            }
+            unit_off[k] = static_cast<int>(all.size());
+            all.insert(all.end(), u.begin(), u.end());
+            maxpart = std::max(maxpart, plan[k].part_elems);
+            const int Q = mode_q(sh, k);
+            maxK = std::max<long long>(maxK, static_cast<long long>(Q) * Q);
+            int m[3], nm = 0;
+            for (int q = 0; q < sh.N; ++q)
+                if (q != k) m[nm++] = q;
+            if (nm == 3) {
+                maxt1 = std::max<long long>(maxt1, static_cast<long long>(sh.I[m[0]]) * sh.I[m[1]] *
+                                                       sh.R[k][m[2]] * sh.R[k][m[2]]);
+                const long long Q2 = static_cast<long long>(sh.R[k][m[1]]) * sh.R[k][m[2]];
+                maxt2 = std::max<long long>(maxt2, sh.I[m[0]] * Q2 * Q2);
+            } else if (nm == 2) {
+                maxt2 = std::max<long long>(maxt2, static_cast<long long>(sh.I[m[0]]) * sh.R[k][m[1]] *
+                                                       sh.R[k][m[1]]);
+            }
+        }
+        xblocks = 4 * num_sms();
+        const long long P = sh.P;
+        bool ok = alloc(X, P) == cudaSuccess && alloc(Gt, sh.gsize) == cudaSuccess &&
+                  alloc(W, sh.wsize) == cudaSuccess && alloc(Kk, maxK) == cudaSuccess &&
+                  alloc(t1, maxt1) == cudaSuccess && alloc(t2, maxt2) == cudaSuccess &&
+                  alloc(part, maxpart) == cudaSuccess && alloc(Gd, sh.gsize) == cudaSuccess &&
+                  alloc(xpart, 3 * xblocks) == cudaSuccess && alloc(mpart, 3 * xblocks) == cudaSuccess &&
+                  alloc(scal, 8) == cudaSuccess && alloc(tol, 1) == cudaSuccess &&
+                  alloc(maskbits, (P + 31) / 32) == cudaSuccess && alloc(units, all.size()) == cudaSuccess &&
+                  alloc(log, LOG_CAP) == cudaSuccess && alloc(ints, 4) == cudaSuccess;
+        for (int k = 0; k < sh.N && ok; ++k)
+            ok = alloc(Mk[k], static_cast<size_t>(sh.I[k]) * mode_q(sh, k)) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            set_error("device allocation failed");
+            return IFCTN_ENOMEM;
+        }
+        CK(cudaMemcpyAsync(units.p, all.data(), all.size() * sizeof(UnitDesc), cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(ints.p, 0, 4 * sizeof(int), st));
+        CK(cudaMemsetAsync(tol.p, 0, sizeof(double), st));
+        // inputs: mask bytes and O go through a scratch buffer
+        {
+            uint8_t* dmask = nullptr;
+            T* dO = nullptr;
+            CK(cudaMallocAsync(reinterpret_cast<void**>(&dmask), P, st));
+            CK(cudaMemcpyAsync(dmask, mask, P, cudaMemcpyDefault, st));
+            CK(launch_pack_mask(P, dmask, maskbits.p, st));
+            CK(cudaMallocAsync(reinterpret_cast<void**>(&dO), P * sizeof(T), st));
+            CK(cudaMemcpyAsync(dO, obs, P * sizeof(T), cudaMemcpyDefault, st));
+            CK(launch_init_x<T>(P, dO, dmask, X.p, st));
+            CK(cudaFreeAsync(dO, st));
+            CK(cudaFreeAsync(dmask, st));
+        }
+        // |Omega| and its complement
+        CK(launch_count_bits((P + 31) / 32, maskbits.p, xpart.p, xblocks, st));
+        CK(launch_sum_partials(xpart.p, xblocks, 3, 0, scal.p, st));
+        double hs[1];
+        CK(cudaMemcpyAsync(hs, scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        nobs = static_cast<long long>(hs[0] + 0.5);
+        nmiss = P - nobs;
+        if (init_f) {
+            CK(cudaMemcpyAsync(Gd.p, init_f, sh.gsize * sizeof(double), cudaMemcpyDefault, st));
+        } else {
+            rs = default_factors();
+            if (rs != IFCTN_OK) return rs;
+        }
+        rs = refresh_factors();
+        if (rs != IFCTN_OK) return rs;
+        CK(cudaStreamSynchronize(st));
+        return build_graph();
+    }
+
+    // seeded splitmix64 U(0,1) entries, scaled so ||iFCTN(G0)|| = ||P_Omega(O)|| / sqrt(|Omega|/P)
+    ifctn_status default_factors() {
+        std::vector<double> g(sh.gsize);
+        uint64_t seed = prob.seed;
+        for (int i = 0; i < sh.gsize; ++i) {
+            uint64_t z = seed + static_cast<uint64_t>(i + 1) * 0x9E3779B97F4A7C15ULL;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+            z ^= z >> 31;
+            g[i] = static_cast<double>(z >> 11) * (1.0 / 9007199254740992.0);
+        }
+        CK(cudaMemcpyAsync(Gd.p, g.data(), sh.gsize * sizeof(double), cudaMemcpyHostToDevice, st));
+        ifctn_status rs = refresh_factors();
+        if (rs != IFCTN_OK) return rs;
+        CK(launch_reconstruct<T>(sh, W.p, nullptr, xpart.p, xblocks, st));
+        CK(launch_sum_partials(xpart.p, xblocks, 3, 0, scal.p, st));
+        CK(launch_sumsq<T>(sh.P, X.p, xpart.p, xblocks, st));
+        CK(launch_sum_partials(xpart.p, xblocks, 3, 0, scal.p + 1, st));
+        double h[2];
+        CK(cudaMemcpyAsync(h, scal.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const double rec2 = h[0], obs2 = h[1];
+        if (rec2 > 0 && obs2 > 0 && nobs > 0) {
+            const double target = std::sqrt(obs2 * static_cast<double>(sh.P) / static_cast<double>(nobs));
+            const double ratio = target / std::sqrt(rec2);
+            const double sc = std::pow(ratio, 1.0 / (sh.N * (sh.N - 1)));
+            for (auto& v : g) v *= sc;
+            CK(cudaMemcpyAsync(Gd.p, g.data(), sh.gsize * sizeof(double), cudaMemcpyHostToDevice, st));
+            CK(cudaStreamSynchronize(st));
+        }
+        return IFCTN_OK;
+    }
+
+    ifctn_status refresh_factors() {
+        CK(launch_cast_factors<T>(sh.gsize, Gd.p, Gt.p, st));
+        CK(launch_pairs<T>(sh, Gd.p, W.p, st));
+        return IFCTN_OK;
+    }
+
+    ContractArgs<T> cargs(int k) {
+        ContractArgs<T> a;
+        a.X = X.p;
+        a.Gt = Gt.p;
+        a.W = W.p;
+        a.sh = sh;
+        a.k = k;
+        a.pl = plan[k];
+        a.units = units.p + unit_off[k];
+        a.part = part.p;
+        a.flags = flags();
+        a.done = done();
+        return a;
+    }
+
+    // mode-k systems: Gram on the side stream, contraction on the main one
+    cudaError_t enqueue_mode_systems(int k) {
+        cudaError_t e;
+        if ((e = cudaEventRecord(ev_fork[k], st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(side, ev_fork[k], 0)) != cudaSuccess) return e;
+        if ((e = launch_gram<T>(sh, k, Gt.p, W.p, t1.p, t2.p, Kk.p, done(), side)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(ev_join[k], side)) != cudaSuccess) return e;
+        if ((e = launch_contract<T>(cargs(k), st)) != cudaSuccess) return e;
+        if ((e = launch_contract_finish<T>(sh, k, plan[k], units.p + unit_off[k], part.p, Gt.p, Mk[k].p,
+                                           done(), st)) != cudaSuccess)
+            return e;
+        return cudaStreamWaitEvent(st, ev_join[k], 0);
+    }
+
+    cudaError_t enqueue_sweep() {
+        cudaError_t e;
+        for (int k = 0; k < sh.N; ++k) {
+            if ((e = enqueue_mode_systems(k)) != cudaSuccess) return e;
+            if ((e = launch_solve<T>(sh, k, prob.rho, Kk.p, Mk[k].p, Gd.p, Gt.p, W.p, flags(), done(), st)) !=
+                cudaSuccess)
+                return e;
+        }
+        if ((e = launch_xupdate<T>(sh, prob.rho, X.p, maskbits.p, W.p, xpart.p, xblocks, done(), st)) !=
+            cudaSuccess)
+            return e;
+        if (logm && truth)
+            if ((e = launch_metrics<T>(sh, X.p, Xt.p, maskbits.p, mpart.p, xblocks, done(), st)) != cudaSuccess)
+                return e;
+        return launch_finalize(xpart.p, xblocks, (logm && truth) ? mpart.p : nullptr, xblocks, nmiss, tol.p,
+                               log.p, LOG_CAP, counter(), done(), flags(), st);
+    }
+
+    int count_launches() const {
+        int n = 0;
+        for (int k = 0; k < sh.N; ++k) {
+            const int nm = sh.N - 1;
+            n += (nm == 3 ? 3 : nm == 2 ? 2 : 1);  // gram chain
+            n += 3;                                 // contract, finish, solve
+        }
+        n += 2;  // xupdate, finalize
+        if (logm && truth) n += 1;
+        return n;
+    }
+    int kernels_per_sweep() const override { return launches; }
+
+    ifctn_status build_graph() {
+        if (gexec) {
+            cudaGraphExecDestroy(gexec);
+            gexec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_sweep();
+        cudaError_t e2 = cudaStreamEndCapture(st, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            set_error(std::string("sweep capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+            return IFCTN_ECUDA;
+        }
+        e = cudaGraphInstantiate(&gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
+            return IFCTN_ECUDA;
+        }
+        launches = count_launches();
+        return IFCTN_OK;
+    }
+
+    ifctn_status check_flags() {
+        int f[3];
+        CK(cudaMemcpyAsync(f, ints.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (f[2] & FLAG_TIMEOUT) {
+            set_error("a bounded device wait expired");
+            return IFCTN_ETIMEOUT;
+        }
+        if (f[2] & FLAG_NOTSPD) {
+            set_error("a proximal normal-equation matrix was not positive definite");
+            return IFCTN_ENOTSPD;
+        }
+        return IFCTN_OK;
+    }
+
+    ifctn_status last_stats(ifctn_stats* out) {
+        int cnt = 0;
+        CK(cudaMemcpyAsync(&cnt, counter(), sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (!out) return IFCTN_OK;
+        memset(out, 0, sizeof(*out));
+        out->rel_change = out->objective = out->rse = out->rmse = NAN;
+        if (cnt == 0) return IFCTN_OK;
+        SweepStat r;
+        CK(cudaMemcpy(&r, log.p + ((cnt - 1) % LOG_CAP), sizeof(r), cudaMemcpyDeviceToHost));
+        out->sweeps_done = r.sweep;
+        out->converged = r.converged;
+        out->rel_change = r.rel_change;
+        out->objective = r.objective;
+        out->rse = r.rse;
+        out->rmse = r.rmse;
+        return IFCTN_OK;
+    }
+
+    ifctn_status run(int n, double tolv, ifctn_stats* out) {
+        if (n < 0) {
+            set_error("n must be >= 0");
+            return IFCTN_EINVAL;
+        }
+        CK(cudaMemcpyAsync(tol.p, &tolv, sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(done(), 0, sizeof(int), st));
+        const int chunkn = tolv > 0 ? 16 : (1 << 30);
+        int doneh = 0;
+        for (int s = 0; s < n;) {
+            const int m = std::min(chunkn, n - s);
+            for (int i = 0; i < m; ++i) CK(cudaGraphLaunch(gexec, st));
+            s += m;
+            if (tolv > 0 && s < n) {
+                CK(cudaMemcpyAsync(&doneh, done(), sizeof(int), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (doneh) break;
+            }
+        }
+        ifctn_status rs = check_flags();
+        if (rs != IFCTN_OK) return rs;
+        return last_stats(out);
+    }
+
+    ifctn_status sweep(int n, ifctn_stats* out) override { return run(n, 0.0, out); }
+
+    ifctn_status enqueue(int n, double tolv, bool reset) override {
+        if (reset) {
+            CK(cudaMemcpyAsync(tol.p, &tolv, sizeof(double), cudaMemcpyHostToDevice, st));
+            CK(cudaMemsetAsync(done(), 0, sizeof(int), st));
+        }
+        for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(gexec, st));
+        return IFCTN_OK;
+    }
+    cudaStream_t stream() const override { return st; }
+
+    ifctn_status launch_stage(int stage, int k) override {
+        if (k < 0 || k >= sh.N) {
+            set_error("mode out of range");
+            return IFCTN_EINVAL;
+        }
+        switch (stage) {
+            case 0: CK(launch_contract<T>(cargs(k), st)); break;
+            case 1: CK(launch_gram<T>(sh, k, Gt.p, W.p, t1.p, t2.p, Kk.p, done(), st)); break;
+            case 2: CK(launch_solve<T>(sh, k, prob.rho, Kk.p, Mk[k].p, Gd.p, Gt.p, W.p, flags(), done(), st)); break;
+            case 3: CK(launch_xupdate<T>(sh, prob.rho, X.p, maskbits.p, W.p, xpart.p, xblocks, done(), st)); break;
+            default: set_error("unknown stage"); return IFCTN_EINVAL;
+        }
+        return IFCTN_OK;
+    }
+
+    ifctn_status complete(void* out_X, ifctn_stats* out) override {
+        ifctn_status rs = run(prob.max_sweeps, prob.tol, out);
+        if (rs != IFCTN_OK) return rs;
+        if (out_X) return get_x(out_X);
+        return IFCTN_OK;
+    }
+
+    ifctn_status reconstruct(void* out) override {
+        if (!out) {
+            set_error("null output");
+            return IFCTN_EINVAL;
+        }
+        T* dst = nullptr;
+        CK(cudaMallocAsync(reinterpret_cast<void**>(&dst), sh.P * sizeof(T), st));
+        CK(launch_reconstruct<T>(sh, W.p, dst, nullptr, xblocks, st));
+        CK(cudaMemcpyAsync(out, dst, sh.P * sizeof(T), cudaMemcpyDefault, st));
+        CK(cudaFreeAsync(dst, st));
+        CK(cudaStreamSynchronize(st));
+        return IFCTN_OK;
+    }
+
+    ifctn_status get_factors(double* out) override {
+        if (!out) return IFCTN_EINVAL;
+        CK(cudaMemcpyAsync(out, Gd.p, sh.gsize * sizeof(double), cudaMemcpyDefault, st));
+        CK(cudaStreamSynchronize(st));
+        return IFCTN_OK;
+    }
+
+    ifctn_status set_factors(const double* in) override {
+        if (!in) return IFCTN_EINVAL;
+        CK(cudaMemcpyAsync(Gd.p, in, sh.gsize * sizeof(double), cudaMemcpyDefault, st));
+        ifctn_status rs = refresh_factors();
+        if (rs != IFCTN_OK) return rs;
+        CK(cudaStreamSynchronize(st));
+        return IFCTN_OK;
+    }
+
+    ifctn_status get_x(void* out) override {
+        if (!out) return IFCTN_EINVAL;
+        CK(cudaMemcpyAsync(out, X.p, sh.P * sizeof(T), cudaMemcpyDefault, st));
+        CK(cudaStreamSynchronize(st));
+        return IFCTN_OK;
+    }
+
+    ifctn_status set_x(const void* in) override {
+        if (!in) return IFCTN_EINVAL;
+        CK(cudaMemcpyAsync(X.p, in, sh.P * sizeof(T), cudaMemcpyDefault, st));
+        CK(cudaStreamSynchronize(st));
+        return IFCTN_OK;
+    }
+
+    ifctn_status set_truth(const void* xt, int lg) override {
+        if (xt) {
+            if (!Xt.p && alloc(Xt, sh.P) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("device allocation failed");
+                return IFCTN_ENOMEM;
+            }
+            CK(cudaMemcpyAsync(Xt.p, xt, sh.P * sizeof(T), cudaMemcpyDefault, st));
+            truth = true;
+        }
+        logm = lg != 0;
+        CK(cudaStreamSynchronize(st));
+        return build_graph();
+    }
+
+    ifctn_status get_log(ifctn_stats* out, int max, int* n) override {
+        int cnt = 0;
+        CK(cudaMemcpyAsync(&cnt, counter(), sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const int avail = std::min(cnt, LOG_CAP);
+        const int take = std::max(0, std::min(avail, max));
+        std::vector<SweepStat> h(LOG_CAP);
+        CK(cudaMemcpy(h.data(), log.p, LOG_CAP * sizeof(SweepStat), cudaMemcpyDeviceToHost));
+        const int first = cnt - avail;
+        for (int i = 0; i < take; ++i) {
+            const SweepStat& r = h[(first + i) % LOG_CAP];
+            out[i].sweeps_done = r.sweep;
+            out[i].converged = r.converged;
+            out[i].rel_change = r.rel_change;
+            out[i].objective = r.objective;
+            out[i].rse = r.rse;
+            out[i].rmse = r.rmse;
+        }
+        if (n) *n = take;
+        return IFCTN_OK;
+    }
+
+    ifctn_status mode_system(int k, double* Mout, double* Kout) override {
+        if (k < 0 || k >= sh.N) {
+            set_error("mode out of range");
+            return IFCTN_EINVAL;
+        }
+        CK(cudaMemsetAsync(done(), 0, sizeof(int), st));
+        CK(enqueue_mode_systems(k));
+        const int Q = mode_q(sh, k);
+        if (Mout) CK(cudaMemcpyAsync(Mout, Mk[k].p, static_cast<size_t>(sh.I[k]) * Q * sizeof(double),
+                                     cudaMemcpyDefault, st));
+        if (Kout) {
+            if (sizeof(T) == sizeof(double)) {
+                CK(cudaMemcpyAsync(Kout, Kk.p, static_cast<size_t>(Q) * Q * sizeof(double), cudaMemcpyDefault, st));
+            } else {
+                double* tmp = nullptr;
+                CK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), static_cast<size_t>(Q) * Q * sizeof(double), st));
+                CK(launch_to_double(static_cast<long long>(Q) * Q, reinterpret_cast<const float*>(Kk.p), tmp, st));
+                CK(cudaMemcpyAsync(Kout, tmp, static_cast<size_t>(Q) * Q * sizeof(double), cudaMemcpyDefault, st));
+                CK(cudaFreeAsync(tmp, st));
+            }
+        }
+        CK(cudaStreamSynchronize(st));
+        return check_flags();
+    }
+};
+
+template struct Engine<float>;
+template struct Engine<double>;
+
+ifctn_status create_ctx(const ifctn_problem* prob, const void* obs, const uint8_t* mask, const double* init,
+                        void* stream, ifctn_ctx** out) {
+    if (!out || !prob) {
+        set_error("null argument");
+        return IFCTN_EINVAL;
+    }
+    *out = nullptr;
+    ifctn_ctx* c = nullptr;
+    ifctn_status rs;
+    if (prob->precision == IFCTN_FP64) {
+        auto* e = new Engine<double>();
+        rs = e->init(prob, obs, mask, init, stream);
+        c = e;
+    } else {
+        auto* e = new Engine<float>();
+        rs = e->init(prob, obs, mask, init, stream);
+        c = e;
+    }
+    if (rs != IFCTN_OK) {
+        delete c;
+        return rs;
+    }
+    *out = c;
+    return IFCTN_OK;
+}
+
+size_t ctx_device_bytes(const ifctn_ctx* c) { return c ? c->device_bytes() : 0; }
+ifctn_status ctx_enqueue(ifctn_ctx* c, int n, double tol, bool reset) { return c->enqueue(n, tol, reset); }
+cudaStream_t ctx_stream(ifctn_ctx* c) { return c->stream(); }
+
+}  // namespace ifctn
+
+extern "C" {
+
+ifctn_status ifctn_create(const ifctn_problem* prob, const void* obs, const uint8_t* mask,
+                          const double* init_factors, void* cuda_stream, ifctn_ctx** out) {
+    g_last_error.clear();
+    return create_ctx(prob, obs, mask, init_factors, cuda_stream, out);
+}
+
+#define IFCTN_CTX_CALL(ctx, expr)          \
+    do {                                   \
+        if (!(ctx)) {                      \
+            set_error("null context");     \
+            return IFCTN_EINVAL;           \
+        }                                  \
+        return (ctx)->expr;                \
+    } while (0)
+
+ifctn_status ifctn_sweep(ifctn_ctx* ctx, int32_t n, ifctn_stats* out) { IFCTN_CTX_CALL(ctx, sweep(n, out)); }
+ifctn_status ifctn_complete(ifctn_ctx* ctx, void* out_X, ifctn_stats* out) {
+    IFCTN_CTX_CALL(ctx, complete(out_X, out));
+}
+ifctn_status ifctn_reconstruct(ifctn_ctx* ctx, void* out) { IFCTN_CTX_CALL(ctx, reconstruct(out)); }
+ifctn_status ifctn_get_factors(ifctn_ctx* ctx, double* out) { IFCTN_CTX_CALL(ctx, get_factors(out)); }
+ifctn_status ifctn_set_factors(ifctn_ctx* ctx, const double* in) { IFCTN_CTX_CALL(ctx, set_factors(in)); }
+ifctn_status ifctn_get_x(ifctn_ctx* ctx, void* out) { IFCTN_CTX_CALL(ctx, get_x(out)); }
+ifctn_status ifctn_set_x(ifctn_ctx* ctx, const void* in) { IFCTN_CTX_CALL(ctx, set_x(in)); }
+ifctn_status ifctn_set_truth(ifctn_ctx* ctx, const void* xt, int32_t log) { IFCTN_CTX_CALL(ctx, set_truth(xt, log)); }
+ifctn_status ifctn_get_log(ifctn_ctx* ctx, ifctn_stats* out, int32_t max, int32_t* n) {
+    IFCTN_CTX_CALL(ctx, get_log(out, max, n));
+}
+ifctn_status ifctn_mode_system(ifctn_ctx* ctx, int32_t k, double* Mk, double* Kk) {
+    IFCTN_CTX_CALL(ctx, mode_system(k, Mk, Kk));
+}
+int32_t ifctn_kernels_per_sweep(const ifctn_ctx* ctx) { return ctx ? ctx->kernels_per_sweep() : 0; }
+ifctn_status ifctn_sweep_async(ifctn_ctx* ctx, int32_t n) {
+    if (n < 0) {
+        set_error("n must be >= 0");
+        return IFCTN_EINVAL;
+    }
+    IFCTN_CTX_CALL(ctx, enqueue(n, 0.0, true));
+}
+ifctn_status ifctn_launch_stage(ifctn_ctx* ctx, int32_t stage, int32_t k) {
+    IFCTN_CTX_CALL(ctx, launch_stage(stage, k));
+}
+void ifctn_destroy(ifctn_ctx* ctx) { delete ctx; }
+const char* ifctn_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,23 @@
+// ifctn_api_internal.h -- host-side declarations shared by the API and the server.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/ifctn.h"
+#include "ifctn_internal.cuh"
+
+namespace ifctn {
+
+void set_error(const std::string& m);
+ifctn_status build_shape(const ifctn_problem* p, Shape& s);
+int mode_q(const Shape& s, int k);
+ifctn_status create_ctx(const ifctn_problem* prob, const void* obs, const uint8_t* mask, const double* init,
+                        void* stream, ifctn_ctx** out);
+size_t ctx_device_bytes(const ifctn_ctx* c);
+// asynchronous use by the server: enqueue n sweeps (tolerance tol) on the
+// context's stream without waiting.
+ifctn_status ctx_enqueue(ifctn_ctx* c, int n, double tol, bool reset);
+cudaStream_t ctx_stream(ifctn_ctx* c);
+
+}  // namespace ifctn

@@ -1,0 +1,95 @@
+// ifctn_launch.h -- host-side launchers of the iFCTN kernels (one TU per group).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ifctn_internal.cuh"
+
+namespace ifctn {
+
+template <typename T>
+struct ContractArgs {
+    const T* X;
+    const T* Gt;  // cherry factors in the tensor dtype
+    const T* W;   // pair matrices in the tensor dtype
+    Shape sh;
+    int k;
+    ContractPlan pl;
+    const UnitDesc* units;
+    T* part;
+    int* flags;
+    const int* done;
+};
+
+// M_k partials (Prop. 1: M_k = X_(k) Z_k, Z_k generated on the fly).
+template <typename T>
+cudaError_t launch_contract(const ContractArgs<T>& a, cudaStream_t st);
+
+// M_k = reduction of the partials (FP64 output, I_k x Q_k).
+template <typename T>
+cudaError_t launch_contract_finish(const Shape& sh, int k, const ContractPlan& pl,
+                                   const UnitDesc* units, const T* part, const T* Gt, double* Mk,
+                                   const int* done, cudaStream_t st);
+
+// K_k = Z_k^T Z_k via the mode-by-mode chain (t1, t2 scratch; output in T).
+template <typename T>
+cudaError_t launch_gram(const Shape& sh, int k, const T* Gt, const T* W, T* t1, T* t2, T* Kk,
+                        const int* done, cudaStream_t st);
+
+// Per-column proximal solves of mode k (eq. (updateG)), Gauss-Seidel over i,
+// plus the refresh of the pair matrices W_{k,i}.
+template <typename T>
+cudaError_t launch_solve(const Shape& sh, int k, double rho, const T* Kk, const double* Mk,
+                         double* Gd, T* Gt, T* W, int* flags, const int* done, cudaStream_t st);
+
+// eq. (updateX) fused with the reconstruction and the sweep's reductions.
+template <typename T>
+cudaError_t launch_xupdate(const Shape& sh, double rho, T* X, const uint32_t* maskbits, const T* W,
+                           double* xpart, int nblocks, const int* done, cudaStream_t st);
+
+// Reconstruction only (out may be null: then only sum of squares into xpart).
+template <typename T>
+cudaError_t launch_reconstruct(const Shape& sh, const T* W, T* out, double* xpart, int nblocks,
+                               cudaStream_t st);
+
+// RSE / RMSE partial sums against a ground truth.
+template <typename T>
+cudaError_t launch_metrics(const Shape& sh, const T* X, const T* Xt, const uint32_t* maskbits,
+                           double* mpart, int nblocks, const int* done, cudaStream_t st);
+
+// All pair matrices from the FP64 master factors.
+template <typename T>
+cudaError_t launch_pairs(const Shape& sh, const double* Gd, T* W, cudaStream_t st);
+
+// X^0 = P_Omega(O) and the mask bitset.
+template <typename T>
+cudaError_t launch_init_x(long long P, const T* O, const uint8_t* mask, T* X, cudaStream_t st);
+cudaError_t launch_pack_mask(long long P, const uint8_t* mask, uint32_t* bits, cudaStream_t st);
+
+// FP64 master -> working-dtype copy of the factors.
+template <typename T>
+cudaError_t launch_cast_factors(int n, const double* Gd, T* Gt, cudaStream_t st);
+
+// Fixed-order reduction of the sweep partials into the log record.
+struct SweepStat {
+    double rel_change, objective, rse, rmse, dx2, x2;
+    int sweep, converged, flags, pad;
+};
+cudaError_t launch_finalize(const double* xpart, int nblocks, const double* mpart, int mblocks,
+                            long long nmiss_total, const double* tol, SweepStat* log, int log_cap,
+                            int* sweep_counter, int* done, const int* flags, cudaStream_t st);
+
+// Sum of squares of xpart[0] slots (used for the default initial scaling).
+cudaError_t launch_sum_partials(const double* xpart, int nblocks, int stride, int slot,
+                                double* out, cudaStream_t st);
+
+// scale factors in place by a device scalar: G *= s^(1/(N(N-1)))
+cudaError_t launch_scale_factors(int n, double* Gd, const double* ratio, double expo,
+                                 cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_sumsq(long long P, const T* X, double* part, int nblocks, cudaStream_t st);
+cudaError_t launch_count_bits(long long nwords, const uint32_t* bits, double* part, int nblocks,
+                              cudaStream_t st);
+cudaError_t launch_to_double(long long n, const float* a, double* b, cudaStream_t st);
+
+}  // namespace ifctn

@@ -1,0 +1,104 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+entry point include/ifctn.h declares; arguments are validated before any GPU
+work; the oracle and the CUDA path share no code."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ifctn.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_16358_gb300 import _build, binding
+    _build.build()
+    return binding.load()
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ifctn_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("ifctn_create", "ifctn_sweep", "ifctn_reconstruct", "ifctn_complete", "ifctn_submit",
+              "ifctn_poll"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2511_16358_gb300 import binding
+    so = binding.LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (ifctn_\w+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+    assert set(binding.EXPORTED) == set(_declared())
+
+
+def test_library_is_built_for_sm_103a(lib):
+    from paper_2511_16358_gb300 import binding
+    out = subprocess.run(["cuobjdump", "--list-elf", binding.LIB_PATH], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def _prob(**kw):
+    from paper_2511_16358_gb300 import binding as b
+    base = dict(dims=(4, 5, 6), ranks=np.full((3, 3), 2), rho=0.1, max_sweeps=3, tol=0.0,
+                precision=b.FP64)
+    base.update(kw)
+    return b.make_problem(**base)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(ranks=np.array([[0, 2, 2], [2, 0, 2], [2, 2, 0]]) * 0),
+    dict(ranks=np.array([[0, 9, 2], [9, 0, 2], [2, 2, 0]])),
+    dict(ranks=np.array([[0, 2, 3], [2, 0, 2], [2, 2, 0]])),  # not symmetric
+    dict(rho=0.0),
+    dict(rho=-1.0),
+    dict(max_sweeps=-1),
+    dict(dims=(4,)),
+    dict(dims=(4, 0, 3)),
+    dict(precision=7),
+])
+def test_invalid_problems_rejected_before_gpu_work(lib, bad):
+    from paper_2511_16358_gb300 import binding as b
+    dims = bad.get("dims", (4, 5, 6))
+    n = int(np.prod([max(d, 1) for d in dims]))
+    obs = np.zeros(n)
+    mask = np.zeros(n, dtype=np.uint8)
+    with pytest.raises(b.IfctnError) as ei:
+        b.create(_prob(**bad), obs, mask)
+    assert ei.value.status == b.EINVAL
+    assert b.last_error()
+
+
+def test_null_context_and_server_arguments(lib):
+    from paper_2511_16358_gb300 import binding as b
+    assert lib.ifctn_sweep(None, 1, None) == b.EINVAL
+    assert lib.ifctn_poll(None, 1, None, None, 0) == b.EINVAL
+    assert lib.ifctn_kernels_per_sweep(None) == 0
+    lib.ifctn_destroy(None)
+    lib.ifctn_server_destroy(None)
+
+
+def test_oracle_and_cuda_path_share_no_code():
+    pkg = os.path.join(ROOT, "paper_2511_16358_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
+                assert "ifctn_oracle" not in src and "ifo_" not in src, f
+    osrc = open(os.path.join(ROOT, "oracle", "ifctn_oracle.c")).read()
+    assert "#include \"" not in osrc  # only system headers
+    opy = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+    assert "paper_2511_16358_gb300" not in opy
