@@ -262,8 +262,23 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    lc0 = b.launch_count(ctx)
     times, st_last = time_steps(b, torch, ctx, stream, X0, G0, sweeps, args.steps, args.warmup, flush)
     ck = clocks.stop()
+    launches_timed = (b.launch_count(ctx) - lc0) * args.steps // (args.steps + args.warmup)
+    ph = b.phase_times(ctx)
+    names = []
+    for k in range(len(w.dims)):
+        names += [f"m{k}_contract", f"m{k}_bar1", f"m{k}_reduce", f"m{k}_bar2", f"m{k}_solve", f"m{k}_bar3"]
+    names = names[: 6 * len(w.dims)]
+    phases = {}
+    prev = 0.0
+    for nm, t in zip(names, ph[: 6 * len(w.dims)]):
+        phases[nm] = t - prev
+        prev = t
+    if len(ph) >= 26:
+        phases["xupdate"] = ph[24] - prev
+        phases["xupdate_bar"] = ph[25] - ph[24]
     torch.cuda.synchronize()
     tot = sum(times)
     if dist:
@@ -355,7 +370,8 @@ def main():
                            "precision": "mixed (FP32 tensor/contractions, FP64 solves)" if prec == b.MIXED else "fp64",
                            "l2": "flushed (256 MiB write) before every timed step",
                            "parallelism": f"replicas x{world}"},
-                "gpu_launches": kps * sweeps * args.steps,
+                "gpu_launches": launches_timed,
+                "persistent_phases_first_sweep_s": phases,
                 "clocks": ck, "roofline": roofline}
         line.update(extras)
         line.setdefault("e2e", None)

@@ -146,8 +146,21 @@ ifctn_status ifctn_mode_system(ifctn_ctx* ctx, int32_t k, double* Mk, double* Kk
    k is ignored by stage 3. */
 ifctn_status ifctn_launch_stage(ifctn_ctx* ctx, int32_t stage, int32_t k);
 
-/* Number of kernel launches one sweep issues (for launch accounting). */
+/* Number of kernel launches one sweep issues when sweeps run as a CUDA graph
+   of per-stage kernels (for launch accounting). */
 int32_t ifctn_kernels_per_sweep(const ifctn_ctx* ctx);
+
+/* Total number of kernel launches this context has issued for sweeps so far.
+   When the device can hold the whole grid co-resident, each sweep call is one
+   persistent cooperative launch that runs all its sweeps. */
+int64_t ifctn_launch_count(const ifctn_ctx* ctx);
+
+/* Profiling aid for the persistent path: seconds from the start of the first
+   sweep of the last persistent launch to the end of each of its phases, in
+   order (per mode k: contraction, its barrier, reduction, its barrier, solves,
+   their barrier; for k = 0..3; then the X update and its barrier), up to max
+   values.  *n receives the count (0 when sweeps run as a graph). */
+ifctn_status ifctn_phase_times(ifctn_ctx* ctx, double* out, int32_t max, int32_t* n);
 
 void ifctn_destroy(ifctn_ctx* ctx);
 

@@ -29,6 +29,7 @@ EXPORTED = [
     "ifctn_mode_system", "ifctn_kernels_per_sweep", "ifctn_destroy", "ifctn_server_create",
     "ifctn_submit", "ifctn_poll", "ifctn_server_info_get", "ifctn_server_latency",
     "ifctn_server_destroy", "ifctn_last_error", "ifctn_sweep_async", "ifctn_launch_stage",
+    "ifctn_launch_count", "ifctn_phase_times",
 ]
 
 
@@ -95,6 +96,8 @@ def load(path: str | None = None):
         "ifctn_last_error": (ctypes.c_char_p, []),
         "ifctn_sweep_async": (i32, [vp, i32]),
         "ifctn_launch_stage": (i32, [vp, i32, i32]),
+        "ifctn_launch_count": (i64, [vp]),
+        "ifctn_phase_times": (i32, [vp, P(dp), i32, P(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -219,6 +222,17 @@ def mode_system(ctx, k, Mk, Kk):
 
 def kernels_per_sweep(ctx) -> int:
     return int(load().ifctn_kernels_per_sweep(ctx))
+
+
+def launch_count(ctx) -> int:
+    return int(load().ifctn_launch_count(ctx))
+
+
+def phase_times(ctx) -> list:
+    arr = (ctypes.c_double * 64)()
+    n = ctypes.c_int32(0)
+    _check(load().ifctn_phase_times(ctx, arr, 64, ctypes.byref(n)))
+    return [arr[i] for i in range(n.value)]
 
 
 def destroy(ctx):

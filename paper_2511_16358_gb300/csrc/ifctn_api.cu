@@ -15,6 +15,7 @@
 #include "../../include/ifctn.h"
 #include "ifctn_api_internal.h"
 #include "ifctn_launch.h"
+#include "ifctn_persistent.h"
 
 namespace ifctn {
 
@@ -136,6 +137,11 @@ int mode_q(const Shape& s, int k) {
 }
 
 // Launch geometry of the mode-k contraction and its work units.
+// Tensors up to this size stay in L2 across a sweep; for them the N = 3 modes
+// A and B use one work unit per slab with mode 0 deferred to the reduction
+// (more CTAs, smaller partials) instead of folding mode 0 in registers.
+constexpr long long L2_RESIDENT_BYTES = 96LL << 20;
+
 ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>& units) {
     ContractPlan pl;
     memset(&pl, 0, sizeof(pl));
@@ -161,12 +167,16 @@ ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>&
     if (k == Bm) {  // COL
         pl.kcase = CASE_COL;
         pl.R1 = s.R[k][Am];
+        const bool slab3 = N == 3 && s.P * sz <= L2_RESIDENT_BYTES;
         if (N == 4) {
             pl.l2 = 1;
             pl.dmode = 0;
-        } else if (N == 3) {
+        } else if (N == 3 && !slab3) {
             pl.l2 = 0;
             pl.dmode = -1;
+        } else if (N == 3) {
+            pl.l2 = -1;
+            pl.dmode = 0;
         } else {
             pl.l2 = -1;
             pl.dmode = -1;
@@ -190,6 +200,13 @@ ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>&
                         add(i0 * I1 + lo, 1, hi - lo, i0, 0, IA, b0, b1, 0);
                         maxns = std::max(maxns, hi - lo);
                     }
+        } else if (N == 3 && slab3) {
+            for (int i0 = 0; i0 < s.I[0]; ++i0)
+                for (int bc = 0; bc < nbch; ++bc) {
+                    int b0, b1;
+                    chunk(IB, nbch, bc, b0, b1);
+                    add(i0, 1, 1, i0, 0, IA, b0, b1, 0);
+                }
         } else if (N == 3) {
             const int I0 = s.I[0];
             const int nsmin = std::max(gmax, cdiv(4LL * pl.Qp, IA));
@@ -212,13 +229,16 @@ ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>&
                     add(0, 1, 1, -1, a0, a1, b0, b1, 0);
                 }
         }
-        int G = std::max(1, std::min(gmax, maxns));
+        // a unit with a single slab and no register fold: the groups split its rows
+        pl.split = (maxns == 1 && pl.l2 < 0) ? 1 : 0;
+        int G = pl.split ? std::max(1, std::min(gmax, IA / 4)) : std::max(1, std::min(gmax, maxns));
         for (;;) {
-            int TAc = std::max(1, std::min(IA, STAGE_BYTES / (G * IB * sz)));
-            const int nthr = round_up(TB * G, 32);
+            const int GS = pl.split ? 1 : G;
+            int TAc = std::max(1, std::min(IA, STAGE_BYTES / (GS * IB * sz)));
+            const int nthr = 256;
             const int sub = round_up(TAc * IB + 32 / sz, 16 / sz);
-            const long long smem = 128 + static_cast<long long>(NSTAGES) * G * sub * sz +
-                                   static_cast<long long>(G) * TAc * (pl.R1 | 1) * sz +
+            const long long smem = 128 + static_cast<long long>(NSTAGES) * GS * sub * sz +
+                                   static_cast<long long>(GS) * TAc * (pl.R1 | 1) * sz +
                                    static_cast<long long>(nthr) * pl.Qp * sz;
             if (smem <= SMEM_LIMIT || G == 1) {
                 pl.TA = TB;
@@ -234,6 +254,12 @@ ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>&
         pl.nrow = IB;
         pl.nunits = static_cast<int>(units.size());
         pl.part_elems = static_cast<long long>(pl.nunits) * IB * pl.Qp;
+        pl.key_div = 0;
+        if (nbch == 1 && N >= 3) {
+            if (N == 3 && slab3) pl.key_div = 1;
+            else if (N == 4) pl.key_div = static_cast<int>(units.size()) / s.I[0];
+            else pl.key_div = 1 << 30;  // no deferral: any positive value
+        }
         return pl;
     }
     // ROW kinds
@@ -254,6 +280,9 @@ ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>&
     } else {
         if (N == 4) {
             pl.l2 = 1;
+            pl.dmode = 0;
+        } else if (N == 3 && s.P * sz <= L2_RESIDENT_BYTES) {
+            pl.l2 = -1;
             pl.dmode = 0;
         } else if (N == 3) {
             pl.l2 = 0;
@@ -299,6 +328,8 @@ ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>&
                 add(i0 * I1 + lo, 1, hi - lo, i0, 0, IA, 0, IB, 0);
                 maxns = std::max(maxns, hi - lo);
             }
+    } else if (N == 3 && pl.dmode == 0) {
+        for (int i0 = 0; i0 < s.I[0]; ++i0) add(i0, 1, 1, i0, 0, IA, 0, IB, 0);
     } else if (N == 3) {
         const int I0 = s.I[0];
         const int nsmin = std::max(gmax, cdiv(4LL * pl.Qp, IB));
@@ -317,13 +348,16 @@ ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>&
         }
     }
     if (!isF) pl.part_elems = static_cast<long long>(units.size()) * IA * pl.Qp;
-    int G = std::max(1, std::min(gmax, maxns));
+    // a unit with a single slab and no register fold: the groups split its columns
+    pl.split = (maxns == 1 && pl.Rl2 == 1 && (pl.l2 < 0 || isF)) ? 1 : 0;
+    int G = pl.split ? std::max(1, std::min(std::max(1, 256 / TA), IB / 4)) : std::max(1, std::min(gmax, maxns));
     for (;;) {
-        const int nthr = round_up(TA * G, 32);
+        const int GS = pl.split ? 1 : G;
+        const int nthr = 256;
         const int nwarp = nthr / 32;
         const int sub = round_up(TA * IB + 32 / sz, 16 / sz);
-        long long smem = 128 + static_cast<long long>(NSTAGES) * G * sub * sz +
-                         static_cast<long long>(G) * IB * (pl.R1 | 1) * sz;
+        long long smem = 128 + static_cast<long long>(NSTAGES) * GS * sub * sz +
+                         static_cast<long long>(GS) * IB * (pl.R1 | 1) * sz;
         if (isF)
             smem += static_cast<long long>(TA) * IB * sz + static_cast<long long>(nwarp + 1) * pl.Q * sz;
         else
@@ -341,6 +375,12 @@ ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>&
     pl.skew = (IB % 2 == 0) ? 1 : 0;
     pl.nrow = IA;
     pl.nunits = static_cast<int>(units.size());
+    pl.key_div = 0;
+    if (!isF && N >= 3) {
+        if (N == 3 && pl.dmode == 0) pl.key_div = 1;
+        else if (N == 4) pl.key_div = static_cast<int>(units.size()) / s.I[0];
+        else pl.key_div = 1 << 30;
+    }
     return pl;
 }
 
@@ -382,6 +422,9 @@ struct ifctn_ctx {
     virtual size_t device_bytes() const = 0;
     virtual ifctn_status enqueue(int n, double tol, bool reset) = 0;
     virtual ifctn_status launch_stage(int stage, int k) = 0;
+    virtual long long launch_total() const = 0;
+    virtual ifctn_status phase_times(double* out, int max, int* n) = 0;
+    virtual void set_grid_cap(int g) = 0;
     virtual cudaStream_t stream() const = 0;
 };
 
@@ -408,6 +451,13 @@ struct Engine : ifctn_ctx {
     cudaGraphExec_t gexec = nullptr;
     int launches = 0;
     size_t bytes = 0;
+    // persistent path
+    bool persistent = false;
+    int pgrid = 0, psmem = 0, grid_cap = 0;
+    SweepParams<T> pp;
+    DevBuf<unsigned> bar;
+    DevBuf<unsigned long long> tstamp;
+    long long launch_count = 0;
 
     int* counter() { return ints.p; }
     int* done() { return ints.p + 1; }
@@ -421,6 +471,8 @@ struct Engine : ifctn_ctx {
             if (ev_join[k]) cudaEventDestroy(ev_join[k]);
             Mk[k].release();
         }
+        bar.release();
+        tstamp.release();
         X.release(); Xt.release(); Gt.release(); W.release(); Kk.release(); t1.release(); t2.release();
         part.release(); tmpT.release(); Gd.release(); xpart.release(); mpart.release(); scal.release();
         tmpD.release(); tol.release(); maskbits.release(); units.release(); log.release(); ints.release();
@@ -485,12 +537,14 @@ struct Engine : ifctn_ctx {
             }
         }
         xblocks = 4 * num_sms();
+        const int xpart_n = std::max(3 * xblocks, 16 * 4 * num_sms());
         const long long P = sh.P;
         bool ok = alloc(X, P) == cudaSuccess && alloc(Gt, sh.gsize) == cudaSuccess &&
                   alloc(W, sh.wsize) == cudaSuccess && alloc(Kk, maxK) == cudaSuccess &&
                   alloc(t1, maxt1) == cudaSuccess && alloc(t2, maxt2) == cudaSuccess &&
                   alloc(part, maxpart) == cudaSuccess && alloc(Gd, sh.gsize) == cudaSuccess &&
-                  alloc(xpart, 3 * xblocks) == cudaSuccess && alloc(mpart, 3 * xblocks) == cudaSuccess &&
+                  alloc(xpart, xpart_n) == cudaSuccess && alloc(mpart, 3 * xblocks) == cudaSuccess &&
+                  alloc(bar, 4) == cudaSuccess && alloc(tstamp, 64) == cudaSuccess &&
                   alloc(scal, 8) == cudaSuccess && alloc(tol, 1) == cudaSuccess &&
                   alloc(maskbits, (P + 31) / 32) == cudaSuccess && alloc(units, all.size()) == cudaSuccess &&
                   alloc(log, LOG_CAP) == cudaSuccess && alloc(ints, 4) == cudaSuccess;
@@ -503,6 +557,7 @@ struct Engine : ifctn_ctx {
         }
         CK(cudaMemcpyAsync(units.p, all.data(), all.size() * sizeof(UnitDesc), cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(ints.p, 0, 4 * sizeof(int), st));
+        CK(cudaMemsetAsync(bar.p, 0, 4 * sizeof(unsigned), st));
         CK(cudaMemsetAsync(tol.p, 0, sizeof(double), st));
         // inputs: mask bytes and O go through a scratch buffer
         {
@@ -534,7 +589,85 @@ struct Engine : ifctn_ctx {
         rs = refresh_factors();
         if (rs != IFCTN_OK) return rs;
         CK(cudaStreamSynchronize(st));
-        return build_graph();
+        rs = build_graph();
+        if (rs != IFCTN_OK) return rs;
+        setup_persistent();
+        return IFCTN_OK;
+    }
+
+    // The whole run in one cooperative launch when the grid fits co-resident.
+    void setup_persistent() {
+        memset(&pp, 0, sizeof(pp));
+        pp.sh = sh;
+        int m[3];
+        bool k_fits = true;
+        for (int k = 0; k < sh.N; ++k) {
+            pp.pl[k] = plan[k];
+            pp.units[k] = units.p + unit_off[k];
+            int nm = 0;
+            for (int q = 0; q < sh.N; ++q)
+                if (q != k) m[nm++] = q;
+            pp.gunits[k] = nm == 2 ? (sh.I[m[0]] + 7) / 8 : nm == 3 ? sh.I[m[0]] : 0;
+            const long long Q = mode_q(sh, k);
+            if (Q * Q * static_cast<long long>(sizeof(T)) > 96 * 1024) k_fits = false;
+        }
+        pp.solve_k_in_smem = k_fits ? 1 : 0;
+        int gc = 1 << 30;
+        for (int k = 0; k < sh.N; ++k) {
+            int nm = 0;
+            for (int q = 0; q < sh.N; ++q)
+                if (q != k) m[nm++] = q;
+            if (nm == 3) {
+                const int Rl = sh.R[k][m[2]];
+                gc = std::min(gc, std::max(1, static_cast<int>(32 * 1024 / (Rl * Rl * sizeof(T)))));
+            }
+        }
+        pp.gram_chunk = gc == (1 << 30) ? 1 : gc;
+        pp.X = X.p;
+        pp.mb = maskbits.p;
+        pp.Xt = nullptr;
+        pp.Gd = Gd.p;
+        pp.Gt = Gt.p;
+        pp.W = W.p;
+        pp.part = part.p;
+        pp.gbuf = t2.p;
+        pp.Kk = Kk.p;
+        for (int k = 0; k < sh.N; ++k) pp.Mk[k] = Mk[k].p;
+        pp.xpart = xpart.p;
+        pp.log = log.p;
+        pp.log_cap = LOG_CAP;
+        pp.counter = counter();
+        pp.done = done();
+        pp.flags = flags();
+        pp.tol = tol.p;
+        pp.bar_count = bar.p;
+        pp.bar_gen = bar.p + 1;
+        pp.rho = prob.rho;
+        pp.nmiss = nmiss;
+        pp.nstages = NSTAGES;
+        pp.tstamp = tstamp.p;
+        psmem = persistent_smem_bytes<T>(pp);
+        persistent = false;
+        if (psmem > 227 * 1024) return;
+        int g = persistent_max_grid<T>(psmem);
+        if (grid_cap > 0) g = std::min(g, grid_cap);
+        if (g < 1 || 16LL * g > static_cast<long long>(xpart.n)) return;
+        pgrid = g;
+        persistent = true;
+    }
+
+    ifctn_status launch_run(int n) {
+        if (n <= 0) return IFCTN_OK;
+        if (persistent) {
+            pp.nsweeps = n;
+            pp.Xt = (logm && truth) ? Xt.p : nullptr;
+            CK(launch_persistent<T>(pp, pgrid, psmem, st));
+            ++launch_count;
+        } else {
+            for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(gexec, st));
+            launch_count += static_cast<long long>(n) * launches;
+        }
+        return IFCTN_OK;
     }
 
     // seeded splitmix64 U(0,1) entries, scaled so ||iFCTN(G0)|| = ||P_Omega(O)|| / sqrt(|Omega|/P)
@@ -702,11 +835,12 @@ struct Engine : ifctn_ctx {
         }
         CK(cudaMemcpyAsync(tol.p, &tolv, sizeof(double), cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(done(), 0, sizeof(int), st));
-        const int chunkn = tolv > 0 ? 16 : (1 << 30);
+        const int chunkn = (tolv > 0 && !persistent) ? 16 : (1 << 30);
         int doneh = 0;
         for (int s = 0; s < n;) {
             const int m = std::min(chunkn, n - s);
-            for (int i = 0; i < m; ++i) CK(cudaGraphLaunch(gexec, st));
+            ifctn_status rs0 = launch_run(m);
+            if (rs0 != IFCTN_OK) return rs0;
             s += m;
             if (tolv > 0 && s < n) {
                 CK(cudaMemcpyAsync(&doneh, done(), sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -726,10 +860,23 @@ struct Engine : ifctn_ctx {
             CK(cudaMemcpyAsync(tol.p, &tolv, sizeof(double), cudaMemcpyHostToDevice, st));
             CK(cudaMemsetAsync(done(), 0, sizeof(int), st));
         }
-        for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(gexec, st));
-        return IFCTN_OK;
+        return launch_run(n);
     }
     cudaStream_t stream() const override { return st; }
+    long long launch_total() const override { return launch_count; }
+    ifctn_status phase_times(double* out, int max, int* n) override {
+        unsigned long long h[64];
+        CK(cudaMemcpyAsync(h, tstamp.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const int cnt = std::min(max, 26);
+        for (int i = 0; i < cnt; ++i) out[i] = (h[i + 1] >= h[0] && h[0]) ? 1e-9 * static_cast<double>(h[i + 1] - h[0]) : NAN;
+        if (n) *n = persistent ? cnt : 0;
+        return IFCTN_OK;
+    }
+    void set_grid_cap(int g) override {
+        grid_cap = g;
+        setup_persistent();
+    }
 
     ifctn_status launch_stage(int stage, int k) override {
         if (k < 0 || k >= sh.N) {
@@ -891,6 +1038,7 @@ ifctn_status create_ctx(const ifctn_problem* prob, const void* obs, const uint8_
 
 size_t ctx_device_bytes(const ifctn_ctx* c) { return c ? c->device_bytes() : 0; }
 ifctn_status ctx_enqueue(ifctn_ctx* c, int n, double tol, bool reset) { return c->enqueue(n, tol, reset); }
+void ctx_set_grid_cap(ifctn_ctx* c, int g) { c->set_grid_cap(g); }
 cudaStream_t ctx_stream(ifctn_ctx* c) { return c->stream(); }
 
 }  // namespace ifctn
@@ -929,6 +1077,10 @@ ifctn_status ifctn_mode_system(ifctn_ctx* ctx, int32_t k, double* Mk, double* Kk
     IFCTN_CTX_CALL(ctx, mode_system(k, Mk, Kk));
 }
 int32_t ifctn_kernels_per_sweep(const ifctn_ctx* ctx) { return ctx ? ctx->kernels_per_sweep() : 0; }
+int64_t ifctn_launch_count(const ifctn_ctx* ctx) { return ctx ? ctx->launch_total() : 0; }
+ifctn_status ifctn_phase_times(ifctn_ctx* ctx, double* out, int32_t max, int32_t* n) {
+    IFCTN_CTX_CALL(ctx, phase_times(out, max, n));
+}
 ifctn_status ifctn_sweep_async(ifctn_ctx* ctx, int32_t n) {
     if (n < 0) {
         set_error("n must be >= 0");

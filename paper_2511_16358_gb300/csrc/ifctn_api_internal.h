@@ -19,5 +19,7 @@ size_t ctx_device_bytes(const ifctn_ctx* c);
 // context's stream without waiting.
 ifctn_status ctx_enqueue(ifctn_ctx* c, int n, double tol, bool reset);
 cudaStream_t ctx_stream(ifctn_ctx* c);
+// caps the persistent grid (the server gives each resident job a share)
+void ctx_set_grid_cap(ifctn_ctx* c, int g);
 
 }  // namespace ifctn

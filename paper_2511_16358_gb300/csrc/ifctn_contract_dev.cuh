@@ -1,33 +1,11 @@
-// ifctn_contract.cu -- the streaming mode-k contraction M_k = X_(k) Z_k.
-//
-// Prop. 1 writes the mode-k sub-network as
-//     Z_k(i_{-k}, r) = S_k(i_{-k}) * prod_{m != k} G_{m,k}(r_m, i_m),
-//     S_k = broadcast product of W_{p,q} = G_{p,q}^T G_{q,p} over pairs p,q != k,
-// and eq. (updateG) needs, for every column j of every G_{k,i}, the vector
-// A_j^T x_j.  All of these are contractions of one matrix,
-//     M_k(j, r) = sum_{i_{-k}} X(i_k = j, i_{-k}) Z_k(i_{-k}, r),
-// against the Kronecker vector E_j of the other columns G_{k,m}(:, j), so the
-// whole mode needs a single pass over X.  Z_k is never formed: its entries are
-// built on the fly from the small W and G matrices (the "coefficient builder").
-//
-// The pass is one-read HBM streaming.  The tensor is cut into slabs (all
-// entries sharing the indices of modes 0..N-3); each CTA takes a list of slabs
-// and moves contiguous slab tiles into a shared-memory ring with 1-D TMA bulk
-// copies (cp.async.bulk + mbarrier), several stages ahead of the compute.
-// Inside a tile the contraction is hierarchical, so each tensor entry costs
-// about R_{k,B} + 2 FMAs:
-//   ROW kernel (k is not the last mode): a thread owns one row a of mode N-2,
-//     contracts the contiguous mode N-1 in registers (u = R values), folds the
-//     row into a register tile z over one more mode, and the remaining modes
-//     are contracted at the flush or in the finisher.
-//   COL kernel (k is the last mode): a thread owns one column b, contracts
-//     mode N-2 in registers and folds slabs into z the same way.
-// Partials are written per work unit and reduced by the finisher in a fixed
-// order, so results are deterministic (no atomics).
+// ifctn_contract_dev.cuh -- per-unit device code of the streaming mode-k
+// contraction M_k = X_(k) Z_k (see ifctn_contract.cu for the design).  Used by
+// the standalone contraction kernels and by the persistent sweep kernel.
+#pragma once
 #include "ifctn_launch.h"
 
 namespace ifctn {
-namespace {
+namespace cdev {
 
 __device__ __forceinline__ void decode_f(const Shape& s, long long f, int& i0, int& i1) {
     if (s.N == 4) {
@@ -43,10 +21,13 @@ __device__ __forceinline__ void decode_f(const Shape& s, long long f, int& i0, i
 // r2 runs over mode l2 (mode 1 for N = 4, mode 0 for N = 3) and coef carries
 // G_{l2,k} and, for N = 4, the pair matrix W_{0,1}.
 template <typename T, int R>
-__device__ __forceinline__ void fold_outer(const Shape& s, const T* Gt, const T* W, int k,
+__device__ __forceinline__ void fold_outer(const Shape& s, const T* Gt, const T* W, int k, int l2,
                                            int Rl2, int i0, int i1, const T (&u)[R],
                                            T (&z)[RMAX][R]) {
-    if (s.N == 4) {
+    if (l2 < 0) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) z[0][r] += u[r];
+    } else if (s.N == 4) {
         const T w01 = W[s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1];
 #pragma unroll
         for (int r2 = 0; r2 < RMAX; ++r2)
@@ -78,7 +59,7 @@ __device__ __forceinline__ void tile_range(const T* X, long long e0, long long n
 }
 
 // Bounded drain of stages issued but never consumed (error path only).
-__device__ void drain(uint64_t* bars, int S, int from, int to, int* flags) {
+static __device__ void drain(uint64_t* bars, int S, int from, int to, int* flags) {
     for (int it = from; it < to; ++it) {
         const long long t0 = clock64();
         while (!mbar_try_wait(&bars[it % S], static_cast<unsigned>((it / S) & 1)))
@@ -91,9 +72,8 @@ __device__ void drain(uint64_t* bars, int S, int from, int to, int* flags) {
 // ROW kernel: k in F (CASE_F) or k = N-2 (CASE_A)
 // ---------------------------------------------------------------------------
 template <typename T, int RB>
-__global__ void __launch_bounds__(256) k_contract_row(const ContractArgs<T> A) {
-    if (*A.done) return;
-    extern __shared__ __align__(128) unsigned char smem[];
+__device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const int uidx, unsigned char* smem,
+                                  uint64_t* bars, int& pipe) {
     const Shape& s = A.sh;
     const ContractPlan& pl = A.pl;
     const int N = s.N, k = A.k, IA = s.IA, IB = s.IB;
@@ -101,27 +81,27 @@ __global__ void __launch_bounds__(256) k_contract_row(const ContractArgs<T> A) {
     const int TA = pl.TA, G = pl.G, S = pl.nstages;
     constexpr int RBP = RB | 1;
     const bool isF = pl.kcase == CASE_F;
-    const UnitDesc u = A.units[blockIdx.x];
+    const UnitDesc u = A.units[uidx];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
     const int g = tid / TA, al = tid - g * TA;
     const bool in_grid = g < G;
 
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    T* stage = reinterpret_cast<T*>(smem + 128);
-    T* psi = stage + static_cast<size_t>(S) * G * pl.sub_elems;
-    T* wab = psi + static_cast<size_t>(G) * IB * RBP;
+    const bool split = pl.split != 0;
+    const int GS = split ? 1 : G;  // slabs per stage
+    T* stage = reinterpret_cast<T*>(smem);
+    T* psi = stage + static_cast<size_t>(S) * GS * pl.sub_elems;
+    T* wab = psi + static_cast<size_t>(GS) * IB * RBP;
     T* red = wab + (isF ? static_cast<size_t>(TA) * IB : 0);
 
     const int na_tot = u.a1 - u.a0;
     const int npass = (na_tot + TA - 1) / TA;
-    const int nbatch = (u.ns + G - 1) / G;
+    const int nbatch = (u.ns + GS - 1) / GS;
     const int nst = npass * nbatch;
+    // split mode: group g covers columns [bg0, bg1) of every row
+    const int bg0 = split ? static_cast<int>(static_cast<long long>(IB) * g / G) : 0;
+    const int bg1 = split ? static_cast<int>(static_cast<long long>(IB) * (g + 1) / G) : IB;
 
-    if (tid == 0) {
-        for (int i = 0; i < S; ++i) mbar_init(&bars[i], 1);
-        fence_mbar_init();
-    }
     T* outs = red + static_cast<size_t>(nwarp) * pl.Q;
     if (isF)
         for (int q = tid; q < pl.Q; q += nthr) outs[q] = T(0);
@@ -131,21 +111,21 @@ __global__ void __launch_bounds__(256) k_contract_row(const ContractArgs<T> A) {
         const int p = it / nbatch, bt = it - p * nbatch;
         const int a0 = u.a0 + p * TA;
         const int na = min(TA, u.a1 - a0);
-        const int buf = it % S;
-        const int gmax = min(G, u.ns - bt * G);
+        const int buf = (pipe + it) % S;
+        const int gmax = min(GS, u.ns - bt * GS);
         unsigned total = 0;
         for (int gg = 0; gg < gmax; ++gg) {
-            const long long f = u.f0 + static_cast<long long>(bt * G + gg) * u.fstride;
+            const long long f = u.f0 + static_cast<long long>(bt * GS + gg) * u.fstride;
             uintptr_t lo, hi;
             tile_range(A.X, (f * IA + a0) * IB, static_cast<long long>(na) * IB, lo, hi);
             total += static_cast<unsigned>(hi - lo);
         }
         mbar_arrive_expect_tx(&bars[buf], total);
         for (int gg = 0; gg < gmax; ++gg) {
-            const long long f = u.f0 + static_cast<long long>(bt * G + gg) * u.fstride;
+            const long long f = u.f0 + static_cast<long long>(bt * GS + gg) * u.fstride;
             uintptr_t lo, hi;
             tile_range(A.X, (f * IA + a0) * IB, static_cast<long long>(na) * IB, lo, hi);
-            bulk_g2s(stage + (static_cast<size_t>(buf) * G + gg) * pl.sub_elems,
+            bulk_g2s(stage + (static_cast<size_t>(buf) * GS + gg) * pl.sub_elems,
                      reinterpret_cast<const void*>(lo), static_cast<unsigned>(hi - lo), &bars[buf]);
         }
     };
@@ -162,22 +142,30 @@ __global__ void __launch_bounds__(256) k_contract_row(const ContractArgs<T> A) {
         const int p = it / nbatch, bt = it - p * nbatch;
         const int a0 = u.a0 + p * TA;
         const int na = min(TA, u.a1 - a0);
-        const int buf = it % S;
-        const unsigned par = static_cast<unsigned>((it / S) & 1);
+        const int buf = (pipe + it) % S;
+        const unsigned par = static_cast<unsigned>(((pipe + it) / S) & 1);
         if (isF && bt == 0) {  // pair matrix W_{A,B} rows of this pass
             const T* src = A.W + s.woff[Am][Bm] + static_cast<long long>(a0) * IB;
             for (int idx = tid; idx < na * IB; idx += nthr) wab[idx] = src[idx];
         }
-        const int sidx = bt * G + g;
+        const int gsl = split ? 0 : g;  // this thread's slab within the stage
+        const int sidx = bt * GS + gsl;
         const bool has = in_grid && sidx < u.ns;
         long long f = 0;
         int i0 = 0, i1 = 0;
         if (has) {
             f = u.f0 + static_cast<long long>(sidx) * u.fstride;
             decode_f(s, f, i0, i1);
-            // psi(b, r) = prod_{p in F, p != k} W_{p,B}(i_p, b) * G_{B,k}(r, b)
-            T* pg = psi + static_cast<size_t>(g) * IB * RBP;
-            for (int idx = al; idx < IB * RB; idx += TA) {
+        }
+        // psi(b, r) = prod_{p in F, p != k} W_{p,B}(i_p, b) * G_{B,k}(r, b)
+        if (split ? (bt < u.ns) : has) {
+            if (split && !has) {  // padding threads help fill the shared table
+                f = u.f0 + static_cast<long long>(bt) * u.fstride;
+                decode_f(s, f, i0, i1);
+            }
+            T* pg = psi + static_cast<size_t>(gsl) * IB * RBP;
+            const int t0 = split ? tid : al, tst = split ? nthr : TA;
+            for (int idx = t0; idx < IB * RB; idx += tst) {
                 const int b = idx / RB, r = idx - b * RB;
                 T om = T(1);
                 if (N >= 3 && k != 0) om *= A.W[s.woff[0][Bm] + static_cast<long long>(i0) * IB + b];
@@ -188,28 +176,29 @@ __global__ void __launch_bounds__(256) k_contract_row(const ContractArgs<T> A) {
         __syncthreads();
         const bool ok = mbar_wait_bounded(&bars[buf], par, A.flags);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) drain(bars, S, it + 1, min(nst, it + S), A.flags);
-            return;
+            if (tid == 0) drain(bars, S, pipe + it + 1, pipe + min(nst, it + S), A.flags);
+            return false;
         }
         if (has && al < na) {
             const long long e0 = (f * IA + a0) * IB;
             const int shift = static_cast<int>((reinterpret_cast<uintptr_t>(A.X + e0) & 15) / sizeof(T));
-            const T* xr = stage + (static_cast<size_t>(buf) * G + g) * pl.sub_elems + shift +
+            const T* xr = stage + (static_cast<size_t>(buf) * GS + gsl) * pl.sub_elems + shift +
                           static_cast<size_t>(al) * IB;
-            const T* pg = psi + static_cast<size_t>(g) * IB * RBP;
+            const T* pg = psi + static_cast<size_t>(gsl) * IB * RBP;
             T uu[RB];
 #pragma unroll
             for (int r = 0; r < RB; ++r) uu[r] = T(0);
-            const int bst = pl.skew ? (al % IB) : 0;
+            const int blen = bg1 - bg0;
+            const int bst = (pl.skew && blen > 0) ? bg0 + (al % blen) : bg0;
             if (isF) {
                 const T* wr = wab + static_cast<size_t>(al) * IB;
-                for (int b = bst; b < IB; ++b) {
+                for (int b = bst; b < bg1; ++b) {
                     const T x = xr[b] * wr[b];
                     const T* pr = pg + b * RBP;
 #pragma unroll
                     for (int r = 0; r < RB; ++r) uu[r] = fma(x, pr[r], uu[r]);
                 }
-                for (int b = 0; b < bst; ++b) {
+                for (int b = bg0; b < bst; ++b) {
                     const T x = xr[b] * wr[b];
                     const T* pr = pg + b * RBP;
 #pragma unroll
@@ -232,19 +221,19 @@ __global__ void __launch_bounds__(256) k_contract_row(const ContractArgs<T> A) {
                     for (int r = 0; r < RB; ++r) z[0][r] += uu[r];
                 }
             } else {
-                for (int b = bst; b < IB; ++b) {
+                for (int b = bst; b < bg1; ++b) {
                     const T x = xr[b];
                     const T* pr = pg + b * RBP;
 #pragma unroll
                     for (int r = 0; r < RB; ++r) uu[r] = fma(x, pr[r], uu[r]);
                 }
-                for (int b = 0; b < bst; ++b) {
+                for (int b = bg0; b < bst; ++b) {
                     const T x = xr[b];
                     const T* pr = pg + b * RBP;
 #pragma unroll
                     for (int r = 0; r < RB; ++r) uu[r] = fma(x, pr[r], uu[r]);
                 }
-                fold_outer<T, RB>(s, A.Gt, A.W, k, pl.Rl2, i0, i1, uu, z);
+                fold_outer<T, RB>(s, A.Gt, A.W, k, pl.l2, pl.Rl2, i0, i1, uu, z);
             }
         }
         __syncthreads();
@@ -291,7 +280,7 @@ __global__ void __launch_bounds__(256) k_contract_row(const ContractArgs<T> A) {
                     const int row = idx / Qp, q = idx - row * Qp;
                     T acc = T(0);
                     for (int gg = 0; gg < G; ++gg) acc += red[(gg * TA + row) * Qp + q];
-                    A.part[(static_cast<size_t>(blockIdx.x) * IA + a0 + row) * Qp + q] = acc;
+                    A.part[(static_cast<size_t>(uidx) * IA + a0 + row) * Qp + q] = acc;
                 }
                 __syncthreads();
             }
@@ -304,63 +293,62 @@ __global__ void __launch_bounds__(256) k_contract_row(const ContractArgs<T> A) {
     if (isF)
         for (int q = tid; q < pl.Q; q += nthr)
             A.part[(static_cast<size_t>(u.key) * pl.nslot + u.slot) * pl.Q + q] = outs[q];
+    __syncthreads();
+    pipe += nst;
+    return true;
 }
 
 // ---------------------------------------------------------------------------
 // COL kernel: k = N-1 (the contiguous mode is the output index)
 // ---------------------------------------------------------------------------
 template <typename T, int RA>
-__global__ void __launch_bounds__(256) k_contract_col(const ContractArgs<T> A) {
-    if (*A.done) return;
-    extern __shared__ __align__(128) unsigned char smem[];
+__device__ __noinline__ bool contract_col_unit(const ContractArgs<T>& A, const int uidx, unsigned char* smem,
+                                  uint64_t* bars, int& pipe) {
     const Shape& s = A.sh;
     const ContractPlan& pl = A.pl;
     const int N = s.N, k = A.k, IA = s.IA, IB = s.IB;
     const int Am = N - 2;
     const int TB = pl.TA, G = pl.G, S = pl.nstages, TAc = pl.TAc;
     constexpr int RAP = RA | 1;
-    const UnitDesc u = A.units[blockIdx.x];
+    const UnitDesc u = A.units[uidx];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int g = tid / TB, bl = tid - g * TB;
     const bool in_grid = g < G;
     const int b = u.b0 + bl;
     const bool colok = in_grid && b < u.b1;
 
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    T* stage = reinterpret_cast<T*>(smem + 128);
-    T* phi = stage + static_cast<size_t>(S) * G * pl.sub_elems;
-    T* red = phi + static_cast<size_t>(G) * TAc * RAP;
+    const bool split = pl.split != 0;
+    const int GS = split ? 1 : G;  // slabs per stage
+    T* stage = reinterpret_cast<T*>(smem);
+    T* phi = stage + static_cast<size_t>(S) * GS * pl.sub_elems;
+    T* red = phi + static_cast<size_t>(GS) * TAc * RAP;
 
     const int na_tot = u.a1 - u.a0;
     const int nch = (na_tot + TAc - 1) / TAc;
-    const int nbatch = (u.ns + G - 1) / G;
+    const int nbatch = (u.ns + GS - 1) / GS;
     const int nst = nbatch * nch;
 
-    if (tid == 0) {
-        for (int i = 0; i < S; ++i) mbar_init(&bars[i], 1);
-        fence_mbar_init();
-    }
     __syncthreads();
 
     auto issue = [&](int it) {
         const int bt = it / nch, c = it - bt * nch;
         const int a0 = u.a0 + c * TAc;
         const int na = min(TAc, u.a1 - a0);
-        const int buf = it % S;
-        const int gmax = min(G, u.ns - bt * G);
+        const int buf = (pipe + it) % S;
+        const int gmax = min(GS, u.ns - bt * GS);
         unsigned total = 0;
         for (int gg = 0; gg < gmax; ++gg) {
-            const long long f = u.f0 + static_cast<long long>(bt * G + gg) * u.fstride;
+            const long long f = u.f0 + static_cast<long long>(bt * GS + gg) * u.fstride;
             uintptr_t lo, hi;
             tile_range(A.X, (f * IA + a0) * IB, static_cast<long long>(na) * IB, lo, hi);
             total += static_cast<unsigned>(hi - lo);
         }
         mbar_arrive_expect_tx(&bars[buf], total);
         for (int gg = 0; gg < gmax; ++gg) {
-            const long long f = u.f0 + static_cast<long long>(bt * G + gg) * u.fstride;
+            const long long f = u.f0 + static_cast<long long>(bt * GS + gg) * u.fstride;
             uintptr_t lo, hi;
             tile_range(A.X, (f * IA + a0) * IB, static_cast<long long>(na) * IB, lo, hi);
-            bulk_g2s(stage + (static_cast<size_t>(buf) * G + gg) * pl.sub_elems,
+            bulk_g2s(stage + (static_cast<size_t>(buf) * GS + gg) * pl.sub_elems,
                      reinterpret_cast<const void*>(lo), static_cast<unsigned>(hi - lo), &bars[buf]);
         }
     };
@@ -379,18 +367,26 @@ __global__ void __launch_bounds__(256) k_contract_col(const ContractArgs<T> A) {
         const int bt = it / nch, c = it - bt * nch;
         const int a0 = u.a0 + c * TAc;
         const int na = min(TAc, u.a1 - a0);
-        const int buf = it % S;
-        const unsigned par = static_cast<unsigned>((it / S) & 1);
-        const int sidx = bt * G + g;
+        const int buf = (pipe + it) % S;
+        const unsigned par = static_cast<unsigned>(((pipe + it) / S) & 1);
+        const int gsl = split ? 0 : g;
+        const int sidx = bt * GS + gsl;
         const bool has = in_grid && sidx < u.ns;
         long long f = 0;
         int i0 = 0, i1 = 0;
         if (has) {
             f = u.f0 + static_cast<long long>(sidx) * u.fstride;
             decode_f(s, f, i0, i1);
-            // phi(a, r) = prod_{p in F} W_{p,A}(i_p, a) * G_{A,k}(r, a)
-            T* pg = phi + static_cast<size_t>(g) * TAc * RAP;
-            for (int idx = bl; idx < na * RA; idx += TB) {
+        }
+        // phi(a, r) = prod_{p in F} W_{p,A}(i_p, a) * G_{A,k}(r, a)
+        if (split ? (bt < u.ns) : has) {
+            if (split && !has) {
+                f = u.f0 + static_cast<long long>(bt) * u.fstride;
+                decode_f(s, f, i0, i1);
+            }
+            T* pg = phi + static_cast<size_t>(gsl) * TAc * RAP;
+            const int t0 = split ? tid : bl, tst = split ? nthr : TB;
+            for (int idx = t0; idx < na * RA; idx += tst) {
                 const int ar = idx / RA, r = idx - ar * RA;
                 const int a = a0 + ar;
                 T om = T(1);
@@ -402,15 +398,16 @@ __global__ void __launch_bounds__(256) k_contract_col(const ContractArgs<T> A) {
         __syncthreads();
         const bool ok = mbar_wait_bounded(&bars[buf], par, A.flags);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) drain(bars, S, it + 1, min(nst, it + S), A.flags);
-            return;
+            if (tid == 0) drain(bars, S, pipe + it + 1, pipe + min(nst, it + S), A.flags);
+            return false;
         }
         if (has && colok) {
             const long long e0 = (f * IA + a0) * IB;
             const int shift = static_cast<int>((reinterpret_cast<uintptr_t>(A.X + e0) & 15) / sizeof(T));
-            const T* xr = stage + (static_cast<size_t>(buf) * G + g) * pl.sub_elems + shift + b;
-            const T* pg = phi + static_cast<size_t>(g) * TAc * RAP;
-            for (int ar = 0; ar < na; ++ar) {
+            const T* xr = stage + (static_cast<size_t>(buf) * GS + gsl) * pl.sub_elems + shift + b;
+            const T* pg = phi + static_cast<size_t>(gsl) * TAc * RAP;
+            const int ar0 = split ? g : 0, ars = split ? G : 1;
+            for (int ar = ar0; ar < na; ar += ars) {
                 const T x = xr[static_cast<size_t>(ar) * IB];
                 const T* pr = pg + ar * RAP;
 #pragma unroll
@@ -418,7 +415,7 @@ __global__ void __launch_bounds__(256) k_contract_col(const ContractArgs<T> A) {
             }
         }
         if (c == nch - 1) {
-            if (has && colok) fold_outer<T, RA>(s, A.Gt, A.W, k, pl.Rl2, i0, i1, uu, z);
+            if (has && colok) fold_outer<T, RA>(s, A.Gt, A.W, k, pl.l2, pl.Rl2, i0, i1, uu, z);
 #pragma unroll
             for (int r = 0; r < RA; ++r) uu[r] = T(0);
         }
@@ -440,108 +437,12 @@ __global__ void __launch_bounds__(256) k_contract_col(const ContractArgs<T> A) {
         const int row = idx / Qp, q = idx - row * Qp;
         T acc = T(0);
         for (int gg = 0; gg < G; ++gg) acc += red[(gg * TB + row) * Qp + q];
-        A.part[(static_cast<size_t>(blockIdx.x) * IB + u.b0 + row) * Qp + q] = acc;
+        A.part[(static_cast<size_t>(uidx) * IB + u.b0 + row) * Qp + q] = acc;
     }
+    __syncthreads();
+    pipe += nst;
+    return true;
 }
 
-// ---------------------------------------------------------------------------
-// finisher: M_k(row, q) from the partials (fixed order)
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_contract_finish(const Shape s, const int k,
-                                                         const ContractPlan pl,
-                                                         const UnitDesc* __restrict__ units,
-                                                         const T* __restrict__ part,
-                                                         const T* __restrict__ Gt,
-                                                         double* __restrict__ Mk,
-                                                         const int* __restrict__ done) {
-    if (*done) return;
-    const int Ik = s.I[k], Q = pl.Q, Qp = pl.Qp;
-    const long long total = static_cast<long long>(Ik) * Q;
-    for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total;
-         idx += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int row = static_cast<int>(idx / Q), q = static_cast<int>(idx - static_cast<long long>(row) * Q);
-        T acc = T(0);
-        if (pl.kcase == CASE_F) {
-            for (int sl = 0; sl < pl.nslot; ++sl)
-                acc += part[(static_cast<size_t>(row) * pl.nslot + sl) * Q + q];
-        } else {
-            const int rd = pl.dmode >= 0 ? q / Qp : 0;
-            const int qp = q - rd * Qp;
-            const bool colcase = pl.kcase == CASE_COL;
-            for (int un = 0; un < pl.nunits; ++un) {
-                const int lo = colcase ? units[un].b0 : units[un].a0;
-                const int hi = colcase ? units[un].b1 : units[un].a1;
-                if (row < lo || row >= hi) continue;
-                T v = part[(static_cast<size_t>(un) * pl.nrow + row) * Qp + qp];
-                if (pl.dmode >= 0) v *= gfac(Gt, s, pl.dmode, k, rd, units[un].key);
-                acc += v;
-            }
-        }
-        Mk[idx] = static_cast<double>(acc);
-    }
-}
-
-template <typename T, int R>
-cudaError_t launch_row_r(const ContractArgs<T>& a, cudaStream_t st) {
-    auto kern = k_contract_row<T, R>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
-    if (e != cudaSuccess) return e;
-    kern<<<a.pl.nunits, a.pl.nthreads, a.pl.smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename T, int R>
-cudaError_t launch_col_r(const ContractArgs<T>& a, cudaStream_t st) {
-    auto kern = k_contract_col<T, R>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
-    if (e != cudaSuccess) return e;
-    kern<<<a.pl.nunits, a.pl.nthreads, a.pl.smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-}  // namespace
-
-template <typename T>
-cudaError_t launch_contract(const ContractArgs<T>& a, cudaStream_t st) {
-    const bool col = a.pl.kcase == CASE_COL;
-    switch (a.pl.R1) {
-#define IFCTN_CASE(R) \
-    case R:           \
-        return col ? launch_col_r<T, R>(a, st) : launch_row_r<T, R>(a, st);
-        IFCTN_CASE(1)
-        IFCTN_CASE(2)
-        IFCTN_CASE(3)
-        IFCTN_CASE(4)
-        IFCTN_CASE(5)
-        IFCTN_CASE(6)
-        IFCTN_CASE(7)
-        IFCTN_CASE(8)
-#undef IFCTN_CASE
-        default:
-            return cudaErrorInvalidValue;
-    }
-}
-
-template <typename T>
-cudaError_t launch_contract_finish(const Shape& sh, int k, const ContractPlan& pl,
-                                   const UnitDesc* units, const T* part, const T* Gt, double* Mk,
-                                   const int* done, cudaStream_t st) {
-    const long long total = static_cast<long long>(sh.I[k]) * pl.Q;
-    int blocks = static_cast<int>((total + 255) / 256);
-    if (blocks > 1216) blocks = 1216;
-    if (blocks < 1) blocks = 1;
-    k_contract_finish<T><<<blocks, 256, 0, st>>>(sh, k, pl, units, part, Gt, Mk, done);
-    return cudaGetLastError();
-}
-
-template cudaError_t launch_contract<float>(const ContractArgs<float>&, cudaStream_t);
-template cudaError_t launch_contract<double>(const ContractArgs<double>&, cudaStream_t);
-template cudaError_t launch_contract_finish<float>(const Shape&, int, const ContractPlan&,
-                                                   const UnitDesc*, const float*, const float*,
-                                                   double*, const int*, cudaStream_t);
-template cudaError_t launch_contract_finish<double>(const Shape&, int, const ContractPlan&,
-                                                    const UnitDesc*, const double*, const double*,
-                                                    double*, const int*, cudaStream_t);
-
+}  // namespace cdev
 }  // namespace ifctn

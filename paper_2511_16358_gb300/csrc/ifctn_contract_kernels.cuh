@@ -1,0 +1,154 @@
+// ifctn_contract_kernels.cuh -- the streaming mode-k contraction M_k = X_(k) Z_k.
+// (standalone kernels; instantiated per dtype in ifctn_persistent_f{32,64}.cu)
+//
+// Prop. 1 writes the mode-k sub-network as
+//     Z_k(i_{-k}, r) = S_k(i_{-k}) * prod_{m != k} G_{m,k}(r_m, i_m),
+//     S_k = broadcast product of W_{p,q} = G_{p,q}^T G_{q,p} over pairs p,q != k,
+// and eq. (updateG) needs, for every column j of every G_{k,i}, the vector
+// A_j^T x_j.  All of these are contractions of one matrix,
+//     M_k(j, r) = sum_{i_{-k}} X(i_k = j, i_{-k}) Z_k(i_{-k}, r),
+// against the Kronecker vector E_j of the other columns G_{k,m}(:, j), so the
+// whole mode needs a single pass over X.  Z_k is never formed: its entries are
+// built on the fly from the small W and G matrices (the "coefficient builder").
+//
+// The pass is one-read HBM streaming.  The tensor is cut into slabs (all
+// entries sharing the indices of modes 0..N-3); each CTA takes a list of slabs
+// and moves contiguous slab tiles into a shared-memory ring with 1-D TMA bulk
+// copies (cp.async.bulk + mbarrier), several stages ahead of the compute.
+// Inside a tile the contraction is hierarchical, so each tensor entry costs
+// about R_{k,B} + 2 FMAs:
+//   ROW kernel (k is not the last mode): a thread owns one row a of mode N-2,
+//     contracts the contiguous mode N-1 in registers (u = R values), folds the
+//     row into a register tile z over one more mode, and the remaining modes
+//     are contracted at the flush or in the finisher.
+//   COL kernel (k is the last mode): a thread owns one column b, contracts
+//     mode N-2 in registers and folds slabs into z the same way.
+// Partials are written per work unit and reduced by the finisher in a fixed
+// order, so results are deterministic (no atomics).
+#pragma once
+#include "ifctn_contract_dev.cuh"
+
+namespace ifctn {
+namespace {
+using namespace cdev;
+
+template <typename T, int RB>
+__global__ void __launch_bounds__(256) k_contract_row(const ContractArgs<T> A) {
+    if (*A.done) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < A.pl.nstages; ++i) mbar_init(&bars[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int pipe = 0;
+    contract_row_unit<T, RB>(A, blockIdx.x, smem + 128, bars, pipe);
+}
+
+template <typename T, int RA>
+__global__ void __launch_bounds__(256) k_contract_col(const ContractArgs<T> A) {
+    if (*A.done) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < A.pl.nstages; ++i) mbar_init(&bars[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int pipe = 0;
+    contract_col_unit<T, RA>(A, blockIdx.x, smem + 128, bars, pipe);
+}
+
+// ---------------------------------------------------------------------------
+// finisher: M_k(row, q) from the partials (fixed order)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_contract_finish(const Shape s, const int k,
+                                                         const ContractPlan pl,
+                                                         const UnitDesc* __restrict__ units,
+                                                         const T* __restrict__ part,
+                                                         const T* __restrict__ Gt,
+                                                         double* __restrict__ Mk,
+                                                         const int* __restrict__ done) {
+    if (*done) return;
+    const int Ik = s.I[k], Q = pl.Q, Qp = pl.Qp;
+    const long long total = static_cast<long long>(Ik) * Q;
+    for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int row = static_cast<int>(idx / Q), q = static_cast<int>(idx - static_cast<long long>(row) * Q);
+        T acc = T(0);
+        if (pl.kcase == CASE_F) {
+            for (int sl = 0; sl < pl.nslot; ++sl)
+                acc += part[(static_cast<size_t>(row) * pl.nslot + sl) * Q + q];
+        } else {
+            const int rd = pl.dmode >= 0 ? q / Qp : 0;
+            const int qp = q - rd * Qp;
+            const bool colcase = pl.kcase == CASE_COL;
+            for (int un = 0; un < pl.nunits; ++un) {
+                const int lo = colcase ? units[un].b0 : units[un].a0;
+                const int hi = colcase ? units[un].b1 : units[un].a1;
+                if (row < lo || row >= hi) continue;
+                T v = part[(static_cast<size_t>(un) * pl.nrow + row) * Qp + qp];
+                if (pl.dmode >= 0) v *= gfac(Gt, s, pl.dmode, k, rd, units[un].key);
+                acc += v;
+            }
+        }
+        Mk[idx] = static_cast<double>(acc);
+    }
+}
+
+template <typename T, int R>
+cudaError_t launch_row_r(const ContractArgs<T>& a, cudaStream_t st) {
+    auto kern = k_contract_row<T, R>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
+    if (e != cudaSuccess) return e;
+    kern<<<a.pl.nunits, a.pl.nthreads, a.pl.smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int R>
+cudaError_t launch_col_r(const ContractArgs<T>& a, cudaStream_t st) {
+    auto kern = k_contract_col<T, R>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
+    if (e != cudaSuccess) return e;
+    kern<<<a.pl.nunits, a.pl.nthreads, a.pl.smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_contract(const ContractArgs<T>& a, cudaStream_t st) {
+    const bool col = a.pl.kcase == CASE_COL;
+    switch (a.pl.R1) {
+#define IFCTN_CASE(R) \
+    case R:           \
+        return col ? launch_col_r<T, R>(a, st) : launch_row_r<T, R>(a, st);
+        IFCTN_CASE(1)
+        IFCTN_CASE(2)
+        IFCTN_CASE(3)
+        IFCTN_CASE(4)
+        IFCTN_CASE(5)
+        IFCTN_CASE(6)
+        IFCTN_CASE(7)
+        IFCTN_CASE(8)
+#undef IFCTN_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t launch_contract_finish(const Shape& sh, int k, const ContractPlan& pl,
+                                   const UnitDesc* units, const T* part, const T* Gt, double* Mk,
+                                   const int* done, cudaStream_t st) {
+    const long long total = static_cast<long long>(sh.I[k]) * pl.Q;
+    int blocks = static_cast<int>((total + 255) / 256);
+    if (blocks > 1216) blocks = 1216;
+    if (blocks < 1) blocks = 1;
+    k_contract_finish<T><<<blocks, 256, 0, st>>>(sh, k, pl, units, part, Gt, Mk, done);
+    return cudaGetLastError();
+}
+
+}  // namespace ifctn

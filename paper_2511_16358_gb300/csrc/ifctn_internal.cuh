@@ -64,6 +64,11 @@ struct ContractPlan {
     int nstages;
     int smem;        // dynamic shared memory bytes
     int skew;        // ROW: rotate the b loop (IB even)
+    int split;       // 1: one slab per stage, the G groups split its reduction
+                     //    range (ROW: columns b, COL: rows a); 0: groups take
+                     //    different slabs
+    int key_div;     // > 0: every unit covers all rows and its deferred key is
+                     //      unit / key_div (no descriptor loads in the reduction)
     long long part_elems;
 };
 

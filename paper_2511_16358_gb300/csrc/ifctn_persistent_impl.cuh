@@ -1,0 +1,861 @@
+// ifctn_persistent_impl.cuh -- the whole PAM run (Algorithm 1) in one cooperative
+// launch.
+//
+// One sweep is a chain of dependent phases (per mode k: contraction + Gram
+// partials, their reduction, the column solves; then the X update).  Issued
+// as separate kernels every phase pays a launch and a cold start, which
+// dominates for tensors that live in L2.  Here one persistent grid (as many
+// CTAs as fit co-resident, guaranteed by a cooperative launch) runs every
+// phase of every sweep and separates them with a software grid barrier:
+//
+//   mode k:  P1  streaming contraction units (TMA-fed, ifctn_contract_dev.cuh)
+//                + Gram chain units, grid-strided over CTAs        | barrier
+//            P2  K_k and M_k reductions of the partials, one lane
+//                group per output                                   | barrier
+//            P3  column solves of eq. (updateG) + W_{k,.} refresh   | barrier
+//   then     P4  fused reconstruct + masked X update (eq. (updateX))| barrier
+//            P5  every CTA reduces the per-CTA sums in the same fixed
+//                order, so all CTAs take the same stop decision.
+//
+// All reductions are fixed-order, so the factors and the tensor do not depend
+// on the grid size.  Every wait is bounded; on expiry a flag is raised and
+// the kernel returns.
+#pragma once
+#include <algorithm>
+
+#include "ifctn_contract_dev.cuh"
+#include "ifctn_persistent.h"
+
+namespace ifctn {
+namespace {
+
+using cdev::contract_col_unit;
+using cdev::contract_row_unit;
+
+constexpr int PT = 256;  // threads per CTA
+constexpr int PW = PT / 32;
+constexpr int GRAM_IOB = 8;  // io values per Gram unit (N = 3)
+
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* flags) {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g) {
+                if (clock64() - t0 > 4000000000LL) {
+                    atomicOr(flags, FLAG_TIMEOUT);
+                    break;
+                }
+                __nanosleep(20);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return (*reinterpret_cast<volatile int*>(flags) & FLAG_TIMEOUT) == 0;
+}
+
+__device__ __forceinline__ int nonk(const Shape& s, int k, int* m) {
+    int t = 0;
+    for (int q = 0; q < s.N; ++q)
+        if (q != k) m[t++] = q;
+    return t;
+}
+
+// sum over a group of L lanes (L a power of two, groups aligned in the warp)
+template <typename T>
+__device__ __forceinline__ T group_sum(T v, int L) {
+    for (int o = L >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int pow2_at_least(int x) {
+    int L = 1;
+    while (L < x && L < 32) L <<= 1;
+    return L;
+}
+
+template <typename T>
+__device__ bool contract_dispatch(const SweepParams<T>& p, int k, int uidx, unsigned char* smem,
+                                  uint64_t* bars, int& pipe) {
+    ContractArgs<T> a;
+    a.X = p.X;
+    a.Gt = p.Gt;
+    a.W = p.W;
+    a.sh = p.sh;
+    a.k = k;
+    a.pl = p.pl[k];
+    a.units = p.units[k];
+    a.part = p.part;
+    a.flags = p.flags;
+    a.done = p.done;
+    const bool col = p.pl[k].kcase == CASE_COL;
+    switch (p.pl[k].R1) {
+#define IFCTN_PCASE(R) \
+    case R:            \
+        return col ? contract_col_unit<T, R>(a, uidx, smem, bars, pipe) : contract_row_unit<T, R>(a, uidx, smem, bars, pipe);
+        IFCTN_PCASE(1)
+        IFCTN_PCASE(2)
+        IFCTN_PCASE(3)
+        IFCTN_PCASE(4)
+        IFCTN_PCASE(5)
+        IFCTN_PCASE(6)
+        IFCTN_PCASE(7)
+        IFCTN_PCASE(8)
+#undef IFCTN_PCASE
+        default:
+            return false;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gram units (phase 1).  Non-k modes ascending: [o, l] (N=3), [o, c, l] (N=4).
+//   N=3: T2[io][x][y] = sum_il W_ol(io,il)^2 g_l(x,il) g_l(y,il)
+//   N=4: T1[ic][x][y] = W_oc(io,ic)^2 sum_il (W_ol(io,il) W_cl(ic,il))^2 g_l g_l
+//        T2[io][(xc,xl)][(yc,yl)] = sum_ic g_c(xc,ic) g_c(yc,ic) T1[ic][xl][yl]
+// with g_m = G_{m,k}.  K_k = sum_io g_o g_o^T (x) T2[io] is formed in phase 2.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void gram_unit(const SweepParams<T>& p, int k, int gu, unsigned char* smem) {
+    const Shape& s = p.sh;
+    int m[3];
+    nonk(s, k, m);
+    T* sm = reinterpret_cast<T*>(smem);
+    const int tid = threadIdx.x;
+    if (s.N == 3) {
+        const int o = m[0], l = m[1];
+        const int Io = s.I[o], Il = s.I[l], Rl = s.R[k][l];
+        const int io0 = gu * GRAM_IOB, io1 = min(Io, io0 + GRAM_IOB);
+        T* gl = sm;  // Rl x Il
+        for (int idx = tid; idx < Rl * Il; idx += PT) gl[idx] = p.Gt[s.goff[l][k] + idx];
+        T* wr = gl + Rl * Il;  // (io1-io0) x Il, squared
+        for (int idx = tid; idx < (io1 - io0) * Il; idx += PT) {
+            const T w = p.W[s.woff[o][l] + static_cast<long long>(io0) * Il + idx];
+            wr[idx] = w * w;
+        }
+        __syncthreads();
+        const int nout = (io1 - io0) * Rl * Rl;
+        for (int idx = tid; idx < nout; idx += PT) {
+            const int y = idx % Rl, x = (idx / Rl) % Rl, ir = idx / (Rl * Rl);
+            const T* gx = gl + x * Il;
+            const T* gy = gl + y * Il;
+            const T* w2 = wr + ir * Il;
+            T a0 = T(0), a1 = T(0);
+            int il = 0;
+            for (; il + 1 < Il; il += 2) {
+                a0 = fma(w2[il], gx[il] * gy[il], a0);
+                a1 = fma(w2[il + 1], gx[il + 1] * gy[il + 1], a1);
+            }
+            if (il < Il) a0 = fma(w2[il], gx[il] * gy[il], a0);
+            p.gbuf[(static_cast<long long>(io0 + ir) * Rl + x) * Rl + y] = a0 + a1;
+        }
+        __syncthreads();
+        return;
+    }
+    // N = 4: one io per unit
+    const int o = m[0], c = m[1], l = m[2];
+    const int io = gu;
+    const int Ic = s.I[c], Il = s.I[l], Rc = s.R[k][c], Rl = s.R[k][l];
+    const int Q2 = Rc * Rl;
+    T* gl = sm;                    // Rl x Il
+    T* gc = gl + Rl * Il;          // Rc x Ic
+    T* wol = gc + Rc * Ic;         // Il
+    T* t2a = wol + Il;             // Q2 x Q2 accumulators
+    T* t1 = t2a + Q2 * Q2;         // chunk x Rl x Rl
+    for (int idx = tid; idx < Rl * Il; idx += PT) gl[idx] = p.Gt[s.goff[l][k] + idx];
+    for (int idx = tid; idx < Rc * Ic; idx += PT) gc[idx] = p.Gt[s.goff[c][k] + idx];
+    for (int idx = tid; idx < Il; idx += PT) wol[idx] = p.W[s.woff[o][l] + static_cast<long long>(io) * Il + idx];
+    for (int idx = tid; idx < Q2 * Q2; idx += PT) t2a[idx] = T(0);
+    const int chunk = max(1, min(Ic, p.gram_chunk));
+    __syncthreads();
+    for (int ic0 = 0; ic0 < Ic; ic0 += chunk) {
+        const int nc = min(chunk, Ic - ic0);
+        for (int idx = tid; idx < nc * Rl * Rl; idx += PT) {
+            const int y = idx % Rl, x = (idx / Rl) % Rl, icr = idx / (Rl * Rl);
+            const int ic = ic0 + icr;
+            const T* wcl = p.W + s.woff[c][l] + static_cast<long long>(ic) * Il;
+            const T* gx = gl + x * Il;
+            const T* gy = gl + y * Il;
+            T acc = T(0);
+            for (int il = 0; il < Il; ++il) {
+                const T w = wol[il] * wcl[il];
+                acc = fma(w * w, gx[il] * gy[il], acc);
+            }
+            const T woc = p.W[s.woff[o][c] + static_cast<long long>(io) * Ic + ic];
+            t1[idx] = acc * woc * woc;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < Q2 * Q2; idx += PT) {
+            const int Y = idx % Q2, X = idx / Q2;
+            const int xc = X / Rl, xl = X - xc * Rl, yc = Y / Rl, yl = Y - yc * Rl;
+            T acc = t2a[idx];
+            for (int icr = 0; icr < nc; ++icr) {
+                const int ic = ic0 + icr;
+                acc = fma(gc[xc * Ic + ic] * gc[yc * Ic + ic], t1[(icr * Rl + xl) * Rl + yl], acc);
+            }
+            t2a[idx] = acc;
+        }
+        __syncthreads();
+    }
+    T* dst = p.gbuf + static_cast<long long>(io) * Q2 * Q2;
+    for (int idx = tid; idx < Q2 * Q2; idx += PT) dst[idx] = t2a[idx];
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Phase 2: K_k and M_k from the partials.  A group of L lanes reduces one
+// output; the groups of the whole grid share the outputs.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void reduce_phase(const SweepParams<T>& p, int k) {
+    const Shape& s = p.sh;
+    const ContractPlan& pl = p.pl[k];
+    int m[3];
+    const int nm = nonk(s, k, m);
+    const int o = m[0], Io = s.I[o], Ro = s.R[k][o];
+    int Q2 = 1;
+    for (int t = 1; t < nm; ++t) Q2 *= s.R[k][m[t]];
+    const int Q = Ro * Q2;
+    const int lane = threadIdx.x & 31;
+    const long long gwarp = static_cast<long long>(blockIdx.x) * PW + (threadIdx.x >> 5);
+    const long long nwarps = static_cast<long long>(gridDim.x) * PW;
+    // --- K (upper triangle, mirrored) ---
+    {
+        const int L = pow2_at_least((Io + 3) / 4);
+        const int per = 32 / L;
+        const long long gid = gwarp * per + lane / L;
+        const long long ngroups = nwarps * per;
+        const int sub = lane % L;
+        const long long nout = static_cast<long long>(Q) * (Q + 1) / 2;
+        const long long iters = (nout + ngroups - 1) / ngroups;
+        for (long long it = 0; it < iters; ++it) {
+            const long long out = gid + it * ngroups;
+            T acc = T(0);
+            int row = 0, col = 0;
+            if (out < nout) {
+                // out -> (row <= col) in row-major upper-triangle order
+                long long r = 0, rem = out;
+                while (rem >= Q - r) {
+                    rem -= Q - r;
+                    ++r;
+                }
+                row = static_cast<int>(r);
+                col = static_cast<int>(r + rem);
+                const int xo = row / Q2, X = row - xo * Q2, yo = col / Q2, Y = col - yo * Q2;
+                const T* gx = p.Gt + s.goff[o][k] + xo * Io;
+                const T* gy = p.Gt + s.goff[o][k] + yo * Io;
+                if (nm == 1) {
+                    for (int io = sub; io < Io; io += L) acc = fma(gx[io], gy[io], acc);
+                } else {
+                    const T* tp = p.gbuf + static_cast<long long>(X) * Q2 + Y;
+                    const long long st = static_cast<long long>(Q2) * Q2;
+                    for (int io = sub; io < Io; io += L) acc = fma(gx[io] * gy[io], tp[io * st], acc);
+                }
+            }
+            acc = group_sum(acc, L);
+            if (out < nout && sub == 0) {
+                p.Kk[static_cast<long long>(row) * Q + col] = acc;
+                p.Kk[static_cast<long long>(col) * Q + row] = acc;
+            }
+        }
+    }
+    // --- M ---
+    {
+        const int Ik = s.I[k], Qp = pl.Qp;
+        const bool isF = pl.kcase == CASE_F;
+        const int nterm = isF ? pl.nslot : pl.nunits;
+        const int L = pow2_at_least((nterm + 1) / 2);
+        const int per = 32 / L;
+        const long long gid = gwarp * per + lane / L;
+        const long long ngroups = nwarps * per;
+        const int sub = lane % L;
+        const long long nout = static_cast<long long>(Ik) * Q;
+        const long long iters = (nout + ngroups - 1) / ngroups;
+        const bool colcase = pl.kcase == CASE_COL;
+        for (long long it = 0; it < iters; ++it) {
+            const long long out = gid + it * ngroups;
+            T acc = T(0);
+            if (out < nout) {
+                const int row = static_cast<int>(out / Q), q = static_cast<int>(out - static_cast<long long>(row) * Q);
+                if (isF) {
+                    for (int sl = sub; sl < pl.nslot; sl += L)
+                        acc += p.part[(static_cast<size_t>(row) * pl.nslot + sl) * Q + q];
+                } else if (pl.key_div > 0) {
+                    // every unit covers every row; the deferred key is u / key_div
+                    const int rd = pl.dmode >= 0 ? q / Qp : 0;
+                    const int qp = q - rd * Qp;
+                    const T* pp0 = p.part + static_cast<size_t>(row) * Qp + qp;
+                    const size_t ust = static_cast<size_t>(pl.nrow) * Qp;
+                    if (pl.dmode >= 0) {
+                        const T* gd = p.Gt + s.goff[pl.dmode][k] + rd * s.I[pl.dmode];
+#pragma unroll 4
+                        for (int u = sub; u < pl.nunits; u += L) acc = fma(pp0[u * ust], gd[u / pl.key_div], acc);
+                    } else {
+#pragma unroll 4
+                        for (int u = sub; u < pl.nunits; u += L) acc += pp0[u * ust];
+                    }
+                } else {
+                    const int rd = pl.dmode >= 0 ? q / Qp : 0;
+                    const int qp = q - rd * Qp;
+                    const UnitDesc* un = p.units[k];
+                    for (int u = sub; u < pl.nunits; u += L) {
+                        const int lo = colcase ? un[u].b0 : un[u].a0;
+                        const int hi = colcase ? un[u].b1 : un[u].a1;
+                        if (row < lo || row >= hi) continue;
+                        T v = p.part[(static_cast<size_t>(u) * pl.nrow + row) * Qp + qp];
+                        if (pl.dmode >= 0) v *= gfac(p.Gt, s, pl.dmode, k, rd, un[u].key);
+                        acc += v;
+                    }
+                }
+            }
+            acc = group_sum(acc, L);
+            if (out < nout && sub == 0) p.Mk[k][out] = static_cast<double>(acc);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Phase 3: eq. (updateG) for every column j of mode k, one warp per column.
+// H = E_j^T K_k E_j + rho I and b = E_j^T M_k(j,:) + rho g_old with E_j the
+// Kronecker product of the current columns G_{k,m}(:,j), m != i (identity in
+// slot i); stages i ascending (Gauss-Seidel within the column).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem) {
+    const Shape& s = p.sh;
+    const int Ik = s.I[k];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (static_cast<long long>(blockIdx.x) * PW >= Ik) return;  // no columns for this CTA
+    int m[3];
+    const int nm = nonk(s, k, m);
+    int Rm[3] = {1, 1, 1}, st[3] = {1, 1, 1};
+    int Q = 1;
+    for (int t = 0; t < nm; ++t) {
+        Rm[t] = s.R[k][m[t]];
+        Q *= Rm[t];
+    }
+    for (int t = nm - 2; t >= 0; --t) st[t] = st[t + 1] * Rm[t + 1];
+    // shared layout: [per-warp scratch][G_{i,k} fp64][K (optional)]
+    constexpr int WS = 8 * RMAX * RMAX + 8 * 3 * RMAX + 8 * RMAX * 2;  // bytes-ish per warp, in doubles below
+    double* wsd = reinterpret_cast<double*>(smem);
+    double* my = wsd + warp * (RMAX * RMAX + 3 * RMAX + 2 * RMAX);
+    double* Hs = my;                       // RMAX*RMAX
+    double* vs = Hs + RMAX * RMAX;         // 3 x RMAX
+    double* bs = vs + 3 * RMAX;            // RMAX
+    double* ivd = bs + RMAX;               // RMAX
+    double* gik = wsd + PW * (RMAX * RMAX + 3 * RMAX + 2 * RMAX);
+    int gko[3];
+    int tot = 0;
+    for (int t = 0; t < nm; ++t) {
+        gko[t] = tot;
+        tot += Rm[t] * s.I[m[t]];
+    }
+    for (int t = 0; t < nm; ++t)
+        for (int idx = tid; idx < Rm[t] * s.I[m[t]]; idx += PT) gik[gko[t] + idx] = p.Gd[s.goff[m[t]][k] + idx];
+    T* om = reinterpret_cast<T*>(gik + tot) + warp * 512;  // per-warp omega (Q <= 512)
+    T* Ks = reinterpret_cast<T*>(gik + tot) + PW * 512;
+    const bool ksm = p.solve_k_in_smem != 0;
+    if (ksm)
+        for (int idx = tid; idx < Q * Q; idx += PT) Ks[idx] = p.Kk[idx];
+    const T* K = ksm ? Ks : p.Kk;
+    __syncthreads();
+    const int rho_ok = 1;
+    (void)rho_ok;
+    (void)WS;
+    for (int j = blockIdx.x * PW + warp; j < Ik; j += gridDim.x * PW) {
+        for (int t = 0; t < nm; ++t)
+            for (int r = lane; r < Rm[t]; r += 32) vs[t * RMAX + r] = p.Gd[s.goff[k][m[t]] + r * Ik + j];
+        __syncwarp();
+        const double* Mj = p.Mk[k] + static_cast<long long>(j) * Q;
+        for (int ti = 0; ti < nm; ++ti) {
+            const int i = m[ti], Ri = Rm[ti], sp = st[ti];
+            const int Qo = Q / Ri;
+            for (int o2 = lane; o2 < Qo; o2 += 32) {
+                double w = 1.0;
+                int rem = o2;
+                for (int t = nm - 1; t >= 0; --t) {
+                    if (t == ti) continue;
+                    const int d = rem % Rm[t];
+                    rem /= Rm[t];
+                    w *= vs[t * RMAX + d];
+                }
+                om[o2] = static_cast<T>(w);
+            }
+            __syncwarp();
+            // H(c, c2) for c <= c2: lanes take pairs, each sums over (o, o2)
+            const int npair = Ri * (Ri + 1) / 2;
+            for (int pr = lane; pr < npair; pr += 32) {
+                int c = 0, rem = pr;
+                while (rem >= Ri - c) {
+                    rem -= Ri - c;
+                    ++c;
+                }
+                const int c2 = c + rem;
+                T acc0 = T(0), acc1 = T(0);
+                for (int o = 0; o < Qo; ++o) {
+                    const int hi = o / sp, lo = o - hi * sp;
+                    const T* kr = K + static_cast<long long>(hi * Ri * sp + c * sp + lo) * Q + c2 * sp;
+                    T sacc0 = T(0), sacc1 = T(0);
+                    for (int h2 = 0; h2 < Qo / sp; ++h2) {
+                        const T* kk = kr + h2 * Ri * sp;
+                        const T* ow = om + h2 * sp;
+                        int l2 = 0;
+                        for (; l2 + 1 < sp; l2 += 2) {
+                            sacc0 = fma(kk[l2], ow[l2], sacc0);
+                            sacc1 = fma(kk[l2 + 1], ow[l2 + 1], sacc1);
+                        }
+                        if (l2 < sp) sacc0 = fma(kk[l2], ow[l2], sacc0);
+                    }
+                    if (o & 1)
+                        acc1 = fma(om[o], sacc0 + sacc1, acc1);
+                    else
+                        acc0 = fma(om[o], sacc0 + sacc1, acc0);
+                }
+                const double h = static_cast<double>(acc0 + acc1);
+                Hs[c * Ri + c2] = h;
+                Hs[c2 * Ri + c] = h;
+            }
+            // b(c) in FP64: lanes take c
+            for (int c = lane; c < Ri; c += 32) {
+                double acc = 0.0;
+                for (int o = 0; o < Qo; ++o) {
+                    const int hi = o / sp, lo = o - hi * sp;
+                    acc = fma(static_cast<double>(om[o]), Mj[hi * Ri * sp + c * sp + lo], acc);
+                }
+                bs[c] = acc + p.rho * vs[ti * RMAX + c];
+            }
+            __syncwarp();
+            // Cholesky H + rho I = L L^T, column by column; lanes take the rows
+            bool okc = true;
+            for (int c = 0; c < Ri; ++c) {
+                if (lane == 0) {
+                    double d = Hs[c * Ri + c] + p.rho;
+                    for (int t = 0; t < c; ++t) d -= Hs[c * Ri + t] * Hs[c * Ri + t];
+                    const double sd = d > 0.0 ? sqrt(d) : -1.0;
+                    Hs[c * Ri + c] = sd;
+                    ivd[c] = sd > 0.0 ? 1.0 / sd : 0.0;
+                }
+                __syncwarp();
+                if (!(Hs[c * Ri + c] > 0.0)) {
+                    okc = false;
+                    break;
+                }
+                const int r = c + 1 + lane;
+                if (r < Ri) {
+                    double v = Hs[r * Ri + c];
+                    for (int t = 0; t < c; ++t) v -= Hs[r * Ri + t] * Hs[c * Ri + t];
+                    Hs[r * Ri + c] = v * ivd[c];
+                }
+                __syncwarp();
+            }
+            if (lane == 0) {
+                if (okc) {
+                    for (int r = 0; r < Ri; ++r) {
+                        double v = bs[r];
+                        for (int t = 0; t < r; ++t) v -= Hs[r * Ri + t] * bs[t];
+                        bs[r] = v * ivd[r];
+                    }
+                    for (int r = Ri - 1; r >= 0; --r) {
+                        double v = bs[r];
+                        for (int t = r + 1; t < Ri; ++t) v -= Hs[t * Ri + r] * bs[t];
+                        bs[r] = v * ivd[r];
+                    }
+                    for (int r = 0; r < Ri; ++r)
+                        if (!isfinite(bs[r])) okc = false;
+                }
+                if (!okc) {
+                    atomicOr(p.flags, FLAG_NOTSPD);
+                    for (int r = 0; r < Ri; ++r) bs[r] = vs[ti * RMAX + r];
+                }
+            }
+            __syncwarp();
+            for (int r = lane; r < Ri; r += 32) {
+                const double g = bs[r];
+                vs[ti * RMAX + r] = g;
+                p.Gd[s.goff[k][i] + r * Ik + j] = g;
+                p.Gt[s.goff[k][i] + r * Ik + j] = static_cast<T>(g);
+            }
+            __syncwarp();
+        }
+        // refresh W_{k,i}(j, :) for every i != k
+        for (int t = 0; t < nm; ++t) {
+            const int i = m[t], Ri = Rm[t], Ii = s.I[i];
+            const double* gk = gik + gko[t];
+            for (int b = lane; b < Ii; b += 32) {
+                double w = 0.0;
+                for (int r = 0; r < Ri; ++r) w = fma(vs[t * RMAX + r], gk[r * Ii + b], w);
+                if (k < i)
+                    p.W[s.woff[k][i] + static_cast<long long>(j) * Ii + b] = static_cast<T>(w);
+                else
+                    p.W[s.woff[i][k] + static_cast<long long>(b) * Ik + j] = static_cast<T>(w);
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Phase 4: eq. (updateX) fused with the reconstruction and the sums of the
+// stop test, the objective and (optionally) RSE / RMSE.
+// ---------------------------------------------------------------------------
+struct Walk4 {
+    int i0, i1, a, b;
+};
+
+__device__ __forceinline__ void walk4_from(const Shape& s, long long e, Walk4& w) {
+    w.b = static_cast<int>(e % s.IB);
+    long long r = e / s.IB;
+    w.a = static_cast<int>(r % s.IA);
+    long long f = r / s.IA;
+    if (s.N == 4) {
+        w.i1 = static_cast<int>(f % s.I[1]);
+        w.i0 = static_cast<int>(f / s.I[1]);
+    } else {
+        w.i0 = static_cast<int>(f);
+        w.i1 = 0;
+    }
+}
+
+__device__ __forceinline__ void walk4_inc(const Shape& s, Walk4& w) {
+    if (++w.b == s.IB) {
+        w.b = 0;
+        if (++w.a == s.IA) {
+            w.a = 0;
+            if (s.N == 4) {
+                if (++w.i1 == s.I[1]) {
+                    w.i1 = 0;
+                    ++w.i0;
+                }
+            } else {
+                ++w.i0;
+            }
+        }
+    }
+}
+
+// a fixed element stride decomposed into single-carry digit increments
+struct Step4 {
+    int d0, d1, da, db;
+};
+
+__device__ __forceinline__ Step4 step4_of(const Shape& s, long long d) {
+    Step4 t;
+    t.db = static_cast<int>(d % s.IB);
+    long long r = d / s.IB;
+    t.da = static_cast<int>(r % s.IA);
+    long long f = r / s.IA;
+    if (s.N == 4) {
+        t.d1 = static_cast<int>(f % s.I[1]);
+        t.d0 = static_cast<int>(f / s.I[1]);
+    } else {
+        t.d0 = static_cast<int>(f);
+        t.d1 = 0;
+    }
+    return t;
+}
+
+__device__ __forceinline__ void walk4_add(const Shape& s, Walk4& w, const Step4& t) {
+    w.b += t.db;
+    int ca = 0;
+    if (w.b >= s.IB) {
+        w.b -= s.IB;
+        ca = 1;
+    }
+    w.a += t.da + ca;
+    int cf = 0;
+    if (w.a >= s.IA) {
+        w.a -= s.IA;
+        cf = 1;
+    }
+    if (s.N == 4) {
+        w.i1 += t.d1 + cf;
+        int c0 = 0;
+        if (w.i1 >= s.I[1]) {
+            w.i1 -= s.I[1];
+            c0 = 1;
+        }
+        w.i0 += t.d0 + c0;
+    } else {
+        w.i0 += t.d0 + cf;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T recon4(const Shape& s, const T* __restrict__ W, const Walk4& w) {
+    const int N = s.N, Am = N - 2, Bm = N - 1;
+    T v = W[s.woff[Am][Bm] + static_cast<long long>(w.a) * s.IB + w.b];
+    if (N >= 3)
+        v *= W[s.woff[0][Am] + static_cast<long long>(w.i0) * s.IA + w.a] *
+             W[s.woff[0][Bm] + static_cast<long long>(w.i0) * s.IB + w.b];
+    if (N == 4)
+        v *= W[s.woff[1][Am] + static_cast<long long>(w.i1) * s.IA + w.a] *
+             W[s.woff[1][Bm] + static_cast<long long>(w.i1) * s.IB + w.b] *
+             W[s.woff[0][1] + static_cast<long long>(w.i0) * s.I[1] + w.i1];
+    return v;
+}
+
+template <typename T> struct V16;
+template <> struct V16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct V16<double> { using type = double2; static constexpr int n = 2; };
+__device__ __forceinline__ float v16get(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+__device__ __forceinline__ double v16get(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+__device__ __forceinline__ void v16set(float4& v, int i, float x) {
+    if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
+}
+__device__ __forceinline__ void v16set(double2& v, int i, double x) {
+    if (i == 0) v.x = x; else v.y = x;
+}
+
+template <typename T>
+__device__ __forceinline__ void xelem(const SweepParams<T>& p, const T rho, const T inv1p, const long long e,
+                                      const T xo, T& xn, const T rec, const bool obs, T (&fa)[6], const bool met) {
+    xn = obs ? xo : (rec + rho * xo) * inv1p;
+    const T d = xn - xo, r = xn - rec;
+    fa[0] = fma(d, d, fa[0]);
+    fa[1] = fma(xo, xo, fa[1]);
+    fa[2] = fma(r, r, fa[2]);
+    if (met) {
+        const T xt = p.Xt[e];
+        const T de = xt - xn;
+        fa[3] = fma(de, de, fa[3]);
+        fa[4] = fma(xt, xt, fa[4]);
+        if (!obs) fa[5] = fma(de, de, fa[5]);
+    }
+}
+
+template <typename T>
+__device__ void xupdate_phase(const SweepParams<T>& p, double* out6) {
+    using V = typename V16<T>::type;
+    constexpr int NV = V16<T>::n;
+    const Shape& s = p.sh;
+    const T rho = static_cast<T>(p.rho), inv1p = static_cast<T>(1.0 / (1.0 + p.rho));
+    const long long P = s.P;
+    const long long nvec = P / NV;
+    const long long gtid = static_cast<long long>(blockIdx.x) * PT + threadIdx.x;
+    const long long gstr = static_cast<long long>(gridDim.x) * PT;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    T fa[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    int run = 0;
+    const bool met = p.Xt != nullptr;
+    V* Xv = reinterpret_cast<V*>(p.X);
+    Walk4 w;
+    walk4_from(s, gtid * NV, w);
+    const Step4 stp = step4_of(s, gstr * NV - NV);
+    for (long long v = gtid; v < nvec; v += gstr) {
+        V xv = Xv[v];
+        const long long e0 = v * NV;
+        const uint32_t word = p.mb[e0 >> 5];
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            T xn;
+            const T rec = recon4(s, p.W, w);
+            xelem(p, rho, inv1p, e0 + t, v16get(xv, t), xn, rec, (word >> ((e0 + t) & 31)) & 1u, fa, met);
+            v16set(xv, t, xn);
+            walk4_inc(s, w);
+        }
+        Xv[v] = xv;
+        walk4_add(s, w, stp);
+        if (++run == 16) {
+            for (int t = 0; t < 6; ++t) {
+                acc[t] += static_cast<double>(fa[t]);
+                fa[t] = T(0);
+            }
+            run = 0;
+        }
+    }
+    if (gtid == 0) {  // ragged tail
+        Walk4 wt;
+        walk4_from(s, nvec * NV, wt);
+        for (long long e = nvec * NV; e < P; ++e) {
+            T xn;
+            const T rec = recon4(s, p.W, wt);
+            xelem(p, rho, inv1p, e, p.X[e], xn, rec, (p.mb[e >> 5] >> (e & 31)) & 1u, fa, met);
+            p.X[e] = xn;
+            walk4_inc(s, wt);
+        }
+    }
+    for (int t = 0; t < 6; ++t) acc[t] += static_cast<double>(fa[t]);
+    __shared__ double sh[PW][6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = 0; t < 6; ++t) acc[t] = warp_sum(acc[t]);
+    if (lane == 0)
+        for (int t = 0; t < 6; ++t) sh[warp][t] = acc[t];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double v = 0.0;
+        for (int w2 = 0; w2 < PW; ++w2) v += sh[w2][threadIdx.x];
+        out6[threadIdx.x] = v;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// CTA 0 stamps the end of every phase of the first sweep (profiling aid)
+#define IFCTN_STAMP(p, sw, slot)                                                        \
+    do {                                                                              \
+        if ((p).tstamp && (sw) == 0 && blockIdx.x == 0 && threadIdx.x == 0 &&         \
+            (slot) < 64)                                                              \
+            (p).tstamp[(slot)] = gtimer();                                            \
+    } while (0)
+
+template <typename T>
+__global__ void __launch_bounds__(PT, 1) k_sweep_persistent(const SweepParams<T> p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    unsigned char* work = smem + 128;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < p.nstages; ++i) mbar_init(&bars[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (*reinterpret_cast<volatile const int*>(p.done)) return;
+    int pipe = 0;
+    const Shape& s = p.sh;
+    __shared__ double red[8];
+    for (int sw = 0; sw < p.nsweeps; ++sw) {
+        IFCTN_STAMP(p, sw, 0);
+        for (int k = 0; k < s.N; ++k) {
+            const int nU = p.pl[k].nunits, nG = p.gunits[k];
+            for (int w = blockIdx.x; w < nU + nG; w += gridDim.x) {
+                if (w < nU) {
+                    if (!contract_dispatch<T>(p, k, w, work, bars, pipe)) return;
+                } else {
+                    gram_unit<T>(p, k, w - nU, work);
+                }
+            }
+            IFCTN_STAMP(p, sw, 1 + 6 * k);
+            if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
+            IFCTN_STAMP(p, sw, 2 + 6 * k);
+            reduce_phase<T>(p, k);
+            IFCTN_STAMP(p, sw, 3 + 6 * k);
+            if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
+            IFCTN_STAMP(p, sw, 4 + 6 * k);
+            solve_phase<T>(p, k, work);
+            IFCTN_STAMP(p, sw, 5 + 6 * k);
+            if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
+            IFCTN_STAMP(p, sw, 6 + 6 * k);
+        }
+        double* xp = p.xpart + 8LL * gridDim.x * (sw & 1);
+        xupdate_phase<T>(p, xp + 8 * blockIdx.x);
+        IFCTN_STAMP(p, sw, 25);
+        if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
+        IFCTN_STAMP(p, sw, 26);
+        // every CTA reduces the per-CTA sums in the same order
+        if (threadIdx.x < 32) {
+            double a[6] = {0, 0, 0, 0, 0, 0};
+            for (int b = threadIdx.x; b < gridDim.x; b += 32)
+                for (int t = 0; t < 6; ++t) a[t] += reinterpret_cast<volatile double*>(xp)[8 * b + t];
+            for (int t = 0; t < 6; ++t) a[t] = warp_sum(a[t]);
+            if (threadIdx.x == 0)
+                for (int t = 0; t < 6; ++t) red[t] = a[t];
+        }
+        __syncthreads();
+        const double dx2 = red[0], x2 = red[1];
+        const double rel = x2 > 0 ? sqrt(dx2) / sqrt(x2) : (dx2 > 0 ? INFINITY : 0.0);
+        const double tol = *p.tol;
+        const bool conv = tol > 0 && rel < tol;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            SweepStat r;
+            r.rel_change = rel;
+            r.objective = 0.5 * red[2];
+            if (p.Xt) {
+                r.rse = red[4] > 0 ? sqrt(red[3]) / sqrt(red[4]) : NAN;
+                r.rmse = p.nmiss > 0 ? sqrt(red[5] / static_cast<double>(p.nmiss)) : 0.0;
+            } else {
+                r.rse = NAN;
+                r.rmse = NAN;
+            }
+            r.dx2 = dx2;
+            r.x2 = x2;
+            const int sidx = *p.counter;
+            r.sweep = sidx + 1;
+            r.converged = conv ? 1 : 0;
+            r.flags = *p.flags;
+            r.pad = 0;
+            if (!isfinite(r.rel_change) || !isfinite(r.objective)) r.flags |= FLAG_NONFINITE;
+            p.log[sidx % p.log_cap] = r;
+            *p.counter = sidx + 1;
+            if (conv) *p.done = 1;
+        }
+        if (conv) return;
+        // xpart is double-buffered by sweep parity: the buffer read here is
+        // rewritten two sweeps later, after many more grid barriers.
+    }
+}
+
+}  // namespace
+
+template <typename T>
+int persistent_smem_bytes(const SweepParams<T>& p) {
+    const Shape& s = p.sh;
+    long long need = 0;
+    for (int k = 0; k < s.N; ++k) {
+        need = std::max<long long>(need, p.pl[k].smem - 128);
+        int m[3], nm = 0;
+        for (int q = 0; q < s.N; ++q)
+            if (q != k) m[nm++] = q;
+        int Q = 1, tot = 0;
+        for (int t = 0; t < nm; ++t) {
+            Q *= s.R[k][m[t]];
+            tot += s.R[k][m[t]] * s.I[m[t]];
+        }
+        long long solve = static_cast<long long>(PW) * (RMAX * RMAX + 5 * RMAX) * 8 + static_cast<long long>(tot) * 8 +
+                          static_cast<long long>(PW) * 512 * sizeof(T);
+        if (p.solve_k_in_smem) solve += static_cast<long long>(Q) * Q * sizeof(T);
+        need = std::max(need, solve);
+        if (nm == 2) {
+            const int l = m[1];
+            need = std::max<long long>(need, static_cast<long long>(s.R[k][l] * s.I[l] + GRAM_IOB * s.I[l]) * sizeof(T));
+        } else if (nm == 3) {
+            const int c = m[1], l = m[2];
+            const long long Q2 = static_cast<long long>(s.R[k][c]) * s.R[k][l];
+            const int chunk = std::max(1, std::min(s.I[c], p.gram_chunk));
+            need = std::max<long long>(need, (static_cast<long long>(s.R[k][l]) * s.I[l] + s.R[k][c] * s.I[c] + s.I[l] +
+                                              Q2 * Q2 + static_cast<long long>(chunk) * s.R[k][l] * s.R[k][l]) *
+                                                 sizeof(T));
+        }
+    }
+    return static_cast<int>(need + 128 + 256);
+}
+
+template <typename T>
+cudaError_t launch_persistent(const SweepParams<T>& p, int grid, int smem, cudaStream_t st) {
+    void* args[] = {const_cast<SweepParams<T>*>(&p)};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_sweep_persistent<T>), dim3(grid), dim3(PT), args,
+                                       smem, st);
+}
+
+template <typename T>
+int persistent_max_grid(int smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_persistent<T>, PT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return per * sms;
+}
+
+}  // namespace ifctn

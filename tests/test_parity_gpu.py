@@ -210,3 +210,14 @@ def test_checkpoint_resume_is_exact():
     np.testing.assert_array_equal(c3.x(), ref_X)
     c1.close()
     c3.close()
+
+
+def test_whole_run_is_one_persistent_launch():
+    """A sweep call runs every sweep in one cooperative launch when the grid fits."""
+    dims = (32, 28, 24)
+    case = make_case(dims, 3, 0.3, seed=101)
+    c = _ctx(case, precision=b.MIXED, max_sweeps=20)
+    n0 = b.launch_count(c.ctx)
+    c.sweep(20)
+    assert b.launch_count(c.ctx) - n0 == 1
+    c.close()
