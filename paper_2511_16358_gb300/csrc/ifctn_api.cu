@@ -646,6 +646,16 @@ struct Engine : ifctn_ctx {
         pp.nmiss = nmiss;
         pp.nstages = NSTAGES;
         pp.tstamp = tstamp.p;
+        {
+            // X-update work units: row ranges of slabs, about 4 per CTA
+            const long long target_units = 4LL * 2 * num_sms();
+            const long long rows_total = static_cast<long long>(sh.nF) * sh.IA;
+            long long rows = std::max<long long>(1, rows_total / target_units);
+            rows = std::min<long long>(rows, sh.IA);
+            rows = std::min<long long>(rows, std::max(1, 16384 / sh.IB));
+            pp.xu_rows = static_cast<int>(std::max<long long>(rows, 1));
+            pp.xu_wab_smem = static_cast<long long>(sh.IA) * sh.IB * sizeof(T) <= 64 * 1024 ? 1 : 0;
+        }
         psmem = persistent_smem_bytes<T>(pp);
         persistent = false;
         if (psmem > 227 * 1024) return;

@@ -73,7 +73,7 @@ static __device__ void drain(uint64_t* bars, int S, int from, int to, int* flags
 // ---------------------------------------------------------------------------
 template <typename T, int RB>
 __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const int uidx, unsigned char* smem,
-                                  uint64_t* bars, int& pipe) {
+                                  uint64_t* bars, int& pipe, int* wtag) {
     const Shape& s = A.sh;
     const ContractPlan& pl = A.pl;
     const int N = s.N, k = A.k, IA = s.IA, IB = s.IB;
@@ -144,7 +144,10 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
         const int na = min(TA, u.a1 - a0);
         const int buf = (pipe + it) % S;
         const unsigned par = static_cast<unsigned>(((pipe + it) / S) & 1);
-        if (isF && bt == 0) {  // pair matrix W_{A,B} rows of this pass
+        // pair matrix W_{A,B} rows of this pass; a caller may keep them across
+        // units through *wtag (the first row + 1 of the rows held, 0 = none)
+        const bool wload = isF && bt == 0 && !(wtag && *wtag == a0 + 1 && na == TA);
+        if (wload) {
             const T* src = A.W + s.woff[Am][Bm] + static_cast<long long>(a0) * IB;
             for (int idx = tid; idx < na * IB; idx += nthr) wab[idx] = src[idx];
         }
@@ -174,6 +177,7 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
             }
         }
         __syncthreads();
+        if (wload && wtag && tid == 0) *wtag = (na == TA) ? a0 + 1 : 0;
         const bool ok = mbar_wait_bounded(&bars[buf], par, A.flags);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) drain(bars, S, pipe + it + 1, pipe + min(nst, it + S), A.flags);

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256) k_contract_row(const ContractArgs<T> A) {
     }
     __syncthreads();
     int pipe = 0;
-    contract_row_unit<T, RB>(A, blockIdx.x, smem + 128, bars, pipe);
+    contract_row_unit<T, RB>(A, blockIdx.x, smem + 128, bars, pipe, nullptr);
 }
 
 template <typename T, int RA>

@@ -36,6 +36,8 @@ struct SweepParams {
     int solve_k_in_smem;
     int gram_chunk;
     unsigned long long* tstamp;  // optional phase timestamps of the first sweep
+    int xu_rows;                 // X update: rows of a slab per work unit
+    int xu_wab_smem;             // X update: W_{A,B} kept in shared memory
 };
 
 template <typename T>

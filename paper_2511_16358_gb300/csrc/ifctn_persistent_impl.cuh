@@ -22,6 +22,7 @@
 // the kernel returns.
 #pragma once
 #include <algorithm>
+#include <type_traits>
 
 #include "ifctn_contract_dev.cuh"
 #include "ifctn_persistent.h"
@@ -36,29 +37,44 @@ constexpr int PT = 256;  // threads per CTA
 constexpr int PW = PT / 32;
 constexpr int GRAM_IOB = 8;  // io values per Gram unit (N = 3)
 
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned atom_add_acqrel_u32(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Software grid barrier (the grid is co-resident: cooperative launch).
+// Arrival is an acq_rel add on a counter; the last CTA resets the counter and
+// publishes the next generation with a release store; the others spin with
+// acquire loads, bounded by a clock budget.
 __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* flags) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* vgen = gen;
-        const unsigned g = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(count, 1u) + 1u;
+        const unsigned g = ld_acquire_u32(gen);
+        const unsigned arrived = atom_add_acqrel_u32(count, 1u) + 1u;
         if (arrived == gridDim.x) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
+            *reinterpret_cast<volatile unsigned*>(count) = 0u;
+            st_release_u32(gen, g + 1u);
         } else {
             const long long t0 = clock64();
-            while (*vgen == g) {
+            while (ld_acquire_u32(gen) == g) {
                 if (clock64() - t0 > 4000000000LL) {
                     atomicOr(flags, FLAG_TIMEOUT);
                     break;
                 }
-                __nanosleep(20);
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return (*reinterpret_cast<volatile int*>(flags) & FLAG_TIMEOUT) == 0;
@@ -86,7 +102,7 @@ __device__ __forceinline__ int pow2_at_least(int x) {
 
 template <typename T>
 __device__ bool contract_dispatch(const SweepParams<T>& p, int k, int uidx, unsigned char* smem,
-                                  uint64_t* bars, int& pipe) {
+                                  uint64_t* bars, int& pipe, int* wtag) {
     ContractArgs<T> a;
     a.X = p.X;
     a.Gt = p.Gt;
@@ -102,7 +118,7 @@ __device__ bool contract_dispatch(const SweepParams<T>& p, int k, int uidx, unsi
     switch (p.pl[k].R1) {
 #define IFCTN_PCASE(R) \
     case R:            \
-        return col ? contract_col_unit<T, R>(a, uidx, smem, bars, pipe) : contract_row_unit<T, R>(a, uidx, smem, bars, pipe);
+        return col ? contract_col_unit<T, R>(a, uidx, smem, bars, pipe) : contract_row_unit<T, R>(a, uidx, smem, bars, pipe, wtag);
         IFCTN_PCASE(1)
         IFCTN_PCASE(2)
         IFCTN_PCASE(3)
@@ -216,7 +232,7 @@ __device__ void gram_unit(const SweepParams<T>& p, int k, int gu, unsigned char*
 // output; the groups of the whole grid share the outputs.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void reduce_phase(const SweepParams<T>& p, int k) {
+__device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem) {
     const Shape& s = p.sh;
     const ContractPlan& pl = p.pl[k];
     int m[3];
@@ -267,6 +283,55 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k) {
                 p.Kk[static_cast<long long>(col) * Q + row] = acc;
             }
         }
+    }
+    // --- M, units covering every row: 32-column tiles, warps split the units ---
+    if (pl.kcase != CASE_F && pl.key_div > 0) {
+        const int Qp = pl.Qp;
+        const int ncol = pl.nrow * Qp;
+        const int ntile = (ncol + 31) / 32;
+        const int Rd = pl.dmode >= 0 ? s.R[k][pl.dmode] : 1;
+        const int nu = pl.nunits;
+        T* coef = reinterpret_cast<T*>(smem);      // Rd x nu
+        T* red = coef + ((Rd * nu + 3) & ~3);      // PW x RMAX x 32
+        if (static_cast<int>(blockIdx.x) < ntile) {
+            for (int idx = threadIdx.x; idx < Rd * nu; idx += PT) {
+                const int rdd = idx / nu, u = idx - rdd * nu;
+                coef[idx] = pl.dmode >= 0 ? gfac(p.Gt, s, pl.dmode, k, rdd, u / pl.key_div) : T(1);
+            }
+            __syncthreads();
+            const int warp = threadIdx.x >> 5;
+            for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+                const int c = tile * 32 + lane;
+                const bool valid = c < ncol;
+                T acc[RMAX];
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r) acc[r] = T(0);
+                const T* pc = p.part + c;
+#pragma unroll 4
+                for (int u = warp; u < nu; u += PW) {
+                    const T v = valid ? pc[static_cast<size_t>(u) * ncol] : T(0);
+#pragma unroll
+                    for (int r = 0; r < RMAX; ++r)
+                        if (r < Rd) acc[r] = fma(coef[r * nu + u], v, acc[r]);
+                }
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r)
+                    if (r < Rd) red[(warp * RMAX + r) * 32 + lane] = acc[r];
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < Rd * 32; idx += PT) {
+                    const int r = idx / 32, ln = idx - r * 32;
+                    const int cc = tile * 32 + ln;
+                    if (cc < ncol) {
+                        T v = T(0);
+                        for (int w2 = 0; w2 < PW; ++w2) v += red[(w2 * RMAX + r) * 32 + ln];
+                        const int row = cc / Qp, qp = cc - row * Qp;
+                        p.Mk[k][static_cast<long long>(row) * Q + r * Qp + qp] = static_cast<double>(v);
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        return;
     }
     // --- M ---
     {
@@ -324,17 +389,92 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k) {
 }
 
 // ---------------------------------------------------------------------------
-// Phase 3: eq. (updateG) for every column j of mode k, one warp per column.
-// H = E_j^T K_k E_j + rho I and b = E_j^T M_k(j,:) + rho g_old with E_j the
-// Kronecker product of the current columns G_{k,m}(:,j), m != i (identity in
-// slot i); stages i ascending (Gauss-Seidel within the column).
+// Phase 3: eq. (updateG) for every column j of mode k, one warp per column
+// (columns dealt round-robin over the CTAs first, so every SM gets work).
+// H = E_j^T K_k E_j and b = E_j^T M_k(j,:) + rho g_old with E_j the Kronecker
+// product of the current columns G_{k,m}(:,j), m != i (identity in slot i);
+// stages i ascending (Gauss-Seidel within the column).
+//
+// (H + rho I) g = b is solved by a lane-parallel LDL^T factorisation (the
+// matrix is SPD with eigenvalues >= rho, so no pivoting).  FP64 path: the
+// factorisation and the solves in FP64.  Mixed path: the factorisation in
+// FP32 followed by two steps of iterative refinement whose residual
+// b - (H + rho I) g is formed in FP64, which recovers FP64-level accuracy for
+// the conditioning these systems have while keeping GB300's narrow FP64 pipe
+// nearly idle.
 // ---------------------------------------------------------------------------
+template <typename F>
+__device__ __forceinline__ F recip_nr(F d) {
+    // reciprocal: FP32 estimate refined by Newton-Raphson x <- x (2 - d x)
+    F x = static_cast<F>(1.0f / static_cast<float>(d));
+    if (sizeof(F) == 8) {
+        x = x * (F(2) - d * x);
+        x = x * (F(2) - d * x);
+    }
+    return x;
+}
+
+// Lane-parallel LDL^T of the n x n SPD matrix A (row-major in shared memory,
+// F precision) in place: unit-lower L below the diagonal, D on the diagonal,
+// 1/D in inv.  Returns false if a pivot is not positive.
+template <typename F>
+__device__ bool ldlt_warp(F* A, F* inv, int n, int lane) {
+    for (int c = 0; c < n; ++c) {
+        const F d = A[c * n + c];
+        if (!(d > F(0))) return false;
+        const F id = recip_nr<F>(d);
+        if (lane == 0) inv[c] = id;
+        // trailing update A[r][s] -= A[r][c] A[s][c] / d for c < s <= r
+        const int m = n - c - 1;
+        const int npair = m * (m + 1) / 2;
+        F lrc = F(0), lsc = F(0);
+        int r = 0, sx = 0;
+        if (lane < npair) {
+            int rem = lane, rr = 0;
+            while (rem > rr) {
+                rem -= rr + 1;
+                ++rr;
+            }
+            r = c + 1 + rr;
+            sx = c + 1 + rem;
+            lrc = A[r * n + c];
+            lsc = A[sx * n + c];
+        }
+        __syncwarp();
+        if (lane < npair) A[r * n + sx] -= lrc * lsc * id;
+        __syncwarp();
+        if (lane > c && lane < n) A[lane * n + c] *= id;
+        __syncwarp();
+    }
+    return true;
+}
+
+// solve L D L^T x = rhs (x overwrites rhs), lane-parallel over rows
+template <typename F>
+__device__ void ldlt_solve_warp(const F* A, const F* inv, F* x, int n, int lane) {
+    for (int c = 0; c < n; ++c) {  // forward, unit lower
+        const F xc = x[c];
+        __syncwarp();
+        if (lane > c && lane < n) x[lane] -= A[lane * n + c] * xc;
+        __syncwarp();
+    }
+    if (lane < n) x[lane] *= inv[lane];
+    __syncwarp();
+    for (int c = n - 1; c >= 0; --c) {  // backward, unit upper = L^T
+        const F xc = x[c];
+        __syncwarp();
+        if (lane < c) x[lane] -= A[c * n + lane] * xc;
+        __syncwarp();
+    }
+}
+
 template <typename T>
 __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem) {
     const Shape& s = p.sh;
     const int Ik = s.I[k];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (static_cast<long long>(blockIdx.x) * PW >= Ik) return;  // no columns for this CTA
+    if (static_cast<int>(blockIdx.x) >= Ik) return;  // no columns for this CTA
+    constexpr bool MIXED = sizeof(T) == 4;
     int m[3];
     const int nm = nonk(s, k, m);
     int Rm[3] = {1, 1, 1}, st[3] = {1, 1, 1};
@@ -344,15 +484,20 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem)
         Q *= Rm[t];
     }
     for (int t = nm - 2; t >= 0; --t) st[t] = st[t + 1] * Rm[t + 1];
-    // shared layout: [per-warp scratch][G_{i,k} fp64][K (optional)]
-    constexpr int WS = 8 * RMAX * RMAX + 8 * 3 * RMAX + 8 * RMAX * 2;  // bytes-ish per warp, in doubles below
-    double* wsd = reinterpret_cast<double*>(smem);
-    double* my = wsd + warp * (RMAX * RMAX + 3 * RMAX + 2 * RMAX);
-    double* Hs = my;                       // RMAX*RMAX
-    double* vs = Hs + RMAX * RMAX;         // 3 x RMAX
-    double* bs = vs + 3 * RMAX;            // RMAX
-    double* ivd = bs + RMAX;               // RMAX
-    double* gik = wsd + PW * (RMAX * RMAX + 3 * RMAX + 2 * RMAX);
+    // shared layout: per-warp scratch (doubles), then G_{i,k} in T, then
+    // per-warp omega (T, Q <= 512), then K (T) when it fits
+    constexpr int WSD = 2 * RMAX * RMAX + 8 * RMAX;  // doubles per warp
+    double* my = reinterpret_cast<double*>(smem) + warp * WSD;
+    double* Hd = my;                      // RMAX*RMAX: H (FP64)
+    double* vs = Hd + RMAX * RMAX;        // 3 x RMAX current columns
+    double* bd = vs + 3 * RMAX;           // RMAX rhs (FP64)
+    double* gd = bd + RMAX;               // RMAX solution (FP64)
+    double* rd = gd + RMAX;               // RMAX residual (FP64)
+    using F = typename std::conditional<MIXED, float, double>::type;
+    F* Af = reinterpret_cast<F*>(rd + RMAX);   // RMAX*RMAX factor
+    F* invf = Af + RMAX * RMAX;                  // RMAX
+    F* xf = invf + RMAX;                         // RMAX
+    T* gik = reinterpret_cast<T*>(reinterpret_cast<double*>(smem) + PW * WSD);
     int gko[3];
     int tot = 0;
     for (int t = 0; t < nm; ++t) {
@@ -360,18 +505,16 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem)
         tot += Rm[t] * s.I[m[t]];
     }
     for (int t = 0; t < nm; ++t)
-        for (int idx = tid; idx < Rm[t] * s.I[m[t]]; idx += PT) gik[gko[t] + idx] = p.Gd[s.goff[m[t]][k] + idx];
-    T* om = reinterpret_cast<T*>(gik + tot) + warp * 512;  // per-warp omega (Q <= 512)
-    T* Ks = reinterpret_cast<T*>(gik + tot) + PW * 512;
+        for (int idx = tid; idx < Rm[t] * s.I[m[t]]; idx += PT) gik[gko[t] + idx] = p.Gt[s.goff[m[t]][k] + idx];
+    T* om = gik + ((tot + 1) & ~1) + warp * 512;
+    T* Ks = gik + ((tot + 1) & ~1) + PW * 512;
     const bool ksm = p.solve_k_in_smem != 0;
     if (ksm)
         for (int idx = tid; idx < Q * Q; idx += PT) Ks[idx] = p.Kk[idx];
     const T* K = ksm ? Ks : p.Kk;
     __syncthreads();
-    const int rho_ok = 1;
-    (void)rho_ok;
-    (void)WS;
-    for (int j = blockIdx.x * PW + warp; j < Ik; j += gridDim.x * PW) {
+    const double rho = p.rho;
+    for (int j = warp * gridDim.x + blockIdx.x; j < Ik; j += gridDim.x * PW) {
         for (int t = 0; t < nm; ++t)
             for (int r = lane; r < Rm[t]; r += 32) vs[t * RMAX + r] = p.Gd[s.goff[k][m[t]] + r * Ik + j];
         __syncwarp();
@@ -380,18 +523,18 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem)
             const int i = m[ti], Ri = Rm[ti], sp = st[ti];
             const int Qo = Q / Ri;
             for (int o2 = lane; o2 < Qo; o2 += 32) {
-                double w = 1.0;
+                T w = T(1);
                 int rem = o2;
                 for (int t = nm - 1; t >= 0; --t) {
                     if (t == ti) continue;
                     const int d = rem % Rm[t];
                     rem /= Rm[t];
-                    w *= vs[t * RMAX + d];
+                    w *= static_cast<T>(vs[t * RMAX + d]);
                 }
-                om[o2] = static_cast<T>(w);
+                om[o2] = w;
             }
             __syncwarp();
-            // H(c, c2) for c <= c2: lanes take pairs, each sums over (o, o2)
+            // H(c, c2), c <= c2: lanes take pairs, each sums over (o, o2)
             const int npair = Ri * (Ri + 1) / 2;
             for (int pr = lane; pr < npair; pr += 32) {
                 int c = 0, rem = pr;
@@ -421,82 +564,75 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem)
                         acc0 = fma(om[o], sacc0 + sacc1, acc0);
                 }
                 const double h = static_cast<double>(acc0 + acc1);
-                Hs[c * Ri + c2] = h;
-                Hs[c2 * Ri + c] = h;
+                Hd[c * Ri + c2] = h + (c == c2 ? rho : 0.0);
+                Hd[c2 * Ri + c] = h + (c == c2 ? rho : 0.0);
             }
-            // b(c) in FP64: lanes take c
+            // b(c) = E^T M(j,:) + rho g_old: lanes take c
             for (int c = lane; c < Ri; c += 32) {
-                double acc = 0.0;
+                T acc = T(0);
                 for (int o = 0; o < Qo; ++o) {
                     const int hi = o / sp, lo = o - hi * sp;
-                    acc = fma(static_cast<double>(om[o]), Mj[hi * Ri * sp + c * sp + lo], acc);
+                    acc = fma(om[o], static_cast<T>(Mj[hi * Ri * sp + c * sp + lo]), acc);
                 }
-                bs[c] = acc + p.rho * vs[ti * RMAX + c];
+                bd[c] = static_cast<double>(acc) + rho * vs[ti * RMAX + c];
             }
             __syncwarp();
-            // Cholesky H + rho I = L L^T, column by column; lanes take the rows
-            bool okc = true;
-            for (int c = 0; c < Ri; ++c) {
-                if (lane == 0) {
-                    double d = Hs[c * Ri + c] + p.rho;
-                    for (int t = 0; t < c; ++t) d -= Hs[c * Ri + t] * Hs[c * Ri + t];
-                    const double sd = d > 0.0 ? sqrt(d) : -1.0;
-                    Hs[c * Ri + c] = sd;
-                    ivd[c] = sd > 0.0 ? 1.0 / sd : 0.0;
-                }
+            for (int idx = lane; idx < Ri * Ri; idx += 32) Af[idx] = static_cast<F>(Hd[idx]);
+            __syncwarp();
+            bool okc = ldlt_warp<F>(Af, invf, Ri, lane);
+            __syncwarp();
+            if (okc) {
+                if (lane < Ri) xf[lane] = static_cast<F>(bd[lane]);
                 __syncwarp();
-                if (!(Hs[c * Ri + c] > 0.0)) {
-                    okc = false;
-                    break;
-                }
-                const int r = c + 1 + lane;
-                if (r < Ri) {
-                    double v = Hs[r * Ri + c];
-                    for (int t = 0; t < c; ++t) v -= Hs[r * Ri + t] * Hs[c * Ri + t];
-                    Hs[r * Ri + c] = v * ivd[c];
-                }
+                ldlt_solve_warp<F>(Af, invf, xf, Ri, lane);
+                if (lane < Ri) gd[lane] = static_cast<double>(xf[lane]);
                 __syncwarp();
+                if (MIXED) {
+                    for (int it = 0; it < 2; ++it) {
+                        // residual in FP64, correction in FP32
+                        if (lane < Ri) {
+                            double r = bd[lane];
+                            for (int t = 0; t < Ri; ++t) r -= Hd[lane * Ri + t] * gd[t];
+                            xf[lane] = static_cast<F>(r);
+                        }
+                        __syncwarp();
+                        ldlt_solve_warp<F>(Af, invf, xf, Ri, lane);
+                        if (lane < Ri) gd[lane] += static_cast<double>(xf[lane]);
+                        __syncwarp();
+                    }
+                }
+                if (lane < Ri && !isfinite(gd[lane])) okc = false;
+                okc = __all_sync(0xffffffffu, okc);
             }
-            if (lane == 0) {
-                if (okc) {
-                    for (int r = 0; r < Ri; ++r) {
-                        double v = bs[r];
-                        for (int t = 0; t < r; ++t) v -= Hs[r * Ri + t] * bs[t];
-                        bs[r] = v * ivd[r];
-                    }
-                    for (int r = Ri - 1; r >= 0; --r) {
-                        double v = bs[r];
-                        for (int t = r + 1; t < Ri; ++t) v -= Hs[t * Ri + r] * bs[t];
-                        bs[r] = v * ivd[r];
-                    }
-                    for (int r = 0; r < Ri; ++r)
-                        if (!isfinite(bs[r])) okc = false;
-                }
-                if (!okc) {
-                    atomicOr(p.flags, FLAG_NOTSPD);
-                    for (int r = 0; r < Ri; ++r) bs[r] = vs[ti * RMAX + r];
-                }
+            if (!okc) {
+                if (lane == 0) atomicOr(p.flags, FLAG_NOTSPD);
+                if (lane < Ri) gd[lane] = vs[ti * RMAX + lane];
             }
             __syncwarp();
             for (int r = lane; r < Ri; r += 32) {
-                const double g = bs[r];
+                const double g = gd[r];
                 vs[ti * RMAX + r] = g;
                 p.Gd[s.goff[k][i] + r * Ik + j] = g;
                 p.Gt[s.goff[k][i] + r * Ik + j] = static_cast<T>(g);
             }
             __syncwarp();
         }
-        // refresh W_{k,i}(j, :) for every i != k
+        // refresh W_{k,i}(j, :) for every i != k (in the tensor dtype)
         for (int t = 0; t < nm; ++t) {
             const int i = m[t], Ri = Rm[t], Ii = s.I[i];
-            const double* gk = gik + gko[t];
+            const T* gk = gik + gko[t];
+            T v[RMAX];
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r) v[r] = r < Ri ? static_cast<T>(vs[t * RMAX + r]) : T(0);
             for (int b = lane; b < Ii; b += 32) {
-                double w = 0.0;
-                for (int r = 0; r < Ri; ++r) w = fma(vs[t * RMAX + r], gk[r * Ii + b], w);
+                T w = T(0);
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r)
+                    if (r < Ri) w = fma(v[r], gk[r * Ii + b], w);
                 if (k < i)
-                    p.W[s.woff[k][i] + static_cast<long long>(j) * Ii + b] = static_cast<T>(w);
+                    p.W[s.woff[k][i] + static_cast<long long>(j) * Ii + b] = w;
                 else
-                    p.W[s.woff[i][k] + static_cast<long long>(b) * Ik + j] = static_cast<T>(w);
+                    p.W[s.woff[i][k] + static_cast<long long>(b) * Ik + j] = w;
             }
         }
         __syncwarp();
@@ -634,54 +770,97 @@ __device__ __forceinline__ void xelem(const SweepParams<T>& p, const T rho, cons
 }
 
 template <typename T>
-__device__ void xupdate_phase(const SweepParams<T>& p, double* out6) {
-    using V = typename V16<T>::type;
-    constexpr int NV = V16<T>::n;
+__device__ __forceinline__ void xacc(const SweepParams<T>& p, const T rho, const T inv1p, const long long e,
+                                     const T rec, const bool obs, T (&fa)[6], const bool met) {
+    const T xo = p.X[e];
+    const T xn = obs ? xo : (rec + rho * xo) * inv1p;
+    p.X[e] = xn;
+    const T d = xn - xo, r = xn - rec;
+    fa[0] = fma(d, d, fa[0]);
+    fa[1] = fma(xo, xo, fa[1]);
+    fa[2] = fma(r, r, fa[2]);
+    if (met) {
+        const T xt = p.Xt[e];
+        const T de = xt - xn;
+        fa[3] = fma(de, de, fa[3]);
+        fa[4] = fma(xt, xt, fa[4]);
+        if (!obs) fa[5] = fma(de, de, fa[5]);
+    }
+}
+
+// eq. (updateX) over the slab geometry: a work unit is a row range of one
+// slab; the slab's factors alpha(a) = prod_{p in F} W_{p,A}(i_p, a),
+// beta(b) = prod_{p in F} W_{p,B}(i_p, b) and C = W_{0,1}(i0, i1) (N = 4) are
+// built once per unit in shared memory, and W_{A,B} is kept in shared memory
+// when it fits, so that iFCTN(G)(i) = C alpha(a) beta(b) W_{A,B}(a, b) costs
+// three shared loads per entry.
+template <typename T>
+__device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned char* smem) {
     const Shape& s = p.sh;
+    const int N = s.N, IA = s.IA, IB = s.IB, Am = N - 2, Bm = N - 1;
     const T rho = static_cast<T>(p.rho), inv1p = static_cast<T>(1.0 / (1.0 + p.rho));
-    const long long P = s.P;
-    const long long nvec = P / NV;
-    const long long gtid = static_cast<long long>(blockIdx.x) * PT + threadIdx.x;
-    const long long gstr = static_cast<long long>(gridDim.x) * PT;
+    const bool met = p.Xt != nullptr;
+    const bool wsm = p.xu_wab_smem != 0;
+    T* wab = reinterpret_cast<T*>(smem);
+    T* alpha = wab + (wsm ? IA * IB : 0);
+    T* beta = alpha + p.xu_rows;
+    const T* WAB = p.W + s.woff[Am][Bm];
+    if (wsm)
+        for (int idx = threadIdx.x; idx < IA * IB; idx += PT) wab[idx] = WAB[idx];
+    const T* wab_r = wsm ? wab : WAB;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     T fa[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-    int run = 0;
-    const bool met = p.Xt != nullptr;
-    V* Xv = reinterpret_cast<V*>(p.X);
-    Walk4 w;
-    walk4_from(s, gtid * NV, w);
-    const Step4 stp = step4_of(s, gstr * NV - NV);
-    for (long long v = gtid; v < nvec; v += gstr) {
-        V xv = Xv[v];
-        const long long e0 = v * NV;
-        const uint32_t word = p.mb[e0 >> 5];
-#pragma unroll
-        for (int t = 0; t < NV; ++t) {
-            T xn;
-            const T rec = recon4(s, p.W, w);
-            xelem(p, rho, inv1p, e0 + t, v16get(xv, t), xn, rec, (word >> ((e0 + t) & 31)) & 1u, fa, met);
-            v16set(xv, t, xn);
-            walk4_inc(s, w);
+    const int nac = (IA + p.xu_rows - 1) / p.xu_rows;
+    const long long nunit = static_cast<long long>(s.nF) * nac;
+    for (long long un = blockIdx.x; un < nunit; un += gridDim.x) {
+        const long long f = un / nac;
+        const int a0 = static_cast<int>(un - f * nac) * p.xu_rows;
+        const int na = min(p.xu_rows, IA - a0);
+        int i0 = 0, i1 = 0;
+        if (N == 4) {
+            i0 = static_cast<int>(f / s.I[1]);
+            i1 = static_cast<int>(f - static_cast<long long>(i0) * s.I[1]);
+        } else {
+            i0 = static_cast<int>(f);
         }
-        Xv[v] = xv;
-        walk4_add(s, w, stp);
-        if (++run == 16) {
-            for (int t = 0; t < 6; ++t) {
-                acc[t] += static_cast<double>(fa[t]);
-                fa[t] = T(0);
+        __syncthreads();  // previous unit done with alpha / beta
+        for (int a = threadIdx.x; a < na; a += PT) {
+            T v = T(1);
+            if (N >= 3) v *= p.W[s.woff[0][Am] + static_cast<long long>(i0) * IA + a0 + a];
+            if (N == 4) v *= p.W[s.woff[1][Am] + static_cast<long long>(i1) * IA + a0 + a];
+            alpha[a] = v;
+        }
+        const T cf = N == 4 ? p.W[s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1] : T(1);
+        for (int b = threadIdx.x; b < IB; b += PT) {
+            T v = cf;
+            if (N >= 3) v *= p.W[s.woff[0][Bm] + static_cast<long long>(i0) * IB + b];
+            if (N == 4) v *= p.W[s.woff[1][Bm] + static_cast<long long>(i1) * IB + b];
+            beta[b] = v;
+        }
+        __syncthreads();
+        const long long e0 = (f * IA + a0) * IB;
+        const int n = na * IB;
+        int a = threadIdx.x / IB, b = threadIdx.x - (threadIdx.x / IB) * IB;
+        const int da = PT / IB, db = PT - da * IB;
+        int run = 0;
+        for (int o = threadIdx.x; o < n; o += PT) {
+            const long long e = e0 + o;
+            const T rec = wab_r[static_cast<long long>(a0 + a) * IB + b] * alpha[a] * beta[b];
+            const bool obs = (p.mb[e >> 5] >> (e & 31)) & 1u;
+            xacc(p, rho, inv1p, e, rec, obs, fa, met);
+            b += db;
+            a += da;
+            if (b >= IB) {
+                b -= IB;
+                ++a;
             }
-            run = 0;
-        }
-    }
-    if (gtid == 0) {  // ragged tail
-        Walk4 wt;
-        walk4_from(s, nvec * NV, wt);
-        for (long long e = nvec * NV; e < P; ++e) {
-            T xn;
-            const T rec = recon4(s, p.W, wt);
-            xelem(p, rho, inv1p, e, p.X[e], xn, rec, (p.mb[e >> 5] >> (e & 31)) & 1u, fa, met);
-            p.X[e] = xn;
-            walk4_inc(s, wt);
+            if (++run == 16) {
+                for (int t = 0; t < 6; ++t) {
+                    acc[t] += static_cast<double>(fa[t]);
+                    fa[t] = T(0);
+                }
+                run = 0;
+            }
         }
     }
     for (int t = 0; t < 6; ++t) acc[t] += static_cast<double>(fa[t]);
@@ -727,21 +906,27 @@ __global__ void __launch_bounds__(PT, 1) k_sweep_persistent(const SweepParams<T>
     int pipe = 0;
     const Shape& s = p.sh;
     __shared__ double red[8];
+    __shared__ int wtag;
     for (int sw = 0; sw < p.nsweeps; ++sw) {
         IFCTN_STAMP(p, sw, 0);
         for (int k = 0; k < s.N; ++k) {
             const int nU = p.pl[k].nunits, nG = p.gunits[k];
+            if (threadIdx.x == 0) wtag = 0;  // W_{A,B} changes between modes
+            __syncthreads();
+            // contraction units first, then the Gram units (they clobber the
+            // shared W_{A,B} cache, so the tag is cleared before them)
             for (int w = blockIdx.x; w < nU + nG; w += gridDim.x) {
                 if (w < nU) {
-                    if (!contract_dispatch<T>(p, k, w, work, bars, pipe)) return;
+                    if (!contract_dispatch<T>(p, k, w, work, bars, pipe, &wtag)) return;
                 } else {
+                    if (threadIdx.x == 0) wtag = 0;
                     gram_unit<T>(p, k, w - nU, work);
                 }
             }
             IFCTN_STAMP(p, sw, 1 + 6 * k);
             if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
             IFCTN_STAMP(p, sw, 2 + 6 * k);
-            reduce_phase<T>(p, k);
+            reduce_phase<T>(p, k, work);
             IFCTN_STAMP(p, sw, 3 + 6 * k);
             if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
             IFCTN_STAMP(p, sw, 4 + 6 * k);
@@ -751,7 +936,7 @@ __global__ void __launch_bounds__(PT, 1) k_sweep_persistent(const SweepParams<T>
             IFCTN_STAMP(p, sw, 6 + 6 * k);
         }
         double* xp = p.xpart + 8LL * gridDim.x * (sw & 1);
-        xupdate_phase<T>(p, xp + 8 * blockIdx.x);
+        xupdate_phase<T>(p, xp + 8 * blockIdx.x, work);
         IFCTN_STAMP(p, sw, 25);
         if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
         IFCTN_STAMP(p, sw, 26);
@@ -814,10 +999,13 @@ int persistent_smem_bytes(const SweepParams<T>& p) {
             Q *= s.R[k][m[t]];
             tot += s.R[k][m[t]] * s.I[m[t]];
         }
-        long long solve = static_cast<long long>(PW) * (RMAX * RMAX + 5 * RMAX) * 8 + static_cast<long long>(tot) * 8 +
-                          static_cast<long long>(PW) * 512 * sizeof(T);
+        long long solve = static_cast<long long>(PW) * (2 * RMAX * RMAX + 8 * RMAX) * 8 +
+                          static_cast<long long>(tot + 2) * sizeof(T) + static_cast<long long>(PW) * 512 * sizeof(T);
         if (p.solve_k_in_smem) solve += static_cast<long long>(Q) * Q * sizeof(T);
         need = std::max(need, solve);
+        // reduce_phase (column tiles): coefficients + cross-warp sums
+        need = std::max<long long>(need, (static_cast<long long>(RMAX) * p.pl[k].nunits + 4 +
+                                          static_cast<long long>(PW) * RMAX * 32) * sizeof(T));
         if (nm == 2) {
             const int l = m[1];
             need = std::max<long long>(need, static_cast<long long>(s.R[k][l] * s.I[l] + GRAM_IOB * s.I[l]) * sizeof(T));
@@ -830,6 +1018,9 @@ int persistent_smem_bytes(const SweepParams<T>& p) {
                                                  sizeof(T));
         }
     }
+    // xupdate: W_{A,B} (when kept in shared memory) + alpha + beta
+    need = std::max<long long>(need, (static_cast<long long>(p.xu_wab_smem ? s.IA * s.IB : 0) + p.xu_rows + s.IB) *
+                                         sizeof(T));
     return static_cast<int>(need + 128 + 256);
 }
 
