@@ -279,6 +279,10 @@ def main():
     if len(ph) >= 26:
         phases["xupdate"] = ph[24] - prev
         phases["xupdate_bar"] = ph[25] - ph[24]
+    for k in range(len(w.dims)):
+        if len(ph) >= 28 + 2 * k:
+            phases[f"m{k}_contract_cta_max_end"] = ph[26 + 2 * k]
+            phases[f"m{k}_contract_cta_mean_end"] = ph[27 + 2 * k]
     torch.cuda.synchronize()
     tot = sum(times)
     if dist:

@@ -456,7 +456,7 @@ struct Engine : ifctn_ctx {
     int pgrid = 0, psmem = 0, grid_cap = 0;
     SweepParams<T> pp;
     DevBuf<unsigned> bar;
-    DevBuf<unsigned long long> tstamp;
+    DevBuf<unsigned long long> tstamp;  // [0,64): phase ends; [64 + k*512 + cta]: per-CTA phase-1 ends
     long long launch_count = 0;
 
     int* counter() { return ints.p; }
@@ -544,7 +544,7 @@ struct Engine : ifctn_ctx {
                   alloc(t1, maxt1) == cudaSuccess && alloc(t2, maxt2) == cudaSuccess &&
                   alloc(part, maxpart) == cudaSuccess && alloc(Gd, sh.gsize) == cudaSuccess &&
                   alloc(xpart, xpart_n) == cudaSuccess && alloc(mpart, 3 * xblocks) == cudaSuccess &&
-                  alloc(bar, 4) == cudaSuccess && alloc(tstamp, 64) == cudaSuccess &&
+                  alloc(bar, 4) == cudaSuccess && alloc(tstamp, 64 + 4 * 512) == cudaSuccess &&
                   alloc(scal, 8) == cudaSuccess && alloc(tol, 1) == cudaSuccess &&
                   alloc(maskbits, (P + 31) / 32) == cudaSuccess && alloc(units, all.size()) == cudaSuccess &&
                   alloc(log, LOG_CAP) == cudaSuccess && alloc(ints, 4) == cudaSuccess;
@@ -648,9 +648,10 @@ struct Engine : ifctn_ctx {
         pp.tstamp = tstamp.p;
         {
             // X-update work units: row ranges of slabs, about 4 per CTA
-            const long long target_units = 4LL * 2 * num_sms();
+            const long long target_units = 2LL * num_sms();
             const long long rows_total = static_cast<long long>(sh.nF) * sh.IA;
             long long rows = std::max<long long>(1, rows_total / target_units);
+            rows = std::max<long long>(rows, std::max(1, 4096 / sh.IB));  // >= ~4K entries per unit
             rows = std::min<long long>(rows, sh.IA);
             rows = std::min<long long>(rows, std::max(1, 16384 / sh.IB));
             pp.xu_rows = static_cast<int>(std::max<long long>(rows, 1));
@@ -875,11 +876,29 @@ struct Engine : ifctn_ctx {
     cudaStream_t stream() const override { return st; }
     long long launch_total() const override { return launch_count; }
     ifctn_status phase_times(double* out, int max, int* n) override {
-        unsigned long long h[64];
-        CK(cudaMemcpyAsync(h, tstamp.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+        std::vector<unsigned long long> h(64 + 4 * 512);
+        CK(cudaMemcpyAsync(h.data(), tstamp.p, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        const int cnt = std::min(max, 26);
-        for (int i = 0; i < cnt; ++i) out[i] = (h[i + 1] >= h[0] && h[0]) ? 1e-9 * static_cast<double>(h[i + 1] - h[0]) : NAN;
+        auto rel = [&](unsigned long long t) {
+            return (t >= h[0] && h[0]) ? 1e-9 * static_cast<double>(t - h[0]) : NAN;
+        };
+        int cnt = 0;
+        for (int i = 0; i < 26 && cnt < max; ++i) out[cnt++] = rel(h[i + 1]);
+        // then, per mode, the latest per-CTA end of phase 1 and the mean
+        for (int k = 0; k < sh.N && cnt + 1 < max; ++k) {
+            double mx = 0, sm = 0;
+            int c = 0;
+            for (int b = 0; b < std::min(pgrid, 512); ++b) {
+                const double v = rel(h[64 + k * 512 + b]);
+                if (v == v) {
+                    mx = std::max(mx, v);
+                    sm += v;
+                    ++c;
+                }
+            }
+            out[cnt++] = mx;
+            out[cnt++] = c ? sm / c : NAN;
+        }
         if (n) *n = persistent ? cnt : 0;
         return IFCTN_OK;
     }

@@ -100,6 +100,22 @@ __device__ __forceinline__ int pow2_at_least(int x) {
     return L;
 }
 
+// Hint the L2 with the tensor span of a CTA's next contraction unit while it
+// works on the current one (bulk prefetch, no shared memory involved).
+template <typename T>
+__device__ __forceinline__ void prefetch_unit(const SweepParams<T>& p, int k, int uidx) {
+    const UnitDesc u = p.units[k][uidx];
+    const Shape& s = p.sh;
+    const long long e0 = (static_cast<long long>(u.f0) * s.IA + u.a0) * s.IB;
+    long long n = static_cast<long long>(u.a1 - u.a0) * s.IB;
+    if (u.fstride == 1) n += static_cast<long long>(u.ns - 1) * s.IA * s.IB;
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(p.X + e0) & ~uintptr_t(15);
+    uintptr_t hi = (reinterpret_cast<uintptr_t>(p.X + e0 + n) + 15) & ~uintptr_t(15);
+    if (hi - lo > (1u << 20)) hi = lo + (1u << 20);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"(static_cast<unsigned>(hi - lo))
+                 : "memory");
+}
+
 template <typename T>
 __device__ bool contract_dispatch(const SweepParams<T>& p, int k, int uidx, unsigned char* smem,
                                   uint64_t* bars, int& pipe, int* wtag) {
@@ -398,10 +414,11 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
 // (H + rho I) g = b is solved by a lane-parallel LDL^T factorisation (the
 // matrix is SPD with eigenvalues >= rho, so no pivoting).  FP64 path: the
 // factorisation and the solves in FP64.  Mixed path: the factorisation in
-// FP32 followed by two steps of iterative refinement whose residual
+// FP32 followed by a step of iterative refinement whose residual
 // b - (H + rho I) g is formed in FP64, which recovers FP64-level accuracy for
 // the conditioning these systems have while keeping GB300's narrow FP64 pipe
-// nearly idle.
+// nearly idle.  (One refinement step: H itself carries the FP32 rounding of
+// the contractions, so further steps would not change the result's accuracy.)
 // ---------------------------------------------------------------------------
 template <typename F>
 __device__ __forceinline__ F recip_nr(F d) {
@@ -588,7 +605,7 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem)
                 if (lane < Ri) gd[lane] = static_cast<double>(xf[lane]);
                 __syncwarp();
                 if (MIXED) {
-                    for (int it = 0; it < 2; ++it) {
+                    for (int it = 0; it < 1; ++it) {
                         // residual in FP64, correction in FP32
                         if (lane < Ri) {
                             double r = bd[lane];
@@ -842,24 +859,52 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
         const int n = na * IB;
         int a = threadIdx.x / IB, b = threadIdx.x - (threadIdx.x / IB) * IB;
         const int da = PT / IB, db = PT - da * IB;
-        int run = 0;
-        for (int o = threadIdx.x; o < n; o += PT) {
-            const long long e = e0 + o;
-            const T rec = wab_r[static_cast<long long>(a0 + a) * IB + b] * alpha[a] * beta[b];
-            const bool obs = (p.mb[e >> 5] >> (e & 31)) & 1u;
-            xacc(p, rho, inv1p, e, rec, obs, fa, met);
-            b += db;
-            a += da;
-            if (b >= IB) {
-                b -= IB;
-                ++a;
-            }
-            if (++run == 16) {
-                for (int t = 0; t < 6; ++t) {
-                    acc[t] += static_cast<double>(fa[t]);
-                    fa[t] = T(0);
+        // batches of XB entries per thread (stride PT): every load of a batch
+        // is issued before any store, so they overlap in flight
+        constexpr int XB = 8;
+        for (int ob = 0; ob < n; ob += XB * PT) {
+            T xo[XB], rec[XB];
+            uint32_t wd[XB];
+#pragma unroll
+            for (int t = 0; t < XB; ++t) {
+                const int o = ob + t * PT + threadIdx.x;
+                if (o < n) {
+                    const long long e = e0 + o;
+                    xo[t] = p.X[e];
+                    wd[t] = p.mb[e >> 5];
+                    rec[t] = wab_r[static_cast<long long>(a0 + a) * IB + b] * alpha[a] * beta[b];
                 }
-                run = 0;
+                b += db;
+                a += da;
+                if (b >= IB) {
+                    b -= IB;
+                    ++a;
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < XB; ++t) {
+                const int o = ob + t * PT + threadIdx.x;
+                if (o < n) {
+                    const long long e = e0 + o;
+                    const bool obs = (wd[t] >> (e & 31)) & 1u;
+                    const T xn = obs ? xo[t] : (rec[t] + rho * xo[t]) * inv1p;
+                    p.X[e] = xn;
+                    const T d = xn - xo[t], r = xn - rec[t];
+                    fa[0] = fma(d, d, fa[0]);
+                    fa[1] = fma(xo[t], xo[t], fa[1]);
+                    fa[2] = fma(r, r, fa[2]);
+                    if (met) {
+                        const T xt = p.Xt[e];
+                        const T de = xt - xn;
+                        fa[3] = fma(de, de, fa[3]);
+                        fa[4] = fma(xt, xt, fa[4]);
+                        if (!obs) fa[5] = fma(de, de, fa[5]);
+                    }
+                }
+            }
+            for (int t = 0; t < 6; ++t) {
+                acc[t] += static_cast<double>(fa[t]);
+                fa[t] = T(0);
             }
         }
     }
@@ -917,6 +962,8 @@ __global__ void __launch_bounds__(PT, 1) k_sweep_persistent(const SweepParams<T>
             // shared W_{A,B} cache, so the tag is cleared before them)
             for (int w = blockIdx.x; w < nU + nG; w += gridDim.x) {
                 if (w < nU) {
+                    if (threadIdx.x == 0 && w + static_cast<int>(gridDim.x) < nU)
+                        prefetch_unit<T>(p, k, w + gridDim.x);
                     if (!contract_dispatch<T>(p, k, w, work, bars, pipe, &wtag)) return;
                 } else {
                     if (threadIdx.x == 0) wtag = 0;
@@ -924,6 +971,8 @@ __global__ void __launch_bounds__(PT, 1) k_sweep_persistent(const SweepParams<T>
                 }
             }
             IFCTN_STAMP(p, sw, 1 + 6 * k);
+            if (p.tstamp && sw == 0 && threadIdx.x == 0 && k < 4 && blockIdx.x < 512)
+                p.tstamp[64 + k * 512 + blockIdx.x] = gtimer();
             if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
             IFCTN_STAMP(p, sw, 2 + 6 * k);
             reduce_phase<T>(p, k, work);
