@@ -142,6 +142,22 @@ int mode_q(const Shape& s, int k) {
 // (more CTAs, smaller partials) instead of folding mode 0 in registers.
 constexpr long long L2_RESIDENT_BYTES = 96LL << 20;
 
+// Largest number of pipeline stages any unit of the plan consumes.
+static int max_unit_stages(const ContractPlan& pl, const std::vector<UnitDesc>& units) {
+    int mx = 1;
+    const int GS = pl.split ? 1 : pl.G;
+    for (const UnitDesc& u : units) {
+        const int nb = (u.ns + GS - 1) / GS;
+        int n = 1;
+        if (pl.kcase == CASE_COL)
+            n = nb * ((u.a1 - u.a0 + pl.TAc - 1) / pl.TAc);
+        else
+            n = nb * ((u.a1 - u.a0 + pl.TA - 1) / pl.TA);
+        mx = std::max(mx, n);
+    }
+    return mx;
+}
+
 ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>& units) {
     ContractPlan pl;
     memset(&pl, 0, sizeof(pl));
@@ -250,6 +266,14 @@ ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>&
                 break;
             }
             --G;
+        }
+        {
+            const int need = std::min(NSTAGES, max_unit_stages(pl, units));
+            if (need < NSTAGES) {
+                const int GS = pl.split ? 1 : pl.G;
+                pl.smem -= (NSTAGES - need) * GS * pl.sub_elems * sz;
+                pl.nstages = need;
+            }
         }
         pl.nrow = IB;
         pl.nunits = static_cast<int>(units.size());
@@ -373,6 +397,14 @@ ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>&
         --G;
     }
     pl.skew = (IB % 2 == 0) ? 1 : 0;
+    {
+        const int need = std::min(NSTAGES, max_unit_stages(pl, units));
+        if (need < NSTAGES) {
+            const int GS = pl.split ? 1 : pl.G;
+            pl.smem -= (NSTAGES - need) * GS * pl.sub_elems * sz;
+            pl.nstages = need;
+        }
+    }
     pl.nrow = IA;
     pl.nunits = static_cast<int>(units.size());
     pl.key_div = 0;
@@ -607,7 +639,7 @@ struct Engine : ifctn_ctx {
             int nm = 0;
             for (int q = 0; q < sh.N; ++q)
                 if (q != k) m[nm++] = q;
-            pp.gunits[k] = nm == 2 ? (sh.I[m[0]] + 7) / 8 : nm == 3 ? sh.I[m[0]] : 0;
+            pp.gunits[k] = nm == 2 ? (sh.I[m[0]] + 1) / 2 : nm == 3 ? sh.I[m[0]] : 0;
             const long long Q = mode_q(sh, k);
             if (Q * Q * static_cast<long long>(sizeof(T)) > 96 * 1024) k_fits = false;
         }
@@ -644,16 +676,20 @@ struct Engine : ifctn_ctx {
         pp.bar_gen = bar.p + 1;
         pp.rho = prob.rho;
         pp.nmiss = nmiss;
-        pp.nstages = NSTAGES;
+        pp.nstages = 1;
+        for (int k = 0; k < sh.N; ++k) pp.nstages = std::max(pp.nstages, plan[k].nstages);
         pp.tstamp = tstamp.p;
         {
             // X-update work units: row ranges of slabs, about 4 per CTA
-            const long long target_units = 2LL * num_sms();
+            const long long target_units = 4LL * num_sms();
             const long long rows_total = static_cast<long long>(sh.nF) * sh.IA;
             long long rows = std::max<long long>(1, rows_total / target_units);
-            rows = std::max<long long>(rows, std::max(1, 4096 / sh.IB));  // >= ~4K entries per unit
+            rows = std::max<long long>(rows, std::max(1, 2048 / sh.IB));  // >= ~2K entries per unit
             rows = std::min<long long>(rows, sh.IA);
             rows = std::min<long long>(rows, std::max(1, 16384 / sh.IB));
+            // equal row ranges per slab
+            const long long nac = (sh.IA + rows - 1) / rows;
+            rows = (sh.IA + nac - 1) / nac;
             pp.xu_rows = static_cast<int>(std::max<long long>(rows, 1));
             pp.xu_wab_smem = static_cast<long long>(sh.IA) * sh.IB * sizeof(T) <= 64 * 1024 ? 1 : 0;
         }

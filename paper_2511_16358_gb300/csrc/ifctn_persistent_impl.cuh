@@ -35,7 +35,7 @@ using cdev::contract_row_unit;
 
 constexpr int PT = 256;  // threads per CTA
 constexpr int PW = PT / 32;
-constexpr int GRAM_IOB = 8;  // io values per Gram unit (N = 3)
+constexpr int GRAM_IOB = 2;  // io values per Gram unit (N = 3)
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
@@ -938,7 +938,7 @@ __device__ __forceinline__ unsigned long long gtimer() {
     } while (0)
 
 template <typename T>
-__global__ void __launch_bounds__(PT, 1) k_sweep_persistent(const SweepParams<T> p) {
+__global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const SweepParams<T> p) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     unsigned char* work = smem + 128;
@@ -960,14 +960,21 @@ __global__ void __launch_bounds__(PT, 1) k_sweep_persistent(const SweepParams<T>
             __syncthreads();
             // contraction units first, then the Gram units (they clobber the
             // shared W_{A,B} cache, so the tag is cleared before them)
+            // Gram units first (they start the longest dependency-free work),
+            // then the contraction units; a Gram unit clobbers the shared
+            // W_{A,B} cache, so the tag is cleared around it
             for (int w = blockIdx.x; w < nU + nG; w += gridDim.x) {
-                if (w < nU) {
-                    if (threadIdx.x == 0 && w + static_cast<int>(gridDim.x) < nU)
-                        prefetch_unit<T>(p, k, w + gridDim.x);
-                    if (!contract_dispatch<T>(p, k, w, work, bars, pipe, &wtag)) return;
-                } else {
+                if (w < nG) {
                     if (threadIdx.x == 0) wtag = 0;
-                    gram_unit<T>(p, k, w - nU, work);
+                    gram_unit<T>(p, k, w, work);
+                    if (threadIdx.x == 0 && w + static_cast<int>(gridDim.x) >= nG &&
+                        w + static_cast<int>(gridDim.x) < nU + nG)
+                        prefetch_unit<T>(p, k, w + gridDim.x - nG);
+                } else {
+                    const int cu = w - nG;
+                    if (threadIdx.x == 0 && cu + static_cast<int>(gridDim.x) < nU)
+                        prefetch_unit<T>(p, k, cu + gridDim.x);
+                    if (!contract_dispatch<T>(p, k, cu, work, bars, pipe, &wtag)) return;
                 }
             }
             IFCTN_STAMP(p, sw, 1 + 6 * k);
