@@ -147,10 +147,7 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
         // pair matrix W_{A,B} rows of this pass; a caller may keep them across
         // units through *wtag (the first row + 1 of the rows held, 0 = none)
         const bool wload = isF && bt == 0 && !(wtag && *wtag == a0 + 1 && na == TA);
-        if (wload) {
-            const T* src = A.W + s.woff[Am][Bm] + static_cast<long long>(a0) * IB;
-            for (int idx = tid; idx < na * IB; idx += nthr) wab[idx] = src[idx];
-        }
+        if (wload) stage_async(wab, A.W + s.woff[Am][Bm] + static_cast<long long>(a0) * IB, na * IB);
         const int gsl = split ? 0 : g;  // this thread's slab within the stage
         const int sidx = bt * GS + gsl;
         const bool has = in_grid && sidx < u.ns;
@@ -168,6 +165,7 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
             }
             T* pg = psi + static_cast<size_t>(gsl) * IB * RBP;
             const int t0 = split ? tid : al, tst = split ? nthr : TA;
+#pragma unroll 4
             for (int idx = t0; idx < IB * RB; idx += tst) {
                 const int b = idx / RB, r = idx - b * RB;
                 T om = T(1);
@@ -176,6 +174,7 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
                 pg[b * RBP + r] = om * gfac(A.Gt, s, Bm, k, r, b);
             }
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
         if (wload && wtag && tid == 0) *wtag = (na == TA) ? a0 + 1 : 0;
         const bool ok = mbar_wait_bounded(&bars[buf], par, A.flags);
@@ -390,6 +389,7 @@ __device__ __noinline__ bool contract_col_unit(const ContractArgs<T>& A, const i
             }
             T* pg = phi + static_cast<size_t>(gsl) * TAc * RAP;
             const int t0 = split ? tid : bl, tst = split ? nthr : TB;
+#pragma unroll 4
             for (int idx = t0; idx < na * RA; idx += tst) {
                 const int ar = idx / RA, r = idx - ar * RA;
                 const int a = a0 + ar;

@@ -136,6 +136,24 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         : "memory");
 }
 
+// Asynchronous element-wise copy global -> shared by all threads of the CTA
+// (cp.async: every copy is in flight before any wait).  Completes at
+// stage_wait(), which also synchronises the CTA.
+template <typename T>
+__device__ __forceinline__ void stage_async(T* dst, const T* src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (sizeof(T) == 4)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst + i)), "l"(src + i) : "memory");
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst + i)), "l"(src + i) : "memory");
+    }
+}
+
+__device__ __forceinline__ void stage_wait() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

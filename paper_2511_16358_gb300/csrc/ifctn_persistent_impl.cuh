@@ -168,13 +168,10 @@ __device__ void gram_unit(const SweepParams<T>& p, int k, int gu, unsigned char*
         const int Io = s.I[o], Il = s.I[l], Rl = s.R[k][l];
         const int io0 = gu * GRAM_IOB, io1 = min(Io, io0 + GRAM_IOB);
         T* gl = sm;  // Rl x Il
-        for (int idx = tid; idx < Rl * Il; idx += PT) gl[idx] = p.Gt[s.goff[l][k] + idx];
-        T* wr = gl + Rl * Il;  // (io1-io0) x Il, squared
-        for (int idx = tid; idx < (io1 - io0) * Il; idx += PT) {
-            const T w = p.W[s.woff[o][l] + static_cast<long long>(io0) * Il + idx];
-            wr[idx] = w * w;
-        }
-        __syncthreads();
+        stage_async(gl, p.Gt + s.goff[l][k], Rl * Il);
+        T* wr = gl + Rl * Il;  // (io1-io0) x Il
+        stage_async(wr, p.W + s.woff[o][l] + static_cast<long long>(io0) * Il, (io1 - io0) * Il);
+        stage_wait();
         const int nout = (io1 - io0) * Rl * Rl;
         for (int idx = tid; idx < nout; idx += PT) {
             const int y = idx % Rl, x = (idx / Rl) % Rl, ir = idx / (Rl * Rl);
@@ -184,10 +181,10 @@ __device__ void gram_unit(const SweepParams<T>& p, int k, int gu, unsigned char*
             T a0 = T(0), a1 = T(0);
             int il = 0;
             for (; il + 1 < Il; il += 2) {
-                a0 = fma(w2[il], gx[il] * gy[il], a0);
-                a1 = fma(w2[il + 1], gx[il + 1] * gy[il + 1], a1);
+                a0 = fma(w2[il] * w2[il], gx[il] * gy[il], a0);
+                a1 = fma(w2[il + 1] * w2[il + 1], gx[il + 1] * gy[il + 1], a1);
             }
-            if (il < Il) a0 = fma(w2[il], gx[il] * gy[il], a0);
+            if (il < Il) a0 = fma(w2[il] * w2[il], gx[il] * gy[il], a0);
             p.gbuf[(static_cast<long long>(io0 + ir) * Rl + x) * Rl + y] = a0 + a1;
         }
         __syncthreads();
@@ -203,12 +200,12 @@ __device__ void gram_unit(const SweepParams<T>& p, int k, int gu, unsigned char*
     T* wol = gc + Rc * Ic;         // Il
     T* t2a = wol + Il;             // Q2 x Q2 accumulators
     T* t1 = t2a + Q2 * Q2;         // chunk x Rl x Rl
-    for (int idx = tid; idx < Rl * Il; idx += PT) gl[idx] = p.Gt[s.goff[l][k] + idx];
-    for (int idx = tid; idx < Rc * Ic; idx += PT) gc[idx] = p.Gt[s.goff[c][k] + idx];
-    for (int idx = tid; idx < Il; idx += PT) wol[idx] = p.W[s.woff[o][l] + static_cast<long long>(io) * Il + idx];
+    stage_async(gl, p.Gt + s.goff[l][k], Rl * Il);
+    stage_async(gc, p.Gt + s.goff[c][k], Rc * Ic);
+    stage_async(wol, p.W + s.woff[o][l] + static_cast<long long>(io) * Il, Il);
     for (int idx = tid; idx < Q2 * Q2; idx += PT) t2a[idx] = T(0);
     const int chunk = max(1, min(Ic, p.gram_chunk));
-    __syncthreads();
+    stage_wait();
     for (int ic0 = 0; ic0 < Ic; ic0 += chunk) {
         const int nc = min(chunk, Ic - ic0);
         for (int idx = tid; idx < nc * Rl * Rl; idx += PT) {
@@ -310,6 +307,7 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
         T* coef = reinterpret_cast<T*>(smem);      // Rd x nu
         T* red = coef + ((Rd * nu + 3) & ~3);      // PW x RMAX x 32
         if (static_cast<int>(blockIdx.x) < ntile) {
+#pragma unroll 4
             for (int idx = threadIdx.x; idx < Rd * nu; idx += PT) {
                 const int rdd = idx / nu, u = idx - rdd * nu;
                 coef[idx] = pl.dmode >= 0 ? gfac(p.Gt, s, pl.dmode, k, rdd, u / pl.key_div) : T(1);
@@ -521,15 +519,13 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem)
         gko[t] = tot;
         tot += Rm[t] * s.I[m[t]];
     }
-    for (int t = 0; t < nm; ++t)
-        for (int idx = tid; idx < Rm[t] * s.I[m[t]]; idx += PT) gik[gko[t] + idx] = p.Gt[s.goff[m[t]][k] + idx];
+    for (int t = 0; t < nm; ++t) stage_async(gik + gko[t], p.Gt + s.goff[m[t]][k], Rm[t] * s.I[m[t]]);
     T* om = gik + ((tot + 1) & ~1) + warp * 512;
     T* Ks = gik + ((tot + 1) & ~1) + PW * 512;
     const bool ksm = p.solve_k_in_smem != 0;
-    if (ksm)
-        for (int idx = tid; idx < Q * Q; idx += PT) Ks[idx] = p.Kk[idx];
+    if (ksm) stage_async(Ks, p.Kk, Q * Q);
     const T* K = ksm ? Ks : p.Kk;
-    __syncthreads();
+    stage_wait();
     const double rho = p.rho;
     for (int j = warp * gridDim.x + blockIdx.x; j < Ik; j += gridDim.x * PW) {
         for (int t = 0; t < nm; ++t)
@@ -822,8 +818,8 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
     T* alpha = wab + (wsm ? IA * IB : 0);
     T* beta = alpha + p.xu_rows;
     const T* WAB = p.W + s.woff[Am][Bm];
-    if (wsm)
-        for (int idx = threadIdx.x; idx < IA * IB; idx += PT) wab[idx] = WAB[idx];
+    if (wsm) stage_async(wab, WAB, IA * IB);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     const T* wab_r = wsm ? wab : WAB;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     T fa[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
