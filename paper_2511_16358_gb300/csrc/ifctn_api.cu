@@ -490,6 +490,7 @@ struct Engine : ifctn_ctx {
     DevBuf<unsigned> bar;
     DevBuf<unsigned long long> tstamp;  // [0,64): phase ends; [64 + k*512 + cta]: per-CTA phase-1 ends
     long long launch_count = 0;
+    double cur_tol = 0.0;
 
     int* counter() { return ints.p; }
     int* done() { return ints.p + 1; }
@@ -675,6 +676,7 @@ struct Engine : ifctn_ctx {
         pp.bar_count = bar.p;
         pp.bar_gen = bar.p + 1;
         pp.rho = prob.rho;
+        pp.inv1p = 1.0 / (1.0 + prob.rho);
         pp.nmiss = nmiss;
         pp.nstages = 1;
         for (int k = 0; k < sh.N; ++k) pp.nstages = std::max(pp.nstages, plan[k].nstages);
@@ -707,6 +709,7 @@ struct Engine : ifctn_ctx {
         if (n <= 0) return IFCTN_OK;
         if (persistent) {
             pp.nsweeps = n;
+            pp.tolv = cur_tol;
             pp.Xt = (logm && truth) ? Xt.p : nullptr;
             CK(launch_persistent<T>(pp, pgrid, psmem, st));
             ++launch_count;
@@ -882,6 +885,7 @@ struct Engine : ifctn_ctx {
         }
         CK(cudaMemcpyAsync(tol.p, &tolv, sizeof(double), cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(done(), 0, sizeof(int), st));
+        cur_tol = tolv;
         const int chunkn = (tolv > 0 && !persistent) ? 16 : (1 << 30);
         int doneh = 0;
         for (int s = 0; s < n;) {
@@ -906,6 +910,7 @@ struct Engine : ifctn_ctx {
         if (reset) {
             CK(cudaMemcpyAsync(tol.p, &tolv, sizeof(double), cudaMemcpyHostToDevice, st));
             CK(cudaMemsetAsync(done(), 0, sizeof(int), st));
+            cur_tol = tolv;
         }
         return launch_run(n);
     }

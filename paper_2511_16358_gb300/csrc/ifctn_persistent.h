@@ -36,6 +36,8 @@ struct SweepParams {
     int solve_k_in_smem;
     int gram_chunk;
     unsigned long long* tstamp;  // optional phase timestamps of the first sweep
+    double inv1p;                // 1 / (1 + rho), precomputed
+    double tolv;                 // stop tolerance of this launch (0 = none)
     int xu_rows;                 // X update: rows of a slab per work unit
     int xu_wab_smem;             // X update: W_{A,B} kept in shared memory
 };

@@ -811,7 +811,7 @@ template <typename T>
 __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned char* smem) {
     const Shape& s = p.sh;
     const int N = s.N, IA = s.IA, IB = s.IB, Am = N - 2, Bm = N - 1;
-    const T rho = static_cast<T>(p.rho), inv1p = static_cast<T>(1.0 / (1.0 + p.rho));
+    const T rho = static_cast<T>(p.rho), inv1p = static_cast<T>(p.inv1p);
     const bool met = p.Xt != nullptr;
     const bool wsm = p.xu_wab_smem != 0;
     T* wab = reinterpret_cast<T*>(smem);
@@ -823,6 +823,7 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
     const T* wab_r = wsm ? wab : WAB;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     T fa[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    T run2[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     const int nac = (IA + p.xu_rows - 1) / p.xu_rows;
     const long long nunit = static_cast<long long>(s.nF) * nac;
     for (long long un = blockIdx.x; un < nunit; un += gridDim.x) {
@@ -898,18 +899,23 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
                     }
                 }
             }
+            // two-level accumulation: batch sums fold into running sums in the
+            // tensor dtype; FP64 only once per thread (GB300's FP64 pipe is narrow)
+#pragma unroll
             for (int t = 0; t < 6; ++t) {
-                acc[t] += static_cast<double>(fa[t]);
+                run2[t] += fa[t];
                 fa[t] = T(0);
             }
         }
     }
-    for (int t = 0; t < 6; ++t) acc[t] += static_cast<double>(fa[t]);
+    (void)acc;
+    // per-CTA sums: warp reduction in the tensor dtype, FP64 across warps
     __shared__ double sh[PW][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int t = 0; t < 6; ++t) acc[t] = warp_sum(acc[t]);
+#pragma unroll
+    for (int t = 0; t < 6; ++t) run2[t] = warp_sum(run2[t]);
     if (lane == 0)
-        for (int t = 0; t < 6; ++t) sh[warp][t] = acc[t];
+        for (int t = 0; t < 6; ++t) sh[warp][t] = static_cast<double>(run2[t]);
     __syncthreads();
     if (threadIdx.x < 6) {
         double v = 0.0;
@@ -946,7 +952,7 @@ __global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const SweepParams<T>
     if (*reinterpret_cast<volatile const int*>(p.done)) return;
     int pipe = 0;
     const Shape& s = p.sh;
-    __shared__ double red[8];
+    __shared__ int redc;
     __shared__ int wtag;
     for (int sw = 0; sw < p.nsweeps; ++sw) {
         IFCTN_STAMP(p, sw, 0);
@@ -992,42 +998,58 @@ __global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const SweepParams<T>
         IFCTN_STAMP(p, sw, 25);
         if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
         IFCTN_STAMP(p, sw, 26);
-        // every CTA reduces the per-CTA sums in the same order
-        if (threadIdx.x < 32) {
+        // Stop decision (only when a tolerance is set): every CTA sums the
+        // per-CTA values in the same order, so all take the same
+        // decision without another barrier.  The FP64 log record is written
+        // by the last CTA, which carries the least work in the next phases.
+        bool conv = false;
+        if (p.tolv > 0) {
+            if (threadIdx.x < 32) {
+                // in the tensor dtype: FP64 on the FP64 path, FP32 on the mixed one
+                T a0 = T(0), a1 = T(0);
+                for (int b = threadIdx.x; b < gridDim.x; b += 32) {
+                    a0 += static_cast<T>(reinterpret_cast<volatile double*>(xp)[8 * b + 0]);
+                    a1 += static_cast<T>(reinterpret_cast<volatile double*>(xp)[8 * b + 1]);
+                }
+                a0 = warp_sum(a0);
+                a1 = warp_sum(a1);
+                if (threadIdx.x == 0) {
+                    const T tf = static_cast<T>(p.tolv);
+                    redc = (a1 > T(0) && a0 < tf * tf * a1) ? 1 : 0;
+                }
+            }
+            __syncthreads();
+            conv = redc != 0;
+        }
+        if (blockIdx.x == gridDim.x - 1 && threadIdx.x < 32) {
             double a[6] = {0, 0, 0, 0, 0, 0};
             for (int b = threadIdx.x; b < gridDim.x; b += 32)
                 for (int t = 0; t < 6; ++t) a[t] += reinterpret_cast<volatile double*>(xp)[8 * b + t];
             for (int t = 0; t < 6; ++t) a[t] = warp_sum(a[t]);
-            if (threadIdx.x == 0)
-                for (int t = 0; t < 6; ++t) red[t] = a[t];
-        }
-        __syncthreads();
-        const double dx2 = red[0], x2 = red[1];
-        const double rel = x2 > 0 ? sqrt(dx2) / sqrt(x2) : (dx2 > 0 ? INFINITY : 0.0);
-        const double tol = *p.tol;
-        const bool conv = tol > 0 && rel < tol;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            SweepStat r;
-            r.rel_change = rel;
-            r.objective = 0.5 * red[2];
-            if (p.Xt) {
-                r.rse = red[4] > 0 ? sqrt(red[3]) / sqrt(red[4]) : NAN;
-                r.rmse = p.nmiss > 0 ? sqrt(red[5] / static_cast<double>(p.nmiss)) : 0.0;
-            } else {
-                r.rse = NAN;
-                r.rmse = NAN;
+            if (threadIdx.x == 0) {
+                const double dx2 = a[0], x2 = a[1];
+                SweepStat r;
+                r.rel_change = x2 > 0 ? sqrt(dx2) / sqrt(x2) : (dx2 > 0 ? INFINITY : 0.0);
+                r.objective = 0.5 * a[2];
+                if (p.Xt) {
+                    r.rse = a[4] > 0 ? sqrt(a[3]) / sqrt(a[4]) : NAN;
+                    r.rmse = p.nmiss > 0 ? sqrt(a[5] / static_cast<double>(p.nmiss)) : 0.0;
+                } else {
+                    r.rse = NAN;
+                    r.rmse = NAN;
+                }
+                r.dx2 = dx2;
+                r.x2 = x2;
+                const int sidx = *p.counter;
+                r.sweep = sidx + 1;
+                r.converged = conv ? 1 : 0;
+                r.flags = *p.flags;
+                r.pad = 0;
+                if (!isfinite(r.rel_change) || !isfinite(r.objective)) r.flags |= FLAG_NONFINITE;
+                p.log[sidx % p.log_cap] = r;
+                *p.counter = sidx + 1;
+                if (conv) *p.done = 1;
             }
-            r.dx2 = dx2;
-            r.x2 = x2;
-            const int sidx = *p.counter;
-            r.sweep = sidx + 1;
-            r.converged = conv ? 1 : 0;
-            r.flags = *p.flags;
-            r.pad = 0;
-            if (!isfinite(r.rel_change) || !isfinite(r.objective)) r.flags |= FLAG_NONFINITE;
-            p.log[sidx % p.log_cap] = r;
-            *p.counter = sidx + 1;
-            if (conv) *p.done = 1;
         }
         if (conv) return;
         // xpart is double-buffered by sweep parity: the buffer read here is
