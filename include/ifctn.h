@@ -164,6 +164,28 @@ ifctn_status ifctn_phase_times(ifctn_ctx* ctx, double* out, int32_t max, int32_t
 
 void ifctn_destroy(ifctn_ctx* ctx);
 
+/* Allocation-free reconstruction (an addition of this library; the paper has
+   no counterpart).  For callers that cannot call cudaMalloc -- their device
+   memory is owned by another allocator, or they must not pay for or
+   synchronise on an allocation on their path -- this writes iFCTN(G) (eq.
+   (iFCTN)) of the packed FP64 factors into out without allocating anything.
+   factors and out must be device memory of the current device (out in the
+   tensor dtype of precision: FP64 for IFCTN_FP64, FP32 for IFCTN_MIXED); the
+   shape arguments follow ifctn_problem (dims[0..order-1], ranks[16]).
+   Scratch: the pair matrices W_{p,q} live in a fixed 8 MiB device array
+   inside the library, loaded on every GPU that loads the library and held
+   until the process exits; problems whose pair matrices need more
+   (sum_{p<q} I_p I_q entries of the tensor dtype) are rejected with
+   IFCTN_EINVAL.  The first call on a device looks the array's address up;
+   make that first call before any stream capture.  The work is enqueued on
+   cuda_stream (NULL = the legacy default stream) and the call returns without
+   waiting.  All calls share the one array, and each call overwrites it: calls
+   whose work overlaps on the GPU (different streams, or concurrent host
+   threads) race. */
+ifctn_status ifctn_reconstruct_noalloc(int32_t order, const int64_t* dims, const int32_t* ranks,
+                                       int32_t precision, const double* factors, void* out,
+                                       void* cuda_stream);
+
 /* ---------------------------------------------------------------------------
    Serving: continuous batching of completion jobs on one GPU.
    A server owns a device-memory budget and up to max_slots resident jobs.

@@ -29,7 +29,7 @@ EXPORTED = [
     "ifctn_mode_system", "ifctn_kernels_per_sweep", "ifctn_destroy", "ifctn_server_create",
     "ifctn_submit", "ifctn_poll", "ifctn_server_info_get", "ifctn_server_latency",
     "ifctn_server_destroy", "ifctn_last_error", "ifctn_sweep_async", "ifctn_launch_stage",
-    "ifctn_launch_count", "ifctn_phase_times",
+    "ifctn_launch_count", "ifctn_phase_times", "ifctn_reconstruct_noalloc",
 ]
 
 
@@ -98,6 +98,7 @@ def load(path: str | None = None):
         "ifctn_launch_stage": (i32, [vp, i32, i32]),
         "ifctn_launch_count": (i64, [vp]),
         "ifctn_phase_times": (i32, [vp, P(dp), i32, P(i32)]),
+        "ifctn_reconstruct_noalloc": (i32, [i32, P(i64), P(i32), i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -233,6 +234,20 @@ def phase_times(ctx) -> list:
     n = ctypes.c_int32(0)
     _check(load().ifctn_phase_times(ctx, arr, 64, ctypes.byref(n)))
     return [arr[i] for i in range(n.value)]
+
+
+def reconstruct_noalloc(dims, ranks, precision, factors_dev, out_dev, stream=None):
+    """Allocation-free reconstruction: factors_dev / out_dev are device buffers
+    (e.g. CUDA torch tensors); nothing is allocated by the library."""
+    d = (ctypes.c_int64 * 4)(*([int(x) for x in dims] + [0] * (4 - len(dims))))
+    r = (ctypes.c_int32 * 16)()
+    R = np.asarray(ranks)
+    for k in range(R.shape[0]):
+        for l in range(R.shape[1]):
+            r[k * 4 + l] = int(R[k, l])
+    _check(load().ifctn_reconstruct_noalloc(len(dims), d, r, int(precision), ptr(factors_dev), ptr(out_dev),
+                                            stream))
+    return out_dev
 
 
 def destroy(ctx):
