@@ -248,14 +248,22 @@ ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>&
         // a unit with a single slab and no register fold: the groups split its rows
         pl.split = (maxns == 1 && pl.l2 < 0) ? 1 : 0;
         int G = pl.split ? std::max(1, std::min(gmax, IA / 4)) : std::max(1, std::min(gmax, maxns));
+        {  // the unit's G_{A,k} and G_{l2,k} tables, staged in shared memory when small
+            const long long ge = static_cast<long long>(pl.R1) * IA + (pl.l2 >= 0 ? pl.Rl2 * s.I[pl.l2] : 0);
+            pl.gtab_smem = ge * sz <= 48 * 1024 ? 1 : 0;
+            pl.gtab_elems = pl.gtab_smem ? static_cast<int>(ge) : 0;
+        }
         for (;;) {
             const int GS = pl.split ? 1 : G;
             int TAc = std::max(1, std::min(IA, STAGE_BYTES / (GS * IB * sz)));
             const int nthr = 256;
-            const int sub = round_up(TAc * IB + 32 / sz, 16 / sz);
+            const int SL = round_up(TAc + 32 / sz, 16 / sz);
+            const int sub = round_up(TAc * IB + 32 / sz, 16 / sz) + 3 * SL;
             const long long smem = 128 + static_cast<long long>(NSTAGES) * GS * sub * sz +
                                    static_cast<long long>(GS) * TAc * (pl.R1 | 1) * sz +
-                                   static_cast<long long>(nthr) * pl.Qp * sz;
+                                   static_cast<long long>(nthr) * pl.Qp * sz +
+                                   static_cast<long long>(pl.gtab_elems) * sz;
+            pl.aux_slot = SL;
             if (smem <= SMEM_LIMIT || G == 1) {
                 pl.TA = TB;
                 pl.TAc = TAc;
@@ -375,13 +383,22 @@ ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>&
     // a unit with a single slab and no register fold: the groups split its columns
     pl.split = (maxns == 1 && pl.Rl2 == 1 && (pl.l2 < 0 || isF)) ? 1 : 0;
     int G = pl.split ? std::max(1, std::min(std::max(1, 256 / TA), IB / 4)) : std::max(1, std::min(gmax, maxns));
+    {  // the unit's G_{B,k}, G_{l2,k} and (CASE_F) G_{A,k} tables
+        const long long ge = static_cast<long long>(pl.R1) * IB + (pl.l2 >= 0 ? pl.Rl2 * s.I[pl.l2] : 0) +
+                             (isF ? static_cast<long long>(pl.RA) * IA : 0);
+        pl.gtab_smem = ge * sz <= 48 * 1024 ? 1 : 0;
+        pl.gtab_elems = pl.gtab_smem ? static_cast<int>(ge) : 0;
+    }
     for (;;) {
         const int GS = pl.split ? 1 : G;
         const int nthr = 256;
         const int nwarp = nthr / 32;
-        const int sub = round_up(TA * IB + 32 / sz, 16 / sz);
+        const int SL = round_up(std::max(IB, TA) + 32 / sz, 16 / sz);
+        const int sub = round_up(TA * IB + 32 / sz, 16 / sz) + 3 * SL;
+        pl.aux_slot = SL;
         long long smem = 128 + static_cast<long long>(NSTAGES) * GS * sub * sz +
-                         static_cast<long long>(GS) * IB * (pl.R1 | 1) * sz;
+                         static_cast<long long>(GS) * IB * (pl.R1 | 1) * sz +
+                         static_cast<long long>(pl.gtab_elems) * sz;
         if (isF)
             smem += static_cast<long long>(TA) * IB * sz + static_cast<long long>(nwarp + 1) * pl.Q * sz;
         else
@@ -622,10 +639,8 @@ struct Engine : ifctn_ctx {
         rs = refresh_factors();
         if (rs != IFCTN_OK) return rs;
         CK(cudaStreamSynchronize(st));
-        rs = build_graph();
-        if (rs != IFCTN_OK) return rs;
         setup_persistent();
-        return IFCTN_OK;
+        return build_graph();
     }
 
     // The whole run in one cooperative launch when the grid fits co-resident.
@@ -683,20 +698,22 @@ struct Engine : ifctn_ctx {
         pp.tstamp = tstamp.p;
         {
             // X-update work units: row ranges of slabs, about 4 per CTA
-            const long long target_units = 4LL * num_sms();
+            // contiguous row ranges of 2K..16K entries, about 4 units per CTA
+            const long long target_units = 4LL * 2 * num_sms();
             const long long rows_total = static_cast<long long>(sh.nF) * sh.IA;
             long long rows = std::max<long long>(1, rows_total / target_units);
-            rows = std::max<long long>(rows, std::max(1, 2048 / sh.IB));  // >= ~2K entries per unit
-            rows = std::min<long long>(rows, sh.IA);
+            rows = std::max<long long>(rows, std::max(1, 2048 / sh.IB));
             rows = std::min<long long>(rows, std::max(1, 16384 / sh.IB));
-            // equal row ranges per slab
-            const long long nac = (sh.IA + rows - 1) / rows;
-            rows = (sh.IA + nac - 1) / nac;
+            rows = std::min<long long>(rows, rows_total);
             pp.xu_rows = static_cast<int>(std::max<long long>(rows, 1));
             pp.xu_wab_smem = static_cast<long long>(sh.IA) * sh.IB * sizeof(T) <= 64 * 1024 ? 1 : 0;
         }
         psmem = persistent_smem_bytes<T>(pp);
         persistent = false;
+        // One launch per run pays off when the tensor stays in L2 and the
+        // phases are latency-bound; HBM-sized tensors stream better through
+        // the per-stage kernels at full occupancy (graph path).
+        if (sh.P * static_cast<long long>(sizeof(T)) > L2_RESIDENT_BYTES) return;
         if (psmem > 227 * 1024) return;
         int g = persistent_max_grid<T>(psmem);
         if (grid_cap > 0) g = std::min(g, grid_cap);
@@ -796,15 +813,14 @@ struct Engine : ifctn_ctx {
                 cudaSuccess)
                 return e;
         }
-        if ((e = launch_xupdate<T>(sh, prob.rho, X.p, maskbits.p, W.p, xpart.p, xblocks, done(), st)) !=
-            cudaSuccess)
-            return e;
-        if (logm && truth)
-            if ((e = launch_metrics<T>(sh, X.p, Xt.p, maskbits.p, mpart.p, xblocks, done(), st)) != cudaSuccess)
-                return e;
-        return launch_finalize(xpart.p, xblocks, (logm && truth) ? mpart.p : nullptr, xblocks, nmiss, tol.p,
-                               log.p, LOG_CAP, counter(), done(), flags(), st);
+        pp.Xt = (logm && truth) ? Xt.p : nullptr;
+        const int xb = slab_xblocks();
+        if ((e = launch_xupdate_slab<T>(pp, xpart.p, xb, st)) != cudaSuccess) return e;
+        return launch_finalize8(xpart.p, xb, (logm && truth) ? 1 : 0, nmiss, tol.p, log.p, LOG_CAP, counter(),
+                                done(), flags(), st);
     }
+
+    int slab_xblocks() const { return static_cast<int>(std::min<long long>(xpart.n / 8, 8LL * num_sms())); }
 
     int count_launches() const {
         int n = 0;
@@ -814,7 +830,6 @@ struct Engine : ifctn_ctx {
             n += 3;                                 // contract, finish, solve
         }
         n += 2;  // xupdate, finalize
-        if (logm && truth) n += 1;
         return n;
     }
     int kernels_per_sweep() const override { return launches; }
@@ -946,6 +961,7 @@ struct Engine : ifctn_ctx {
     void set_grid_cap(int g) override {
         grid_cap = g;
         setup_persistent();
+        build_graph();
     }
 
     ifctn_status launch_stage(int stage, int k) override {
@@ -957,7 +973,7 @@ struct Engine : ifctn_ctx {
             case 0: CK(launch_contract<T>(cargs(k), st)); break;
             case 1: CK(launch_gram<T>(sh, k, Gt.p, W.p, t1.p, t2.p, Kk.p, done(), st)); break;
             case 2: CK(launch_solve<T>(sh, k, prob.rho, Kk.p, Mk[k].p, Gd.p, Gt.p, W.p, flags(), done(), st)); break;
-            case 3: CK(launch_xupdate<T>(sh, prob.rho, X.p, maskbits.p, W.p, xpart.p, xblocks, done(), st)); break;
+            case 3: CK(launch_xupdate_slab<T>(pp, xpart.p, slab_xblocks(), st)); break;
             default: set_error("unknown stage"); return IFCTN_EINVAL;
         }
         return IFCTN_OK;
@@ -1026,6 +1042,7 @@ struct Engine : ifctn_ctx {
         }
         logm = lg != 0;
         CK(cudaStreamSynchronize(st));
+        pp.Xt = (logm && truth) ? Xt.p : nullptr;
         return build_graph();
     }
 

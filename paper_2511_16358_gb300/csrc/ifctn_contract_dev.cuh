@@ -1,6 +1,14 @@
 // ifctn_contract_dev.cuh -- per-unit device code of the streaming mode-k
-// contraction M_k = X_(k) Z_k (see ifctn_contract.cu for the design).  Used by
-// the standalone contraction kernels and by the persistent sweep kernel.
+// contraction M_k = X_(k) Z_k (design notes in ifctn_contract_kernels.cuh).
+// Used by the standalone contraction kernels and by the persistent sweep
+// kernel.
+//
+// Every pipeline stage is one mbarrier phase fed by 1-D TMA bulk copies: the
+// X tile of each slab of the stage plus the few short W vectors that slab
+// needs (the rows of W_{p,B} or W_{p,A} that build the coefficient table, the
+// row of W_{o,A} of the level-2 weight, or the scalar W_{0,1}(i0,i1)).  The
+// static G_{m,k} tables are staged once per unit.  So no global load sits on
+// the per-stage path: a stage waits only for its own bulk copies.
 #pragma once
 #include "ifctn_launch.h"
 
@@ -17,45 +25,90 @@ __device__ __forceinline__ void decode_f(const Shape& s, long long f, int& i0, i
     }
 }
 
-// Level-2 fold shared by CASE_A and COL: z(r2, r) += coef(r2) * u(r), where
-// r2 runs over mode l2 (mode 1 for N = 4, mode 0 for N = 3) and coef carries
-// G_{l2,k} and, for N = 4, the pair matrix W_{0,1}.
-template <typename T, int R>
-__device__ __forceinline__ void fold_outer(const Shape& s, const T* Gt, const T* W, int k, int l2,
-                                           int Rl2, int i0, int i1, const T (&u)[R],
-                                           T (&z)[RMAX][R]) {
-    if (l2 < 0) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) z[0][r] += u[r];
-    } else if (s.N == 4) {
-        const T w01 = W[s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1];
-#pragma unroll
-        for (int r2 = 0; r2 < RMAX; ++r2)
-            if (r2 < Rl2) {
-                const T c = gfac(Gt, s, 1, k, r2, i1) * w01;
-#pragma unroll
-                for (int r = 0; r < R; ++r) z[r2][r] = fma(c, u[r], z[r2][r]);
-            }
-    } else if (s.N == 3) {
-#pragma unroll
-        for (int r2 = 0; r2 < RMAX; ++r2)
-            if (r2 < Rl2) {
-                const T c = gfac(Gt, s, 0, k, r2, i0);
-#pragma unroll
-                for (int r = 0; r < R; ++r) z[r2][r] = fma(c, u[r], z[r2][r]);
-            }
-    } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) z[0][r] += u[r];
-    }
+// Byte range [lo, hi) covering elements [p, p+n) rounded out to 16 bytes.
+template <typename T>
+__device__ __forceinline__ void range16(const T* p, long long n, uintptr_t& lo, uintptr_t& hi) {
+    lo = reinterpret_cast<uintptr_t>(p) & ~uintptr_t(15);
+    hi = (reinterpret_cast<uintptr_t>(p + n) + 15) & ~uintptr_t(15);
 }
 
-// Byte range [lo, hi) covering elements [e0, e0+n) rounded out to 16 bytes.
 template <typename T>
-__device__ __forceinline__ void tile_range(const T* X, long long e0, long long n, uintptr_t& lo,
-                                           uintptr_t& hi) {
-    lo = reinterpret_cast<uintptr_t>(X + e0) & ~uintptr_t(15);
-    hi = (reinterpret_cast<uintptr_t>(X + e0 + n) + 15) & ~uintptr_t(15);
+__device__ __forceinline__ int shift16(const T* p) {
+    return static_cast<int>((reinterpret_cast<uintptr_t>(p) & 15) / sizeof(T));
+}
+
+// Short W vectors a slab's stage carries (element offsets into W, lengths).
+struct Aux {
+    int n;
+    long long off[3];
+    int len[3];
+};
+
+// ROW kind (k != N-1): the psi rows W_{p,B}(i_p, :) for F modes p != k, then
+// (CASE_F, N = 4) the row W_{o,A}(i_o, a0:a0+na), or (CASE_A, N = 4) W_{0,1}(i0,i1).
+__device__ __forceinline__ Aux row_aux(const Shape& s, int k, bool isF, long long f, int a0, int na) {
+    int i0, i1;
+    decode_f(s, f, i0, i1);
+    const int N = s.N, Am = N - 2, Bm = N - 1;
+    Aux a;
+    a.n = 0;
+    if (N >= 3 && k != 0) {
+        a.off[a.n] = s.woff[0][Bm] + static_cast<long long>(i0) * s.IB;
+        a.len[a.n++] = s.IB;
+    }
+    if (N == 4 && k != 1) {
+        a.off[a.n] = s.woff[1][Bm] + static_cast<long long>(i1) * s.IB;
+        a.len[a.n++] = s.IB;
+    }
+    if (isF && N == 4) {
+        const int o = 1 - k, io = o == 0 ? i0 : i1;
+        a.off[a.n] = s.woff[o][Am] + static_cast<long long>(io) * s.IA + a0;
+        a.len[a.n++] = na;
+    }
+    if (!isF && N == 4) {
+        a.off[a.n] = s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1;
+        a.len[a.n++] = 1;
+    }
+    return a;
+}
+
+// COL kind (k = N-1): the phi rows W_{p,A}(i_p, a0:a0+na) for every F mode p,
+// then (N = 4) W_{0,1}(i0,i1).
+__device__ __forceinline__ Aux col_aux(const Shape& s, long long f, int a0, int na) {
+    int i0, i1;
+    decode_f(s, f, i0, i1);
+    const int N = s.N, Am = N - 2;
+    Aux a;
+    a.n = 0;
+    if (N >= 3) {
+        a.off[a.n] = s.woff[0][Am] + static_cast<long long>(i0) * s.IA + a0;
+        a.len[a.n++] = na;
+    }
+    if (N == 4) {
+        a.off[a.n] = s.woff[1][Am] + static_cast<long long>(i1) * s.IA + a0;
+        a.len[a.n++] = na;
+        a.off[a.n] = s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1;
+        a.len[a.n++] = 1;
+    }
+    return a;
+}
+
+// Issues the bulk copies of one slab (X tile + aux vectors) into sub-buffer
+// `sub` and returns their byte count (count_only: nothing is copied).
+template <typename T>
+__device__ __forceinline__ unsigned slab_copies(const T* X, const T* W, long long e0, long long n, const Aux& ax,
+                                                T* sub, int xcap, int SL, uint64_t* bar, bool count_only) {
+    uintptr_t lo, hi;
+    range16(X + e0, n, lo, hi);
+    unsigned total = static_cast<unsigned>(hi - lo);
+    if (!count_only) bulk_g2s(sub, reinterpret_cast<const void*>(lo), static_cast<unsigned>(hi - lo), bar);
+    for (int j = 0; j < ax.n; ++j) {
+        range16(W + ax.off[j], ax.len[j], lo, hi);
+        total += static_cast<unsigned>(hi - lo);
+        if (!count_only)
+            bulk_g2s(sub + xcap + j * SL, reinterpret_cast<const void*>(lo), static_cast<unsigned>(hi - lo), bar);
+    }
+    return total;
 }
 
 // Bounded drain of stages issued but never consumed (error path only).
@@ -69,11 +122,13 @@ static __device__ void drain(uint64_t* bars, int S, int from, int to, int* flags
 }
 
 // ---------------------------------------------------------------------------
-// ROW kernel: k in F (CASE_F) or k = N-2 (CASE_A)
+// ROW kind: k in F (CASE_F) or k = N-2 (CASE_A).  A thread owns row a of the
+// slab tile, contracts the contiguous mode B in registers (u, RB values) and
+// folds the row into z over the level-2 mode.
 // ---------------------------------------------------------------------------
 template <typename T, int RB>
 __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const int uidx, unsigned char* smem,
-                                  uint64_t* bars, int& pipe, int* wtag) {
+                                               uint64_t* bars, int& pipe, int* wtag) {
     const Shape& s = A.sh;
     const ContractPlan& pl = A.pl;
     const int N = s.N, k = A.k, IA = s.IA, IB = s.IB;
@@ -86,13 +141,25 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
     const int g = tid / TA, al = tid - g * TA;
     const bool in_grid = g < G;
-
     const bool split = pl.split != 0;
     const int GS = split ? 1 : G;  // slabs per stage
+    const int SL = pl.aux_slot, xcap = pl.sub_elems - 3 * SL;
+    const int npsi = (N >= 3 && k != 0 ? 1 : 0) + (N == 4 && k != 1 ? 1 : 0);
+
     T* stage = reinterpret_cast<T*>(smem);
     T* psi = stage + static_cast<size_t>(S) * GS * pl.sub_elems;
     T* wab = psi + static_cast<size_t>(GS) * IB * RBP;
     T* red = wab + (isF ? static_cast<size_t>(TA) * IB : 0);
+    T* outs = red + static_cast<size_t>(nwarp) * pl.Q;
+    T* gtab = red + (isF ? static_cast<size_t>(nwarp + 1) * pl.Q : static_cast<size_t>(nthr) * pl.Qp);
+    const int l2 = pl.l2;
+    const int nB = pl.R1 * IB;
+    const int nL = l2 >= 0 ? pl.Rl2 * s.I[l2] : 0;
+    const int nA = isF ? pl.RA * IA : 0;
+    const bool gsm = pl.gtab_smem != 0;
+    const T* gB = gsm ? gtab : A.Gt + s.goff[Bm][k];
+    const T* gL = l2 >= 0 ? (gsm ? gtab + nB : A.Gt + s.goff[l2][k]) : nullptr;
+    const T* gA = isF ? (gsm ? gtab + nB + nL : A.Gt + s.goff[Am][k]) : nullptr;
 
     const int na_tot = u.a1 - u.a0;
     const int npass = (na_tot + TA - 1) / TA;
@@ -101,11 +168,6 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
     // split mode: group g covers columns [bg0, bg1) of every row
     const int bg0 = split ? static_cast<int>(static_cast<long long>(IB) * g / G) : 0;
     const int bg1 = split ? static_cast<int>(static_cast<long long>(IB) * (g + 1) / G) : IB;
-
-    T* outs = red + static_cast<size_t>(nwarp) * pl.Q;
-    if (isF)
-        for (int q = tid; q < pl.Q; q += nthr) outs[q] = T(0);
-    __syncthreads();
 
     auto issue = [&](int it) {
         const int p = it / nbatch, bt = it - p * nbatch;
@@ -116,21 +178,28 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
         unsigned total = 0;
         for (int gg = 0; gg < gmax; ++gg) {
             const long long f = u.f0 + static_cast<long long>(bt * GS + gg) * u.fstride;
-            uintptr_t lo, hi;
-            tile_range(A.X, (f * IA + a0) * IB, static_cast<long long>(na) * IB, lo, hi);
-            total += static_cast<unsigned>(hi - lo);
+            const Aux ax = row_aux(s, k, isF, f, a0, na);
+            total += slab_copies(A.X, A.W, (f * IA + a0) * IB, static_cast<long long>(na) * IB, ax, stage, xcap,
+                                 SL, &bars[buf], true);
         }
         mbar_arrive_expect_tx(&bars[buf], total);
         for (int gg = 0; gg < gmax; ++gg) {
             const long long f = u.f0 + static_cast<long long>(bt * GS + gg) * u.fstride;
-            uintptr_t lo, hi;
-            tile_range(A.X, (f * IA + a0) * IB, static_cast<long long>(na) * IB, lo, hi);
-            bulk_g2s(stage + (static_cast<size_t>(buf) * GS + gg) * pl.sub_elems,
-                     reinterpret_cast<const void*>(lo), static_cast<unsigned>(hi - lo), &bars[buf]);
+            const Aux ax = row_aux(s, k, isF, f, a0, na);
+            slab_copies(A.X, A.W, (f * IA + a0) * IB, static_cast<long long>(na) * IB, ax,
+                        stage + (static_cast<size_t>(buf) * GS + gg) * pl.sub_elems, xcap, SL, &bars[buf], false);
         }
     };
     if (tid == 0)
         for (int it = 0; it < min(S, nst); ++it) issue(it);
+    if (isF)
+        for (int q = tid; q < pl.Q; q += nthr) outs[q] = T(0);
+    if (gsm) {
+        stage_async(gtab, A.Gt + s.goff[Bm][k], nB);
+        if (nL) stage_async(gtab + nB, A.Gt + s.goff[l2][k], nL);
+        if (nA) stage_async(gtab + nB + nL, A.Gt + s.goff[Am][k], nA);
+    }
+    stage_wait();
 
     T z[RMAX][RB];
 #pragma unroll
@@ -151,42 +220,41 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
         const int gsl = split ? 0 : g;  // this thread's slab within the stage
         const int sidx = bt * GS + gsl;
         const bool has = in_grid && sidx < u.ns;
-        long long f = 0;
-        int i0 = 0, i1 = 0;
-        if (has) {
-            f = u.f0 + static_cast<long long>(sidx) * u.fstride;
-            decode_f(s, f, i0, i1);
-        }
-        // psi(b, r) = prod_{p in F, p != k} W_{p,B}(i_p, b) * G_{B,k}(r, b)
-        if (split ? (bt < u.ns) : has) {
-            if (split && !has) {  // padding threads help fill the shared table
-                f = u.f0 + static_cast<long long>(bt) * u.fstride;
-                decode_f(s, f, i0, i1);
-            }
-            T* pg = psi + static_cast<size_t>(gsl) * IB * RBP;
-            const int t0 = split ? tid : al, tst = split ? nthr : TA;
-#pragma unroll 4
-            for (int idx = t0; idx < IB * RB; idx += tst) {
-                const int b = idx / RB, r = idx - b * RB;
-                T om = T(1);
-                if (N >= 3 && k != 0) om *= A.W[s.woff[0][Bm] + static_cast<long long>(i0) * IB + b];
-                if (N == 4 && k != 1) om *= A.W[s.woff[1][Bm] + static_cast<long long>(i1) * IB + b];
-                pg[b * RBP + r] = om * gfac(A.Gt, s, Bm, k, r, b);
-            }
-        }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();
-        if (wload && wtag && tid == 0) *wtag = (na == TA) ? a0 + 1 : 0;
         const bool ok = mbar_wait_bounded(&bars[buf], par, A.flags);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) drain(bars, S, pipe + it + 1, pipe + min(nst, it + S), A.flags);
             return false;
         }
+        // psi(b, r) = prod_{p in F, p != k} W_{p,B}(i_p, b) * G_{B,k}(r, b), from
+        // the rows the stage brought along
+        {
+            const bool build = split ? (bt < u.ns) : has;
+            if (build) {
+                const long long fb = u.f0 + static_cast<long long>(bt * GS + gsl) * u.fstride;
+                const Aux ax = row_aux(s, k, isF, fb, a0, na);
+                const T* sub = stage + (static_cast<size_t>(buf) * GS + gsl) * pl.sub_elems;
+                const T* w0 = npsi > 0 ? sub + xcap + shift16(A.W + ax.off[0]) : nullptr;
+                const T* w1 = npsi > 1 ? sub + xcap + SL + shift16(A.W + ax.off[1]) : nullptr;
+                T* pg = psi + static_cast<size_t>(gsl) * IB * RBP;
+                const int t0 = split ? tid : al, tst = split ? nthr : TA;
+                for (int idx = t0; idx < IB * RB; idx += tst) {
+                    const int b = idx / RB, r = idx - b * RB;
+                    T om = T(1);
+                    if (npsi > 0) om *= w0[b];
+                    if (npsi > 1) om *= w1[b];
+                    pg[b * RBP + r] = om * gB[r * IB + b];
+                }
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+        if (wload && wtag && tid == 0) *wtag = (na == TA) ? a0 + 1 : 0;
         if (has && al < na) {
-            const long long e0 = (f * IA + a0) * IB;
-            const int shift = static_cast<int>((reinterpret_cast<uintptr_t>(A.X + e0) & 15) / sizeof(T));
-            const T* xr = stage + (static_cast<size_t>(buf) * GS + gsl) * pl.sub_elems + shift +
-                          static_cast<size_t>(al) * IB;
+            const long long f = u.f0 + static_cast<long long>(sidx) * u.fstride;
+            int i0, i1;
+            decode_f(s, f, i0, i1);
+            const T* sub = stage + (static_cast<size_t>(buf) * GS + gsl) * pl.sub_elems;
+            const T* xr = sub + shift16(A.X + (f * IA + a0) * IB) + static_cast<size_t>(al) * IB;
             const T* pg = psi + static_cast<size_t>(gsl) * IB * RBP;
             T uu[RB];
 #pragma unroll
@@ -207,22 +275,6 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
 #pragma unroll
                     for (int r = 0; r < RB; ++r) uu[r] = fma(x, pr[r], uu[r]);
                 }
-                if (N == 4) {
-                    // coef(r2) = G_{o,k}(r2, i_o) W_{o,A}(i_o, a), o = the other F mode
-                    const int o = 1 - k;
-                    const int io = o == 0 ? i0 : i1;
-                    const T alpha = A.W[s.woff[o][Am] + static_cast<long long>(io) * IA + a0 + al];
-#pragma unroll
-                    for (int r2 = 0; r2 < RMAX; ++r2)
-                        if (r2 < pl.Rl2) {
-                            const T c = gfac(A.Gt, s, o, k, r2, io) * alpha;
-#pragma unroll
-                            for (int r = 0; r < RB; ++r) z[r2][r] = fma(c, uu[r], z[r2][r]);
-                        }
-                } else {
-#pragma unroll
-                    for (int r = 0; r < RB; ++r) z[0][r] += uu[r];
-                }
             } else {
                 for (int b = bst; b < bg1; ++b) {
                     const T x = xr[b];
@@ -236,7 +288,33 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
 #pragma unroll
                     for (int r = 0; r < RB; ++r) uu[r] = fma(x, pr[r], uu[r]);
                 }
-                fold_outer<T, RB>(s, A.Gt, A.W, k, pl.l2, pl.Rl2, i0, i1, uu, z);
+            }
+            // level-2 fold: z(r2, r) += coef(r2) u(r)
+            if (l2 < 0) {
+#pragma unroll
+                for (int r = 0; r < RB; ++r) z[0][r] += uu[r];
+            } else {
+                const Aux ax = row_aux(s, k, isF, f, a0, na);
+                T scale = T(1);
+                int il2;
+                if (isF) {  // N = 4: coef = G_{o,k}(r2, i_o) W_{o,A}(i_o, a)
+                    il2 = l2 == 0 ? i0 : i1;
+                    scale = (sub + xcap + npsi * SL + shift16(A.W + ax.off[npsi]))[al];
+                } else if (N == 4) {  // coef = G_{1,k}(r2, i1) W_{0,1}(i0, i1)
+                    il2 = i1;
+                    scale = (sub + xcap + npsi * SL + shift16(A.W + ax.off[npsi]))[0];
+                } else {  // N = 3: coef = G_{0,k}(r2, i0)
+                    il2 = i0;
+                }
+                const T* gl = gL + il2;
+                const int Il2 = s.I[l2];
+#pragma unroll
+                for (int r2 = 0; r2 < RMAX; ++r2)
+                    if (r2 < pl.Rl2) {
+                        const T c = gl[r2 * Il2] * scale;
+#pragma unroll
+                        for (int r = 0; r < RB; ++r) z[r2][r] = fma(c, uu[r], z[r2][r]);
+                    }
             }
         }
         __syncthreads();
@@ -248,10 +326,9 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
             const bool act = in_grid && al < na;
             if (isF) {
                 // out(r2, rA, rB) += sum_a G_{A,k}(rA, a) z_a(r2, rB)
-                T gA[RMAX];
+                T gAv[RMAX];
 #pragma unroll
-                for (int rA = 0; rA < RMAX; ++rA)
-                    gA[rA] = (act && rA < pl.RA) ? gfac(A.Gt, s, Am, k, rA, a0 + al) : T(0);
+                for (int rA = 0; rA < RMAX; ++rA) gAv[rA] = (act && rA < pl.RA) ? gA[rA * IA + a0 + al] : T(0);
                 T* wsum = red;
 #pragma unroll
                 for (int r2 = 0; r2 < RMAX; ++r2)
@@ -261,7 +338,7 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
                             if (rA < pl.RA)
 #pragma unroll
                                 for (int r = 0; r < RB; ++r) {
-                                    const T v = warp_sum(gA[rA] * z[r2][r]);
+                                    const T v = warp_sum(gAv[rA] * z[r2][r]);
                                     if (lane == 0) wsum[warp * pl.Q + (r2 * pl.RA + rA) * RB + r] = v;
                                 }
                 __syncthreads();
@@ -302,11 +379,12 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
 }
 
 // ---------------------------------------------------------------------------
-// COL kernel: k = N-1 (the contiguous mode is the output index)
+// COL kind: k = N-1 (the contiguous mode is the output index).  A thread owns
+// column b, contracts mode A in registers and folds each slab into z.
 // ---------------------------------------------------------------------------
 template <typename T, int RA>
 __device__ __noinline__ bool contract_col_unit(const ContractArgs<T>& A, const int uidx, unsigned char* smem,
-                                  uint64_t* bars, int& pipe) {
+                                               uint64_t* bars, int& pipe) {
     const Shape& s = A.sh;
     const ContractPlan& pl = A.pl;
     const int N = s.N, k = A.k, IA = s.IA, IB = s.IB;
@@ -319,19 +397,26 @@ __device__ __noinline__ bool contract_col_unit(const ContractArgs<T>& A, const i
     const bool in_grid = g < G;
     const int b = u.b0 + bl;
     const bool colok = in_grid && b < u.b1;
-
     const bool split = pl.split != 0;
     const int GS = split ? 1 : G;  // slabs per stage
+    const int SL = pl.aux_slot, xcap = pl.sub_elems - 3 * SL;
+    const int nphi = (N >= 3 ? 1 : 0) + (N == 4 ? 1 : 0);
+
     T* stage = reinterpret_cast<T*>(smem);
     T* phi = stage + static_cast<size_t>(S) * GS * pl.sub_elems;
     T* red = phi + static_cast<size_t>(GS) * TAc * RAP;
+    T* gtab = red + static_cast<size_t>(nthr) * pl.Qp;
+    const int l2 = pl.l2;
+    const int nAg = pl.R1 * IA;
+    const int nL = l2 >= 0 ? pl.Rl2 * s.I[l2] : 0;
+    const bool gsm = pl.gtab_smem != 0;
+    const T* gAt = gsm ? gtab : A.Gt + s.goff[Am][k];
+    const T* gL = l2 >= 0 ? (gsm ? gtab + nAg : A.Gt + s.goff[l2][k]) : nullptr;
 
     const int na_tot = u.a1 - u.a0;
     const int nch = (na_tot + TAc - 1) / TAc;
     const int nbatch = (u.ns + GS - 1) / GS;
     const int nst = nbatch * nch;
-
-    __syncthreads();
 
     auto issue = [&](int it) {
         const int bt = it / nch, c = it - bt * nch;
@@ -342,21 +427,25 @@ __device__ __noinline__ bool contract_col_unit(const ContractArgs<T>& A, const i
         unsigned total = 0;
         for (int gg = 0; gg < gmax; ++gg) {
             const long long f = u.f0 + static_cast<long long>(bt * GS + gg) * u.fstride;
-            uintptr_t lo, hi;
-            tile_range(A.X, (f * IA + a0) * IB, static_cast<long long>(na) * IB, lo, hi);
-            total += static_cast<unsigned>(hi - lo);
+            const Aux ax = col_aux(s, f, a0, na);
+            total += slab_copies(A.X, A.W, (f * IA + a0) * IB, static_cast<long long>(na) * IB, ax, stage, xcap,
+                                 SL, &bars[buf], true);
         }
         mbar_arrive_expect_tx(&bars[buf], total);
         for (int gg = 0; gg < gmax; ++gg) {
             const long long f = u.f0 + static_cast<long long>(bt * GS + gg) * u.fstride;
-            uintptr_t lo, hi;
-            tile_range(A.X, (f * IA + a0) * IB, static_cast<long long>(na) * IB, lo, hi);
-            bulk_g2s(stage + (static_cast<size_t>(buf) * GS + gg) * pl.sub_elems,
-                     reinterpret_cast<const void*>(lo), static_cast<unsigned>(hi - lo), &bars[buf]);
+            const Aux ax = col_aux(s, f, a0, na);
+            slab_copies(A.X, A.W, (f * IA + a0) * IB, static_cast<long long>(na) * IB, ax,
+                        stage + (static_cast<size_t>(buf) * GS + gg) * pl.sub_elems, xcap, SL, &bars[buf], false);
         }
     };
     if (tid == 0)
         for (int it = 0; it < min(S, nst); ++it) issue(it);
+    if (gsm) {
+        stage_async(gtab, A.Gt + s.goff[Am][k], nAg);
+        if (nL) stage_async(gtab + nAg, A.Gt + s.goff[l2][k], nL);
+    }
+    stage_wait();
 
     T z[RMAX][RA], uu[RA];
 #pragma unroll
@@ -375,40 +464,37 @@ __device__ __noinline__ bool contract_col_unit(const ContractArgs<T>& A, const i
         const int gsl = split ? 0 : g;
         const int sidx = bt * GS + gsl;
         const bool has = in_grid && sidx < u.ns;
-        long long f = 0;
-        int i0 = 0, i1 = 0;
-        if (has) {
-            f = u.f0 + static_cast<long long>(sidx) * u.fstride;
-            decode_f(s, f, i0, i1);
-        }
-        // phi(a, r) = prod_{p in F} W_{p,A}(i_p, a) * G_{A,k}(r, a)
-        if (split ? (bt < u.ns) : has) {
-            if (split && !has) {
-                f = u.f0 + static_cast<long long>(bt) * u.fstride;
-                decode_f(s, f, i0, i1);
-            }
-            T* pg = phi + static_cast<size_t>(gsl) * TAc * RAP;
-            const int t0 = split ? tid : bl, tst = split ? nthr : TB;
-#pragma unroll 4
-            for (int idx = t0; idx < na * RA; idx += tst) {
-                const int ar = idx / RA, r = idx - ar * RA;
-                const int a = a0 + ar;
-                T om = T(1);
-                if (N >= 3) om *= A.W[s.woff[0][Am] + static_cast<long long>(i0) * IA + a];
-                if (N == 4) om *= A.W[s.woff[1][Am] + static_cast<long long>(i1) * IA + a];
-                pg[ar * RAP + r] = om * gfac(A.Gt, s, Am, k, r, a);
-            }
-        }
-        __syncthreads();
         const bool ok = mbar_wait_bounded(&bars[buf], par, A.flags);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) drain(bars, S, pipe + it + 1, pipe + min(nst, it + S), A.flags);
             return false;
         }
+        // phi(a, r) = prod_{p in F} W_{p,A}(i_p, a) * G_{A,k}(r, a), from the
+        // rows the stage brought along
+        {
+            const bool build = split ? (bt < u.ns) : has;
+            if (build) {
+                const long long fb = u.f0 + static_cast<long long>(bt * GS + gsl) * u.fstride;
+                const Aux ax = col_aux(s, fb, a0, na);
+                const T* sub = stage + (static_cast<size_t>(buf) * GS + gsl) * pl.sub_elems;
+                const T* w0 = nphi > 0 ? sub + xcap + shift16(A.W + ax.off[0]) : nullptr;
+                const T* w1 = nphi > 1 ? sub + xcap + SL + shift16(A.W + ax.off[1]) : nullptr;
+                T* pg = phi + static_cast<size_t>(gsl) * TAc * RAP;
+                const int t0 = split ? tid : bl, tst = split ? nthr : TB;
+                for (int idx = t0; idx < na * RA; idx += tst) {
+                    const int ar = idx / RA, r = idx - ar * RA;
+                    T om = T(1);
+                    if (nphi > 0) om *= w0[ar];
+                    if (nphi > 1) om *= w1[ar];
+                    pg[ar * RAP + r] = om * gAt[r * IA + a0 + ar];
+                }
+            }
+        }
+        __syncthreads();
         if (has && colok) {
-            const long long e0 = (f * IA + a0) * IB;
-            const int shift = static_cast<int>((reinterpret_cast<uintptr_t>(A.X + e0) & 15) / sizeof(T));
-            const T* xr = stage + (static_cast<size_t>(buf) * GS + gsl) * pl.sub_elems + shift + b;
+            const long long f = u.f0 + static_cast<long long>(sidx) * u.fstride;
+            const T* sub = stage + (static_cast<size_t>(buf) * GS + gsl) * pl.sub_elems;
+            const T* xr = sub + shift16(A.X + (f * IA + a0) * IB) + b;
             const T* pg = phi + static_cast<size_t>(gsl) * TAc * RAP;
             const int ar0 = split ? g : 0, ars = split ? G : 1;
             for (int ar = ar0; ar < na; ar += ars) {
@@ -419,7 +505,33 @@ __device__ __noinline__ bool contract_col_unit(const ContractArgs<T>& A, const i
             }
         }
         if (c == nch - 1) {
-            if (has && colok) fold_outer<T, RA>(s, A.Gt, A.W, k, pl.l2, pl.Rl2, i0, i1, uu, z);
+            if (has && colok) {
+                if (l2 < 0) {
+#pragma unroll
+                    for (int r = 0; r < RA; ++r) z[0][r] += uu[r];
+                } else {
+                    const long long f = u.f0 + static_cast<long long>(sidx) * u.fstride;
+                    int i0, i1;
+                    decode_f(s, f, i0, i1);
+                    T scale = T(1);
+                    int il2 = i0;
+                    if (N == 4) {  // coef = G_{1,k}(r2, i1) W_{0,1}(i0, i1)
+                        const Aux ax = col_aux(s, f, a0, na);
+                        const T* sub = stage + (static_cast<size_t>(buf) * GS + gsl) * pl.sub_elems;
+                        scale = (sub + xcap + nphi * SL + shift16(A.W + ax.off[nphi]))[0];
+                        il2 = i1;
+                    }
+                    const T* gl = gL + il2;
+                    const int Il2 = s.I[l2];
+#pragma unroll
+                    for (int r2 = 0; r2 < RMAX; ++r2)
+                        if (r2 < pl.Rl2) {
+                            const T cf = gl[r2 * Il2] * scale;
+#pragma unroll
+                            for (int r = 0; r < RA; ++r) z[r2][r] = fma(cf, uu[r], z[r2][r]);
+                        }
+                }
+            }
 #pragma unroll
             for (int r = 0; r < RA; ++r) uu[r] = T(0);
         }

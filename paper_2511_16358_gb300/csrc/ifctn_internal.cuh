@@ -67,6 +67,9 @@ struct ContractPlan {
     int split;       // 1: one slab per stage, the G groups split its reduction
                      //    range (ROW: columns b, COL: rows a); 0: groups take
                      //    different slabs
+    int aux_slot;    // elements per auxiliary-vector slot in a stage sub-buffer
+    int gtab_smem;   // 1: the unit's G_{m,k} tables are staged in shared memory
+    int gtab_elems;  // their size (elements)
     int key_div;     // > 0: every unit covers all rows and its deferred key is
                      //      unit / key_div (no descriptor loads in the reduction)
     long long part_elems;

@@ -656,6 +656,51 @@ __global__ void k_finalize(const double* __restrict__ xpart, const int nblocks, 
     }
 }
 
+// Fixed-order reduction of the per-CTA sums of the slab X update (8-double
+// stride: ||X1-X0||^2, ||X0||^2, ||X1-rec||^2, then the three RSE/RMSE sums).
+__global__ void k_finalize8(const double* __restrict__ xpart, const int nblocks, const int met, const long long nmiss,
+                            const double* __restrict__ tolp, SweepStat* __restrict__ log, const int cap,
+                            int* __restrict__ counter, int* __restrict__ done, const int* __restrict__ flags) {
+    if (*done) return;
+    __shared__ double sh[256][6];
+    const int t = threadIdx.x;
+    double a[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = t; b < nblocks; b += blockDim.x)
+        for (int c = 0; c < 6; ++c) a[c] += xpart[8 * b + c];
+    for (int c = 0; c < 6; ++c) sh[t][c] = a[c];
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (t < h)
+            for (int c = 0; c < 6; ++c) sh[t][c] += sh[t + h][c];
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double tol = *tolp;
+        const double dx2 = sh[0][0], x2 = sh[0][1];
+        SweepStat r;
+        r.rel_change = x2 > 0 ? sqrt(dx2) / sqrt(x2) : (dx2 > 0 ? INFINITY : 0.0);
+        r.objective = 0.5 * sh[0][2];
+        if (met) {
+            r.rse = sh[0][4] > 0 ? sqrt(sh[0][3]) / sqrt(sh[0][4]) : NAN;
+            r.rmse = nmiss > 0 ? sqrt(sh[0][5] / static_cast<double>(nmiss)) : 0.0;
+        } else {
+            r.rse = NAN;
+            r.rmse = NAN;
+        }
+        r.dx2 = dx2;
+        r.x2 = x2;
+        const int sidx = *counter;
+        r.sweep = sidx + 1;
+        r.converged = (tol > 0 && r.rel_change < tol) ? 1 : 0;
+        r.flags = *flags;
+        r.pad = 0;
+        if (!isfinite(r.rel_change) || !isfinite(r.objective)) r.flags |= FLAG_NONFINITE;
+        log[sidx % cap] = r;
+        *counter = sidx + 1;
+        if (r.converged) *done = 1;
+    }
+}
+
 __global__ void k_sum_partials(const double* __restrict__ xpart, const int nblocks, const int stride,
                                const int slot, double* __restrict__ out) {
     __shared__ double sh[256];
@@ -764,6 +809,13 @@ cudaError_t launch_finalize(const double* xpart, int nblocks, const double* mpar
                             int* sweep_counter, int* done, const int* flags, cudaStream_t st) {
     k_finalize<<<1, 256, 0, st>>>(xpart, nblocks, mpart, mblocks, nmiss_total, tol, log, log_cap,
                                   sweep_counter, done, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize8(const double* xpart, int nblocks, int met, long long nmiss, const double* tol,
+                             SweepStat* log, int log_cap, int* sweep_counter, int* done, const int* flags,
+                             cudaStream_t st) {
+    k_finalize8<<<1, 256, 0, st>>>(xpart, nblocks, met, nmiss, tol, log, log_cap, sweep_counter, done, flags);
     return cudaGetLastError();
 }
 

@@ -78,6 +78,10 @@ cudaError_t launch_finalize(const double* xpart, int nblocks, const double* mpar
                             long long nmiss_total, const double* tol, SweepStat* log, int log_cap,
                             int* sweep_counter, int* done, const int* flags, cudaStream_t st);
 
+cudaError_t launch_finalize8(const double* xpart, int nblocks, int met, long long nmiss, const double* tol,
+                             SweepStat* log, int log_cap, int* sweep_counter, int* done, const int* flags,
+                             cudaStream_t st);
+
 // Sum of squares of xpart[0] slots (used for the default initial scaling).
 cudaError_t launch_sum_partials(const double* xpart, int nblocks, int stride, int slot,
                                 double* out, cudaStream_t st);

@@ -801,12 +801,13 @@ __device__ __forceinline__ void xacc(const SweepParams<T>& p, const T rho, const
     }
 }
 
-// eq. (updateX) over the slab geometry: a work unit is a row range of one
-// slab; the slab's factors alpha(a) = prod_{p in F} W_{p,A}(i_p, a),
-// beta(b) = prod_{p in F} W_{p,B}(i_p, b) and C = W_{0,1}(i0, i1) (N = 4) are
-// built once per unit in shared memory, and W_{A,B} is kept in shared memory
-// when it fits, so that iFCTN(G)(i) = C alpha(a) beta(b) W_{A,B}(a, b) costs
-// three shared loads per entry.
+// eq. (updateX) over the slab geometry: a work unit is a contiguous range of
+// rows (row = (slab f, a)), possibly spanning several slabs.  Per unit, the
+// factors alpha(row) = prod_{p in F} W_{p,A}(i_p, a) and, per slab,
+// beta(f, b) = C_f prod_{p in F} W_{p,B}(i_p, b) with C_f = W_{0,1}(i0, i1)
+// (N = 4) are built in shared memory, and W_{A,B} is kept in shared memory
+// when it fits, so that iFCTN(G)(i) = alpha(row) beta(f, b) W_{A,B}(a, b)
+// costs three shared loads per entry.
 template <typename T>
 __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned char* smem) {
     const Shape& s = p.sh;
@@ -814,9 +815,11 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
     const T rho = static_cast<T>(p.rho), inv1p = static_cast<T>(p.inv1p);
     const bool met = p.Xt != nullptr;
     const bool wsm = p.xu_wab_smem != 0;
+    const int RU = p.xu_rows;
+    const int SU = (RU + IA - 1) / IA + 1;  // slabs a unit can touch
     T* wab = reinterpret_cast<T*>(smem);
     T* alpha = wab + (wsm ? IA * IB : 0);
-    T* beta = alpha + p.xu_rows;
+    T* beta = alpha + RU;
     const T* WAB = p.W + s.woff[Am][Bm];
     if (wsm) stage_async(wab, WAB, IA * IB);
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -824,38 +827,58 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
     double acc[6] = {0, 0, 0, 0, 0, 0};
     T fa[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     T run2[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-    const int nac = (IA + p.xu_rows - 1) / p.xu_rows;
-    const long long nunit = static_cast<long long>(s.nF) * nac;
+    const long long rows_total = static_cast<long long>(s.nF) * IA;
+    const long long nunit = (rows_total + RU - 1) / RU;
     for (long long un = blockIdx.x; un < nunit; un += gridDim.x) {
-        const long long f = un / nac;
-        const int a0 = static_cast<int>(un - f * nac) * p.xu_rows;
-        const int na = min(p.xu_rows, IA - a0);
-        int i0 = 0, i1 = 0;
-        if (N == 4) {
-            i0 = static_cast<int>(f / s.I[1]);
-            i1 = static_cast<int>(f - static_cast<long long>(i0) * s.I[1]);
-        } else {
-            i0 = static_cast<int>(f);
-        }
+        const long long r0 = un * RU;
+        const int nr = static_cast<int>(min(static_cast<long long>(RU), rows_total - r0));
+        const long long f0 = r0 / IA;
+        const int a00 = static_cast<int>(r0 - f0 * IA);
+        const int nsl = static_cast<int>((r0 + nr - 1) / IA - f0) + 1;
         __syncthreads();  // previous unit done with alpha / beta
-        for (int a = threadIdx.x; a < na; a += PT) {
+        for (int rl = threadIdx.x; rl < nr; rl += PT) {
+            const long long row = r0 + rl;
+            const long long f = row / IA;
+            const int a = static_cast<int>(row - f * IA);
+            int i0 = 0, i1 = 0;
+            if (N == 4) {
+                i0 = static_cast<int>(f / s.I[1]);
+                i1 = static_cast<int>(f - static_cast<long long>(i0) * s.I[1]);
+            } else {
+                i0 = static_cast<int>(f);
+            }
             T v = T(1);
-            if (N >= 3) v *= p.W[s.woff[0][Am] + static_cast<long long>(i0) * IA + a0 + a];
-            if (N == 4) v *= p.W[s.woff[1][Am] + static_cast<long long>(i1) * IA + a0 + a];
-            alpha[a] = v;
+            if (N >= 3) v *= p.W[s.woff[0][Am] + static_cast<long long>(i0) * IA + a];
+            if (N == 4) v *= p.W[s.woff[1][Am] + static_cast<long long>(i1) * IA + a];
+            alpha[rl] = v;
         }
-        const T cf = N == 4 ? p.W[s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1] : T(1);
-        for (int b = threadIdx.x; b < IB; b += PT) {
-            T v = cf;
+        for (int idx = threadIdx.x; idx < nsl * IB; idx += PT) {
+            const int sl = idx / IB, b = idx - sl * IB;
+            const long long f = f0 + sl;
+            int i0 = 0, i1 = 0;
+            if (N == 4) {
+                i0 = static_cast<int>(f / s.I[1]);
+                i1 = static_cast<int>(f - static_cast<long long>(i0) * s.I[1]);
+            } else {
+                i0 = static_cast<int>(f);
+            }
+            T v = N == 4 ? p.W[s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1] : T(1);
             if (N >= 3) v *= p.W[s.woff[0][Bm] + static_cast<long long>(i0) * IB + b];
             if (N == 4) v *= p.W[s.woff[1][Bm] + static_cast<long long>(i1) * IB + b];
-            beta[b] = v;
+            beta[idx] = v;
         }
         __syncthreads();
-        const long long e0 = (f * IA + a0) * IB;
-        const int n = na * IB;
-        int a = threadIdx.x / IB, b = threadIdx.x - (threadIdx.x / IB) * IB;
-        const int da = PT / IB, db = PT - da * IB;
+        (void)SU;
+        const long long e0 = r0 * IB;
+        const int n = nr * IB;
+        // walker over (row-in-unit, b) and the slab-local row index a
+        int rl = threadIdx.x / IB, b = threadIdx.x - (threadIdx.x / IB) * IB;
+        int a = a00 + rl, sl = 0;
+        while (a >= IA) {
+            a -= IA;
+            ++sl;
+        }
+        const int drl = PT / IB, db = PT - drl * IB;
         // batches of XB entries per thread (stride PT): every load of a batch
         // is issued before any store, so they overlap in flight
         constexpr int XB = 8;
@@ -869,13 +892,19 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
                     const long long e = e0 + o;
                     xo[t] = p.X[e];
                     wd[t] = p.mb[e >> 5];
-                    rec[t] = wab_r[static_cast<long long>(a0 + a) * IB + b] * alpha[a] * beta[b];
+                    rec[t] = wab_r[static_cast<long long>(a) * IB + b] * alpha[rl] * beta[sl * IB + b];
                 }
                 b += db;
-                a += da;
+                int step = drl;
                 if (b >= IB) {
                     b -= IB;
-                    ++a;
+                    ++step;
+                }
+                rl += step;
+                a += step;
+                while (a >= IA) {
+                    a -= IA;
+                    ++sl;
                 }
             }
 #pragma unroll
@@ -923,6 +952,14 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
         out6[threadIdx.x] = v;
     }
     __syncthreads();
+}
+
+// Standalone form of the X update for the per-stage (graph) path.
+template <typename T>
+__global__ void __launch_bounds__(PT) k_xupdate_slab(const SweepParams<T> p, double* __restrict__ xpart) {
+    if (*reinterpret_cast<volatile const int*>(p.done)) return;
+    extern __shared__ __align__(128) unsigned char xsm[];
+    xupdate_phase<T>(p, xpart + 8 * blockIdx.x, xsm);
 }
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -1093,7 +1130,8 @@ int persistent_smem_bytes(const SweepParams<T>& p) {
         }
     }
     // xupdate: W_{A,B} (when kept in shared memory) + alpha + beta
-    need = std::max<long long>(need, (static_cast<long long>(p.xu_wab_smem ? s.IA * s.IB : 0) + p.xu_rows + s.IB) *
+    need = std::max<long long>(need, (static_cast<long long>(p.xu_wab_smem ? s.IA * s.IB : 0) + p.xu_rows +
+                                      static_cast<long long>((p.xu_rows + s.IA - 1) / s.IA + 1) * s.IB) *
                                          sizeof(T));
     return static_cast<int>(need + 128 + 256);
 }
@@ -1103,6 +1141,17 @@ cudaError_t launch_persistent(const SweepParams<T>& p, int grid, int smem, cudaS
     void* args[] = {const_cast<SweepParams<T>*>(&p)};
     return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_sweep_persistent<T>), dim3(grid), dim3(PT), args,
                                        smem, st);
+}
+
+template <typename T>
+cudaError_t launch_xupdate_slab(const SweepParams<T>& p, double* xpart, int nblocks, cudaStream_t st) {
+    const int smem = static_cast<int>((static_cast<long long>(p.xu_wab_smem ? p.sh.IA * p.sh.IB : 0) + p.xu_rows +
+                                       static_cast<long long>((p.xu_rows + p.sh.IA - 1) / p.sh.IA + 1) * p.sh.IB) *
+                                      sizeof(T)) + 64;
+    cudaError_t e = cudaFuncSetAttribute(k_xupdate_slab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_xupdate_slab<T><<<nblocks, PT, smem, st>>>(p, xpart);
+    return cudaGetLastError();
 }
 
 template <typename T>
