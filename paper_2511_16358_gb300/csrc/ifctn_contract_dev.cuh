@@ -127,8 +127,8 @@ static __device__ void drain(uint64_t* bars, int S, int from, int to, int* flags
 // folds the row into z over the level-2 mode.
 // ---------------------------------------------------------------------------
 template <typename T, int RB>
-__device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const int uidx, unsigned char* smem,
-                                               uint64_t* bars, int& pipe, int* wtag) {
+__device__ __forceinline__ bool row_unit_body(const ContractArgs<T>& A, const int uidx, unsigned char* smem,
+                                              uint64_t* bars, int& pipe, int* wtag) {
     const Shape& s = A.sh;
     const ContractPlan& pl = A.pl;
     const int N = s.N, k = A.k, IA = s.IA, IB = s.IB;
@@ -383,8 +383,8 @@ __device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const i
 // column b, contracts mode A in registers and folds each slab into z.
 // ---------------------------------------------------------------------------
 template <typename T, int RA>
-__device__ __noinline__ bool contract_col_unit(const ContractArgs<T>& A, const int uidx, unsigned char* smem,
-                                               uint64_t* bars, int& pipe) {
+__device__ __forceinline__ bool col_unit_body(const ContractArgs<T>& A, const int uidx, unsigned char* smem,
+                                              uint64_t* bars, int& pipe) {
     const Shape& s = A.sh;
     const ContractPlan& pl = A.pl;
     const int N = s.N, k = A.k, IA = s.IA, IB = s.IB;
@@ -558,6 +558,21 @@ __device__ __noinline__ bool contract_col_unit(const ContractArgs<T>& A, const i
     __syncthreads();
     pipe += nst;
     return true;
+}
+
+// Out-of-line entry points used by the persistent kernel (one copy of each
+// body per rank instead of one per call site).  The standalone kernels inline
+// the bodies instead, which leaves them the whole register file.
+template <typename T, int RB>
+__device__ __noinline__ bool contract_row_unit(const ContractArgs<T>& A, const int uidx, unsigned char* smem,
+                                               uint64_t* bars, int& pipe, int* wtag) {
+    return row_unit_body<T, RB>(A, uidx, smem, bars, pipe, wtag);
+}
+
+template <typename T, int RA>
+__device__ __noinline__ bool contract_col_unit(const ContractArgs<T>& A, const int uidx, unsigned char* smem,
+                                               uint64_t* bars, int& pipe) {
+    return col_unit_body<T, RA>(A, uidx, smem, bars, pipe);
 }
 
 }  // namespace cdev

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256) k_contract_row(const ContractArgs<T> A) {
     }
     __syncthreads();
     int pipe = 0;
-    contract_row_unit<T, RB>(A, blockIdx.x, smem + 128, bars, pipe, nullptr);
+    row_unit_body<T, RB>(A, blockIdx.x, smem + 128, bars, pipe, nullptr);
 }
 
 template <typename T, int RA>
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) k_contract_col(const ContractArgs<T> A) {
     }
     __syncthreads();
     int pipe = 0;
-    contract_col_unit<T, RA>(A, blockIdx.x, smem + 128, bars, pipe);
+    col_unit_body<T, RA>(A, blockIdx.x, smem + 128, bars, pipe);
 }
 
 // ---------------------------------------------------------------------------
