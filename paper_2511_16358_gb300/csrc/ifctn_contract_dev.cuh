@@ -15,12 +15,15 @@
 namespace ifctn {
 namespace cdev {
 
+// slab index f (< 2^31) -> F-mode indices, in 32-bit arithmetic
 __device__ __forceinline__ void decode_f(const Shape& s, long long f, int& i0, int& i1) {
+    const int fi = static_cast<int>(f);
     if (s.N == 4) {
-        i0 = static_cast<int>(f / s.I[1]);
-        i1 = static_cast<int>(f - static_cast<long long>(i0) * s.I[1]);
+        const unsigned q = static_cast<unsigned>(fi) / static_cast<unsigned>(s.I[1]);
+        i0 = static_cast<int>(q);
+        i1 = fi - i0 * s.I[1];
     } else {
-        i0 = static_cast<int>(f);
+        i0 = fi;
         i1 = 0;
     }
 }
@@ -93,20 +96,22 @@ __device__ __forceinline__ Aux col_aux(const Shape& s, long long f, int a0, int 
     return a;
 }
 
-// Issues the bulk copies of one slab (X tile + aux vectors) into sub-buffer
-// `sub` and returns their byte count (count_only: nothing is copied).
+// Issues one slab's bulk copies (X tile + aux vectors) into the stage buffer at
+// element offset `base` and returns their byte count.  A stage's copies are
+// issued before its single arrive.expect_tx: the barrier's transaction count may
+// run negative in between, and the phase cannot complete before that arrive
+// (arrival count 1), so the count is armed once with the stage total.
 template <typename T>
 __device__ __forceinline__ unsigned slab_copies(const T* X, const T* W, long long e0, long long n, const Aux& ax,
-                                                T* sub, int xcap, int SL, uint64_t* bar, bool count_only) {
+                                                T* buf, unsigned base, int xcap, int SL, uint64_t* bar) {
     uintptr_t lo, hi;
     range16(X + e0, n, lo, hi);
     unsigned total = static_cast<unsigned>(hi - lo);
-    if (!count_only) bulk_g2s(sub, reinterpret_cast<const void*>(lo), static_cast<unsigned>(hi - lo), bar);
+    bulk_g2s(buf + base, reinterpret_cast<const void*>(lo), static_cast<unsigned>(hi - lo), bar);
     for (int j = 0; j < ax.n; ++j) {
         range16(W + ax.off[j], ax.len[j], lo, hi);
         total += static_cast<unsigned>(hi - lo);
-        if (!count_only)
-            bulk_g2s(sub + xcap + j * SL, reinterpret_cast<const void*>(lo), static_cast<unsigned>(hi - lo), bar);
+        bulk_g2s(buf + base + xcap + j * SL, reinterpret_cast<const void*>(lo), static_cast<unsigned>(hi - lo), bar);
     }
     return total;
 }
@@ -175,20 +180,15 @@ __device__ __forceinline__ bool row_unit_body(const ContractArgs<T>& A, const in
         const int na = min(TA, u.a1 - a0);
         const int buf = (pipe + it) % S;
         const int gmax = min(GS, u.ns - bt * GS);
+        T* sbuf = stage + static_cast<size_t>(buf) * GS * pl.sub_elems;
         unsigned total = 0;
         for (int gg = 0; gg < gmax; ++gg) {
             const long long f = u.f0 + static_cast<long long>(bt * GS + gg) * u.fstride;
             const Aux ax = row_aux(s, k, isF, f, a0, na);
-            total += slab_copies(A.X, A.W, (f * IA + a0) * IB, static_cast<long long>(na) * IB, ax, stage, xcap,
-                                 SL, &bars[buf], true);
+            total += slab_copies(A.X, A.W, (f * IA + a0) * IB, static_cast<long long>(na) * IB, ax, sbuf,
+                                 static_cast<unsigned>(gg * pl.sub_elems), xcap, SL, &bars[buf]);
         }
         mbar_arrive_expect_tx(&bars[buf], total);
-        for (int gg = 0; gg < gmax; ++gg) {
-            const long long f = u.f0 + static_cast<long long>(bt * GS + gg) * u.fstride;
-            const Aux ax = row_aux(s, k, isF, f, a0, na);
-            slab_copies(A.X, A.W, (f * IA + a0) * IB, static_cast<long long>(na) * IB, ax,
-                        stage + (static_cast<size_t>(buf) * GS + gg) * pl.sub_elems, xcap, SL, &bars[buf], false);
-        }
     };
     if (tid == 0)
         for (int it = 0; it < min(S, nst); ++it) issue(it);
@@ -424,20 +424,15 @@ __device__ __forceinline__ bool col_unit_body(const ContractArgs<T>& A, const in
         const int na = min(TAc, u.a1 - a0);
         const int buf = (pipe + it) % S;
         const int gmax = min(GS, u.ns - bt * GS);
+        T* sbuf = stage + static_cast<size_t>(buf) * GS * pl.sub_elems;
         unsigned total = 0;
         for (int gg = 0; gg < gmax; ++gg) {
             const long long f = u.f0 + static_cast<long long>(bt * GS + gg) * u.fstride;
             const Aux ax = col_aux(s, f, a0, na);
-            total += slab_copies(A.X, A.W, (f * IA + a0) * IB, static_cast<long long>(na) * IB, ax, stage, xcap,
-                                 SL, &bars[buf], true);
+            total += slab_copies(A.X, A.W, (f * IA + a0) * IB, static_cast<long long>(na) * IB, ax, sbuf,
+                                 static_cast<unsigned>(gg * pl.sub_elems), xcap, SL, &bars[buf]);
         }
         mbar_arrive_expect_tx(&bars[buf], total);
-        for (int gg = 0; gg < gmax; ++gg) {
-            const long long f = u.f0 + static_cast<long long>(bt * GS + gg) * u.fstride;
-            const Aux ax = col_aux(s, f, a0, na);
-            slab_copies(A.X, A.W, (f * IA + a0) * IB, static_cast<long long>(na) * IB, ax,
-                        stage + (static_cast<size_t>(buf) * GS + gg) * pl.sub_elems, xcap, SL, &bars[buf], false);
-        }
     };
     if (tid == 0)
         for (int it = 0; it < min(S, nst); ++it) issue(it);

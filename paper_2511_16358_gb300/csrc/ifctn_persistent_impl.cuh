@@ -977,7 +977,7 @@ __device__ __forceinline__ unsigned long long gtimer() {
     } while (0)
 
 template <typename T>
-__global__ void __launch_bounds__(PT, 1) k_sweep_persistent(const SweepParams<T> p) {
+__global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const SweepParams<T> p) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     unsigned char* work = smem + 128;
