@@ -29,7 +29,7 @@
  *     fixed for all factor blocks of sweep s; stop when
  *     ||X^{s+1}-X^s||_F / ||X^s||_F < eps or after t_max sweeps.
  *
- * Readings where the paper is silent or garbled (all listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - fit term weighted 1/2 (as the closed form and Lemma 2 imply);
  *   - X^0 = P_Omega(O), zero elsewhere;
  *   - RSE = ||X_true - X|| / ||X_true||, RMSE over the missing entries.
