@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -433,6 +434,264 @@ ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>&
     return pl;
 }
 
+
+// Plan of the warp-pipelined kernels (one CTA of 8 warps per SM, a TMA ring
+// per warp).  Returns warp = 0 when the shape does not fit their shared-memory
+// layout; the CTA kernels then run the mode.
+ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitDesc>& units) {
+    constexpr int NW = 16;
+    ContractPlan pl;
+    memset(&pl, 0, sizeof(pl));
+    const int N = s.N, Am = N - 2, Bm = N - 1, IA = s.IA, IB = s.IB;
+    const int VN = 16 / sz;
+    const int sms = num_sms();
+    const int target = 8 * sms;
+    const int XBYTES = 4 * 1024;  // at most this many X bytes in one task (per warp, per stage)
+    // rows per task: at most cap, split evenly
+    auto balanced = [](int rows, int cap) {
+        cap = std::max(1, std::min(rows, cap));
+        return cdiv(rows, cdiv(rows, cap));
+    };
+    pl.Q = mode_q(s, k);
+    units.clear();
+    auto add = [&](int f0, int fstride, int ns, int key, int a0, int a1, int b0, int b1, int slot) {
+        UnitDesc u;
+        memset(&u, 0, sizeof(u));
+        u.f0 = f0;
+        u.fstride = fstride;
+        u.ns = ns;
+        u.key = key;
+        u.a0 = a0;
+        u.a1 = a1;
+        u.b0 = b0;
+        u.b1 = b1;
+        u.slot = slot;
+        units.push_back(u);
+    };
+    long long tab_elems = 0, gtab_elems = 0, wab_elems = 0, zs_elems = 0, zmin = 0;
+    int xregion = 0;
+    if (k == Bm) {  // COL
+        pl.kcase = CASE_COL;
+        pl.R1 = s.R[k][Am];
+        if (N == 4) {
+            pl.l2 = 1;
+            pl.dmode = 0;
+        } else if (N == 3) {
+            pl.l2 = 0;
+            pl.dmode = -1;
+        } else {
+            pl.l2 = -1;
+            pl.dmode = -1;
+        }
+        pl.Rl2 = pl.l2 >= 0 ? s.R[k][pl.l2] : 1;
+        pl.Qp = pl.Rl2 * pl.R1;
+        pl.zw = pl.Qp;
+        const int nbc = cdiv(IB, 32);
+        pl.vec = 0;
+        pl.ldx = IB;
+        // a lane builds one row of the coefficient table: at most 32 rows a task
+        const int RBK = balanced(IA, std::min(32, std::max(1, XBYTES / (sz * IB))));
+        pl.TAc = RBK;
+        const int nrb = cdiv(IA, RBK);
+        if (N == 4) {
+            const int I0 = s.I[0], I1 = s.I[1];
+            const int nC = std::max(1, std::min(cdiv(target, static_cast<long long>(I0) * nbc),
+                                                std::max(1, I1 * nrb / NW)));
+            for (int i0 = 0; i0 < I0; ++i0)
+                for (int c = 0; c < nC; ++c)
+                    for (int bc = 0; bc < nbc; ++bc) {
+                        int lo, hi;
+                        chunk(I1, nC, c, lo, hi);
+                        if (hi <= lo) continue;
+                        add(i0 * I1 + lo, 1, hi - lo, i0, 0, IA, bc * 32, std::min(IB, bc * 32 + 32), 0);
+                    }
+        } else if (N == 3) {
+            const int I0 = s.I[0];
+            const int nC = std::max(1, std::min(cdiv(target, nbc), std::max(1, I0 * nrb / NW)));
+            for (int c = 0; c < nC; ++c)
+                for (int bc = 0; bc < nbc; ++bc) {
+                    int lo, hi;
+                    chunk(I0, nC, c, lo, hi);
+                    if (hi <= lo) continue;
+                    add(lo, 1, hi - lo, -1, 0, IA, bc * 32, std::min(IB, bc * 32 + 32), 0);
+                }
+        } else {
+            const int nrc = std::max(1, std::min(cdiv(target, nbc), cdiv(nrb, NW)));
+            for (int rc = 0; rc < nrc; ++rc)
+                for (int bc = 0; bc < nbc; ++bc) {
+                    int lo, hi;
+                    chunk(nrb, nrc, rc, lo, hi);
+                    if (hi <= lo) continue;
+                    add(0, 1, 1, -1, lo * RBK, std::min(IA, hi * RBK), bc * 32, std::min(IB, bc * 32 + 32), 0);
+                }
+        }
+        pl.nrow = IB;
+        pl.nunits = static_cast<int>(units.size());
+        pl.part_elems = static_cast<long long>(pl.nunits) * IB * pl.Qp;
+        xregion = round_up(RBK * IB + 32 / sz, VN);
+        tab_elems = static_cast<long long>(NW) * (32 + VN) * pl.R1;
+        gtab_elems = static_cast<long long>(pl.R1) * IA + (pl.l2 >= 0 ? static_cast<long long>(pl.Rl2) * s.I[pl.l2] : 0);
+        zmin = 32LL * pl.zw;
+        pl.aux_slot = 0;
+    } else {  // ROW
+        const bool isF = k < Am;
+        pl.kcase = isF ? CASE_F : CASE_A;
+        pl.R1 = s.R[k][Bm];
+        const bool foldA = isF && N == 3;
+        if (isF) {
+            pl.RA = s.R[k][Am];
+            pl.dmode = -1;
+            if (N == 4) {
+                pl.l2 = 1 - k;
+                pl.Rl2 = s.R[k][pl.l2];
+                pl.zw = pl.Rl2 * pl.R1;
+            } else {
+                pl.l2 = -1;
+                pl.Rl2 = 1;
+                pl.zw = pl.RA * pl.R1;
+            }
+            pl.Qp = pl.Q;
+        } else {
+            if (N == 4) {
+                pl.l2 = 1;
+                pl.dmode = 0;
+            } else if (N == 3) {
+                pl.l2 = 0;
+                pl.dmode = -1;
+            } else {
+                pl.l2 = -1;
+                pl.dmode = -1;
+            }
+            pl.Rl2 = pl.l2 >= 0 ? s.R[k][pl.l2] : 1;
+            pl.Qp = pl.Rl2 * pl.R1;
+            pl.zw = pl.Qp;
+        }
+        // 16-byte rows are read with 16-byte loads (N = 3, k = 0 reads rows of
+        // W_{A,B} the same way, whose start must then be aligned too).  Eight
+        // consecutive rows of nch 16-byte chunks fall on 8/gcd(nch, 8) bank
+        // groups; from a 4-way conflict on, lanes read their chunks skewed.
+        pl.vec = (IB % VN == 0 && (!foldA || s.woff[Am][Bm] % VN == 0)) ? 1 : 0;
+        if (pl.vec) {
+            const int nch = IB / VN;
+            int g = nch, m = 8;
+            while (m) {
+                const int t = g % m;
+                g = m;
+                m = t;
+            }
+            pl.skew = g >= 4 ? 1 : 0;
+        }
+        // W_{A,B} rows of a unit (staged per unit): padded to an odd number of chunks
+        int ldx = round_up(IB, VN);
+        if ((ldx / VN) % 2 == 0) ldx += VN;
+        pl.ldx = ldx;
+        // a lane owns one row: tasks of up to 32 rows; rows too long for 16 of
+        // them in a task leave the mode to the CTA kernels
+        const int RBK = balanced(IA, std::min(32, XBYTES / (sz * IB)));
+        if (RBK < std::min(IA, 16)) {
+            units.clear();
+            pl.warp = 0;
+            return pl;
+        }
+        pl.TAc = RBK;
+        const int nrc = cdiv(IA, RBK);
+        if (isF && N == 4) {
+            const int o = 1 - k, Io = s.I[o], Ik = s.I[k], I1 = s.I[1];
+            const int nOC = std::max(1, std::min(cdiv(target, static_cast<long long>(Ik) * nrc), std::max(1, Io / NW)));
+            for (int j = 0; j < Ik; ++j)
+                for (int oc = 0; oc < nOC; ++oc)
+                    for (int rc = 0; rc < nrc; ++rc) {
+                        int lo, hi;
+                        chunk(Io, nOC, oc, lo, hi);
+                        const int a0 = rc * RBK, a1 = std::min(IA, a0 + RBK);
+                        if (k == 0)
+                            add(j * I1 + lo, 1, hi - lo, j, a0, a1, 0, IB, oc * nrc + rc);
+                        else
+                            add(lo * I1 + j, I1, hi - lo, j, a0, a1, 0, IB, oc * nrc + rc);
+                    }
+            pl.nslot = nOC * nrc;
+            pl.part_elems = static_cast<long long>(Ik) * pl.nslot * pl.Q;
+            wab_elems = static_cast<long long>(RBK) * ldx;
+            zs_elems = static_cast<long long>(RBK) * pl.zw;
+        } else if (foldA) {  // N = 3, k = 0: one slab per output row, split by rows
+            const int I0 = s.I[0];
+            const int nu = std::max(1, std::min(cdiv(target, I0), cdiv(nrc, NW)));
+            for (int j = 0; j < I0; ++j)
+                for (int c = 0; c < nu; ++c) {
+                    int lo, hi;
+                    chunk(nrc, nu, c, lo, hi);
+                    add(j, 1, 1, j, lo * RBK, std::min(IA, hi * RBK), 0, IB, c);
+                }
+            pl.nslot = nu;
+            pl.part_elems = static_cast<long long>(I0) * nu * pl.Q;
+            pl.xr = round_up(RBK * IB + 32 / sz, VN);
+        } else if (N == 4) {
+            const int I0 = s.I[0], I1 = s.I[1];
+            const int nC = std::max(1, std::min(cdiv(target, static_cast<long long>(I0) * nrc), std::max(1, I1 / NW)));
+            for (int i0 = 0; i0 < I0; ++i0)
+                for (int c = 0; c < nC; ++c)
+                    for (int rc = 0; rc < nrc; ++rc) {
+                        int lo, hi;
+                        chunk(I1, nC, c, lo, hi);
+                        if (hi <= lo) continue;
+                        add(i0 * I1 + lo, 1, hi - lo, i0, rc * RBK, std::min(IA, rc * RBK + RBK), 0, IB, 0);
+                    }
+        } else if (N == 3) {
+            const int I0 = s.I[0];
+            const int nC = std::max(1, std::min(cdiv(target, nrc), std::max(1, I0 / NW)));
+            for (int c = 0; c < nC; ++c)
+                for (int rc = 0; rc < nrc; ++rc) {
+                    int lo, hi;
+                    chunk(I0, nC, c, lo, hi);
+                    if (hi <= lo) continue;
+                    add(lo, 1, hi - lo, -1, rc * RBK, std::min(IA, rc * RBK + RBK), 0, IB, 0);
+                }
+        } else {
+            for (int rc = 0; rc < nrc; ++rc) add(0, 1, 1, -1, rc * RBK, std::min(IA, rc * RBK + RBK), 0, IB, 0);
+        }
+        pl.nrow = IA;
+        pl.nunits = static_cast<int>(units.size());
+        if (!isF) pl.part_elems = static_cast<long long>(pl.nunits) * IA * pl.Qp;
+        xregion = round_up(RBK * IB + 32 / sz, VN);
+        if (foldA) xregion *= 2;
+        const int RBP = round_up(pl.R1, VN);
+        tab_elems = static_cast<long long>(NW) * IB * RBP;
+        gtab_elems = static_cast<long long>(pl.R1) * IB +
+                     (pl.l2 >= 0 ? static_cast<long long>(pl.Rl2) * s.I[pl.l2] : 0) +
+                     (isF ? static_cast<long long>(pl.RA) * IA : 0);
+        zmin = foldA ? pl.zw : static_cast<long long>(RBK) * pl.zw;
+        pl.aux_slot = 0;
+    }
+    long long tc = xregion;
+    tc = std::max(tc, zmin);
+    tc = (tc + VN - 1) / VN * VN;
+    pl.sub_elems = static_cast<int>(tc);
+    auto r128 = [](long long b) { return (b + 127) / 128 * 128; };
+    const long long limit = 225 * 1024;
+    for (int S = 4; S >= 2; --S) {
+        const long long off_tile = 640;
+        const long long off_tab = off_tile + r128(static_cast<long long>(NW) * S * tc * sz);
+        const long long off_gtab = off_tab + r128(tab_elems * sz);
+        const long long off_wab = off_gtab + r128(gtab_elems * sz);
+        const long long off_zs = off_wab + r128(wab_elems * sz);
+        const long long total = off_zs + zs_elems * sz;
+        if (total <= limit) {
+            pl.nstages = S;
+            pl.off_tile = static_cast<int>(off_tile);
+            pl.off_tab = static_cast<int>(off_tab);
+            pl.off_gtab = static_cast<int>(off_gtab);
+            pl.off_wab = static_cast<int>(off_wab);
+            pl.off_zs = static_cast<int>(off_zs);
+            pl.smem = static_cast<int>(total);
+            pl.warp = 1;
+            break;
+        }
+    }
+    pl.grid = std::max(1, std::min(pl.nunits, sms));
+    if (!pl.warp) units.clear();
+    return pl;
+}
+
 }  // namespace ifctn
 
 using namespace ifctn;
@@ -479,6 +738,16 @@ struct ifctn_ctx {
 
 namespace ifctn {
 
+// Tensors that do not stay in L2 stream through the per-stage kernels (graph
+// path, warp-pipelined contraction); the rest run as one persistent launch.
+// IFCTN_PATH=graph or =persistent overrides the choice (testing, tuning).
+bool choose_graph_only(const Shape& sh, int sz) {
+    const char* e = getenv("IFCTN_PATH");
+    if (e && strcmp(e, "graph") == 0) return true;
+    if (e && strcmp(e, "persistent") == 0) return false;
+    return sh.P * static_cast<long long>(sz) > L2_RESIDENT_BYTES;
+}
+
 template <typename T>
 struct Engine : ifctn_ctx {
     Shape sh;
@@ -502,6 +771,7 @@ struct Engine : ifctn_ctx {
     size_t bytes = 0;
     // persistent path
     bool persistent = false;
+    bool graph_only = false;  // HBM-sized tensor (or forced): per-stage kernels, warp-pipelined contraction
     int pgrid = 0, psmem = 0, grid_cap = 0;
     SweepParams<T> pp;
     DevBuf<unsigned> bar;
@@ -561,10 +831,13 @@ struct Engine : ifctn_ctx {
         const int sz = sizeof(T);
         std::vector<UnitDesc> all;
         long long maxpart = 1, maxt1 = 1, maxt2 = 1, maxK = 1;
+        graph_only = choose_graph_only(sh, sz);
         for (int k = 0; k < sh.N; ++k) {
             std::vector<UnitDesc> u;
-            plan[k] = plan_contract(sh, k, sz, u);
-            if (plan[k].smem > SMEM_LIMIT) {
+            plan[k].warp = 0;
+            if (graph_only) plan[k] = plan_contract_warp(sh, k, sz, u);
+            if (!plan[k].warp) plan[k] = plan_contract(sh, k, sz, u);
+            if (plan[k].smem > SMEM_LIMIT && !plan[k].warp) {
                 set_error("tensor shape needs more shared memory than available");
                 return IFCTN_EINVAL;
             }
@@ -693,8 +966,20 @@ struct Engine : ifctn_ctx {
         pp.rho = prob.rho;
         pp.inv1p = 1.0 / (1.0 + prob.rho);
         pp.nmiss = nmiss;
+        // One pipeline counter runs through every mode of the persistent
+        // kernel, and an mbarrier's phase parity follows from it only if the
+        // ring has the same number of stages in every mode: give each mode the
+        // largest stage count (and the shared memory that goes with it).
         pp.nstages = 1;
         for (int k = 0; k < sh.N; ++k) pp.nstages = std::max(pp.nstages, plan[k].nstages);
+        for (int k = 0; k < sh.N; ++k) {
+            ContractPlan& q = pp.pl[k];
+            if (q.nstages < pp.nstages) {
+                const int GS = q.split ? 1 : q.G;
+                q.smem += (pp.nstages - q.nstages) * GS * q.sub_elems * static_cast<int>(sizeof(T));
+                q.nstages = pp.nstages;
+            }
+        }
         pp.tstamp = tstamp.p;
         {
             // X-update work units: row ranges of slabs, about 4 per CTA
@@ -713,7 +998,7 @@ struct Engine : ifctn_ctx {
         // One launch per run pays off when the tensor stays in L2 and the
         // phases are latency-bound; HBM-sized tensors stream better through
         // the per-stage kernels at full occupancy (graph path).
-        if (sh.P * static_cast<long long>(sizeof(T)) > L2_RESIDENT_BYTES) return;
+        if (graph_only) return;
         if (psmem > 227 * 1024) return;
         int g = persistent_max_grid<T>(psmem);
         if (grid_cap > 0) g = std::min(g, grid_cap);

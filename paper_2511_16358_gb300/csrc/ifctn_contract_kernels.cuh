@@ -120,6 +120,7 @@ cudaError_t launch_col_r(const ContractArgs<T>& a, cudaStream_t st) {
 
 template <typename T>
 cudaError_t launch_contract(const ContractArgs<T>& a, cudaStream_t st) {
+    if (a.pl.warp) return launch_contract_warp<T>(a, a.pl.grid, st);
     const bool col = a.pl.kcase == CASE_COL;
     switch (a.pl.R1) {
 #define IFCTN_CASE(R) \

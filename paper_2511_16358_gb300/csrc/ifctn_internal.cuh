@@ -72,6 +72,15 @@ struct ContractPlan {
     int gtab_elems;  // their size (elements)
     int key_div;     // > 0: every unit covers all rows and its deferred key is
                      //      unit / key_div (no descriptor loads in the reduction)
+    // warp-pipelined kernels (HBM-streaming tensors)
+    int warp;        // 1: k_contract_roww / k_contract_colw run this mode
+    int vec;         // ROW: rows copied one by one into a padded layout and read
+                     //      with 16-byte loads; COL: only the unit's columns copied
+    int ldx;         // row stride of the X tile in shared memory (elements)
+    int xr;          // ROW, N = 3, k = 0: offset of the W_{A,B} rows in a stage
+    int zw;          // width of one register-fold row (elements)
+    int grid;        // CTAs (one per SM)
+    int off_tile, off_tab, off_gtab, off_wab, off_zs;  // shared-memory carve-up (bytes)
     long long part_elems;
 };
 

@@ -24,6 +24,9 @@ struct ContractArgs {
 template <typename T>
 cudaError_t launch_contract(const ContractArgs<T>& a, cudaStream_t st);
 
+// Warp-pipelined variant for tensors streamed from HBM (plan.warp = 1).
+template <typename T>
+cudaError_t launch_contract_warp(const ContractArgs<T>& a, int grid, cudaStream_t st);
 // M_k = reduction of the partials (FP64 output, I_k x Q_k).
 template <typename T>
 cudaError_t launch_contract_finish(const Shape& sh, int k, const ContractPlan& pl,

@@ -5,6 +5,9 @@ FP64 path: every factor and the completed tensor within 1e-10 relative
 state, and after whole runs.  Mixed path (FP32 tensor and contractions, FP64
 solves): RSE within 1e-3 relative of the oracle's.
 """
+import contextlib
+import os
+
 import numpy as np
 import pytest
 
@@ -16,6 +19,24 @@ from tests._cases import make_case, rel_err
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-10
+
+# "persistent": one cooperative launch per call (the default for tensors that
+# stay in L2); "graph": per-stage kernels with the warp-pipelined contraction
+# (the default for HBM-sized tensors), forced here on small shapes.
+PATHS = ["persistent", "graph"]
+
+
+@contextlib.contextmanager
+def path(name):
+    old = os.environ.get("IFCTN_PATH")
+    os.environ["IFCTN_PATH"] = name
+    try:
+        yield
+    finally:
+        if old is None:
+            del os.environ["IFCTN_PATH"]
+        else:
+            os.environ["IFCTN_PATH"] = old
 
 
 def _ctx(case, precision=b.FP64, rho=0.1, max_sweeps=10, tol=0.0):
@@ -38,10 +59,16 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("dims,edge", SHAPES)
-def test_one_sweep_fp64_matches_oracle(dims, edge):
+@pytest.mark.parametrize("which", PATHS)
+@pytest.mark.parametrize("dims,edge", SHAPES + [
+    ((9, 7, 6, 24), {(0, 1): 2, (0, 2): 3, (0, 3): 4, (1, 2): 5, (1, 3): 3, (2, 3): 2}),  # 16-byte rows
+    ((5, 4, 70, 36), 3),                                    # row blocks and column chunks
+    ((3, 130, 40), {(0, 1): 7, (0, 2): 8, (1, 2): 6}),      # two row blocks, two column chunks
+])
+def test_one_sweep_fp64_matches_oracle(dims, edge, which):
     case = make_case(dims, edge, 0.4, seed=sum(dims))
-    c = _ctx(case)
+    with path(which):
+        c = _ctx(case)
     st = c.sweep(1)
     G, X = case["G0"].copy(), case["X0"].copy()
     ost = oracle.sweep(dims, case["R"], 0.1, G, X, case["mask"])
@@ -52,15 +79,17 @@ def test_one_sweep_fp64_matches_oracle(dims, edge):
     c.close()
 
 
+@pytest.mark.parametrize("which", PATHS)
 @pytest.mark.parametrize("dims,edge", [
     ((30, 30, 30), 3),
     ((8, 9, 10, 11), 2),
 ])
-def test_whole_run_fp64_matches_oracle(dims, edge):
+def test_whole_run_fp64_matches_oracle(dims, edge, which):
     """Config of the small planted workload: 30^3, R = 3, 30% observed, 50 sweeps."""
     case = make_case(dims, edge, 0.3, seed=5)
     n = 50 if len(dims) == 3 else 20
-    c = _ctx(case, max_sweeps=n)
+    with path(which):
+        c = _ctx(case, max_sweeps=n)
     c.sweep(n)
     G, X = case["G0"].copy(), case["X0"].copy()
     oracle.complete(dims, case["R"], 0.1, G, X, case["mask"], max_sweeps=n)
@@ -69,12 +98,14 @@ def test_whole_run_fp64_matches_oracle(dims, edge):
     c.close()
 
 
-@pytest.mark.parametrize("dims,edge", SHAPES[:3])
-def test_mode_systems_match_oracle_block_systems(dims, edge):
+@pytest.mark.parametrize("which", PATHS)
+@pytest.mark.parametrize("dims,edge", SHAPES[:3] + [((6, 5, 7, 8), 3)])
+def test_mode_systems_match_oracle_block_systems(dims, edge, which):
     """Prop. 1 regrouping on the GPU: H_j = E_j^T K_k E_j and b_j = E_j^T M_k(j,:)
     equal the oracle's A_j^T A_j and A_j^T x_j, for every block (k, i) and column j."""
     case = make_case(dims, edge, 0.5, seed=11)
-    c = _ctx(case)
+    with path(which):
+        c = _ctx(case)
     N = len(dims)
     R = case["R"]
     F = inp.unpack_factors(case["G0"], dims, R)
@@ -137,12 +168,14 @@ def test_full_observation_planted_fixed_point():
     c.close()
 
 
-def test_deterministic_bitwise():
-    dims = (20, 17, 13)
+@pytest.mark.parametrize("which", PATHS)
+def test_deterministic_bitwise(which):
+    dims = (20, 17, 13, 8) if which == "graph" else (20, 17, 13)
     case = make_case(dims, 3, 0.3, seed=51)
     outs = []
     for _ in range(2):
-        c = _ctx(case, precision=b.MIXED)
+        with path(which):
+            c = _ctx(case, precision=b.MIXED)
         c.sweep(5)
         outs.append((c.factors(), c.x()))
         c.close()
@@ -150,11 +183,13 @@ def test_deterministic_bitwise():
     np.testing.assert_array_equal(outs[0][1], outs[1][1])
 
 
-def test_mixed_precision_rse_within_bound_of_fp64_oracle():
-    dims = (40, 36, 31)
+@pytest.mark.parametrize("which,dims", [("persistent", (40, 36, 31)), ("graph", (40, 36, 31)),
+                                        ("graph", (12, 16, 15, 24))])
+def test_mixed_precision_rse_within_bound_of_fp64_oracle(which, dims):
     case = make_case(dims, 4, 0.2, seed=61, kind="minmax01", sigma=0.01)
     n = 40
-    c = _ctx(case, precision=b.MIXED, max_sweeps=n)
+    with path(which):
+        c = _ctx(case, precision=b.MIXED, max_sweeps=n)
     c.sweep(n)
     G, X = case["G0"].copy(), case["X0"].copy()
     oracle.complete(dims, case["R"], 0.1, G, X, case["mask"], max_sweeps=n)
