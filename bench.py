@@ -132,23 +132,14 @@ def time_steps(b, torch, ctx, stream, X0_dev, G0_dev, sweeps, steps, warmup, flu
 
 
 def stage_times(b, torch, ctx, stream, N, reps=20):
-    """Average device time per launch of each stage kernel (CUDA events on the
-    context's stream)."""
+    """Average device time per launch of each stage (CUDA events on the
+    context's stream around back-to-back launches)."""
+    from paper_2511_16358_gb300.stage_timer import time_stage
     out = {}
-    for stage, name in ((0, "contract"), (1, "gram"), (2, "solve"), (3, "xupdate")):
+    for stage, name in ((0, "contract"), (4, "finish"), (1, "gram"), (2, "solve"), (3, "xupdate")):
         modes = range(N) if stage != 3 else [0]
         for k in modes:
-            for _ in range(3):
-                b.launch_stage(ctx, stage, k)
-            with torch.cuda.stream(stream):
-                s = torch.cuda.Event(enable_timing=True)
-                e = torch.cuda.Event(enable_timing=True)
-                s.record(stream)
-                for _ in range(reps):
-                    b.launch_stage(ctx, stage, k)
-                e.record(stream)
-            stream.synchronize()
-            out[f"{name}{k}" if stage != 3 else name] = s.elapsed_time(e) / reps / 1000.0
+            out[f"{name}{k}" if stage != 3 else name] = time_stage(torch, b, ctx, stream, stage, k, reps)
     return out
 
 

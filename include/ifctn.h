@@ -142,7 +142,8 @@ ifctn_status ifctn_mode_system(ifctn_ctx* ctx, int32_t k, double* Mk, double* Kk
    without waiting (for per-kernel timing with CUDA events).  stage:
      0 = the HBM-streaming mode-k contraction (partials of M_k),
      1 = the mode-k Gram chain (K_k), 2 = the mode-k proximal solves (updates
-     the factors), 3 = the fused reconstruct + masked X update (updates X).
+     the factors), 3 = the fused reconstruct + masked X update (updates X),
+     4 = the reduction of the contraction partials into M_k.
    k is ignored by stage 3. */
 ifctn_status ifctn_launch_stage(ifctn_ctx* ctx, int32_t stage, int32_t k);
 

@@ -445,7 +445,9 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
     const int N = s.N, Am = N - 2, Bm = N - 1, IA = s.IA, IB = s.IB;
     const int VN = 16 / sz;
     const int sms = num_sms();
-    const int target = 8 * sms;
+    // work units: enough for balance; where the partials are kept per unit
+    // (CASE_A, COL) fewer, since the finisher sums over them
+    const int target = (k < N - 2) ? 8 * sms : 4 * sms;
     const int XBYTES = 4 * 1024;  // at most this many X bytes in one task (per warp, per stage)
     // rows per task: at most cap, split evenly
     auto balanced = [](int rows, int cap) {
@@ -495,8 +497,8 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
         const int nrb = cdiv(IA, RBK);
         if (N == 4) {
             const int I0 = s.I[0], I1 = s.I[1];
-            const int nC = std::max(1, std::min(cdiv(target, static_cast<long long>(I0) * nbc),
-                                                std::max(1, I1 * nrb / NW)));
+            const int nC = std::max(1, std::min(std::min(cdiv(target, static_cast<long long>(I0) * nbc),
+                                                         std::max(1, I1 * nrb / NW)), I1));
             for (int i0 = 0; i0 < I0; ++i0)
                 for (int c = 0; c < nC; ++c)
                     for (int bc = 0; bc < nbc; ++bc) {
@@ -507,7 +509,7 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
                     }
         } else if (N == 3) {
             const int I0 = s.I[0];
-            const int nC = std::max(1, std::min(cdiv(target, nbc), std::max(1, I0 * nrb / NW)));
+            const int nC = std::max(1, std::min(std::min(cdiv(target, nbc), std::max(1, I0 * nrb / NW)), I0));
             for (int c = 0; c < nC; ++c)
                 for (int bc = 0; bc < nbc; ++bc) {
                     int lo, hi;
@@ -528,6 +530,8 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
         pl.nrow = IB;
         pl.nunits = static_cast<int>(units.size());
         pl.part_elems = static_cast<long long>(pl.nunits) * IB * pl.Qp;
+        pl.fin_div = 32;  // units covering column b: b / 32, b / 32 + nbc, ...
+        pl.fin_mod = nbc;
         xregion = round_up(RBK * IB + 32 / sz, VN);
         tab_elems = static_cast<long long>(NW) * (32 + VN) * pl.R1;
         gtab_elems = static_cast<long long>(pl.R1) * IA + (pl.l2 >= 0 ? static_cast<long long>(pl.Rl2) * s.I[pl.l2] : 0);
@@ -651,7 +655,11 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
         }
         pl.nrow = IA;
         pl.nunits = static_cast<int>(units.size());
-        if (!isF) pl.part_elems = static_cast<long long>(pl.nunits) * IA * pl.Qp;
+        if (!isF) {
+            pl.part_elems = static_cast<long long>(pl.nunits) * IA * pl.Qp;
+            pl.fin_div = RBK;  // units covering row a: a / RBK, a / RBK + nrc, ...
+            pl.fin_mod = nrc;
+        }
         xregion = round_up(RBK * IB + 32 / sz, VN);
         if (foldA) xregion *= 2;
         const int RBP = round_up(pl.R1, VN);
@@ -1112,7 +1120,7 @@ struct Engine : ifctn_ctx {
         for (int k = 0; k < sh.N; ++k) {
             const int nm = sh.N - 1;
             n += (nm == 3 ? 3 : nm == 2 ? 2 : 1);  // gram chain
-            n += 3;                                 // contract, finish, solve
+            n += 4;                                 // contract, finish, solve, pair refresh
         }
         n += 2;  // xupdate, finalize
         return n;
@@ -1259,6 +1267,10 @@ struct Engine : ifctn_ctx {
             case 1: CK(launch_gram<T>(sh, k, Gt.p, W.p, t1.p, t2.p, Kk.p, done(), st)); break;
             case 2: CK(launch_solve<T>(sh, k, prob.rho, Kk.p, Mk[k].p, Gd.p, Gt.p, W.p, flags(), done(), st)); break;
             case 3: CK(launch_xupdate_slab<T>(pp, xpart.p, slab_xblocks(), st)); break;
+            case 4:
+                CK(launch_contract_finish<T>(sh, k, plan[k], units.p + unit_off[k], part.p, Gt.p, Mk[k].p, done(),
+                                             st));
+                break;
             default: set_error("unknown stage"); return IFCTN_EINVAL;
         }
         return IFCTN_OK;

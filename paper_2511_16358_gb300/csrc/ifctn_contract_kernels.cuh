@@ -140,10 +140,65 @@ cudaError_t launch_contract(const ContractArgs<T>& a, cudaStream_t st) {
     }
 }
 
+// Row-parallel finisher for the unit-keyed partials (CASE_A, CASE_COL): one CTA
+// per output row; thread (g, qp) sums the units g, g + ng, ... that cover the
+// row, times G_{d,k}(rd, key) for every rd of the deferred mode d, and the
+// groups are added in a fixed order (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(256) k_contract_finish_rows(const Shape s, const int k, const ContractPlan pl,
+                                                              const UnitDesc* __restrict__ units,
+                                                              const T* __restrict__ part, const T* __restrict__ Gt,
+                                                              double* __restrict__ Mk, const int* __restrict__ done) {
+    if (*done) return;
+    __shared__ T red[256 * RMAX];
+    const int row = blockIdx.x;
+    const int Qp = pl.Qp;
+    const int ng = blockDim.x / Qp;
+    const int g = threadIdx.x / Qp, qp = threadIdx.x - g * Qp;
+    const bool colcase = pl.kcase == CASE_COL;
+    const int Rd = pl.dmode >= 0 ? s.R[k][pl.dmode] : 1;
+    T acc[RMAX];
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) acc[r] = T(0);
+    if (g < ng) {
+        // the units that cover this row: a stride when the plan knows it
+        const int u0 = pl.fin_mod > 0 ? row / pl.fin_div : 0;
+        const int us = pl.fin_mod > 0 ? pl.fin_mod : 1;
+#pragma unroll 4
+        for (int un = u0 + g * us; un < pl.nunits; un += ng * us) {
+            const UnitDesc u = units[un];
+            const int lo = colcase ? u.b0 : u.a0, hi = colcase ? u.b1 : u.a1;
+            if (row < lo || row >= hi) continue;
+            const T v = part[(static_cast<size_t>(un) * pl.nrow + row) * Qp + qp];
+            if (pl.dmode >= 0) {
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r)
+                    if (r < Rd) acc[r] = fma(gfac(Gt, s, pl.dmode, k, r, u.key), v, acc[r]);
+            } else {
+                acc[0] += v;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+            if (r < Rd) red[(g * RMAX + r) * Qp + qp] = acc[r];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < Rd * Qp; q += blockDim.x) {
+        const int rd = q / Qp, qq = q - rd * Qp;
+        T a = T(0);
+        for (int gg = 0; gg < ng; ++gg) a += red[(gg * RMAX + rd) * Qp + qq];
+        Mk[static_cast<size_t>(row) * pl.Q + q] = static_cast<double>(a);
+    }
+}
+
 template <typename T>
 cudaError_t launch_contract_finish(const Shape& sh, int k, const ContractPlan& pl,
                                    const UnitDesc* units, const T* part, const T* Gt, double* Mk,
                                    const int* done, cudaStream_t st) {
+    if (pl.kcase != CASE_F && pl.Qp <= 256) {
+        k_contract_finish_rows<T><<<sh.I[k], 256, 0, st>>>(sh, k, pl, units, part, Gt, Mk, done);
+        return cudaGetLastError();
+    }
     const long long total = static_cast<long long>(sh.I[k]) * pl.Q;
     int blocks = static_cast<int>((total + 255) / 256);
     if (blocks > 1216) blocks = 1216;

@@ -135,17 +135,21 @@ __global__ void __launch_bounds__(256) k_gram_fin(const Shape s, const int k, co
 // the G_{k,.}, so the I_k chains are independent.  Afterwards row/column j
 // of every W_{k,i} is refreshed.
 // ---------------------------------------------------------------------------
-constexpr int SOLVE_WARPS = 4;
+constexpr int SOLVE_WARPS = 8;
 constexpr int QMAX = 512;
+constexpr int SOLVE_K_SMEM_MAX = 160 * 1024;  // K_k staged in shared memory up to this size
 
+// With kin_smem, the block first copies K_k (Q x Q) into shared memory: every
+// warp's H assembly reads all of it, with strided access, Q^2 times per stage.
 template <typename T>
 __global__ void __launch_bounds__(SOLVE_WARPS * 32) k_solve(const Shape s, const int k, const double rho,
-                                                           const T* __restrict__ Kk,
+                                                           const T* __restrict__ Kg,
                                                            const double* __restrict__ Mk,
                                                            double* __restrict__ Gd, T* __restrict__ Gt,
                                                            T* __restrict__ W, int* __restrict__ flags,
-                                                           const int* __restrict__ done) {
+                                                           const int* __restrict__ done, const int kin_smem) {
     if (*done) return;
+    extern __shared__ __align__(16) unsigned char ksm[];
     __shared__ double vsh[SOLVE_WARPS][3][RMAX];
     __shared__ T om[SOLVE_WARPS][QMAX];
     __shared__ double Hs[SOLVE_WARPS][RMAX * RMAX];
@@ -153,7 +157,6 @@ __global__ void __launch_bounds__(SOLVE_WARPS * 32) k_solve(const Shape s, const
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int Ik = s.I[k];
     const int j = blockIdx.x * SOLVE_WARPS + warp;
-    if (j >= Ik) return;
     int m[3];
     const int nm = nonk_modes(s, k, m);
     int Rm[3] = {1, 1, 1}, st[3] = {1, 1, 1};
@@ -162,6 +165,14 @@ __global__ void __launch_bounds__(SOLVE_WARPS * 32) k_solve(const Shape s, const
         Rm[t] = s.R[k][m[t]];
         Q *= Rm[t];
     }
+    const T* Kk = Kg;
+    if (kin_smem) {
+        T* kd = reinterpret_cast<T*>(ksm);
+        stage_async(kd, Kg, Q * Q);
+        stage_wait();
+        Kk = kd;
+    }
+    if (j >= Ik) return;
     for (int t = nm - 2; t >= 0; --t) st[t] = st[t + 1] * Rm[t + 1];
     for (int t = 0; t < nm; ++t)
         for (int r = lane; r < Rm[t]; r += 32)
@@ -264,19 +275,8 @@ __global__ void __launch_bounds__(SOLVE_WARPS * 32) k_solve(const Shape s, const
         }
         __syncwarp();
     }
-    // refresh W_{k,i}(j, :) for every i != k
-    for (int t = 0; t < nm; ++t) {
-        const int i = m[t], Ri = Rm[t], Ii = s.I[i];
-        const double* gik = Gd + s.goff[i][k];
-        for (int b = lane; b < Ii; b += 32) {
-            double w = 0.0;
-            for (int r = 0; r < Ri; ++r) w = fma(vsh[warp][t][r], gik[r * Ii + b], w);
-            if (k < i)
-                W[s.woff[k][i] + static_cast<long long>(j) * Ii + b] = to_t<T>(w);
-            else
-                W[s.woff[i][k] + static_cast<long long>(b) * Ik + j] = to_t<T>(w);
-        }
-    }
+    // W_{k,i} are refreshed by launch_pairs_mode after the kernel (all entries
+    // at once, instead of a warp per column j walking rows of G_{i,k})
 }
 
 // ---------------------------------------------------------------------------
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(256) k_metrics(const long long P, const T* __r
 }
 
 template <typename T>
-__global__ void k_pairs(const Shape s, const double* __restrict__ Gd, T* __restrict__ W) {
+__global__ void k_pairs(const Shape s, const double* __restrict__ Gd, T* __restrict__ W, const int only) {
     const long long gtid = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     const long long gstr = static_cast<long long>(gridDim.x) * blockDim.x;
     for (long long idx = gtid; idx < s.wsize; idx += gstr) {
@@ -572,6 +572,7 @@ __global__ void k_pairs(const Shape s, const double* __restrict__ Gd, T* __restr
                     p = pp;
                     q = qq;
                 }
+        if (only >= 0 && p != only && q != only) continue;  // pairs of one mode only
         // the last pair whose offset is <= idx (offsets increase in (p,q) order)
         const long long rel = idx - s.woff[p][q];
         const int a = static_cast<int>(rel / s.I[q]), b = static_cast<int>(rel % s.I[q]);
@@ -755,8 +756,20 @@ template <typename T>
 cudaError_t launch_solve(const Shape& sh, int k, double rho, const T* Kk, const double* Mk, double* Gd,
                          T* Gt, T* W, int* flags, const int* done, cudaStream_t st) {
     const int blocks = (sh.I[k] + SOLVE_WARPS - 1) / SOLVE_WARPS;
-    k_solve<T><<<blocks, SOLVE_WARPS * 32, 0, st>>>(sh, k, rho, Kk, Mk, Gd, Gt, W, flags, done);
-    return cudaGetLastError();
+    long long Q = 1;
+    for (int m = 0; m < sh.N; ++m)
+        if (m != k) Q *= sh.R[k][m];
+    const long long kbytes = Q * Q * static_cast<long long>(sizeof(T));
+    const int kin = kbytes <= SOLVE_K_SMEM_MAX ? 1 : 0;
+    const int dyn = kin ? static_cast<int>(kbytes) : 0;
+    if (dyn > 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e != cudaSuccess) return e;
+    }
+    k_solve<T><<<blocks, SOLVE_WARPS * 32, dyn, st>>>(sh, k, rho, Kk, Mk, Gd, Gt, W, flags, done, kin);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_pairs_mode<T>(sh, k, Gd, W, st);
 }
 
 template <typename T>
@@ -783,7 +796,13 @@ cudaError_t launch_metrics(const Shape& sh, const T* X, const T* Xt, const uint3
 
 template <typename T>
 cudaError_t launch_pairs(const Shape& sh, const double* Gd, T* W, cudaStream_t st) {
-    k_pairs<T><<<grid_for(sh.wsize, 256, 4096), 256, 0, st>>>(sh, Gd, W);
+    k_pairs<T><<<grid_for(sh.wsize, 256, 4096), 256, 0, st>>>(sh, Gd, W, -1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pairs_mode(const Shape& sh, int k, const double* Gd, T* W, cudaStream_t st) {
+    k_pairs<T><<<grid_for(sh.wsize, 256, 4096), 256, 0, st>>>(sh, Gd, W, k);
     return cudaGetLastError();
 }
 
@@ -841,6 +860,7 @@ cudaError_t launch_scale_factors(int n, double* Gd, const double* ratio, double 
     template cudaError_t launch_metrics<T>(const Shape&, const T*, const T*, const uint32_t*, double*,    \
                                            int, const int*, cudaStream_t);                               \
     template cudaError_t launch_pairs<T>(const Shape&, const double*, T*, cudaStream_t);                 \
+    template cudaError_t launch_pairs_mode<T>(const Shape&, int, const double*, T*, cudaStream_t);       \
     template cudaError_t launch_init_x<T>(long long, const T*, const uint8_t*, T*, cudaStream_t);        \
     template cudaError_t launch_cast_factors<T>(int, const double*, T*, cudaStream_t);
 IFCTN_INST(float)

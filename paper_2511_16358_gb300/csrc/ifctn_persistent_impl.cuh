@@ -817,9 +817,13 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
     const bool wsm = p.xu_wab_smem != 0;
     const int RU = p.xu_rows;
     const int SU = (RU + IA - 1) / IA + 1;  // slabs a unit can touch
+    constexpr int VN = 16 / static_cast<int>(sizeof(T));
     T* wab = reinterpret_cast<T*>(smem);
     T* alpha = wab + (wsm ? IA * IB : 0);
-    T* beta = alpha + RU;
+    T* beta = alpha + (RU + VN - 1) / VN * VN;  // 16-byte aligned rows
+    // 16-byte path: rows of whole 16-byte chunks (every chunk inside one row and
+    // one 32-bit mask word) with W_{A,B} in shared memory
+    const bool vec = wsm && IB % VN == 0;
     const T* WAB = p.W + s.woff[Am][Bm];
     if (wsm) stage_async(wab, WAB, IA * IB);
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -871,6 +875,92 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
         (void)SU;
         const long long e0 = r0 * IB;
         const int n = nr * IB;
+        if (vec) {
+            const int nch = IB / VN;
+            const int n4 = nr * nch;
+            int rl4 = threadIdx.x / nch, c4 = threadIdx.x - rl4 * nch;
+            int a4 = a00 + rl4, sl4 = 0;
+            while (a4 >= IA) {
+                a4 -= IA;
+                ++sl4;
+            }
+            const int drl4 = PT / nch, dc4 = PT - drl4 * nch;
+            constexpr int XB4 = 4;
+            for (int ob = 0; ob < n4; ob += XB4 * PT) {
+                T xo[XB4][VN], rec[XB4][VN];
+                uint32_t wd[XB4];
+#pragma unroll
+                for (int t = 0; t < XB4; ++t) {
+                    const int o = ob + t * PT + threadIdx.x;
+                    if (o < n4) {
+                        const long long e = e0 + static_cast<long long>(o) * VN;
+                        if constexpr (sizeof(T) == 4) {
+                            const float4 v = *reinterpret_cast<const float4*>(p.X + e);
+                            xo[t][0] = v.x;
+                            xo[t][1] = v.y;
+                            xo[t][2] = v.z;
+                            xo[t][3] = v.w;
+                        } else {
+                            const double2 v = *reinterpret_cast<const double2*>(p.X + e);
+                            xo[t][0] = v.x;
+                            xo[t][1] = v.y;
+                        }
+                        wd[t] = p.mb[e >> 5];
+                        const T al = alpha[rl4];
+                        const T* wr = wab + a4 * IB + c4 * VN;
+                        const T* br = beta + sl4 * IB + c4 * VN;
+#pragma unroll
+                        for (int j = 0; j < VN; ++j) rec[t][j] = wr[j] * al * br[j];
+                    }
+                    c4 += dc4;
+                    int step = drl4;
+                    if (c4 >= nch) {
+                        c4 -= nch;
+                        ++step;
+                    }
+                    rl4 += step;
+                    a4 += step;
+                    while (a4 >= IA) {
+                        a4 -= IA;
+                        ++sl4;
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < XB4; ++t) {
+                    const int o = ob + t * PT + threadIdx.x;
+                    if (o < n4) {
+                        const long long e = e0 + static_cast<long long>(o) * VN;
+                        T xn[VN];
+#pragma unroll
+                        for (int j = 0; j < VN; ++j) {
+                            const bool obs = (wd[t] >> ((e + j) & 31)) & 1u;
+                            xn[j] = obs ? xo[t][j] : (rec[t][j] + rho * xo[t][j]) * inv1p;
+                            const T d = xn[j] - xo[t][j], r = xn[j] - rec[t][j];
+                            fa[0] = fma(d, d, fa[0]);
+                            fa[1] = fma(xo[t][j], xo[t][j], fa[1]);
+                            fa[2] = fma(r, r, fa[2]);
+                            if (met) {
+                                const T xt = p.Xt[e + j];
+                                const T de = xt - xn[j];
+                                fa[3] = fma(de, de, fa[3]);
+                                fa[4] = fma(xt, xt, fa[4]);
+                                if (!obs) fa[5] = fma(de, de, fa[5]);
+                            }
+                        }
+                        if constexpr (sizeof(T) == 4)
+                            *reinterpret_cast<float4*>(p.X + e) = make_float4(xn[0], xn[1], xn[2], xn[3]);
+                        else
+                            *reinterpret_cast<double2*>(p.X + e) = make_double2(xn[0], xn[1]);
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < 6; ++t) {
+                    run2[t] += fa[t];
+                    fa[t] = T(0);
+                }
+            }
+            continue;
+        }
         // walker over (row-in-unit, b) and the slab-local row index a
         int rl = threadIdx.x / IB, b = threadIdx.x - (threadIdx.x / IB) * IB;
         int a = a00 + rl, sl = 0;
@@ -1129,8 +1219,8 @@ int persistent_smem_bytes(const SweepParams<T>& p) {
                                                  sizeof(T));
         }
     }
-    // xupdate: W_{A,B} (when kept in shared memory) + alpha + beta
-    need = std::max<long long>(need, (static_cast<long long>(p.xu_wab_smem ? s.IA * s.IB : 0) + p.xu_rows +
+    // xupdate: W_{A,B} (when kept in shared memory) + alpha + beta (+ alignment of beta)
+    need = std::max<long long>(need, (16 + static_cast<long long>(p.xu_wab_smem ? s.IA * s.IB : 0) + p.xu_rows +
                                       static_cast<long long>((p.xu_rows + s.IA - 1) / s.IA + 1) * s.IB) *
                                          sizeof(T));
     return static_cast<int>(need + 128 + 256);

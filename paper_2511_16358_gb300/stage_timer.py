@@ -17,6 +17,23 @@ import json
 import numpy as np
 
 
+def time_stage(torch, b, ctx, stream, stage, k, reps):
+    """Device seconds per launch of one stage: CUDA events on the context's
+    stream around ``reps`` back-to-back launches (after two warm-up ones)."""
+    for _ in range(2):
+        b.launch_stage(ctx, stage, k)
+    stream.synchronize()
+    with torch.cuda.stream(stream):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            b.launch_stage(ctx, stage, k)
+        e1.record(stream)
+    stream.synchronize()
+    return e0.elapsed_time(e1) / 1000.0 / reps
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--dims", default="288,400,60,8")
@@ -25,7 +42,7 @@ def main(argv=None):
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--observed", type=float, default=0.05)
-    ap.add_argument("--stages", default="contract,gram,solve,xupdate")
+    ap.add_argument("--stages", default="contract,finish,gram,solve,xupdate")
     args = ap.parse_args(argv)
 
     import torch
@@ -48,22 +65,12 @@ def main(argv=None):
     out = {"dims": list(dims), "rank": args.rank, "precision": args.precision, "sweeps": st,
            "kernels_per_sweep": b.kernels_per_sweep(ctx), "stage_us": {}}
     want = set(args.stages.split(","))
-    for stage, name in ((0, "contract"), (1, "gram"), (2, "solve"), (3, "xupdate")):
+    for stage, name in ((0, "contract"), (4, "finish"), (1, "gram"), (2, "solve"), (3, "xupdate")):
         if name not in want:
             continue
         for k in (range(len(dims)) if stage != 3 else [0]):
-            for _ in range(2):
-                b.launch_stage(ctx, stage, k)
-            with torch.cuda.stream(stream):
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                for _ in range(args.reps):
-                    b.launch_stage(ctx, stage, k)
-                e1.record(stream)
-            stream.synchronize()
             key = f"{name}{k}" if stage != 3 else name
-            out["stage_us"][key] = e0.elapsed_time(e1) * 1000.0 / args.reps
+            out["stage_us"][key] = time_stage(torch, b, ctx, stream, stage, k, args.reps) * 1e6
     # Repeating one stage out of order moves the state away from a sweep's
     # (e.g. solves against a stale Gram matrix), so a status raised now says
     # nothing about the sweep and is only reported.
