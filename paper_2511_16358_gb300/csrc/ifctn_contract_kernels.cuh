@@ -33,7 +33,7 @@ namespace {
 using namespace cdev;
 
 template <typename T, int RB>
-__global__ void __launch_bounds__(256) k_contract_row(const ContractArgs<T> A) {
+__global__ void __launch_bounds__(256) k_contract_row(const __grid_constant__ ContractArgs<T> A) {
     if (*A.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256) k_contract_row(const ContractArgs<T> A) {
 }
 
 template <typename T, int RA>
-__global__ void __launch_bounds__(256) k_contract_col(const ContractArgs<T> A) {
+__global__ void __launch_bounds__(256) k_contract_col(const __grid_constant__ ContractArgs<T> A) {
     if (*A.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(256) k_contract_col(const ContractArgs<T> A) {
 // finisher: M_k(row, q) from the partials (fixed order)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_contract_finish(const Shape s, const int k,
-                                                         const ContractPlan pl,
+__global__ void __launch_bounds__(256) k_contract_finish(const __grid_constant__ Shape s, const int k,
+                                                         const __grid_constant__ ContractPlan pl,
                                                          const UnitDesc* __restrict__ units,
                                                          const T* __restrict__ part,
                                                          const T* __restrict__ Gt,
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_contract_finish(const Shape s, const in
 template <typename T, int R>
 cudaError_t launch_row_r(const ContractArgs<T>& a, cudaStream_t st) {
     auto kern = k_contract_row<T, R>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(kern), a.pl.smem);
     if (e != cudaSuccess) return e;
     kern<<<a.pl.nunits, a.pl.nthreads, a.pl.smem, st>>>(a);
     return cudaGetLastError();
@@ -110,7 +110,7 @@ cudaError_t launch_row_r(const ContractArgs<T>& a, cudaStream_t st) {
 template <typename T, int R>
 cudaError_t launch_col_r(const ContractArgs<T>& a, cudaStream_t st) {
     auto kern = k_contract_col<T, R>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(kern), a.pl.smem);
     if (e != cudaSuccess) return e;
     kern<<<a.pl.nunits, a.pl.nthreads, a.pl.smem, st>>>(a);
     return cudaGetLastError();
@@ -145,7 +145,7 @@ cudaError_t launch_contract(const ContractArgs<T>& a, cudaStream_t st) {
 // row, times G_{d,k}(rd, key) for every rd of the deferred mode d, and the
 // groups are added in a fixed order (deterministic).
 template <typename T>
-__global__ void __launch_bounds__(256) k_contract_finish_rows(const Shape s, const int k, const ContractPlan pl,
+__global__ void __launch_bounds__(256) k_contract_finish_rows(const __grid_constant__ Shape s, const int k, const __grid_constant__ ContractPlan pl,
                                                               const UnitDesc* __restrict__ units,
                                                               const T* __restrict__ part, const T* __restrict__ Gt,
                                                               double* __restrict__ Mk, const int* __restrict__ done) {

@@ -127,7 +127,7 @@ struct RowAux {
 };
 
 template <typename T, int RB>
-__global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const ContractArgs<T> A) {
+__global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_constant__ ContractArgs<T> A) {
     if (*A.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int VN = 16 / static_cast<int>(sizeof(T));
@@ -451,7 +451,7 @@ struct ColAux {
 };
 
 template <typename T, int RA>
-__global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const ContractArgs<T> A) {
+__global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_constant__ ContractArgs<T> A) {
     if (*A.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int VN = 16 / static_cast<int>(sizeof(T));
@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const ContractA
 template <typename T, int R>
 cudaError_t launch_roww_r(const ContractArgs<T>& a, int grid, cudaStream_t st) {
     auto kern = k_contract_roww<T, R>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(kern), a.pl.smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, NWARP * 32, a.pl.smem, st>>>(a);
     return cudaGetLastError();
@@ -653,7 +653,7 @@ cudaError_t launch_roww_r(const ContractArgs<T>& a, int grid, cudaStream_t st) {
 template <typename T, int R>
 cudaError_t launch_colw_r(const ContractArgs<T>& a, int grid, cudaStream_t st) {
     auto kern = k_contract_colw<T, R>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(kern), a.pl.smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, NWARP * 32, a.pl.smem, st>>>(a);
     return cudaGetLastError();

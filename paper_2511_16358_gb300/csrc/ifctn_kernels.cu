@@ -25,7 +25,7 @@ __device__ __forceinline__ T to_t(double v) { return static_cast<T>(v); }
 // with g_m = G_{m,k}.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_gram_t1(const Shape s, const int k, const T* __restrict__ Gt,
+__global__ void __launch_bounds__(256) k_gram_t1(const __grid_constant__ Shape s, const int k, const T* __restrict__ Gt,
                                                  const T* __restrict__ W, T* __restrict__ out,
                                                  const int* __restrict__ done) {
     if (*done) return;
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256) k_gram_t1(const Shape s, const int k, con
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_gram_t2(const Shape s, const int k, const T* __restrict__ Gt,
+__global__ void __launch_bounds__(256) k_gram_t2(const __grid_constant__ Shape s, const int k, const T* __restrict__ Gt,
                                                  const T* __restrict__ t1, T* __restrict__ t2,
                                                  const int* __restrict__ done) {
     if (*done) return;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_gram_t2(const Shape s, const int k, con
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_gram_fin(const Shape s, const int k, const T* __restrict__ Gt,
+__global__ void __launch_bounds__(256) k_gram_fin(const __grid_constant__ Shape s, const int k, const T* __restrict__ Gt,
                                                   const T* __restrict__ t2, T* __restrict__ K,
                                                   const int* __restrict__ done) {
     if (*done) return;
@@ -142,7 +142,7 @@ constexpr int SOLVE_K_SMEM_MAX = 160 * 1024;  // K_k staged in shared memory up 
 // With kin_smem, the block first copies K_k (Q x Q) into shared memory: every
 // warp's H assembly reads all of it, with strided access, Q^2 times per stage.
 template <typename T>
-__global__ void __launch_bounds__(SOLVE_WARPS * 32) k_solve(const Shape s, const int k, const double rho,
+__global__ void __launch_bounds__(SOLVE_WARPS * 32) k_solve(const __grid_constant__ Shape s, const int k, const double rho,
                                                            const T* __restrict__ Kg,
                                                            const double* __restrict__ Mk,
                                                            double* __restrict__ Gd, T* __restrict__ Gt,
@@ -435,7 +435,7 @@ __device__ __forceinline__ void block_sum_store(double (&v)[NV], double* out) {
 // vectors.  FP32 accumulation in short runs, carried in FP64.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_xupdate(const Shape s, const T rho, const T inv1p,
+__global__ void __launch_bounds__(256) k_xupdate(const __grid_constant__ Shape s, const T rho, const T inv1p,
                                                  T* __restrict__ X, const uint32_t* __restrict__ mb,
                                                  const T* __restrict__ W, double* __restrict__ xpart,
                                                  const int* __restrict__ done) {
@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(256) k_xupdate(const Shape s, const T rho, con
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_reconstruct(const Shape s, const T* __restrict__ W,
+__global__ void __launch_bounds__(256) k_reconstruct(const __grid_constant__ Shape s, const T* __restrict__ W,
                                                      T* __restrict__ out, double* __restrict__ xpart) {
     const long long P = s.P;
     const long long gtid = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(256) k_metrics(const long long P, const T* __r
 }
 
 template <typename T>
-__global__ void k_pairs(const Shape s, const double* __restrict__ Gd, T* __restrict__ W, const int only) {
+__global__ void k_pairs(const __grid_constant__ Shape s, const double* __restrict__ Gd, T* __restrict__ W, const int only) {
     const long long gtid = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     const long long gstr = static_cast<long long>(gridDim.x) * blockDim.x;
     for (long long idx = gtid; idx < s.wsize; idx += gstr) {
@@ -763,7 +763,7 @@ cudaError_t launch_solve(const Shape& sh, int k, double rho, const T* Kk, const 
     const int kin = kbytes <= SOLVE_K_SMEM_MAX ? 1 : 0;
     const int dyn = kin ? static_cast<int>(kbytes) : 0;
     if (dyn > 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_solve<T>), dyn);
         if (e != cudaSuccess) return e;
     }
     k_solve<T><<<blocks, SOLVE_WARPS * 32, dyn, st>>>(sh, k, rho, Kk, Mk, Gd, Gt, W, flags, done, kin);

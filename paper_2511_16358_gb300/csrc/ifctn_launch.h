@@ -2,9 +2,29 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "ifctn_internal.cuh"
 
 namespace ifctn {
+
+// The dynamic shared-memory limit of a kernel is one setting per function and
+// device for the whole process, while several contexts (each with its own
+// plan) may launch the same kernel: only ever raise it.
+inline cudaError_t raise_dyn_smem(const void* func, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cur;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    int& c = cur[std::make_pair(func, dev)];
+    if (bytes <= c) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) c = bytes;
+    return e;
+}
 
 template <typename T>
 struct ContractArgs {

@@ -116,22 +116,30 @@ __device__ __forceinline__ void prefetch_unit(const SweepParams<T>& p, int k, in
                  : "memory");
 }
 
+// The out-of-line unit bodies read their arguments through a reference; the
+// per-mode arguments live in shared memory (built once per launch), so those
+// reads are shared loads rather than loads from a per-thread stack copy.
 template <typename T>
-__device__ bool contract_dispatch(const SweepParams<T>& p, int k, int uidx, unsigned char* smem,
-                                  uint64_t* bars, int& pipe, int* wtag) {
-    ContractArgs<T> a;
-    a.X = p.X;
-    a.Gt = p.Gt;
-    a.W = p.W;
-    a.sh = p.sh;
-    a.k = k;
-    a.pl = p.pl[k];
-    a.units = p.units[k];
-    a.part = p.part;
-    a.flags = p.flags;
-    a.done = p.done;
-    const bool col = p.pl[k].kcase == CASE_COL;
-    switch (p.pl[k].R1) {
+__device__ void build_contract_args(const SweepParams<T>& p, ContractArgs<T>* a) {
+    for (int k = 0; k < p.sh.N; ++k) {
+        a[k].X = p.X;
+        a[k].Gt = p.Gt;
+        a[k].W = p.W;
+        a[k].sh = p.sh;
+        a[k].k = k;
+        a[k].pl = p.pl[k];
+        a[k].units = p.units[k];
+        a[k].part = p.part;
+        a[k].flags = p.flags;
+        a[k].done = p.done;
+    }
+}
+
+template <typename T>
+__device__ bool contract_dispatch(const ContractArgs<T>& a, int uidx, unsigned char* smem, uint64_t* bars,
+                                  int& pipe, int* wtag) {
+    const bool col = a.pl.kcase == CASE_COL;
+    switch (a.pl.R1) {
 #define IFCTN_PCASE(R) \
     case R:            \
         return col ? contract_col_unit<T, R>(a, uidx, smem, bars, pipe) : contract_row_unit<T, R>(a, uidx, smem, bars, pipe, wtag);
@@ -1046,7 +1054,7 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
 
 // Standalone form of the X update for the per-stage (graph) path.
 template <typename T>
-__global__ void __launch_bounds__(PT) k_xupdate_slab(const SweepParams<T> p, double* __restrict__ xpart) {
+__global__ void __launch_bounds__(PT) k_xupdate_slab(const __grid_constant__ SweepParams<T> p, double* __restrict__ xpart) {
     if (*reinterpret_cast<volatile const int*>(p.done)) return;
     extern __shared__ __align__(128) unsigned char xsm[];
     xupdate_phase<T>(p, xpart + 8 * blockIdx.x, xsm);
@@ -1067,13 +1075,15 @@ __device__ __forceinline__ unsigned long long gtimer() {
     } while (0)
 
 template <typename T>
-__global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const SweepParams<T> p) {
+__global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const __grid_constant__ SweepParams<T> p) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     unsigned char* work = smem + 128;
+    __shared__ ContractArgs<T> cargs[MAXN];
     if (threadIdx.x == 0) {
         for (int i = 0; i < p.nstages; ++i) mbar_init(&bars[i], 1);
         fence_mbar_init();
+        build_contract_args<T>(p, cargs);
     }
     __syncthreads();
     if (*reinterpret_cast<volatile const int*>(p.done)) return;
@@ -1103,7 +1113,7 @@ __global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const SweepParams<T>
                     const int cu = w - nG;
                     if (threadIdx.x == 0 && cu + static_cast<int>(gridDim.x) < nU)
                         prefetch_unit<T>(p, k, cu + gridDim.x);
-                    if (!contract_dispatch<T>(p, k, cu, work, bars, pipe, &wtag)) return;
+                    if (!contract_dispatch<T>(cargs[k], cu, work, bars, pipe, &wtag)) return;
                 }
             }
             IFCTN_STAMP(p, sw, 1 + 6 * k);
@@ -1238,7 +1248,7 @@ cudaError_t launch_xupdate_slab(const SweepParams<T>& p, double* xpart, int nblo
     const int smem = static_cast<int>((static_cast<long long>(p.xu_wab_smem ? p.sh.IA * p.sh.IB : 0) + p.xu_rows +
                                        static_cast<long long>((p.xu_rows + p.sh.IA - 1) / p.sh.IA + 1) * p.sh.IB) *
                                       sizeof(T)) + 64;
-    cudaError_t e = cudaFuncSetAttribute(k_xupdate_slab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_xupdate_slab<T>), smem);
     if (e != cudaSuccess) return e;
     k_xupdate_slab<T><<<nblocks, PT, smem, st>>>(p, xpart);
     return cudaGetLastError();
@@ -1246,7 +1256,7 @@ cudaError_t launch_xupdate_slab(const SweepParams<T>& p, double* xpart, int nblo
 
 template <typename T>
 int persistent_max_grid(int smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_sweep_persistent<T>), smem);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;

@@ -9,6 +9,7 @@
 // admits the next queued job while the others keep running.  Each job runs
 // exactly the kernels (same plans, same reduction order) it would run alone,
 // so its result does not depend on what else is resident.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -117,8 +118,8 @@ void ifctn_server::run() {
                 cv_done.notify_all();
                 continue;
             }
-            // the estimate becomes the measured footprint
-            const size_t real = ctx_device_bytes(c);
+            // reserve the larger of the estimate and the measured footprint
+            const size_t real = std::max(ctx_device_bytes(c), j->bytes);
             in_use = in_use - j->bytes + real;
             j->bytes = real;
             j->ctx = c;
