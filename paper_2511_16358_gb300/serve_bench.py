@@ -1,0 +1,179 @@
+"""Served-stream benchmark: completion jobs arriving while others run.
+
+    python -m paper_2511_16358_gb300.serve_bench [--requests 512 --rate 200 ...]
+
+Stream (defaults): 512 requests with Poisson arrivals at 200 requests/s;
+each request draws its order (3 or 4, uniformly), every mode size uniformly in
+[32, 128], every iFCTN rank R_{k,l} uniformly in [2, 6] (per edge, symmetric),
+and its observed fraction uniformly in [0.1, 0.5].  Its tensor is a planted
+iFCTN tensor (i.i.d. N(0,1) cherry factors), scaled to max |x| = 1, plus
+N(0, 0.01^2) noise, FP32, with a uniform random mask; 50 PAM sweeps each.
+All draws are seeded (request parameters from the splitmix64 stream of
+``inputs``; tensor values from a seeded torch generator on the GPU, the
+planted tensor from the library's allocation-free reconstruction).
+
+The server admits jobs by a device-memory budget (default 100 GB) in arrival
+order.  The client submits each request at its scheduled arrival time (later
+only when the pinned host memory held by outstanding requests exceeds a cap)
+and reports, as one JSON line:
+  - latency from the scheduled arrival to completion (p50, p99, max), which
+    includes any lag of the client itself;
+  - the server's own latency, submit to completion (p50, p99);
+  - jobs/s and PAM sweeps/s over the whole stream.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+
+def draw_requests(n, rate, seed, dmin, dmax, rmin, rmax, pmin, pmax, sweeps):
+    from . import inputs as inp
+    u = inp.uniform(seed, 64 * n).reshape(n, 64)
+    reqs, t = [], 0.0
+    for i in range(n):
+        r = u[i]
+        t += -np.log1p(-r[0]) / rate  # exponential inter-arrival times
+        order = 3 if r[1] < 0.5 else 4
+        dims = tuple(int(dmin + int(x * (dmax - dmin + 1))) for x in r[2:2 + order])
+        edges = {}
+        c = 6
+        for k in range(order):
+            for l in range(k + 1, order):
+                edges[(k, l)] = int(rmin + int(r[c] * (rmax - rmin + 1)))
+                c += 1
+        p = pmin + (pmax - pmin) * r[20]
+        reqs.append(dict(i=i, t=t, dims=dims, R=inp.rank_matrix(order, edges), p=float(p), sweeps=sweeps,
+                         seed=seed + 1 + i))
+    return reqs
+
+
+def make_inputs(torch, b, inp, rq, stream):
+    """Planted tensor on the GPU: FP64 Gaussian factors -> reconstruction ->
+    max-abs scaling -> noise -> mask."""
+    dims, R = rq["dims"], rq["R"]
+    G = torch.from_numpy(inp.gaussian_factors(dims, R, rq["seed"])).cuda()
+    x = torch.empty(dims, dtype=torch.float32, device="cuda")
+    b.reconstruct_noalloc(dims, R, b.MIXED, G, x, stream.cuda_stream)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(rq["seed"])
+    x /= x.abs().max().clamp_min(1e-30)
+    x += 0.01 * torch.randn(dims, generator=gen, device="cuda", dtype=torch.float32)
+    mask = (torch.rand(dims, generator=gen, device="cuda") < rq["p"]).to(torch.uint8)
+    return x, mask
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=512)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--seed", type=int, default=5000)
+    ap.add_argument("--sweeps", type=int, default=50)
+    ap.add_argument("--budget-gb", type=float, default=100.0)
+    ap.add_argument("--slots", type=int, default=16)
+    ap.add_argument("--dmin", type=int, default=32)
+    ap.add_argument("--dmax", type=int, default=128)
+    ap.add_argument("--pinned-cap-gb", type=float, default=32.0)
+    args = ap.parse_args(argv)
+
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from . import binding as b
+    from . import inputs as inp
+
+    reqs = draw_requests(args.requests, args.rate, args.seed, args.dmin, args.dmax, 2, 6, 0.1, 0.5, args.sweeps)
+    torch.cuda.init()
+    # inputs are generated on a stream of their own and waited for there: a
+    # device-wide synchronize is refused while the server captures a job's graph
+    stream = torch.cuda.Stream()
+    srv = b.server_create(int(args.budget_gb * (1 << 30)), args.slots)
+    # warm-up job (module loading, first graph instantiation)
+    with torch.cuda.stream(stream):
+        x, m = make_inputs(torch, b, inp, dict(reqs[0], seed=args.seed - 1), stream)
+    stream.synchronize()
+    t = b.submit(srv, b.make_problem(reqs[0]["dims"], reqs[0]["R"], rho=0.1, max_sweeps=2, tol=0.0,
+                                     precision=b.MIXED, seed=1), x, m, None)
+    b.poll(srv, t, None, timeout_us=-1)
+    del x, m
+
+    pending = {}  # ticket -> (request, bytes)
+    done_at, server_lat, lag = {}, [], []
+    held = 0
+    cap = args.pinned_cap_gb * (1 << 30)
+
+    def reap(block):
+        nonlocal held
+        for tk in list(pending):
+            rc, st = b.poll(srv, tk, None, timeout_us=-1 if block else 0)
+            if rc == b.OK:
+                rq, nb, ts = pending.pop(tk)
+                sl = b.server_latency(srv, tk)  # submit -> done, timed by the server
+                done_at[rq["i"]] = ts + sl
+                server_lat.append(sl)
+                held -= nb
+                if block:
+                    return
+
+    t0 = time.perf_counter()
+    for rq in reqs:
+        while held > cap and pending:
+            reap(True)
+        now = time.perf_counter() - t0
+        if now < rq["t"]:
+            reap(False)
+            time.sleep(max(0.0, rq["t"] - (time.perf_counter() - t0)))
+        with torch.cuda.stream(stream):
+            x, m = make_inputs(torch, b, inp, rq, stream)
+        stream.synchronize()
+        prob = b.make_problem(rq["dims"], rq["R"], rho=0.1, max_sweeps=rq["sweeps"], tol=0.0, precision=b.MIXED,
+                              seed=rq["seed"])
+        ts = time.perf_counter()
+        lag.append(ts - t0 - rq["t"])
+        tk = b.submit(srv, prob, x, m, None)
+        nb = x.numel() * 9
+        pending[tk] = (rq, nb, ts)
+        held += nb
+        del x, m
+        reap(False)
+    while pending:
+        reap(True)
+    t_end = time.perf_counter()
+    info = b.server_info_get(srv)
+    b.server_destroy(srv)
+
+    lat = np.array([done_at[rq["i"]] - t0 - rq["t"] for rq in reqs])
+    slat = np.array(server_lat)
+    span = max(done_at.values()) - t0  # first arrival (t = 0) to last completion
+    del t_end
+    sweeps_total = sum(rq["sweeps"] for rq in reqs)
+    entries = np.array([float(np.prod(rq["dims"])) for rq in reqs])
+    line = {
+        "metric": "served completion latency (p50/p99)",
+        "unit": "s",
+        "requests": len(reqs),
+        "rate_req_s": args.rate,
+        "latency_from_arrival_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                   "max": float(lat.max())},
+        "server_latency_s": {"p50": float(np.percentile(slat, 50)), "p99": float(np.percentile(slat, 99))},
+        "client_submit_lag_s": {"p50": float(np.percentile(lag, 50)), "max": float(np.max(lag))},
+        "jobs_per_s": len(reqs) / span,
+        "sweeps_per_s": sweeps_total / span,
+        "span_s": span,
+        "peak_resident": int(info["peak_resident"]),
+        "budget_gb": args.budget_gb,
+        "slots": args.slots,
+        "config": {"workload": "served stream: order 3/4, I_k in [%d,%d], R in [2,6], p in [0.1,0.5], "
+                               "%d sweeps, FP32 (mixed)" % (args.dmin, args.dmax, args.sweeps),
+                   "entries_mean": float(entries.mean()), "entries_max": float(entries.max()),
+                   "seed": args.seed, "data": "synthetic planted iFCTN + N(0,0.01^2) noise"},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()
