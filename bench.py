@@ -302,6 +302,11 @@ def main():
         if len(ph) >= 28 + 2 * k:
             phases[f"m{k}_contract_cta_max_end"] = ph[26 + 2 * k]
             phases[f"m{k}_contract_cta_mean_end"] = ph[27 + 2 * k]
+    sub = ph[26 + 2 * N: 26 + 2 * N + 12]
+    if len(sub) == 12:
+        names_sub = ["start", "staged", "column_loaded", "omega", "H", "b", "ldlt", "solve", "refine", "stored",
+                     "stages_done", "W_refreshed"]
+        phases["last_mode_solve_first_column_s"] = {nm: (t - sub[0]) for nm, t in zip(names_sub, sub)}
     torch.cuda.synchronize()
     tot = sum(times)
     if dist:

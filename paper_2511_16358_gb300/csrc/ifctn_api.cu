@@ -1248,6 +1248,8 @@ struct Engine : ifctn_ctx {
             out[cnt++] = mx;
             out[cnt++] = c ? sm / c : NAN;
         }
+        // sub-steps of the first column of the last mode's solves (CTA 0)
+        for (int i = 40; i < 52 && cnt < max; ++i) out[cnt++] = rel(h[i]);
         if (n) *n = persistent ? cnt : 0;
         return IFCTN_OK;
     }

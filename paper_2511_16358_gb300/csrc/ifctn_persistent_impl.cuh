@@ -428,8 +428,15 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
 // ---------------------------------------------------------------------------
 template <typename F>
 __device__ __forceinline__ F recip_nr(F d) {
-    // reciprocal: FP32 estimate refined by Newton-Raphson x <- x (2 - d x)
-    F x = static_cast<F>(1.0f / static_cast<float>(d));
+    // reciprocal: hardware FP32 estimate (rcp.approx, about 1 ulp), refined by
+    // Newton-Raphson x <- x (2 - d x): once in FP32, twice more in FP64.  The
+    // mixed path's factorisation only has to be good enough for one step of
+    // FP64 iterative refinement.
+    float xf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(xf) : "f"(static_cast<float>(d)));
+    const float df = static_cast<float>(d);
+    xf = xf * (2.0f - df * xf);
+    F x = static_cast<F>(xf);
     if (sizeof(F) == 8) {
         x = x * (F(2) - d * x);
         x = x * (F(2) - d * x);
@@ -491,11 +498,26 @@ __device__ void ldlt_solve_warp(const F* A, const F* inv, F* x, int n, int lane)
     }
 }
 
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Sub-step timestamps of one column (slots 40..55 of the timestamp buffer):
+// taken by lane 0 of warp 0 of CTA 0 on its first column when `stamp` is set.
+#define IFCTN_SSTAMP(n)                                                        \
+    do {                                                                       \
+        if (stamp_col && lane == 0) p.tstamp[40 + (n)] = gtimer();             \
+    } while (0)
+
 template <typename T>
-__device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem) {
+__device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem, bool stamp = false) {
     const Shape& s = p.sh;
     const int Ik = s.I[k];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    bool stamp_col = stamp && p.tstamp && blockIdx.x == 0 && warp == 0;
+    IFCTN_SSTAMP(0);
     if (static_cast<int>(blockIdx.x) >= Ik) return;  // no columns for this CTA
     constexpr bool MIXED = sizeof(T) == 4;
     int m[3];
@@ -531,15 +553,38 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem)
     T* om = gik + ((tot + 1) & ~1) + warp * 512;
     T* Ks = gik + ((tot + 1) & ~1) + PW * 512;
     const bool ksm = p.solve_k_in_smem != 0;
+    // per-warp copy of the column's row of M_k (FP64), after K
+    double* Ms = reinterpret_cast<double*>(
+                     (reinterpret_cast<uintptr_t>(Ks + (ksm ? Q * Q : 0)) + 15) & ~uintptr_t(15)) +
+                 static_cast<size_t>(warp) * Q;
+    // the current columns G_{k,m}(:, j) and the row M_k(j, :) of a column,
+    // copied asynchronously (the first column's together with the tables)
+    auto fetch_column = [&](int j) {
+        for (int t = 0; t < nm; ++t)
+            for (int r = lane; r < Rm[t]; r += 32)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(vs + t * RMAX + r)),
+                             "l"(p.Gd + s.goff[k][m[t]] + r * Ik + j)
+                             : "memory");
+        const double* Mj = p.Mk[k] + static_cast<long long>(j) * Q;
+        for (int q = lane; q < Q; q += 32)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(Ms + q)), "l"(Mj + q) : "memory");
+    };
+    const int j0 = warp * gridDim.x + blockIdx.x;
+    if (j0 < Ik) fetch_column(j0);
     if (ksm) stage_async(Ks, p.Kk, Q * Q);
     const T* K = ksm ? Ks : p.Kk;
     stage_wait();
+    IFCTN_SSTAMP(1);
     const double rho = p.rho;
-    for (int j = warp * gridDim.x + blockIdx.x; j < Ik; j += gridDim.x * PW) {
-        for (int t = 0; t < nm; ++t)
-            for (int r = lane; r < Rm[t]; r += 32) vs[t * RMAX + r] = p.Gd[s.goff[k][m[t]] + r * Ik + j];
-        __syncwarp();
-        const double* Mj = p.Mk[k] + static_cast<long long>(j) * Q;
+    // W refresh by the whole CTA when every warp has at most one column
+    const bool cta_refresh = static_cast<long long>(gridDim.x) * PW >= Ik;
+    for (int j = j0; j < Ik; j += gridDim.x * PW) {
+        if (j != j0) {
+            fetch_column(j);
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncwarp();
+        }
+        IFCTN_SSTAMP(2);
         for (int ti = 0; ti < nm; ++ti) {
             const int i = m[ti], Ri = Rm[ti], sp = st[ti];
             const int Qo = Q / Ri;
@@ -555,6 +600,7 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem)
                 om[o2] = w;
             }
             __syncwarp();
+            if (ti == 0) IFCTN_SSTAMP(3);
             // H(c, c2), c <= c2: lanes take pairs, each sums over (o, o2)
             const int npair = Ri * (Ri + 1) / 2;
             for (int pr = lane; pr < npair; pr += 32) {
@@ -588,26 +634,31 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem)
                 Hd[c * Ri + c2] = h + (c == c2 ? rho : 0.0);
                 Hd[c2 * Ri + c] = h + (c == c2 ? rho : 0.0);
             }
+            __syncwarp();
+            if (ti == 0) IFCTN_SSTAMP(4);
             // b(c) = E^T M(j,:) + rho g_old: lanes take c
             for (int c = lane; c < Ri; c += 32) {
                 T acc = T(0);
                 for (int o = 0; o < Qo; ++o) {
                     const int hi = o / sp, lo = o - hi * sp;
-                    acc = fma(om[o], static_cast<T>(Mj[hi * Ri * sp + c * sp + lo]), acc);
+                    acc = fma(om[o], static_cast<T>(Ms[hi * Ri * sp + c * sp + lo]), acc);
                 }
                 bd[c] = static_cast<double>(acc) + rho * vs[ti * RMAX + c];
             }
             __syncwarp();
+            if (ti == 0) IFCTN_SSTAMP(5);
             for (int idx = lane; idx < Ri * Ri; idx += 32) Af[idx] = static_cast<F>(Hd[idx]);
             __syncwarp();
             bool okc = ldlt_warp<F>(Af, invf, Ri, lane);
             __syncwarp();
+            if (ti == 0) IFCTN_SSTAMP(6);
             if (okc) {
                 if (lane < Ri) xf[lane] = static_cast<F>(bd[lane]);
                 __syncwarp();
                 ldlt_solve_warp<F>(Af, invf, xf, Ri, lane);
                 if (lane < Ri) gd[lane] = static_cast<double>(xf[lane]);
                 __syncwarp();
+                if (ti == 0) IFCTN_SSTAMP(7);
                 if (MIXED) {
                     for (int it = 0; it < 1; ++it) {
                         // residual in FP64, correction in FP32
@@ -630,6 +681,7 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem)
                 if (lane < Ri) gd[lane] = vs[ti * RMAX + lane];
             }
             __syncwarp();
+            if (ti == 0) IFCTN_SSTAMP(8);
             for (int r = lane; r < Ri; r += 32) {
                 const double g = gd[r];
                 vs[ti * RMAX + r] = g;
@@ -637,7 +689,10 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem)
                 p.Gt[s.goff[k][i] + r * Ik + j] = static_cast<T>(g);
             }
             __syncwarp();
+            if (ti == 0) IFCTN_SSTAMP(9);
         }
+        IFCTN_SSTAMP(10);
+        if (cta_refresh) continue;  // done below by the whole CTA
         // refresh W_{k,i}(j, :) for every i != k (in the tensor dtype)
         for (int t = 0; t < nm; ++t) {
             const int i = m[t], Ri = Rm[t], Ii = s.I[i];
@@ -657,9 +712,36 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem)
             }
         }
         __syncwarp();
+        IFCTN_SSTAMP(11);
+        stamp_col = false;
     }
     __syncthreads();
+    if (cta_refresh) {
+        // columns of this CTA: j = w * gridDim.x + blockIdx.x, their new
+        // G_{k,i}(:, j) in warp w's scratch (same arithmetic as per warp)
+        const int ncol = min(PW, (Ik - static_cast<int>(blockIdx.x) + static_cast<int>(gridDim.x) - 1) /
+                                     static_cast<int>(gridDim.x));
+        for (int t = 0; t < nm; ++t) {
+            const int i = m[t], Ri = Rm[t], Ii = s.I[i];
+            const T* gk = gik + gko[t];
+            for (int idx = tid; idx < ncol * Ii; idx += PT) {
+                const int w = idx / Ii, b = idx - w * Ii;
+                const int j = w * gridDim.x + blockIdx.x;
+                const double* vsw = reinterpret_cast<double*>(smem) + w * WSD + RMAX * RMAX + t * RMAX;
+                T acc = T(0);
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r)
+                    if (r < Ri) acc = fma(static_cast<T>(vsw[r]), gk[r * Ii + b], acc);
+                if (k < i)
+                    p.W[s.woff[k][i] + static_cast<long long>(j) * Ii + b] = acc;
+                else
+                    p.W[s.woff[i][k] + static_cast<long long>(b) * Ik + j] = acc;
+            }
+        }
+        if (stamp && p.tstamp && blockIdx.x == 0 && threadIdx.x == 0) p.tstamp[40 + 11] = gtimer();
+    }
 }
+#undef IFCTN_SSTAMP
 
 // ---------------------------------------------------------------------------
 // Phase 4: eq. (updateX) fused with the reconstruction and the sums of the
@@ -1060,11 +1142,6 @@ __global__ void __launch_bounds__(PT) k_xupdate_slab(const __grid_constant__ Swe
     xupdate_phase<T>(p, xpart + 8 * blockIdx.x, xsm);
 }
 
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
 
 // CTA 0 stamps the end of every phase of the first sweep (profiling aid)
 #define IFCTN_STAMP(p, sw, slot)                                                        \
@@ -1125,7 +1202,7 @@ __global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const __grid_constan
             IFCTN_STAMP(p, sw, 3 + 6 * k);
             if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
             IFCTN_STAMP(p, sw, 4 + 6 * k);
-            solve_phase<T>(p, k, work);
+            solve_phase<T>(p, k, work, sw == 0 && k == s.N - 1);
             IFCTN_STAMP(p, sw, 5 + 6 * k);
             if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
             IFCTN_STAMP(p, sw, 6 + 6 * k);
@@ -1213,6 +1290,7 @@ int persistent_smem_bytes(const SweepParams<T>& p) {
         long long solve = static_cast<long long>(PW) * (2 * RMAX * RMAX + 8 * RMAX) * 8 +
                           static_cast<long long>(tot + 2) * sizeof(T) + static_cast<long long>(PW) * 512 * sizeof(T);
         if (p.solve_k_in_smem) solve += static_cast<long long>(Q) * Q * sizeof(T);
+        solve += 16 + static_cast<long long>(PW) * Q * 8;  // rows of M_k (FP64), 16-byte aligned
         need = std::max(need, solve);
         // reduce_phase (column tiles): coefficients + cross-warp sums
         need = std::max<long long>(need, (static_cast<long long>(RMAX) * p.pl[k].nunits + 4 +
