@@ -150,6 +150,17 @@ def rse_curve(b, ctx, xt, sweeps):
     return [r["rse"] for r in log[-sweeps:]]
 
 
+def aggregate_ranks(torch, dist, seconds, world, units_per_rank, device):
+    """Whole-job throughput of N replicas: every rank timed the same amount of
+    work; the job took as long as the slowest rank (MAX over ranks), and the
+    units of all ranks count.  Returns (max seconds, units per second)."""
+    if dist is not None and world > 1:
+        t = torch.tensor([seconds], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        seconds = float(t.item())
+    return seconds, world * units_per_rank / seconds
+
+
 def source_digest() -> str:
     """Digest of the CUDA sources (as in the build stamp, without the flags)."""
     import hashlib
@@ -308,12 +319,7 @@ def main():
                      "stages_done", "W_refreshed"]
         phases["last_mode_solve_first_column_s"] = {nm: (t - sub[0]) for nm, t in zip(names_sub, sub)}
     torch.cuda.synchronize()
-    tot = sum(times)
-    if dist:
-        t = torch.tensor([tot], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
-    value = world * args.steps * sweeps / tot
+    tot, value = aggregate_ranks(torch, dist, sum(times), world, args.steps * sweeps, "cuda")
 
     extras = {}
     # per-stage device times (separate context: stages mutate the state)

@@ -676,13 +676,16 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
     pl.sub_elems = static_cast<int>(tc);
     auto r128 = [](long long b) { return (b + 127) / 128 * 128; };
     const long long limit = 225 * 1024;
+    // per-warp ring of a task's W entries (cp.async), ROW 160, COL 96 elements a stage
+    const long long auxw = (k == Bm) ? 96 : 160;
     for (int S = 4; S >= 2; --S) {
         const long long off_tile = 640;
         const long long off_tab = off_tile + r128(static_cast<long long>(NW) * S * tc * sz);
         const long long off_gtab = off_tab + r128(tab_elems * sz);
         const long long off_wab = off_gtab + r128(gtab_elems * sz);
         const long long off_zs = off_wab + r128(wab_elems * sz);
-        const long long total = off_zs + zs_elems * sz;
+        const long long off_aux = off_zs + r128(zs_elems * sz);
+        const long long total = off_aux + static_cast<long long>(NW) * S * auxw * sz;
         if (total <= limit) {
             pl.nstages = S;
             pl.off_tile = static_cast<int>(off_tile);
@@ -690,6 +693,7 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
             pl.off_gtab = static_cast<int>(off_gtab);
             pl.off_wab = static_cast<int>(off_wab);
             pl.off_zs = static_cast<int>(off_zs);
+            pl.off_aux = static_cast<int>(off_aux);
             pl.smem = static_cast<int>(total);
             pl.warp = 1;
             break;

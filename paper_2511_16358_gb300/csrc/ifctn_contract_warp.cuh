@@ -74,6 +74,22 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned par, volatile 
     return __all_sync(0xffffffffu, ok) != 0;
 }
 
+// Waits until at most S-1 of this thread's cp.async groups are pending (the
+// group of the oldest stage of an S-stage ring is then complete).
+__device__ __forceinline__ void cp_async_wait_ring(int S) {
+    if (S <= 2) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else if (S == 3) asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else asm volatile("cp.async.wait_group 3;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(sizeof(T))
+                 : "memory");
+}
+
 // One task: slab f, rows [a0, a0 + na).
 struct Task {
     long long f;
@@ -121,10 +137,6 @@ __device__ __forceinline__ Task task_at(const UnitCur& c, int t, int rbk) {
 // of the coefficient table, the fold weight) are loaded by the lanes that use
 // them, one task ahead, into registers.
 // ---------------------------------------------------------------------------
-template <typename T>
-struct RowAux {
-    T w0[2], w1[2], sc;
-};
 
 template <typename T, int RB>
 __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_constant__ ContractArgs<T> A) {
@@ -174,7 +186,14 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
     if (nA) stage_async(gtab + nB + nL, A.Gt + s.goff[Am][k], nA);
     stage_wait();
 
-    // issue path (lane 0): the task's rows of X (and, N = 3 k = 0, of W_{A,B})
+    // per-warp ring of the W entries each task needs besides its tile, filled
+    // by cp.async at issue time (lane-owned: w0/w1 at b = lane, lane + 32; the
+    // fold weight at row = lane) and waited for with the stage
+    constexpr int AUXW = 160;
+    T* auxr = reinterpret_cast<T*>(smem + pl.off_aux) + static_cast<size_t>(warp) * S * AUXW;
+
+    // issue path: the task's rows of X (and, N = 3 k = 0, of W_{A,B}) by TMA
+    // (lane 0), its W entries by every lane, one cp.async group per issue
     UnitCur ic = {};
     int ct = warp;
     auto settle = [&]() {
@@ -186,7 +205,34 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
         }
     };
     auto issue_next = [&](int st) {
-        if (ic.ui >= pl.nunits) return;
+        if (ic.ui >= pl.nunits) {
+            cp_async_commit();  // empty group: keeps one group per stage
+            return;
+        }
+        {
+            const Task tk = task_at(ic, ct, RBK);
+            int i0, i1;
+            decode_f(s, tk.f, i0, i1);
+            T* ax = auxr + st * AUXW;
+            if (p0 >= 0) {
+                const T* r = A.W + s.woff[p0][Bm] + static_cast<long long>(p0 == 0 ? i0 : i1) * IB;
+                if (lane < IB) cp_async_elem(ax + lane, r + lane);
+                if (lane + 32 < IB) cp_async_elem(ax + 32 + lane, r + lane + 32);
+            }
+            if (two_psi) {
+                const T* r = A.W + s.woff[1][Bm] + static_cast<long long>(i1) * IB;
+                if (lane < IB) cp_async_elem(ax + 64 + lane, r + lane);
+                if (lane + 32 < IB) cp_async_elem(ax + 96 + lane, r + lane + 32);
+            }
+            if (isF && N == 4) {
+                const int o = 1 - k, io = o == 0 ? i0 : i1;
+                if (lane < tk.na)
+                    cp_async_elem(ax + 128 + lane, A.W + s.woff[o][Am] + static_cast<long long>(io) * IA + tk.a0 + lane);
+            } else if (!isF && N == 4) {
+                cp_async_elem(ax + 128 + lane, A.W + s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1);
+            }
+            cp_async_commit();
+        }
         if (lane == 0) {
             const Task tk = task_at(ic, ct, RBK);
             T* buf = tiles + (static_cast<size_t>(warp) * S + st) * TC;
@@ -208,33 +254,6 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
     if (ic.ui < pl.nunits) load_unit(A.units, ic.ui, RBK, ic);
     settle();
     for (int i = 0; i < S; ++i) issue_next(i);
-
-    // aux values of a task for this lane (one task ahead)
-    auto load_aux = [&](const UnitCur& c, int t) {
-        const Task tk = task_at(c, t, RBK);
-        int i0, i1;
-        decode_f(s, tk.f, i0, i1);
-        RowAux<T> x;
-        x.w0[0] = x.w0[1] = x.w1[0] = x.w1[1] = T(1);
-        x.sc = T(1);
-        if (p0 >= 0) {
-            const T* r = A.W + s.woff[p0][Bm] + static_cast<long long>(p0 == 0 ? i0 : i1) * IB;
-            if (lane < IB) x.w0[0] = __ldg(r + lane);
-            if (lane + 32 < IB) x.w0[1] = __ldg(r + lane + 32);
-        }
-        if (two_psi) {
-            const T* r = A.W + s.woff[1][Bm] + static_cast<long long>(i1) * IB;
-            if (lane < IB) x.w1[0] = __ldg(r + lane);
-            if (lane + 32 < IB) x.w1[1] = __ldg(r + lane + 32);
-        }
-        if (isF && N == 4) {
-            const int o = 1 - k, io = o == 0 ? i0 : i1;
-            if (lane < tk.na) x.sc = __ldg(A.W + s.woff[o][Am] + static_cast<long long>(io) * IA + tk.a0 + lane);
-        } else if (!isF && N == 4) {
-            x.sc = __ldg(A.W + s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1);
-        }
-        return x;
-    };
 
     int it = 0;  // tasks consumed by this warp
     for (int ui = blockIdx.x; ui < pl.nunits; ui += gridDim.x) {
@@ -259,15 +278,13 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
 #pragma unroll
             for (int r = 0; r < RB; ++r) z[r2][r] = T(0);
 
-        RowAux<T> cur;
-        if (warp < nt) cur = load_aux(uc, warp);
         int zslot = -1;
         for (int t = warp; t < nt; t += NWARP, ++it) {
-            RowAux<T> nxt = cur;
-            if (t + NWARP < nt) nxt = load_aux(uc, t + NWARP);
             const int st = it % S;
             const unsigned par = static_cast<unsigned>((it / S) & 1);
             T* buf = tiles + (static_cast<size_t>(warp) * S + st) * TC;
+            const T* ax = auxr + st * AUXW;
+            cp_async_wait_ring(S);  // this lane's W entries of the task
             const bool ok = warp_wait(&bars[warp * S + st], par, abortf, A.flags) && !*abortf;
             const Task tk = task_at(uc, t, RBK);
             if (ok) {
@@ -278,7 +295,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
                 for (int m = 0; m < 2; ++m) {
                     const int b = lane + 32 * m;
                     if (b < IB) {
-                        const T om = cur.w0[m] * cur.w1[m];
+                        const T om = (p0 >= 0 ? ax[32 * m + lane] : T(1)) * (two_psi ? ax[64 + 32 * m + lane] : T(1));
 #pragma unroll
                         for (int r = 0; r < RBP; ++r)
                             if (r < RB) psi[b * PS + r] = om * gB[r * IB + b];
@@ -354,7 +371,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
 #pragma unroll
                     for (int r = 0; r < RB; ++r) z[0][r] += va ? u0[r] : T(0);
                 } else {
-                    const T sc = va ? cur.sc : T(0);
+                    const T sc = va ? ((N == 4) ? ax[128 + lane] : T(1)) : T(0);
                     // coefficient G_{l2,k}(r2, i_l2) times the fold weight
                     const int il2 = isF ? (l2 == 0 ? i0 : i1) : (N == 4 ? i1 : i0);
                     const T* gl = gL + il2;
@@ -374,7 +391,6 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
             } else {
                 zslot = st;  // keeps z for the unit reduction; refilled after it
             }
-            cur = nxt;
         }
         // ---- unit end: reduce over warps (fixed order) ----
         const int nwk = min(NWARP, nt);
@@ -445,10 +461,6 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
 // G_{1,k}(r2, i1) W_{0,1}(i0, i1), i0 deferred to the finisher; N = 3:
 // G_{0,k}(r2, i0)).
 // ---------------------------------------------------------------------------
-template <typename T>
-struct ColAux {
-    T w0, w1, sc;
-};
 
 template <typename T, int RA>
 __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_constant__ ContractArgs<T> A) {
@@ -476,6 +488,10 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
     const int nL = l2 >= 0 ? RC * s.I[l2] : 0;
     const T* gAt = gtab;
     const T* gL = gtab + nAg;
+    // per-warp ring of the W entries of a task (phi row weights at a = lane,
+    // and W_{0,1}(i0, i1)), filled by cp.async at issue time
+    constexpr int AUXW = 96;
+    T* auxr = reinterpret_cast<T*>(smem + pl.off_aux) + static_cast<size_t>(warp) * S * AUXW;
 
     if (tid == 0) {
         for (int i = 0; i < NWARP * S; ++i) mbar_init(&bars[i], 1);
@@ -497,7 +513,23 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
         }
     };
     auto issue_next = [&](int st) {
-        if (ic.ui >= pl.nunits) return;
+        if (ic.ui >= pl.nunits) {
+            cp_async_commit();
+            return;
+        }
+        {
+            const Task tk = task_at(ic, ct, RBK);
+            int i0, i1;
+            decode_f(s, tk.f, i0, i1);
+            T* ax = auxr + st * AUXW;
+            if (lane < tk.na) {
+                if (N >= 3) cp_async_elem(ax + lane, A.W + s.woff[0][Am] + static_cast<long long>(i0) * IA + tk.a0 + lane);
+                if (N == 4)
+                    cp_async_elem(ax + 32 + lane, A.W + s.woff[1][Am] + static_cast<long long>(i1) * IA + tk.a0 + lane);
+            }
+            if (N == 4) cp_async_elem(ax + 64 + lane, A.W + s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1);
+            cp_async_commit();
+        }
         if (lane == 0) {
             const Task tk = task_at(ic, ct, RBK);
             T* buf = tiles + (static_cast<size_t>(warp) * S + st) * TC;
@@ -516,20 +548,6 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
     settle();
     for (int i = 0; i < S; ++i) issue_next(i);
 
-    auto load_aux = [&](const UnitCur& c, int t) {
-        const Task tk = task_at(c, t, RBK);
-        int i0, i1;
-        decode_f(s, tk.f, i0, i1);
-        ColAux<T> x;
-        x.w0 = x.w1 = x.sc = T(1);
-        if (lane < tk.na) {
-            if (N >= 3) x.w0 = __ldg(A.W + s.woff[0][Am] + static_cast<long long>(i0) * IA + tk.a0 + lane);
-            if (N == 4) x.w1 = __ldg(A.W + s.woff[1][Am] + static_cast<long long>(i1) * IA + tk.a0 + lane);
-        }
-        if (N == 4) x.sc = __ldg(A.W + s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1);
-        return x;
-    };
-
     int it = 0;
     for (int ui = blockIdx.x; ui < pl.nunits; ui += gridDim.x) {
         UnitCur uc;
@@ -543,15 +561,13 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
         for (int r2 = 0; r2 < RMAX; ++r2)
 #pragma unroll
             for (int r = 0; r < RA; ++r) z[r2][r] = T(0);
-        ColAux<T> cur;
-        if (warp < nt) cur = load_aux(uc, warp);
         int zslot = -1;
         for (int t = warp; t < nt; t += NWARP, ++it) {
-            ColAux<T> nxt = cur;
-            if (t + NWARP < nt) nxt = load_aux(uc, t + NWARP);
             const int st = it % S;
             const unsigned par = static_cast<unsigned>((it / S) & 1);
             T* buf = tiles + (static_cast<size_t>(warp) * S + st) * TC;
+            const T* ax = auxr + st * AUXW;
+            cp_async_wait_ring(S);
             const bool ok = warp_wait(&bars[warp * S + st], par, abortf, A.flags) && !*abortf;
             const Task tk = task_at(uc, t, RBK);
             if (ok) {
@@ -560,7 +576,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
                 // phi rows (lane = row); rows past na are zero
                 {
                     const int a = lane;
-                    const T om = cur.w0 * cur.w1;
+                    const T om = (a < tk.na) ? (N >= 3 ? ax[a] : T(1)) * (N == 4 ? ax[32 + a] : T(1)) : T(0);
 #pragma unroll
                     for (int r = 0; r < RA; ++r)
                         phi[a * RA + r] = a < tk.na ? om * gAt[r * IA + tk.a0 + a] : T(0);
@@ -595,7 +611,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
 #pragma unroll
                     for (int r = 0; r < RA; ++r) z[0][r] += colok ? u0[r] : T(0);
                 } else {
-                    const T scale = colok ? cur.sc : T(0);
+                    const T scale = colok ? (N == 4 ? ax[64 + lane] : T(1)) : T(0);
                     const int il2 = N == 4 ? i1 : i0;
                     const T* gl = gL + il2;
                     const int Il2 = s.I[l2];
@@ -613,7 +629,6 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
                 issue_next(st);
             else
                 zslot = st;
-            cur = nxt;
         }
         const int nwk = min(NWARP, nt);
         if (zslot >= 0) {

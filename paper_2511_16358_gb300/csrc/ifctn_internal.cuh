@@ -80,7 +80,7 @@ struct ContractPlan {
     int xr;          // ROW, N = 3, k = 0: offset of the W_{A,B} rows in a stage
     int zw;          // width of one register-fold row (elements)
     int grid;        // CTAs (one per SM)
-    int off_tile, off_tab, off_gtab, off_wab, off_zs;  // shared-memory carve-up (bytes)
+    int off_tile, off_tab, off_gtab, off_wab, off_zs, off_aux;  // shared-memory carve-up (bytes)
     int fin_div, fin_mod;  // > 0: the units covering output row r are r / fin_div + n * fin_mod
     long long part_elems;
 };
