@@ -305,11 +305,16 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
             }
         }
     }
-    // --- M, units covering every row: 32-column tiles, warps split the units ---
+    // --- M, units covering every row: column tiles of TW columns (narrower
+    // when 32-wide tiles would leave CTAs idle); within a warp the lanes of a
+    // column split the units and meet by shuffles, warps meet in shared memory ---
     if (pl.kcase != CASE_F && pl.key_div > 0) {
         const int Qp = pl.Qp;
         const int ncol = pl.nrow * Qp;
-        const int ntile = (ncol + 31) / 32;
+        int TW = 32;
+        while (TW > 8 && (ncol + TW - 1) / TW < static_cast<int>(gridDim.x)) TW >>= 1;
+        const int SUBS = 32 / TW;
+        const int ntile = (ncol + TW - 1) / TW;
         const int Rd = pl.dmode >= 0 ? s.R[k][pl.dmode] : 1;
         const int nu = pl.nunits;
         T* coef = reinterpret_cast<T*>(smem);      // Rd x nu
@@ -322,15 +327,16 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
             }
             __syncthreads();
             const int warp = threadIdx.x >> 5;
+            const int cl = lane % TW, sub = lane / TW;
             for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-                const int c = tile * 32 + lane;
+                const int c = tile * TW + cl;
                 const bool valid = c < ncol;
                 T acc[RMAX];
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r) acc[r] = T(0);
                 const T* pc = p.part + c;
 #pragma unroll 4
-                for (int u = warp; u < nu; u += PW) {
+                for (int u = warp * SUBS + sub; u < nu; u += PW * SUBS) {
                     const T v = valid ? pc[static_cast<size_t>(u) * ncol] : T(0);
 #pragma unroll
                     for (int r = 0; r < RMAX; ++r)
@@ -338,11 +344,16 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
                 }
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r)
-                    if (r < Rd) red[(warp * RMAX + r) * 32 + lane] = acc[r];
+                    if (r < Rd)
+                        for (int o = TW; o < 32; o <<= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+                if (sub == 0)
+#pragma unroll
+                    for (int r = 0; r < RMAX; ++r)
+                        if (r < Rd) red[(warp * RMAX + r) * 32 + cl] = acc[r];
                 __syncthreads();
-                for (int idx = threadIdx.x; idx < Rd * 32; idx += PT) {
-                    const int r = idx / 32, ln = idx - r * 32;
-                    const int cc = tile * 32 + ln;
+                for (int idx = threadIdx.x; idx < Rd * TW; idx += PT) {
+                    const int r = idx / TW, ln = idx - r * TW;
+                    const int cc = tile * TW + ln;
                     if (cc < ncol) {
                         T v = T(0);
                         for (int w2 = 0; w2 < PW; ++w2) v += red[(w2 * RMAX + r) * 32 + ln];
