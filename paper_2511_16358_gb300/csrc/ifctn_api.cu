@@ -1106,8 +1106,7 @@ struct Engine : ifctn_ctx {
         cudaError_t e;
         for (int k = 0; k < sh.N; ++k) {
             if ((e = enqueue_mode_systems(k)) != cudaSuccess) return e;
-            if ((e = launch_solve<T>(sh, k, prob.rho, Kk.p, Mk[k].p, Gd.p, Gt.p, W.p, flags(), done(), st)) !=
-                cudaSuccess)
+            if ((e = launch_solve_cols<T>(pp, k, st)) != cudaSuccess)
                 return e;
         }
         pp.Xt = (logm && truth) ? Xt.p : nullptr;
@@ -1124,7 +1123,7 @@ struct Engine : ifctn_ctx {
         for (int k = 0; k < sh.N; ++k) {
             const int nm = sh.N - 1;
             n += (nm == 3 ? 3 : nm == 2 ? 2 : 1);  // gram chain
-            n += 4;                                 // contract, finish, solve, pair refresh
+            n += 3;                                 // contract, finish, solve (with the W refresh)
         }
         n += 2;  // xupdate, finalize
         return n;
@@ -1271,7 +1270,7 @@ struct Engine : ifctn_ctx {
         switch (stage) {
             case 0: CK(launch_contract<T>(cargs(k), st)); break;
             case 1: CK(launch_gram<T>(sh, k, Gt.p, W.p, t1.p, t2.p, Kk.p, done(), st)); break;
-            case 2: CK(launch_solve<T>(sh, k, prob.rho, Kk.p, Mk[k].p, Gd.p, Gt.p, W.p, flags(), done(), st)); break;
+            case 2: CK(launch_solve_cols<T>(pp, k, st)); break;
             case 3: CK(launch_xupdate_slab<T>(pp, xpart.p, slab_xblocks(), st)); break;
             case 4:
                 CK(launch_contract_finish<T>(sh, k, plan[k], units.p + unit_off[k], part.p, Gt.p, Mk[k].p, done(),

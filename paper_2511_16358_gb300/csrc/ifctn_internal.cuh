@@ -154,7 +154,17 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 // stage_wait(), which also synchronises the CTA.
 template <typename T>
 __device__ __forceinline__ void stage_async(T* dst, const T* src, int n) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int i0 = 0;
+    if (((smem_u32(dst) | static_cast<unsigned>(reinterpret_cast<uintptr_t>(src))) & 15u) == 0) {
+        // both 16-byte aligned: 16-byte copies, then the elements of the tail
+        constexpr int E = 16 / static_cast<int>(sizeof(T));
+        const int nv = n / E;
+        for (int v = threadIdx.x; v < nv; v += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + v * E)), "l"(src + v * E)
+                         : "memory");
+        i0 = nv * E;
+    }
+    for (int i = i0 + threadIdx.x; i < n; i += blockDim.x) {
         if (sizeof(T) == 4)
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst + i)), "l"(src + i) : "memory");
         else

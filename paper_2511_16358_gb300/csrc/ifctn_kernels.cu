@@ -125,161 +125,6 @@ __global__ void __launch_bounds__(256) k_gram_fin(const __grid_constant__ Shape 
 }
 
 // ---------------------------------------------------------------------------
-// Proximal block solves of mode k, eq. (updateG).  One warp per column j.
-// With E_j the Kronecker product of v_m = G_{k,m}(:,j) over m != k, m != i
-// (identity in slot i), the normal equations of column j of G_{k,i} are
-//   (E_j^T K_k E_j + rho I) g = E_j^T M_k(j,:)^T + rho g_old,
-// which equals (A_j^T A_j + rho I) g = A_j^T x_j + rho g_old with
-// A_j = Z_k E_j.  The stages i != k run in ascending order, each with the
-// latest columns (Gauss-Seidel); column j's chain touches only column j of
-// the G_{k,.}, so the I_k chains are independent.  Afterwards row/column j
-// of every W_{k,i} is refreshed.
-// ---------------------------------------------------------------------------
-constexpr int SOLVE_WARPS = 8;
-constexpr int QMAX = 512;
-constexpr int SOLVE_K_SMEM_MAX = 160 * 1024;  // K_k staged in shared memory up to this size
-
-// With kin_smem, the block first copies K_k (Q x Q) into shared memory: every
-// warp's H assembly reads all of it, with strided access, Q^2 times per stage.
-template <typename T>
-__global__ void __launch_bounds__(SOLVE_WARPS * 32) k_solve(const __grid_constant__ Shape s, const int k, const double rho,
-                                                           const T* __restrict__ Kg,
-                                                           const double* __restrict__ Mk,
-                                                           double* __restrict__ Gd, T* __restrict__ Gt,
-                                                           T* __restrict__ W, int* __restrict__ flags,
-                                                           const int* __restrict__ done, const int kin_smem) {
-    if (*done) return;
-    extern __shared__ __align__(16) unsigned char ksm[];
-    __shared__ double vsh[SOLVE_WARPS][3][RMAX];
-    __shared__ T om[SOLVE_WARPS][QMAX];
-    __shared__ double Hs[SOLVE_WARPS][RMAX * RMAX];
-    __shared__ double bs[SOLVE_WARPS][RMAX];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int Ik = s.I[k];
-    const int j = blockIdx.x * SOLVE_WARPS + warp;
-    int m[3];
-    const int nm = nonk_modes(s, k, m);
-    int Rm[3] = {1, 1, 1}, st[3] = {1, 1, 1};
-    int Q = 1;
-    for (int t = 0; t < nm; ++t) {
-        Rm[t] = s.R[k][m[t]];
-        Q *= Rm[t];
-    }
-    const T* Kk = Kg;
-    if (kin_smem) {
-        T* kd = reinterpret_cast<T*>(ksm);
-        stage_async(kd, Kg, Q * Q);
-        stage_wait();
-        Kk = kd;
-    }
-    if (j >= Ik) return;
-    for (int t = nm - 2; t >= 0; --t) st[t] = st[t + 1] * Rm[t + 1];
-    for (int t = 0; t < nm; ++t)
-        for (int r = lane; r < Rm[t]; r += 32)
-            vsh[warp][t][r] = Gd[s.goff[k][m[t]] + r * Ik + j];
-    __syncwarp();
-    const double* Mj = Mk + static_cast<long long>(j) * Q;
-    for (int ti = 0; ti < nm; ++ti) {
-        const int i = m[ti], Ri = Rm[ti], sp = st[ti];
-        const int Qo = Q / Ri;
-        const int nhi = Qo / sp;  // combos of the slots before ti
-        // omega(o) = prod over slots t != ti of v_t(digit_t(o))
-        for (int o = lane; o < Qo; o += 32) {
-            double w = 1.0;
-            int rem = o;
-            for (int t = nm - 1; t >= 0; --t) {
-                if (t == ti) continue;
-                const int d = rem % Rm[t];
-                rem /= Rm[t];
-                w *= vsh[warp][t][d];
-            }
-            om[warp][o] = to_t<T>(w);
-        }
-        __syncwarp();
-        for (int c = 0; c < Ri; ++c) {
-            for (int c2 = c; c2 < Ri; ++c2) {
-                T acc = T(0);
-                for (int o = lane; o < Qo; o += 32) {
-                    const int hi = o / sp, lo = o - hi * sp;
-                    const int q = hi * Ri * sp + c * sp + lo;
-                    T sacc = T(0);
-                    for (int h2 = 0; h2 < nhi; ++h2) {
-                        const T* kr = Kk + static_cast<long long>(h2 * Ri * sp + c2 * sp) * Q + q;
-                        const T* ow = &om[warp][h2 * sp];
-                        for (int l2 = 0; l2 < sp; ++l2) sacc = fma(kr[static_cast<long long>(l2) * Q], ow[l2], sacc);
-                    }
-                    acc = fma(om[warp][o], sacc, acc);
-                }
-                const double h = static_cast<double>(warp_sum(acc));
-                if (lane == 0) {
-                    Hs[warp][c * Ri + c2] = h;
-                    Hs[warp][c2 * Ri + c] = h;
-                }
-            }
-            double bacc = 0.0;
-            for (int o = lane; o < Qo; o += 32) {
-                const int hi = o / sp, lo = o - hi * sp;
-                const int q = hi * Ri * sp + c * sp + lo;
-                bacc = fma(static_cast<double>(om[warp][o]), Mj[q], bacc);
-            }
-            bacc = warp_sum(bacc);
-            if (lane == 0) bs[warp][c] = bacc + rho * vsh[warp][ti][c];
-        }
-        __syncwarp();
-        if (lane == 0) {
-            double* H = Hs[warp];
-            double* b = bs[warp];
-            bool okc = true;
-            for (int c = 0; c < Ri; ++c) H[c * Ri + c] += rho;
-            // textbook Cholesky, H = L L^T in place (lower)
-            for (int c = 0; c < Ri && okc; ++c) {
-                double d = H[c * Ri + c];
-                for (int t = 0; t < c; ++t) d -= H[c * Ri + t] * H[c * Ri + t];
-                if (!(d > 0.0)) {
-                    okc = false;
-                    break;
-                }
-                d = sqrt(d);
-                H[c * Ri + c] = d;
-                for (int r = c + 1; r < Ri; ++r) {
-                    double v = H[r * Ri + c];
-                    for (int t = 0; t < c; ++t) v -= H[r * Ri + t] * H[c * Ri + t];
-                    H[r * Ri + c] = v / d;
-                }
-            }
-            if (okc) {
-                for (int r = 0; r < Ri; ++r) {
-                    double v = b[r];
-                    for (int t = 0; t < r; ++t) v -= H[r * Ri + t] * b[t];
-                    b[r] = v / H[r * Ri + r];
-                }
-                for (int r = Ri - 1; r >= 0; --r) {
-                    double v = b[r];
-                    for (int t = r + 1; t < Ri; ++t) v -= H[t * Ri + r] * b[t];
-                    b[r] = v / H[r * Ri + r];
-                }
-                for (int r = 0; r < Ri; ++r)
-                    if (!isfinite(b[r])) okc = false;
-            }
-            if (!okc) {
-                atomicOr(flags, FLAG_NOTSPD);
-                for (int r = 0; r < Ri; ++r) b[r] = vsh[warp][ti][r];
-            }
-        }
-        __syncwarp();
-        for (int r = lane; r < Ri; r += 32) {
-            const double g = bs[warp][r];
-            vsh[warp][ti][r] = g;
-            Gd[s.goff[k][i] + r * Ik + j] = g;
-            Gt[s.goff[k][i] + r * Ik + j] = to_t<T>(g);
-        }
-        __syncwarp();
-    }
-    // W_{k,i} are refreshed by launch_pairs_mode after the kernel (all entries
-    // at once, instead of a warp per column j walking rows of G_{i,k})
-}
-
-// ---------------------------------------------------------------------------
 // Element index walker over the slab geometry (i0, i1 = F modes; a, b = the
 // last two modes) with carries, so no division runs per element.
 // ---------------------------------------------------------------------------
@@ -561,7 +406,7 @@ __global__ void __launch_bounds__(256) k_metrics(const long long P, const T* __r
 }
 
 template <typename T>
-__global__ void k_pairs(const __grid_constant__ Shape s, const double* __restrict__ Gd, T* __restrict__ W, const int only) {
+__global__ void k_pairs(const __grid_constant__ Shape s, const double* __restrict__ Gd, T* __restrict__ W) {
     const long long gtid = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     const long long gstr = static_cast<long long>(gridDim.x) * blockDim.x;
     for (long long idx = gtid; idx < s.wsize; idx += gstr) {
@@ -572,7 +417,6 @@ __global__ void k_pairs(const __grid_constant__ Shape s, const double* __restric
                     p = pp;
                     q = qq;
                 }
-        if (only >= 0 && p != only && q != only) continue;  // pairs of one mode only
         // the last pair whose offset is <= idx (offsets increase in (p,q) order)
         const long long rel = idx - s.woff[p][q];
         const int a = static_cast<int>(rel / s.I[q]), b = static_cast<int>(rel % s.I[q]);
@@ -753,26 +597,6 @@ cudaError_t launch_gram(const Shape& sh, int k, const T* Gt, const T* W, T* t1, 
 }
 
 template <typename T>
-cudaError_t launch_solve(const Shape& sh, int k, double rho, const T* Kk, const double* Mk, double* Gd,
-                         T* Gt, T* W, int* flags, const int* done, cudaStream_t st) {
-    const int blocks = (sh.I[k] + SOLVE_WARPS - 1) / SOLVE_WARPS;
-    long long Q = 1;
-    for (int m = 0; m < sh.N; ++m)
-        if (m != k) Q *= sh.R[k][m];
-    const long long kbytes = Q * Q * static_cast<long long>(sizeof(T));
-    const int kin = kbytes <= SOLVE_K_SMEM_MAX ? 1 : 0;
-    const int dyn = kin ? static_cast<int>(kbytes) : 0;
-    if (dyn > 0) {
-        cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_solve<T>), dyn);
-        if (e != cudaSuccess) return e;
-    }
-    k_solve<T><<<blocks, SOLVE_WARPS * 32, dyn, st>>>(sh, k, rho, Kk, Mk, Gd, Gt, W, flags, done, kin);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_pairs_mode<T>(sh, k, Gd, W, st);
-}
-
-template <typename T>
 cudaError_t launch_xupdate(const Shape& sh, double rho, T* X, const uint32_t* maskbits, const T* W,
                            double* xpart, int nblocks, const int* done, cudaStream_t st) {
     k_xupdate<T><<<nblocks, 256, 0, st>>>(sh, static_cast<T>(rho), static_cast<T>(1.0 / (1.0 + rho)), X,
@@ -796,13 +620,7 @@ cudaError_t launch_metrics(const Shape& sh, const T* X, const T* Xt, const uint3
 
 template <typename T>
 cudaError_t launch_pairs(const Shape& sh, const double* Gd, T* W, cudaStream_t st) {
-    k_pairs<T><<<grid_for(sh.wsize, 256, 4096), 256, 0, st>>>(sh, Gd, W, -1);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_pairs_mode(const Shape& sh, int k, const double* Gd, T* W, cudaStream_t st) {
-    k_pairs<T><<<grid_for(sh.wsize, 256, 4096), 256, 0, st>>>(sh, Gd, W, k);
+    k_pairs<T><<<grid_for(sh.wsize, 256, 4096), 256, 0, st>>>(sh, Gd, W);
     return cudaGetLastError();
 }
 
@@ -852,15 +670,12 @@ cudaError_t launch_scale_factors(int n, double* Gd, const double* ratio, double 
 #define IFCTN_INST(T)                                                                                    \
     template cudaError_t launch_gram<T>(const Shape&, int, const T*, const T*, T*, T*, T*, const int*,   \
                                         cudaStream_t);                                                   \
-    template cudaError_t launch_solve<T>(const Shape&, int, double, const T*, const double*, double*, T*, \
-                                         T*, int*, const int*, cudaStream_t);                            \
     template cudaError_t launch_xupdate<T>(const Shape&, double, T*, const uint32_t*, const T*, double*,  \
                                            int, const int*, cudaStream_t);                               \
     template cudaError_t launch_reconstruct<T>(const Shape&, const T*, T*, double*, int, cudaStream_t);  \
     template cudaError_t launch_metrics<T>(const Shape&, const T*, const T*, const uint32_t*, double*,    \
                                            int, const int*, cudaStream_t);                               \
     template cudaError_t launch_pairs<T>(const Shape&, const double*, T*, cudaStream_t);                 \
-    template cudaError_t launch_pairs_mode<T>(const Shape&, int, const double*, T*, cudaStream_t);       \
     template cudaError_t launch_init_x<T>(long long, const T*, const uint8_t*, T*, cudaStream_t);        \
     template cudaError_t launch_cast_factors<T>(int, const double*, T*, cudaStream_t);
 IFCTN_INST(float)

@@ -58,12 +58,6 @@ template <typename T>
 cudaError_t launch_gram(const Shape& sh, int k, const T* Gt, const T* W, T* t1, T* t2, T* Kk,
                         const int* done, cudaStream_t st);
 
-// Per-column proximal solves of mode k (eq. (updateG)), Gauss-Seidel over i,
-// followed by the refresh of the pair matrices W_{k,i} (launch_pairs_mode).
-template <typename T>
-cudaError_t launch_solve(const Shape& sh, int k, double rho, const T* Kk, const double* Mk,
-                         double* Gd, T* Gt, T* W, int* flags, const int* done, cudaStream_t st);
-
 // eq. (updateX) fused with the reconstruction and the sweep's reductions.
 template <typename T>
 cudaError_t launch_xupdate(const Shape& sh, double rho, T* X, const uint32_t* maskbits, const T* W,
@@ -82,9 +76,6 @@ cudaError_t launch_metrics(const Shape& sh, const T* X, const T* Xt, const uint3
 // All pair matrices from the FP64 master factors.
 template <typename T>
 cudaError_t launch_pairs(const Shape& sh, const double* Gd, T* W, cudaStream_t st);
-// The pair matrices W_{k,i} (i != k) of one mode.
-template <typename T>
-cudaError_t launch_pairs_mode(const Shape& sh, int k, const double* Gd, T* W, cudaStream_t st);
 
 // X^0 = P_Omega(O) and the mask bitset.
 template <typename T>

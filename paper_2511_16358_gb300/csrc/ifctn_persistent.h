@@ -48,6 +48,9 @@ template <typename T>
 int persistent_max_grid(int smem);
 template <typename T>
 cudaError_t launch_persistent(const SweepParams<T>& p, int grid, int smem, cudaStream_t st);
+// the column solves of mode k with the W_{k,.} refresh (per-stage path)
+template <typename T>
+cudaError_t launch_solve_cols(const SweepParams<T>& p, int k, cudaStream_t st);
 // the X update of the per-stage path: per-CTA sums (6 of 8 slots) into xpart
 template <typename T>
 cudaError_t launch_xupdate_slab(const SweepParams<T>& p, double* xpart, int nblocks, cudaStream_t st);

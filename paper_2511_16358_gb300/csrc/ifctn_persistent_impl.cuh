@@ -522,6 +522,114 @@ __device__ __forceinline__ unsigned long long gtimer() {
         if (stamp_col && lane == 0) p.tstamp[40 + (n)] = gtimer();             \
     } while (0)
 
+// Shared-memory layout of the solve phase (byte offsets from the phase's base):
+//   per-warp scratch (WSD doubles: H, the current columns and their T copies,
+//   rhs, solution, factor), the tables G_{i,k} (T), per-warp omega / M_k row
+//   in T / K index table (Qa entries each), K_k (T, when kept in shared
+//   memory), per-warp M_k row (FP64, the cp.async target).
+constexpr int WSD = 2 * RMAX * RMAX + 11 * RMAX;  // doubles per warp
+
+struct SolveLayout {
+    long long gik, warp, wstride, K, Ms, total;
+};
+
+__host__ __device__ inline SolveLayout solve_layout(int Q, int tot, int sz, bool ksm) {
+    SolveLayout L;
+    const long long Qa = (Q + 3) & ~3;
+    L.gik = static_cast<long long>(PW) * WSD * 8;
+    L.warp = (L.gik + static_cast<long long>(tot) * sz + 15) & ~15LL;
+    L.wstride = Qa * (2 * sz + 4);
+    L.K = (L.warp + PW * L.wstride + 15) & ~15LL;
+    L.Ms = (L.K + (ksm ? static_cast<long long>(Q) * Q * sz : 0) + 15) & ~15LL;
+    L.total = L.Ms + static_cast<long long>(PW) * Q * 8;
+    return L;
+}
+
+// The normal equations of one stage (slot ti of Ri = RI values) of one
+// column, assembled by one warp:
+//   H(c, c2) = sum_{o, o2} omega(o) omega(o2) K[(o2, c2), (o, c)] + rho [c = c2]
+//   b(c)     = sum_o omega(o) M_k(j, (o, c)) + rho g_old(c)
+// where (o, c) is the K index with digit c in slot ti, cb[o] the index of
+// (o, 0) and sp the index step of the slot.  Lanes take (o, o2) combinations
+// and keep every pair c <= c2 in registers (K is symmetric, so H is); the lane
+// sums are reduced across the warp once.
+template <typename T, int RI>
+__device__ __forceinline__ void stage_system(const T* __restrict__ K, const T* __restrict__ om,
+                                             const int* __restrict__ cb, const T* __restrict__ mrow, int Q,
+                                             int Qo, int sp, int lane, double rho, const double* __restrict__ gold,
+                                             double* Hd, double* bd) {
+    constexpr int NP = RI * (RI + 1) / 2;
+    T acc[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) acc[q] = T(0);
+    const int spQ = sp * Q;
+    const int n = Qo * Qo;
+    const int dq = 32 / Qo, dr = 32 - dq * Qo;
+    int o = lane / Qo;
+    int o2 = lane - o * Qo;
+    for (int f = lane; f < n; f += 32) {
+        const T w = om[o] * om[o2];
+        const T* kr = K + cb[o2] * Q + cb[o];
+        int q = 0;
+#pragma unroll
+        for (int c2 = 0; c2 < RI; ++c2)
+#pragma unroll
+            for (int c = 0; c <= c2; ++c, ++q) acc[q] = fma(kr[c2 * spQ + c * sp], w, acc[q]);
+        o += dq;
+        o2 += dr;
+        if (o2 >= Qo) {
+            o2 -= Qo;
+            ++o;
+        }
+    }
+    T bacc[RI];
+#pragma unroll
+    for (int c = 0; c < RI; ++c) bacc[c] = T(0);
+    for (int o1 = lane; o1 < Qo; o1 += 32) {
+        const T w = om[o1];
+        const T* mr = mrow + cb[o1];
+#pragma unroll
+        for (int c = 0; c < RI; ++c) bacc[c] = fma(w, mr[c * sp], bacc[c]);
+    }
+    // lane q keeps pair q (and q + 32), lane c keeps b(c)
+    T hv = T(0), hv2 = T(0), bv = T(0);
+    int hr = 0, hc = 0, hr2 = 0, hc2 = 0;
+    {
+        int q = 0;
+#pragma unroll
+        for (int c2 = 0; c2 < RI; ++c2)
+#pragma unroll
+            for (int c = 0; c <= c2; ++c, ++q) {
+                const T v = warp_sum(acc[q]);
+                if (lane == q) {
+                    hv = v;
+                    hr = c2;
+                    hc = c;
+                } else if (lane + 32 == q) {
+                    hv2 = v;
+                    hr2 = c2;
+                    hc2 = c;
+                }
+            }
+    }
+#pragma unroll
+    for (int c = 0; c < RI; ++c) {
+        const T v = warp_sum(bacc[c]);
+        if (lane == c) bv = v;
+    }
+    if (lane < NP) {
+        const double h = static_cast<double>(hv) + (hr == hc ? rho : 0.0);
+        Hd[hr * RI + hc] = h;
+        Hd[hc * RI + hr] = h;
+    }
+    if (lane + 32 < NP) {
+        const double h = static_cast<double>(hv2) + (hr2 == hc2 ? rho : 0.0);
+        Hd[hr2 * RI + hc2] = h;
+        Hd[hc2 * RI + hr2] = h;
+    }
+    if (lane < RI) bd[lane] = static_cast<double>(bv) + rho * gold[lane];
+}
+
 template <typename T>
 __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem, bool stamp = false) {
     const Shape& s = p.sh;
@@ -540,34 +648,34 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
         Q *= Rm[t];
     }
     for (int t = nm - 2; t >= 0; --t) st[t] = st[t + 1] * Rm[t + 1];
-    // shared layout: per-warp scratch (doubles), then G_{i,k} in T, then
-    // per-warp omega (T, Q <= 512), then K (T) when it fits
-    constexpr int WSD = 2 * RMAX * RMAX + 8 * RMAX;  // doubles per warp
-    double* my = reinterpret_cast<double*>(smem) + warp * WSD;
-    double* Hd = my;                      // RMAX*RMAX: H (FP64)
-    double* vs = Hd + RMAX * RMAX;        // 3 x RMAX current columns
-    double* bd = vs + 3 * RMAX;           // RMAX rhs (FP64)
-    double* gd = bd + RMAX;               // RMAX solution (FP64)
-    double* rd = gd + RMAX;               // RMAX residual (FP64)
-    using F = typename std::conditional<MIXED, float, double>::type;
-    F* Af = reinterpret_cast<F*>(rd + RMAX);   // RMAX*RMAX factor
-    F* invf = Af + RMAX * RMAX;                  // RMAX
-    F* xf = invf + RMAX;                         // RMAX
-    T* gik = reinterpret_cast<T*>(reinterpret_cast<double*>(smem) + PW * WSD);
     int gko[3];
     int tot = 0;
     for (int t = 0; t < nm; ++t) {
         gko[t] = tot;
         tot += Rm[t] * s.I[m[t]];
     }
-    for (int t = 0; t < nm; ++t) stage_async(gik + gko[t], p.Gt + s.goff[m[t]][k], Rm[t] * s.I[m[t]]);
-    T* om = gik + ((tot + 1) & ~1) + warp * 512;
-    T* Ks = gik + ((tot + 1) & ~1) + PW * 512;
     const bool ksm = p.solve_k_in_smem != 0;
-    // per-warp copy of the column's row of M_k (FP64), after K
-    double* Ms = reinterpret_cast<double*>(
-                     (reinterpret_cast<uintptr_t>(Ks + (ksm ? Q * Q : 0)) + 15) & ~uintptr_t(15)) +
-                 static_cast<size_t>(warp) * Q;
+    const SolveLayout L = solve_layout(Q, tot, static_cast<int>(sizeof(T)), ksm);
+    double* my = reinterpret_cast<double*>(smem) + warp * WSD;
+    double* Hd = my;                      // RMAX*RMAX: H (FP64)
+    double* vs = Hd + RMAX * RMAX;        // 3 x RMAX current columns
+    double* bd = vs + 3 * RMAX;           // RMAX rhs (FP64)
+    double* gd = bd + RMAX;               // RMAX solution (FP64)
+    double* rd = gd + RMAX;               // RMAX (spare)
+    using F = typename std::conditional<MIXED, float, double>::type;
+    F* Af = reinterpret_cast<F*>(rd + RMAX);   // RMAX*RMAX factor
+    F* invf = Af + RMAX * RMAX;                  // RMAX
+    F* xf = invf + RMAX;                         // RMAX
+    T* vt = reinterpret_cast<T*>(my + 2 * RMAX * RMAX + 8 * RMAX);  // 3 x RMAX columns in T
+    T* gik = reinterpret_cast<T*>(smem + L.gik);
+    const int Qa = (Q + 3) & ~3;
+    T* om = reinterpret_cast<T*>(smem + L.warp + warp * L.wstride);
+    T* mf = om + Qa;
+    int* cb = reinterpret_cast<int*>(mf + Qa);
+    T* Ks = reinterpret_cast<T*>(smem + L.K);
+    double* Ms = reinterpret_cast<double*>(smem + L.Ms) + static_cast<size_t>(warp) * Q;
+    const T* mrow = MIXED ? mf : reinterpret_cast<const T*>(Ms);
+    for (int t = 0; t < nm; ++t) stage_async(gik + gko[t], p.Gt + s.goff[m[t]][k], Rm[t] * s.I[m[t]]);
     // the current columns G_{k,m}(:, j) and the row M_k(j, :) of a column,
     // copied asynchronously (the first column's together with the tables)
     auto fetch_column = [&](int j) {
@@ -595,68 +703,48 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
             asm volatile("cp.async.wait_all;" ::: "memory");
             __syncwarp();
         }
+        // the column vectors and the M_k row in T, converted once per column
+        for (int idx = lane; idx < nm * RMAX; idx += 32) {
+            const int t = idx / RMAX, r = idx - t * RMAX;
+            if (r < Rm[t]) vt[idx] = static_cast<T>(vs[idx]);
+        }
+        if (MIXED)
+            for (int q = lane; q < Q; q += 32) mf[q] = static_cast<T>(Ms[q]);
+        __syncwarp();
         IFCTN_SSTAMP(2);
         for (int ti = 0; ti < nm; ++ti) {
             const int i = m[ti], Ri = Rm[ti], sp = st[ti];
             const int Qo = Q / Ri;
-            for (int o2 = lane; o2 < Qo; o2 += 32) {
+            // omega(o) = prod over slots t != ti of v_t(digit_t(o)), and the
+            // K index of (o, c = 0)
+            for (int o = lane; o < Qo; o += 32) {
                 T w = T(1);
-                int rem = o2;
+                int rem = o;
                 for (int t = nm - 1; t >= 0; --t) {
                     if (t == ti) continue;
                     const int d = rem % Rm[t];
                     rem /= Rm[t];
-                    w *= static_cast<T>(vs[t * RMAX + d]);
+                    w *= vt[t * RMAX + d];
                 }
-                om[o2] = w;
+                om[o] = w;
+                const int hi = o / sp;
+                cb[o] = hi * Ri * sp + (o - hi * sp);
             }
             __syncwarp();
             if (ti == 0) IFCTN_SSTAMP(3);
-            // H(c, c2), c <= c2: lanes take pairs, each sums over (o, o2)
-            const int npair = Ri * (Ri + 1) / 2;
-            for (int pr = lane; pr < npair; pr += 32) {
-                int c = 0, rem = pr;
-                while (rem >= Ri - c) {
-                    rem -= Ri - c;
-                    ++c;
-                }
-                const int c2 = c + rem;
-                T acc0 = T(0), acc1 = T(0);
-                for (int o = 0; o < Qo; ++o) {
-                    const int hi = o / sp, lo = o - hi * sp;
-                    const T* kr = K + static_cast<long long>(hi * Ri * sp + c * sp + lo) * Q + c2 * sp;
-                    T sacc0 = T(0), sacc1 = T(0);
-                    for (int h2 = 0; h2 < Qo / sp; ++h2) {
-                        const T* kk = kr + h2 * Ri * sp;
-                        const T* ow = om + h2 * sp;
-                        int l2 = 0;
-                        for (; l2 + 1 < sp; l2 += 2) {
-                            sacc0 = fma(kk[l2], ow[l2], sacc0);
-                            sacc1 = fma(kk[l2 + 1], ow[l2 + 1], sacc1);
-                        }
-                        if (l2 < sp) sacc0 = fma(kk[l2], ow[l2], sacc0);
-                    }
-                    if (o & 1)
-                        acc1 = fma(om[o], sacc0 + sacc1, acc1);
-                    else
-                        acc0 = fma(om[o], sacc0 + sacc1, acc0);
-                }
-                const double h = static_cast<double>(acc0 + acc1);
-                Hd[c * Ri + c2] = h + (c == c2 ? rho : 0.0);
-                Hd[c2 * Ri + c] = h + (c == c2 ? rho : 0.0);
+            const double* gold = vs + ti * RMAX;
+            switch (Ri) {
+                case 1: stage_system<T, 1>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
+                case 2: stage_system<T, 2>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
+                case 3: stage_system<T, 3>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
+                case 4: stage_system<T, 4>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
+                case 5: stage_system<T, 5>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
+                case 6: stage_system<T, 6>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
+                case 7: stage_system<T, 7>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
+                default: stage_system<T, 8>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
             }
             __syncwarp();
             if (ti == 0) IFCTN_SSTAMP(4);
-            // b(c) = E^T M(j,:) + rho g_old: lanes take c
-            for (int c = lane; c < Ri; c += 32) {
-                T acc = T(0);
-                for (int o = 0; o < Qo; ++o) {
-                    const int hi = o / sp, lo = o - hi * sp;
-                    acc = fma(om[o], static_cast<T>(Ms[hi * Ri * sp + c * sp + lo]), acc);
-                }
-                bd[c] = static_cast<double>(acc) + rho * vs[ti * RMAX + c];
-            }
-            __syncwarp();
             if (ti == 0) IFCTN_SSTAMP(5);
             for (int idx = lane; idx < Ri * Ri; idx += 32) Af[idx] = static_cast<F>(Hd[idx]);
             __syncwarp();
@@ -671,18 +759,16 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
                 __syncwarp();
                 if (ti == 0) IFCTN_SSTAMP(7);
                 if (MIXED) {
-                    for (int it = 0; it < 1; ++it) {
-                        // residual in FP64, correction in FP32
-                        if (lane < Ri) {
-                            double r = bd[lane];
-                            for (int t = 0; t < Ri; ++t) r -= Hd[lane * Ri + t] * gd[t];
-                            xf[lane] = static_cast<F>(r);
-                        }
-                        __syncwarp();
-                        ldlt_solve_warp<F>(Af, invf, xf, Ri, lane);
-                        if (lane < Ri) gd[lane] += static_cast<double>(xf[lane]);
-                        __syncwarp();
+                    // one step of refinement: residual in FP64, correction in FP32
+                    if (lane < Ri) {
+                        double r = bd[lane];
+                        for (int t = 0; t < Ri; ++t) r -= Hd[lane * Ri + t] * gd[t];
+                        xf[lane] = static_cast<F>(r);
                     }
+                    __syncwarp();
+                    ldlt_solve_warp<F>(Af, invf, xf, Ri, lane);
+                    if (lane < Ri) gd[lane] += static_cast<double>(xf[lane]);
+                    __syncwarp();
                 }
                 if (lane < Ri && !isfinite(gd[lane])) okc = false;
                 okc = __all_sync(0xffffffffu, okc);
@@ -695,9 +781,11 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
             if (ti == 0) IFCTN_SSTAMP(8);
             for (int r = lane; r < Ri; r += 32) {
                 const double g = gd[r];
+                const T gt = static_cast<T>(g);
                 vs[ti * RMAX + r] = g;
+                vt[ti * RMAX + r] = gt;
                 p.Gd[s.goff[k][i] + r * Ik + j] = g;
-                p.Gt[s.goff[k][i] + r * Ik + j] = static_cast<T>(g);
+                p.Gt[s.goff[k][i] + r * Ik + j] = gt;
             }
             __syncwarp();
             if (ti == 0) IFCTN_SSTAMP(9);
@@ -710,7 +798,7 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
             const T* gk = gik + gko[t];
             T v[RMAX];
 #pragma unroll
-            for (int r = 0; r < RMAX; ++r) v[r] = r < Ri ? static_cast<T>(vs[t * RMAX + r]) : T(0);
+            for (int r = 0; r < RMAX; ++r) v[r] = r < Ri ? vt[t * RMAX + r] : T(0);
             for (int b = lane; b < Ii; b += 32) {
                 T w = T(0);
 #pragma unroll
@@ -738,11 +826,13 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
             for (int idx = tid; idx < ncol * Ii; idx += PT) {
                 const int w = idx / Ii, b = idx - w * Ii;
                 const int j = w * gridDim.x + blockIdx.x;
-                const double* vsw = reinterpret_cast<double*>(smem) + w * WSD + RMAX * RMAX + t * RMAX;
+                const T* vtw =
+                    reinterpret_cast<const T*>(reinterpret_cast<double*>(smem) + w * WSD + 2 * RMAX * RMAX + 8 * RMAX) +
+                    t * RMAX;
                 T acc = T(0);
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r)
-                    if (r < Ri) acc = fma(static_cast<T>(vsw[r]), gk[r * Ii + b], acc);
+                    if (r < Ri) acc = fma(vtw[r], gk[r * Ii + b], acc);
                 if (k < i)
                     p.W[s.woff[k][i] + static_cast<long long>(j) * Ii + b] = acc;
                 else
@@ -1154,6 +1244,17 @@ __global__ void __launch_bounds__(PT) k_xupdate_slab(const __grid_constant__ Swe
 }
 
 
+// The column solves of mode k for the per-stage path: the solve phase above
+// on a grid of ceil(I_k / PW) CTAs, so every warp takes one column and the
+// CTA refreshes the W_{k,.} entries of its columns before it exits.
+template <typename T>
+__global__ void __launch_bounds__(PT) k_solve_cols(const __grid_constant__ SweepParams<T> p, const int k) {
+    if (*reinterpret_cast<volatile const int*>(p.done)) return;
+    extern __shared__ __align__(128) unsigned char ssm[];
+    solve_phase<T>(p, k, ssm);
+}
+
+
 // CTA 0 stamps the end of every phase of the first sweep (profiling aid)
 #define IFCTN_STAMP(p, sw, slot)                                                        \
     do {                                                                              \
@@ -1298,11 +1399,7 @@ int persistent_smem_bytes(const SweepParams<T>& p) {
             Q *= s.R[k][m[t]];
             tot += s.R[k][m[t]] * s.I[m[t]];
         }
-        long long solve = static_cast<long long>(PW) * (2 * RMAX * RMAX + 8 * RMAX) * 8 +
-                          static_cast<long long>(tot + 2) * sizeof(T) + static_cast<long long>(PW) * 512 * sizeof(T);
-        if (p.solve_k_in_smem) solve += static_cast<long long>(Q) * Q * sizeof(T);
-        solve += 16 + static_cast<long long>(PW) * Q * 8;  // rows of M_k (FP64), 16-byte aligned
-        need = std::max(need, solve);
+        need = std::max(need, solve_layout(Q, tot, static_cast<int>(sizeof(T)), p.solve_k_in_smem != 0).total);
         // reduce_phase (column tiles): coefficients + cross-warp sums
         need = std::max<long long>(need, (static_cast<long long>(RMAX) * p.pl[k].nunits + 4 +
                                           static_cast<long long>(PW) * RMAX * 32) * sizeof(T));
@@ -1340,6 +1437,25 @@ cudaError_t launch_xupdate_slab(const SweepParams<T>& p, double* xpart, int nblo
     cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_xupdate_slab<T>), smem);
     if (e != cudaSuccess) return e;
     k_xupdate_slab<T><<<nblocks, PT, smem, st>>>(p, xpart);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_solve_cols(const SweepParams<T>& p0, int k, cudaStream_t st) {
+    const Shape& s = p0.sh;
+    int Q = 1, tot = 0;
+    for (int q = 0; q < s.N; ++q)
+        if (q != k) {
+            Q *= s.R[k][q];
+            tot += s.R[k][q] * s.I[q];
+        }
+    SweepParams<T> p = p0;
+    const int sz = static_cast<int>(sizeof(T));
+    p.solve_k_in_smem = solve_layout(Q, tot, sz, true).total + 64 <= 220 * 1024 ? 1 : 0;
+    const int smem = static_cast<int>(solve_layout(Q, tot, sz, p.solve_k_in_smem != 0).total + 64);
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_solve_cols<T>), smem);
+    if (e != cudaSuccess) return e;
+    k_solve_cols<T><<<(s.I[k] + PW - 1) / PW, PT, smem, st>>>(p, k);
     return cudaGetLastError();
 }
 
