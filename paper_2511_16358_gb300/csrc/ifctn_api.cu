@@ -1118,15 +1118,18 @@ struct Engine : ifctn_ctx {
 
     int slab_xblocks() const { return static_cast<int>(std::min<long long>(xpart.n / 8, 8LL * num_sms())); }
 
-    int count_launches() const {
-        int n = 0;
-        for (int k = 0; k < sh.N; ++k) {
-            const int nm = sh.N - 1;
-            n += (nm == 3 ? 3 : nm == 2 ? 2 : 1);  // gram chain
-            n += 3;                                 // contract, finish, solve (with the W refresh)
+    // kernel launches of one sweep: the kernel nodes of its captured graph
+    static int count_kernel_nodes(cudaGraph_t g) {
+        size_t n = 0;
+        if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return 0;
+        std::vector<cudaGraphNode_t> nodes(n);
+        if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+        int kn = 0;
+        for (size_t i = 0; i < n; ++i) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kn;
         }
-        n += 2;  // xupdate, finalize
-        return n;
+        return kn;
     }
     int kernels_per_sweep() const override { return launches; }
 
@@ -1145,13 +1148,13 @@ struct Engine : ifctn_ctx {
             set_error(std::string("sweep capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
             return IFCTN_ECUDA;
         }
+        launches = count_kernel_nodes(g);
         e = cudaGraphInstantiate(&gexec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
             return IFCTN_ECUDA;
         }
-        launches = count_launches();
         return IFCTN_OK;
     }
 

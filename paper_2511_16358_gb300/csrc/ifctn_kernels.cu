@@ -93,34 +93,197 @@ __global__ void __launch_bounds__(256) k_gram_t2(const __grid_constant__ Shape s
     }
 }
 
+// Pair index p of the upper triangle (x <= y, row-major) of an R x R block.
+__device__ __forceinline__ void pair_xy(int p, int R, int& x, int& y) {
+    int r = p, xx = 0;
+    while (r >= R - xx) {
+        r -= R - xx;
+        ++xx;
+    }
+    x = xx;
+    y = xx + r;
+}
+
+// NP consecutive elements from 16-byte aligned shared memory (NP a multiple
+// of 16 / sizeof(T)).
+template <typename T, int NP>
+__device__ __forceinline__ void ld_vec(const T* __restrict__ p, T (&o)[NP]) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int i = 0; i < NP; i += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(p + i);
+            o[i] = v.x;
+            o[i + 1] = v.y;
+            o[i + 2] = v.z;
+            o[i + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NP; i += 2) {
+            const double2 v = *reinterpret_cast<const double2*>(p + i);
+            o[i] = v.x;
+            o[i + 1] = v.y;
+        }
+    }
+}
+
+// Fused first two steps of the chain for N = 4 (non-k modes o < c < l), one
+// CTA per io, with T1 kept in shared memory:
+//   h(il, p)  = W_ol(io, il)^2 g_l(x, il) g_l(y, il),                 p = (x <= y)
+//   T1(ic, p) = W_oc(io, ic)^2 sum_il W_cl(ic, il)^2 h(il, p)
+//   T2[io][(xc, xl)][(yc, yl)] = sum_ic g_c(xc, ic) g_c(yc, ic) T1(ic, p(xl, yl))
+// A warp takes 32 consecutive ic (lane = ic) and streams W_cl through a
+// 32 x 33 shared tile (rows read coalesced, columns read without bank
+// conflicts); every lane keeps all pairs p of its ic in registers.
+constexpr int GRAM_WARPS = 8;
+
+template <typename T, int RL>
+__host__ __device__ constexpr int gram_npp() {
+    constexpr int NP = RL * (RL + 1) / 2, VN = 16 / static_cast<int>(sizeof(T));
+    return (NP + VN - 1) / VN * VN;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_gram_fin(const __grid_constant__ Shape s, const int k, const T* __restrict__ Gt,
-                                                  const T* __restrict__ t2, T* __restrict__ K,
-                                                  const int* __restrict__ done) {
+long long gram_io_smem(int RL, int Il, int Ic, int Rc) {
+    const int NP = RL * (RL + 1) / 2, VN = 16 / static_cast<int>(sizeof(T));
+    const int NPP = (NP + VN - 1) / VN * VN;
+    return (static_cast<long long>(Il) * NPP + static_cast<long long>(Ic) * NP + static_cast<long long>(Rc) * Ic +
+            GRAM_WARPS * 32 * 33) * sizeof(T) + 16;
+}
+
+template <typename T, int RL>
+__global__ void __launch_bounds__(GRAM_WARPS * 32) k_gram_io(const __grid_constant__ Shape s, const int k,
+                                                             const T* __restrict__ Gt, const T* __restrict__ W,
+                                                             T* __restrict__ t2, const int* __restrict__ done) {
     if (*done) return;
+    extern __shared__ __align__(16) unsigned char gsm[];
+    constexpr int NP = RL * (RL + 1) / 2;
+    constexpr int NPP = gram_npp<T, RL>();
+    int m[3];
+    nonk_modes(s, k, m);
+    const int o = m[0], c = m[1], l = m[2];
+    const int Ic = s.I[c], Il = s.I[l];
+    const int Rc = s.R[k][c];
+    const int io = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    T* hs = reinterpret_cast<T*>(gsm);  // [Il][NPP]
+    T* t1s = hs + Il * NPP;              // [Ic][NP]
+    T* gcs = t1s + Ic * NP;              // [Rc][Ic]
+    T* tile = gcs + Rc * Ic + warp * 32 * 33;
+    const T* gl = Gt + s.goff[l][k];
+    const T* wol = W + s.woff[o][l] + static_cast<long long>(io) * Il;
+    const T* woc = W + s.woff[o][c] + static_cast<long long>(io) * Ic;
+    const T* wcl = W + s.woff[c][l];
+    for (int idx = tid; idx < Il * NPP; idx += blockDim.x) {
+        const int il = idx / NPP, p = idx - il * NPP;
+        T v = T(0);
+        if (p < NP) {
+            int x, y;
+            pair_xy(p, RL, x, y);
+            const T w = wol[il];
+            v = w * w * gl[x * Il + il] * gl[y * Il + il];
+        }
+        hs[idx] = v;
+    }
+    for (int idx = tid; idx < Rc * Ic; idx += blockDim.x) gcs[idx] = Gt[s.goff[c][k] + idx];
+    __syncthreads();
+    for (int ic0 = warp * 32; ic0 < Ic; ic0 += GRAM_WARPS * 32) {
+        const int ic = ic0 + lane;
+        const int nr = min(32, Ic - ic0);
+        T acc[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) acc[q] = T(0);
+        for (int il0 = 0; il0 < Il; il0 += 32) {
+            const int nil = min(32, Il - il0);
+            __syncwarp();
+            if (lane < nil)
+                for (int r = 0; r < nr; ++r) tile[r * 33 + lane] = wcl[static_cast<long long>(ic0 + r) * Il + il0 + lane];
+            __syncwarp();
+            if (lane < nr) {
+                for (int j = 0; j < nil; ++j) {
+                    T bw = tile[lane * 33 + j];
+                    bw *= bw;
+                    T hv[NPP];
+                    ld_vec<T, NPP>(hs + (il0 + j) * NPP, hv);
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) acc[q] = fma(bw, hv[q], acc[q]);
+                }
+            }
+        }
+        if (lane < nr) {
+            const T wo = woc[ic];
+            const T w2 = wo * wo;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) t1s[ic * NP + q] = acc[q] * w2;
+        }
+    }
+    __syncthreads();
+    const int Q2 = Rc * RL;
+    T* out = t2 + static_cast<long long>(io) * Q2 * Q2;
+    for (int idx = tid; idx < Rc * Rc * NP; idx += blockDim.x) {
+        const int xy = idx / NP, p = idx - xy * NP;
+        const int xc = xy / Rc, yc = xy - xc * Rc;
+        int xl, yl;
+        pair_xy(p, RL, xl, yl);
+        const T* ga = gcs + xc * Ic;
+        const T* gb = gcs + yc * Ic;
+        const T* tp = t1s + p;
+        T a0 = T(0), a1 = T(0);
+        int ic = 0;
+        for (; ic + 1 < Ic; ic += 2) {
+            a0 = fma(ga[ic] * gb[ic], tp[ic * NP], a0);
+            a1 = fma(ga[ic + 1] * gb[ic + 1], tp[(ic + 1) * NP], a1);
+        }
+        if (ic < Ic) a0 = fma(ga[ic] * gb[ic], tp[ic * NP], a0);
+        const T v = a0 + a1;
+        out[(xc * RL + xl) * Q2 + yc * RL + yl] = v;
+        if (xl != yl) out[(xc * RL + yl) * Q2 + yc * RL + xl] = v;
+    }
+}
+
+// Last step: K[(xo, X), (yo, Y)] = sum_io g_o(xo, io) g_o(yo, io) T2[io][X][Y]
+// (N = 3, 4; for N = 2 directly sum_io g_o(xo, io) g_o(yo, io)).  A CTA takes
+// 32 consecutive entries of K (lane = entry); its warps split the io range and
+// their sums are added in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(GRAM_WARPS * 32) k_gram_fin(const __grid_constant__ Shape s, const int k,
+                                                              const T* __restrict__ Gt, const T* __restrict__ t2,
+                                                              T* __restrict__ K, const int* __restrict__ done) {
+    if (*done) return;
+    __shared__ T red[GRAM_WARPS][32];
     int m[3];
     const int nm = nonk_modes(s, k, m);
     const int o = m[0];
-    const int Io = s.I[o], Ro = s.R[k][o];
+    const int Io = s.I[o];
     int Q2 = 1;
     for (int t = 1; t < nm; ++t) Q2 *= s.R[k][m[t]];
-    const int Q = Ro * Q2;
-    const long long total = static_cast<long long>(Q) * Q;
-    for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total;
-         idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int Q = s.R[k][o] * Q2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long idx = blockIdx.x * 32LL + lane;
+    const bool act = idx < static_cast<long long>(Q) * Q;
+    const int per = (Io + GRAM_WARPS - 1) / GRAM_WARPS;
+    const int io0 = warp * per, io1 = min(Io, io0 + per);
+    T acc = T(0);
+    if (act) {
         const int col = static_cast<int>(idx % Q), row = static_cast<int>(idx / Q);
         const int xo = row / Q2, X = row - xo * Q2, yo = col / Q2, Y = col - yo * Q2;
         const T* gx = Gt + s.goff[o][k] + xo * Io;
         const T* gy = Gt + s.goff[o][k] + yo * Io;
-        T acc = T(0);
         if (nm == 1) {
-            for (int io = 0; io < Io; ++io) acc = fma(gx[io], gy[io], acc);
+            for (int io = io0; io < io1; ++io) acc = fma(gx[io], gy[io], acc);
         } else {
             const T* tp = t2 + static_cast<long long>(X) * Q2 + Y;
             const long long st = static_cast<long long>(Q2) * Q2;
-            for (int io = 0; io < Io; ++io) acc = fma(gx[io] * gy[io], tp[io * st], acc);
+            for (int io = io0; io < io1; ++io) acc = fma(gx[io] * gy[io], tp[io * st], acc);
         }
-        K[idx] = acc;
+    }
+    red[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && act) {
+        T v = red[0][lane];
+#pragma unroll
+        for (int w = 1; w < GRAM_WARPS; ++w) v += red[w][lane];
+        K[idx] = v;
     }
 }
 
@@ -574,6 +737,18 @@ inline int grid_for(long long n, int block, int cap) {
 
 }  // namespace
 
+template <typename T, int RL>
+cudaError_t launch_gram_io(const Shape& sh, int k, const T* Gt, const T* W, T* t2, const int* done, int smem,
+                           cudaStream_t st) {
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_gram_io<T, RL>), smem);
+    if (e != cudaSuccess) return e;
+    int m[3], nm = 0;
+    for (int q = 0; q < sh.N; ++q)
+        if (q != k) m[nm++] = q;
+    k_gram_io<T, RL><<<sh.I[m[0]], GRAM_WARPS * 32, smem, st>>>(sh, k, Gt, W, t2, done);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_gram(const Shape& sh, int k, const T* Gt, const T* W, T* t1, T* t2, T* Kk,
                         const int* done, cudaStream_t st) {
@@ -581,18 +756,37 @@ cudaError_t launch_gram(const Shape& sh, int k, const T* Gt, const T* W, T* t1, 
     for (int q = 0; q < sh.N; ++q)
         if (q != k) m[nm++] = q;
     if (nm == 3) {
-        const long long n1 = static_cast<long long>(sh.I[m[0]]) * sh.I[m[1]] * sh.R[k][m[2]] * sh.R[k][m[2]];
-        k_gram_t1<T><<<grid_for(n1, 256, 2432), 256, 0, st>>>(sh, k, Gt, W, t1, done);
-        const int Q2 = sh.R[k][m[1]] * sh.R[k][m[2]];
-        const long long n2 = static_cast<long long>(sh.I[m[0]]) * Q2 * Q2;
-        k_gram_t2<T><<<grid_for(n2, 256, 2432), 256, 0, st>>>(sh, k, Gt, t1, t2, done);
+        const int RL = sh.R[k][m[2]];
+        const long long smem = gram_io_smem<T>(RL, sh.I[m[2]], sh.I[m[1]], sh.R[k][m[1]]);
+        if (smem <= 200 * 1024) {
+            cudaError_t e;
+            const int sm = static_cast<int>(smem);
+            switch (RL) {
+                case 1: e = launch_gram_io<T, 1>(sh, k, Gt, W, t2, done, sm, st); break;
+                case 2: e = launch_gram_io<T, 2>(sh, k, Gt, W, t2, done, sm, st); break;
+                case 3: e = launch_gram_io<T, 3>(sh, k, Gt, W, t2, done, sm, st); break;
+                case 4: e = launch_gram_io<T, 4>(sh, k, Gt, W, t2, done, sm, st); break;
+                case 5: e = launch_gram_io<T, 5>(sh, k, Gt, W, t2, done, sm, st); break;
+                case 6: e = launch_gram_io<T, 6>(sh, k, Gt, W, t2, done, sm, st); break;
+                case 7: e = launch_gram_io<T, 7>(sh, k, Gt, W, t2, done, sm, st); break;
+                default: e = launch_gram_io<T, 8>(sh, k, Gt, W, t2, done, sm, st); break;
+            }
+            if (e != cudaSuccess) return e;
+        } else {  // T1 too large for shared memory: through global memory
+            const long long n1 = static_cast<long long>(sh.I[m[0]]) * sh.I[m[1]] * RL * RL;
+            k_gram_t1<T><<<grid_for(n1, 256, 2432), 256, 0, st>>>(sh, k, Gt, W, t1, done);
+            const int Q2 = sh.R[k][m[1]] * RL;
+            const long long n2 = static_cast<long long>(sh.I[m[0]]) * Q2 * Q2;
+            k_gram_t2<T><<<grid_for(n2, 256, 2432), 256, 0, st>>>(sh, k, Gt, t1, t2, done);
+        }
     } else if (nm == 2) {
         const long long n1 = static_cast<long long>(sh.I[m[0]]) * sh.R[k][m[1]] * sh.R[k][m[1]];
         k_gram_t1<T><<<grid_for(n1, 256, 2432), 256, 0, st>>>(sh, k, Gt, W, t2, done);
     }
     int Q = 1;
     for (int t = 0; t < nm; ++t) Q *= sh.R[k][m[t]];
-    k_gram_fin<T><<<grid_for(static_cast<long long>(Q) * Q, 256, 2432), 256, 0, st>>>(sh, k, Gt, t2, Kk, done);
+    const long long nK = static_cast<long long>(Q) * Q;
+    k_gram_fin<T><<<static_cast<int>((nK + 31) / 32), GRAM_WARPS * 32, 0, st>>>(sh, k, Gt, t2, Kk, done);
     return cudaGetLastError();
 }
 
