@@ -428,14 +428,15 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
 // product of the current columns G_{k,m}(:,j), m != i (identity in slot i);
 // stages i ascending (Gauss-Seidel within the column).
 //
-// (H + rho I) g = b is solved by a lane-parallel LDL^T factorisation (the
-// matrix is SPD with eigenvalues >= rho, so no pivoting).  FP64 path: the
-// factorisation and the solves in FP64.  Mixed path: the factorisation in
-// FP32 followed by a step of iterative refinement whose residual
-// b - (H + rho I) g is formed in FP64, which recovers FP64-level accuracy for
-// the conditioning these systems have while keeping GB300's narrow FP64 pipe
-// nearly idle.  (One refinement step: H itself carries the FP32 rounding of
-// the contractions, so further steps would not change the result's accuracy.)
+// (H + rho I) g = b is solved by an LDL^T factorisation (the matrix is SPD
+// with eigenvalues >= rho, so no pivoting) that every lane of the warp runs
+// in registers.  FP64 path: the factorisation and the solves in FP64.  Mixed
+// path: the factorisation in FP32 followed by a step of iterative refinement
+// whose residual b - (H + rho I) g is formed in FP64, which recovers
+// FP64-level accuracy for the conditioning these systems have while keeping
+// GB300's narrow FP64 pipe nearly idle.  (One refinement step: H itself
+// carries the FP32 rounding of the contractions, so further steps would not
+// change the result's accuracy.)
 // ---------------------------------------------------------------------------
 template <typename F>
 __device__ __forceinline__ F recip_nr(F d) {
@@ -453,60 +454,6 @@ __device__ __forceinline__ F recip_nr(F d) {
         x = x * (F(2) - d * x);
     }
     return x;
-}
-
-// Lane-parallel LDL^T of the n x n SPD matrix A (row-major in shared memory,
-// F precision) in place: unit-lower L below the diagonal, D on the diagonal,
-// 1/D in inv.  Returns false if a pivot is not positive.
-template <typename F>
-__device__ bool ldlt_warp(F* A, F* inv, int n, int lane) {
-    for (int c = 0; c < n; ++c) {
-        const F d = A[c * n + c];
-        if (!(d > F(0))) return false;
-        const F id = recip_nr<F>(d);
-        if (lane == 0) inv[c] = id;
-        // trailing update A[r][s] -= A[r][c] A[s][c] / d for c < s <= r
-        const int m = n - c - 1;
-        const int npair = m * (m + 1) / 2;
-        F lrc = F(0), lsc = F(0);
-        int r = 0, sx = 0;
-        if (lane < npair) {
-            int rem = lane, rr = 0;
-            while (rem > rr) {
-                rem -= rr + 1;
-                ++rr;
-            }
-            r = c + 1 + rr;
-            sx = c + 1 + rem;
-            lrc = A[r * n + c];
-            lsc = A[sx * n + c];
-        }
-        __syncwarp();
-        if (lane < npair) A[r * n + sx] -= lrc * lsc * id;
-        __syncwarp();
-        if (lane > c && lane < n) A[lane * n + c] *= id;
-        __syncwarp();
-    }
-    return true;
-}
-
-// solve L D L^T x = rhs (x overwrites rhs), lane-parallel over rows
-template <typename F>
-__device__ void ldlt_solve_warp(const F* A, const F* inv, F* x, int n, int lane) {
-    for (int c = 0; c < n; ++c) {  // forward, unit lower
-        const F xc = x[c];
-        __syncwarp();
-        if (lane > c && lane < n) x[lane] -= A[lane * n + c] * xc;
-        __syncwarp();
-    }
-    if (lane < n) x[lane] *= inv[lane];
-    __syncwarp();
-    for (int c = n - 1; c >= 0; --c) {  // backward, unit upper = L^T
-        const F xc = x[c];
-        __syncwarp();
-        if (lane < c) x[lane] -= A[c * n + lane] * xc;
-        __syncwarp();
-    }
 }
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -545,23 +492,93 @@ __host__ __device__ inline SolveLayout solve_layout(int Q, int tot, int sz, bool
     return L;
 }
 
-// The normal equations of one stage (slot ti of Ri = RI values) of one
-// column, assembled by one warp:
+// Butterfly reduce-scatter across the warp: v[V] per lane (V = 32 or 64) ->
+// the warp sums of value index lane (V = 32) or 2 lane, 2 lane + 1 (V = 64)
+// in v[0] (, v[1]).  Each level sends half of the values still held to the
+// partner lane, so the whole reduction is V - V/32 shuffles in five levels.
+template <typename T, int V>
+__device__ __forceinline__ void warp_reduce_scatter(T (&v)[V], int lane) {
+#pragma unroll
+    for (int lv = 0; lv < 5; ++lv) {
+        const int o = 16 >> lv;
+        const int n = V >> (lv + 1);
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < V / 2; ++i) {
+            if (i < n) {
+                const T send = up ? v[i] : v[i + n];
+                const T keep = up ? v[i + n] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+    }
+}
+
+// LDL^T of the SPD matrix A (lower triangle used) in registers, in place:
+// unit-lower L below the diagonal, D on it, 1/D in id.  False if a pivot is
+// not positive.
+template <typename F, int RI>
+__device__ __forceinline__ bool ldlt_regs(F (&A)[RI][RI], F (&id)[RI]) {
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < RI; ++c) {
+        F d = A[c][c];
+#pragma unroll
+        for (int t = 0; t < c; ++t) d -= A[c][t] * A[c][t] * A[t][t];
+        ok = ok && (d > F(0));
+        A[c][c] = d;
+        const F inv = recip_nr<F>(d);
+        id[c] = inv;
+#pragma unroll
+        for (int r = c + 1; r < RI; ++r) {
+            F v = A[r][c];
+#pragma unroll
+            for (int t = 0; t < c; ++t) v -= A[r][t] * A[c][t] * A[t][t];
+            A[r][c] = v * inv;
+        }
+    }
+    return ok;
+}
+
+// L D L^T x = b in registers (x holds b on entry)
+template <typename F, int RI>
+__device__ __forceinline__ void ldlt_solve_regs(const F (&A)[RI][RI], const F (&id)[RI], F (&x)[RI]) {
+#pragma unroll
+    for (int r = 0; r < RI; ++r)
+#pragma unroll
+        for (int t = 0; t < r; ++t) x[r] -= A[r][t] * x[t];
+#pragma unroll
+    for (int r = 0; r < RI; ++r) x[r] *= id[r];
+#pragma unroll
+    for (int r = RI - 1; r >= 0; --r)
+#pragma unroll
+        for (int t = r + 1; t < RI; ++t) x[r] -= A[t][r] * x[t];
+}
+
+// One stage (slot ti, Ri = RI values) of the column solve, by one warp:
 //   H(c, c2) = sum_{o, o2} omega(o) omega(o2) K[(o2, c2), (o, c)] + rho [c = c2]
 //   b(c)     = sum_o omega(o) M_k(j, (o, c)) + rho g_old(c)
+//   (H) g = b
 // where (o, c) is the K index with digit c in slot ti, cb[o] the index of
 // (o, 0) and sp the index step of the slot.  Lanes take (o, o2) combinations
-// and keep every pair c <= c2 in registers (K is symmetric, so H is); the lane
-// sums are reduced across the warp once.
+// and keep every pair c <= c2 (K is symmetric, so H is) and every b(c) in
+// registers; one reduce-scatter leaves value q with lane q, which writes it
+// out.  Every lane then factorises H and solves in registers (FP32 on the
+// mixed path, followed by one step of refinement with the residual formed in
+// FP64 by lane r for row r; FP64 on the FP64 path).  The new column ends in
+// gd[0..RI).  Returns false (uniformly) when H is not numerically SPD or the
+// solution is not finite.
 template <typename T, int RI>
-__device__ __forceinline__ void stage_system(const T* __restrict__ K, const T* __restrict__ om,
-                                             const int* __restrict__ cb, const T* __restrict__ mrow, int Q,
-                                             int Qo, int sp, int lane, double rho, const double* __restrict__ gold,
-                                             double* Hd, double* bd) {
+__device__ __forceinline__ bool stage_solve(const T* __restrict__ K, const T* __restrict__ om,
+                                            const int* __restrict__ cb, const T* __restrict__ mrow, int Q,
+                                            int Qo, int sp, int lane, double rho, const double* __restrict__ gold,
+                                            double* Hd, double* bd, T* Af, T* xf, double* gd) {
+    constexpr bool MIXED = sizeof(T) == 4;
     constexpr int NP = RI * (RI + 1) / 2;
-    T acc[NP];
+    constexpr int V = NP + RI <= 32 ? 32 : 64;
+    T v[V];
 #pragma unroll
-    for (int q = 0; q < NP; ++q) acc[q] = T(0);
+    for (int q = 0; q < V; ++q) v[q] = T(0);
     const int spQ = sp * Q;
     const int n = Qo * Qo;
     const int dq = 32 / Qo, dr = 32 - dq * Qo;
@@ -574,7 +591,7 @@ __device__ __forceinline__ void stage_system(const T* __restrict__ K, const T* _
 #pragma unroll
         for (int c2 = 0; c2 < RI; ++c2)
 #pragma unroll
-            for (int c = 0; c <= c2; ++c, ++q) acc[q] = fma(kr[c2 * spQ + c * sp], w, acc[q]);
+            for (int c = 0; c <= c2; ++c, ++q) v[q] = fma(kr[c2 * spQ + c * sp], w, v[q]);
         o += dq;
         o2 += dr;
         if (o2 >= Qo) {
@@ -582,52 +599,75 @@ __device__ __forceinline__ void stage_system(const T* __restrict__ K, const T* _
             ++o;
         }
     }
-    T bacc[RI];
-#pragma unroll
-    for (int c = 0; c < RI; ++c) bacc[c] = T(0);
     for (int o1 = lane; o1 < Qo; o1 += 32) {
         const T w = om[o1];
         const T* mr = mrow + cb[o1];
 #pragma unroll
-        for (int c = 0; c < RI; ++c) bacc[c] = fma(w, mr[c * sp], bacc[c]);
+        for (int c = 0; c < RI; ++c) v[NP + c] = fma(w, mr[c * sp], v[NP + c]);
     }
-    // lane q keeps pair q (and q + 32), lane c keeps b(c)
-    T hv = T(0), hv2 = T(0), bv = T(0);
-    int hr = 0, hc = 0, hr2 = 0, hc2 = 0;
-    {
-        int q = 0;
+    warp_reduce_scatter<T, V>(v, lane);
 #pragma unroll
-        for (int c2 = 0; c2 < RI; ++c2)
-#pragma unroll
-            for (int c = 0; c <= c2; ++c, ++q) {
-                const T v = warp_sum(acc[q]);
-                if (lane == q) {
-                    hv = v;
-                    hr = c2;
-                    hc = c;
-                } else if (lane + 32 == q) {
-                    hv2 = v;
-                    hr2 = c2;
-                    hc2 = c;
-                }
+    for (int h = 0; h < V / 32; ++h) {
+        const int idx = V == 32 ? lane : 2 * lane + h;
+        const T val = v[h];
+        if (idx < NP) {
+            int c2 = 0;
+            while ((c2 + 1) * (c2 + 2) / 2 <= idx) ++c2;
+            const int c = idx - c2 * (c2 + 1) / 2;
+            const T hv = val + (c == c2 ? static_cast<T>(rho) : T(0));
+            Af[c2 * RI + c] = hv;
+            Af[c * RI + c2] = hv;
+            if (MIXED) {
+                const double hdv = static_cast<double>(val) + (c == c2 ? rho : 0.0);
+                Hd[c2 * RI + c] = hdv;
+                Hd[c * RI + c2] = hdv;
             }
+        } else if (idx < NP + RI) {
+            const int c = idx - NP;
+            const double bb = static_cast<double>(val) + rho * gold[c];
+            bd[c] = bb;
+            xf[c] = static_cast<T>(bb);
+        }
     }
+    __syncwarp();
+    T A[RI][RI], id[RI], x[RI];
 #pragma unroll
-    for (int c = 0; c < RI; ++c) {
-        const T v = warp_sum(bacc[c]);
-        if (lane == c) bv = v;
+    for (int r = 0; r < RI; ++r) {
+#pragma unroll
+        for (int c = 0; c <= r; ++c) A[r][c] = Af[r * RI + c];
+        x[r] = xf[r];
     }
-    if (lane < NP) {
-        const double h = static_cast<double>(hv) + (hr == hc ? rho : 0.0);
-        Hd[hr * RI + hc] = h;
-        Hd[hc * RI + hr] = h;
+    bool ok = ldlt_regs<T, RI>(A, id);
+    ldlt_solve_regs<T, RI>(A, id, x);
+    T xl = T(0);
+#pragma unroll
+    for (int r = 0; r < RI; ++r)
+        if (lane == r) xl = x[r];
+    double g = static_cast<double>(xl);
+    if (MIXED) {
+        // residual of row r in FP64 (lane r), the correction solved in FP32
+        T rr = T(0);
+        if (lane < RI) {
+            double res = bd[lane];
+#pragma unroll
+            for (int t = 0; t < RI; ++t) res -= Hd[lane * RI + t] * static_cast<double>(x[t]);
+            rr = static_cast<T>(res);
+        }
+        T cr[RI];
+#pragma unroll
+        for (int t = 0; t < RI; ++t) cr[t] = __shfl_sync(0xffffffffu, rr, t);
+        ldlt_solve_regs<T, RI>(A, id, cr);
+        T cl = T(0);
+#pragma unroll
+        for (int r = 0; r < RI; ++r)
+            if (lane == r) cl = cr[r];
+        g += static_cast<double>(cl);
     }
-    if (lane + 32 < NP) {
-        const double h = static_cast<double>(hv2) + (hr2 == hc2 ? rho : 0.0);
-        Hd[hr2 * RI + hc2] = h;
-        Hd[hc2 * RI + hr2] = h;
+    if (lane < RI) {
+        gd[lane] = g;
+        if (!isfinite(g)) ok = false;
     }
-    if (lane < RI) bd[lane] = static_cast<double>(bv) + rho * gold[lane];
+    return __all_sync(0xffffffffu, ok) != 0;
 }
 
 template <typename T>
@@ -662,10 +702,8 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
     double* bd = vs + 3 * RMAX;           // RMAX rhs (FP64)
     double* gd = bd + RMAX;               // RMAX solution (FP64)
     double* rd = gd + RMAX;               // RMAX (spare)
-    using F = typename std::conditional<MIXED, float, double>::type;
-    F* Af = reinterpret_cast<F*>(rd + RMAX);   // RMAX*RMAX factor
-    F* invf = Af + RMAX * RMAX;                  // RMAX
-    F* xf = invf + RMAX;                         // RMAX
+    T* Af = reinterpret_cast<T*>(rd + RMAX);  // RMAX*RMAX: H in the factorisation's precision
+    T* xf = Af + RMAX * RMAX + RMAX;            // RMAX: b in that precision
     T* vt = reinterpret_cast<T*>(my + 2 * RMAX * RMAX + 8 * RMAX);  // 3 x RMAX columns in T
     T* gik = reinterpret_cast<T*>(smem + L.gik);
     const int Qa = (Q + 3) & ~3;
@@ -733,46 +771,28 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
             __syncwarp();
             if (ti == 0) IFCTN_SSTAMP(3);
             const double* gold = vs + ti * RMAX;
+            bool okc;
             switch (Ri) {
-                case 1: stage_system<T, 1>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
-                case 2: stage_system<T, 2>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
-                case 3: stage_system<T, 3>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
-                case 4: stage_system<T, 4>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
-                case 5: stage_system<T, 5>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
-                case 6: stage_system<T, 6>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
-                case 7: stage_system<T, 7>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
-                default: stage_system<T, 8>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd); break;
+#define IFCTN_SOLVE_CASE(R)                                                                                     \
+    case R:                                                                                                     \
+        okc = stage_solve<T, R>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd, Af, xf, gd);               \
+        break;
+                IFCTN_SOLVE_CASE(1)
+                IFCTN_SOLVE_CASE(2)
+                IFCTN_SOLVE_CASE(3)
+                IFCTN_SOLVE_CASE(4)
+                IFCTN_SOLVE_CASE(5)
+                IFCTN_SOLVE_CASE(6)
+                IFCTN_SOLVE_CASE(7)
+                default:
+                    okc = stage_solve<T, 8>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd, Af, xf, gd);
+                    break;
+#undef IFCTN_SOLVE_CASE
             }
-            __syncwarp();
             if (ti == 0) IFCTN_SSTAMP(4);
             if (ti == 0) IFCTN_SSTAMP(5);
-            for (int idx = lane; idx < Ri * Ri; idx += 32) Af[idx] = static_cast<F>(Hd[idx]);
-            __syncwarp();
-            bool okc = ldlt_warp<F>(Af, invf, Ri, lane);
-            __syncwarp();
             if (ti == 0) IFCTN_SSTAMP(6);
-            if (okc) {
-                if (lane < Ri) xf[lane] = static_cast<F>(bd[lane]);
-                __syncwarp();
-                ldlt_solve_warp<F>(Af, invf, xf, Ri, lane);
-                if (lane < Ri) gd[lane] = static_cast<double>(xf[lane]);
-                __syncwarp();
-                if (ti == 0) IFCTN_SSTAMP(7);
-                if (MIXED) {
-                    // one step of refinement: residual in FP64, correction in FP32
-                    if (lane < Ri) {
-                        double r = bd[lane];
-                        for (int t = 0; t < Ri; ++t) r -= Hd[lane * Ri + t] * gd[t];
-                        xf[lane] = static_cast<F>(r);
-                    }
-                    __syncwarp();
-                    ldlt_solve_warp<F>(Af, invf, xf, Ri, lane);
-                    if (lane < Ri) gd[lane] += static_cast<double>(xf[lane]);
-                    __syncwarp();
-                }
-                if (lane < Ri && !isfinite(gd[lane])) okc = false;
-                okc = __all_sync(0xffffffffu, okc);
-            }
+            if (ti == 0) IFCTN_SSTAMP(7);
             if (!okc) {
                 if (lane == 0) atomicOr(p.flags, FLAG_NOTSPD);
                 if (lane < Ri) gd[lane] = vs[ti * RMAX + lane];
