@@ -252,6 +252,9 @@ def main():
         run_reference(args, w)
         return
     import torch
+    # the persistent kernel timestamps the phases of one sweep of every launch:
+    # a sweep from the middle of the step (steady state), unless set otherwise
+    os.environ.setdefault("IFCTN_STAMP_SWEEP", str(max(0, w.sweeps // 2)))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -315,9 +318,15 @@ def main():
             phases[f"m{k}_contract_cta_mean_end"] = ph[27 + 2 * k]
     sub = ph[26 + 2 * N: 26 + 2 * N + 12]
     if len(sub) == 12:
-        names_sub = ["start", "staged", "column_loaded", "omega", "H", "b", "ldlt", "solve", "refine", "stored",
-                     "stages_done", "W_refreshed"]
-        phases["last_mode_solve_first_column_s"] = {nm: (t - sub[0]) for nm, t in zip(names_sub, sub)}
+        names_sub = ["start", "staged", "column_loaded", "omega", "H_b_sums", "reduced", "ldlt_solve", "refined",
+                     "checked", "stored", "stages_done", "W_refreshed"]
+        mode = int(os.environ.get("IFCTN_STAMP_MODE", len(w.dims) - 1))
+        phases["solve_first_column_s"] = {nm: (t - sub[0]) for nm, t in zip(names_sub, sub)}
+        phases["solve_first_column_s"]["mode"] = mode
+    red = ph[26 + 2 * N + 12: 26 + 2 * N + 16]
+    if len(red) == 4 and red[0] == red[0]:
+        phases["reduce_substeps_s"] = {"K_done": red[1] - red[0], "coef_done": red[2] - red[0],
+                                       "M_done": red[3] - red[0]}
     torch.cuda.synchronize()
     tot, value = aggregate_ranks(torch, dist, sum(times), world, args.steps * sweeps, "cuda")
 
@@ -421,7 +430,7 @@ def main():
                            "l2": "flushed (256 MiB write) before every timed step",
                            "parallelism": f"replicas x{world}"},
                 "gpu_launches": launches_timed,
-                "persistent_phases_first_sweep_s": phases,
+                "persistent_phases_s": dict(phases, sweep=int(os.environ["IFCTN_STAMP_SWEEP"])),
                 "clocks": ck, "roofline": roofline}
         line.update(extras)
         line.setdefault("e2e", None)

@@ -773,6 +773,8 @@ struct Engine : ifctn_ctx {
     DevBuf<UnitDesc> units;
     DevBuf<SweepStat> log;
     DevBuf<int> ints;  // [0] counter, [1] done, [2] flags
+    DevBuf<int> stab;  // index tables of the column solves, per mode (solve_stage_tables)
+    int stab_off[MAXN] = {};
     ContractPlan plan[MAXN];
     int unit_off[MAXN] = {};
     int xblocks = 0;
@@ -808,6 +810,7 @@ struct Engine : ifctn_ctx {
         X.release(); Xt.release(); Gt.release(); W.release(); Kk.release(); t1.release(); t2.release();
         part.release(); tmpT.release(); Gd.release(); xpart.release(); mpart.release(); scal.release();
         tmpD.release(); tol.release(); maskbits.release(); units.release(); log.release(); ints.release();
+        stab.release();
         if (side) cudaStreamDestroy(side);
         if (own_stream && st) cudaStreamDestroy(st);
     }
@@ -885,12 +888,21 @@ struct Engine : ifctn_ctx {
                   alloc(log, LOG_CAP) == cudaSuccess && alloc(ints, 4) == cudaSuccess;
         for (int k = 0; k < sh.N && ok; ++k)
             ok = alloc(Mk[k], static_cast<size_t>(sh.I[k]) * mode_q(sh, k)) == cudaSuccess;
+        std::vector<int> tabs;
+        for (int k = 0; k < sh.N; ++k) {
+            stab_off[k] = static_cast<int>(tabs.size());
+            const int n = solve_tab_ints(mode_q(sh, k));
+            tabs.resize(tabs.size() + (n + 3) / 4 * 4, 0);  // 16-byte aligned blocks
+            solve_stage_tables(sh, k, tabs.data() + stab_off[k]);
+        }
+        if (ok) ok = alloc(stab, tabs.size()) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
             set_error("device allocation failed");
             return IFCTN_ENOMEM;
         }
         CK(cudaMemcpyAsync(units.p, all.data(), all.size() * sizeof(UnitDesc), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(stab.p, tabs.data(), tabs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(ints.p, 0, 4 * sizeof(int), st));
         CK(cudaMemsetAsync(bar.p, 0, 4 * sizeof(unsigned), st));
         CK(cudaMemsetAsync(tol.p, 0, sizeof(double), st));
@@ -937,6 +949,7 @@ struct Engine : ifctn_ctx {
         for (int k = 0; k < sh.N; ++k) {
             pp.pl[k] = plan[k];
             pp.units[k] = units.p + unit_off[k];
+            pp.stab[k] = stab.p + stab_off[k];
             int nm = 0;
             for (int q = 0; q < sh.N; ++q)
                 if (q != k) m[nm++] = q;
@@ -993,6 +1006,14 @@ struct Engine : ifctn_ctx {
             }
         }
         pp.tstamp = tstamp.p;
+        // profiling aid: the mode whose first column is timestamped (default the last)
+        pp.stamp_mode = sh.N - 1;
+        if (const char* e = getenv("IFCTN_STAMP_MODE")) {
+            const int v = atoi(e);
+            if (v >= 0 && v < sh.N) pp.stamp_mode = v;
+        }
+        pp.stamp_sweep = 0;
+        if (const char* e = getenv("IFCTN_STAMP_SWEEP")) pp.stamp_sweep = std::max(0, atoi(e));
         {
             // X-update work units: row ranges of slabs, about 4 per CTA
             // contiguous row ranges of 2K..16K entries, about 4 units per CTA
@@ -1254,8 +1275,9 @@ struct Engine : ifctn_ctx {
             out[cnt++] = mx;
             out[cnt++] = c ? sm / c : NAN;
         }
-        // sub-steps of the first column of the last mode's solves (CTA 0)
-        for (int i = 40; i < 52 && cnt < max; ++i) out[cnt++] = rel(h[i]);
+        // sub-steps of the profiled mode's first column solve, then of its
+        // reduction phase (CTA 0)
+        for (int i = 40; i < 56 && cnt < max; ++i) out[cnt++] = rel(h[i]);
         if (n) *n = persistent ? cnt : 0;
         return IFCTN_OK;
     }

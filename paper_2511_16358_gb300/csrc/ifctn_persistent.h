@@ -35,12 +35,54 @@ struct SweepParams {
     int nstages;
     int solve_k_in_smem;
     int gram_chunk;
-    unsigned long long* tstamp;  // optional phase timestamps of the first sweep
+    unsigned long long* tstamp;  // optional phase timestamps of one sweep (stamp_sweep)
+    const int* stab[MAXN];       // per-mode index tables of the column solves (solve_stage_tables)
+    int stamp_mode;              // mode whose first column's solve sub-steps are timestamped
+    int stamp_sweep;             // sweep of the launch whose phases are timestamped
     double inv1p;                // 1 / (1 + rho), precomputed
     double tolv;                 // stop tolerance of this launch (0 = none)
     int xu_rows;                 // X update: rows of a slab per work unit
     int xu_wab_smem;             // X update: W_{A,B} kept in shared memory
 };
+
+// Index tables of the column solves of mode k (the same for every column):
+// for each stage slot ti of the non-k modes (ranks Rm, last slot fastest)
+//   cbt[ti][o]  K index of (o, c = 0), o over the other slots' combinations
+//   dgt[ti][o]  digits of o, 3 bits per slot
+//   lnt[ti][l]  lane l's first (o, o2) of the H sums, o | o2 << 16 (l < 32),
+//               and at l = 32 the step of 32 combinations, dq | dr << 16
+// laid out [cbt 3Q][dgt 3Q][lnt 3 x SOLVE_TAB_LANE] (Q = product of Rm).
+constexpr int SOLVE_TAB_LANE = 33;
+__host__ __device__ inline int solve_tab_ints(int Q) { return 6 * Q + 3 * SOLVE_TAB_LANE; }
+inline void solve_stage_tables(const Shape& s, int k, int* out) {
+    int Rm[3] = {1, 1, 1}, st[3] = {1, 1, 1}, nm = 0, Q = 1;
+    for (int q = 0; q < s.N; ++q)
+        if (q != k) {
+            Rm[nm] = s.R[k][q];
+            Q *= Rm[nm++];
+        }
+    for (int t = nm - 2; t >= 0; --t) st[t] = st[t + 1] * Rm[t + 1];
+    int* cbt = out;
+    int* dgt = out + 3 * Q;
+    int* lnt = out + 6 * Q;
+    for (int i = 0; i < solve_tab_ints(Q); ++i) out[i] = 0;
+    for (int ti = 0; ti < nm; ++ti) {
+        const int Ri = Rm[ti], sp = st[ti], Qo = Q / Ri;
+        for (int o = 0; o < Qo; ++o) {
+            const int hi = o / sp;
+            cbt[ti * Q + o] = hi * Ri * sp + (o - hi * sp);
+            int rem = o, pk = 0;
+            for (int t = nm - 1; t >= 0; --t) {
+                if (t == ti) continue;
+                pk |= (rem % Rm[t]) << (3 * t);
+                rem /= Rm[t];
+            }
+            dgt[ti * Q + o] = pk;
+        }
+        for (int l = 0; l < 32; ++l) lnt[ti * SOLVE_TAB_LANE + l] = (l / Qo) | ((l % Qo) << 16);
+        lnt[ti * SOLVE_TAB_LANE + 32] = (32 / Qo) | ((32 % Qo) << 16);
+    }
+}
 
 template <typename T>
 int persistent_smem_bytes(const SweepParams<T>& p);

@@ -37,6 +37,12 @@ constexpr int PT = 256;  // threads per CTA
 constexpr int PW = PT / 32;
 constexpr int GRAM_IOB = 2;  // io values per Gram unit (N = 3)
 
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -253,8 +259,13 @@ __device__ void gram_unit(const SweepParams<T>& p, int k, int gu, unsigned char*
 // output; the groups of the whole grid share the outputs.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem) {
+__device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem, bool stamp = false) {
     const Shape& s = p.sh;
+    // sub-step timestamps (slots 52..55) of CTA 0, thread 0, when `stamp` is set
+    auto rstamp = [&](int n) {
+        if (stamp && p.tstamp && blockIdx.x == 0 && threadIdx.x == 0) p.tstamp[52 + n] = gtimer();
+    };
+    rstamp(0);
     const ContractPlan& pl = p.pl[k];
     int m[3];
     const int nm = nonk(s, k, m);
@@ -290,11 +301,14 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
                 const int xo = row / Q2, X = row - xo * Q2, yo = col / Q2, Y = col - yo * Q2;
                 const T* gx = p.Gt + s.goff[o][k] + xo * Io;
                 const T* gy = p.Gt + s.goff[o][k] + yo * Io;
+                // unrolled so that a lane's loads are in flight together
                 if (nm == 1) {
+#pragma unroll 8
                     for (int io = sub; io < Io; io += L) acc = fma(gx[io], gy[io], acc);
                 } else {
                     const T* tp = p.gbuf + static_cast<long long>(X) * Q2 + Y;
                     const long long st = static_cast<long long>(Q2) * Q2;
+#pragma unroll 8
                     for (int io = sub; io < Io; io += L) acc = fma(gx[io] * gy[io], tp[io * st], acc);
                 }
             }
@@ -305,6 +319,7 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
             }
         }
     }
+    rstamp(1);
     // --- M, units covering every row: column tiles of TW columns (narrower
     // when 32-wide tiles would leave CTAs idle); within a warp the lanes of a
     // column split the units and meet by shuffles, warps meet in shared memory ---
@@ -320,12 +335,19 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
         T* coef = reinterpret_cast<T*>(smem);      // Rd x nu
         T* red = coef + ((Rd * nu + 3) & ~3);      // PW x RMAX x 32
         if (static_cast<int>(blockIdx.x) < ntile) {
+            if (pl.dmode >= 0 && pl.key_div == 1 && nu == s.I[pl.dmode]) {
+                // coef(rd, u) = G_{d,k}(rd, u): the whole table, one copy
+                stage_async(coef, p.Gt + s.goff[pl.dmode][k], Rd * nu);
+                stage_wait();
+            } else {
 #pragma unroll 4
-            for (int idx = threadIdx.x; idx < Rd * nu; idx += PT) {
-                const int rdd = idx / nu, u = idx - rdd * nu;
-                coef[idx] = pl.dmode >= 0 ? gfac(p.Gt, s, pl.dmode, k, rdd, u / pl.key_div) : T(1);
+                for (int idx = threadIdx.x; idx < Rd * nu; idx += PT) {
+                    const int rdd = idx / nu, u = idx - rdd * nu;
+                    coef[idx] = pl.dmode >= 0 ? gfac(p.Gt, s, pl.dmode, k, rdd, u / pl.key_div) : T(1);
+                }
+                __syncthreads();
             }
-            __syncthreads();
+            rstamp(2);
             const int warp = threadIdx.x >> 5;
             const int cl = lane % TW, sub = lane / TW;
             for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
@@ -335,12 +357,24 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r) acc[r] = T(0);
                 const T* pc = p.part + c;
-#pragma unroll 4
-                for (int u = warp * SUBS + sub; u < nu; u += PW * SUBS) {
-                    const T v = valid ? pc[static_cast<size_t>(u) * ncol] : T(0);
+                // batches of UB units: every load of a batch in flight before its FMAs
+                constexpr int UB = 8;
+                const int ustep = PW * SUBS;
+                for (int u0 = warp * SUBS + sub; u0 < nu; u0 += ustep * UB) {
+                    T vv[UB];
 #pragma unroll
-                    for (int r = 0; r < RMAX; ++r)
-                        if (r < Rd) acc[r] = fma(coef[r * nu + u], v, acc[r]);
+                    for (int t = 0; t < UB; ++t) {
+                        const int u = u0 + t * ustep;
+                        vv[t] = (valid && u < nu) ? pc[static_cast<size_t>(u) * ncol] : T(0);
+                    }
+#pragma unroll
+                    for (int t = 0; t < UB; ++t) {
+                        const int u = u0 + t * ustep;
+                        if (u < nu)
+#pragma unroll
+                            for (int r = 0; r < RMAX; ++r)
+                                if (r < Rd) acc[r] = fma(coef[r * nu + u], vv[t], acc[r]);
+                    }
                 }
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r)
@@ -364,6 +398,7 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
                 __syncthreads();
             }
         }
+        rstamp(3);
         return;
     }
     // --- M ---
@@ -432,11 +467,12 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
 // with eigenvalues >= rho, so no pivoting) that every lane of the warp runs
 // in registers.  FP64 path: the factorisation and the solves in FP64.  Mixed
 // path: the factorisation in FP32 followed by a step of iterative refinement
-// whose residual b - (H + rho I) g is formed in FP64, which recovers
-// FP64-level accuracy for the conditioning these systems have while keeping
-// GB300's narrow FP64 pipe nearly idle.  (One refinement step: H itself
-// carries the FP32 rounding of the contractions, so further steps would not
-// change the result's accuracy.)
+// whose residual b - (H + rho I) g is formed in two-float arithmetic (about
+// 48 significant bits from FP32 instructions only), which recovers the
+// accuracy of an FP64 solve for the conditioning these systems have without
+// GB300's FP64 pipe (one FP64 instruction per 64 cycles of a warp scheduler).
+// (One refinement step: H itself carries the FP32 rounding of the
+// contractions, so further steps would not change the result's accuracy.)
 // ---------------------------------------------------------------------------
 template <typename F>
 __device__ __forceinline__ F recip_nr(F d) {
@@ -456,11 +492,6 @@ __device__ __forceinline__ F recip_nr(F d) {
     return x;
 }
 
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
 
 // Sub-step timestamps of one column (slots 40..55 of the timestamp buffer):
 // taken by lane 0 of warp 0 of CTA 0 on its first column when `stamp` is set.
@@ -470,27 +501,40 @@ __device__ __forceinline__ unsigned long long gtimer() {
     } while (0)
 
 // Shared-memory layout of the solve phase (byte offsets from the phase's base):
-//   per-warp scratch (WSD doubles: H, the current columns and their T copies,
-//   rhs, solution, factor), the tables G_{i,k} (T), per-warp omega / M_k row
-//   in T / K index table (Qa entries each), K_k (T, when kept in shared
-//   memory), per-warp M_k row (FP64, the cp.async target).
+//   per-warp scratch (WSD doubles: the current columns in FP64 and in T (with
+//   the low parts of their two-float form on the mixed path), H and b of a
+//   stage, the solution), the tables G_{i,k} (T), the per-stage index tables
+//   of the CTA, per-warp omega and M_k row in T (Qa entries each), K_k (T, when
+//   kept in shared memory), per-warp M_k row (FP64, the cp.async target).
 constexpr int WSD = 2 * RMAX * RMAX + 11 * RMAX;  // doubles per warp
+// offsets inside a warp's scratch, in doubles (vs, gd) and in T (the rest)
+constexpr int SC_VS = 0, SC_GD = 3 * RMAX, SC_T = 4 * RMAX;
+constexpr int SC_AF = 0, SC_HV = RMAX * RMAX, SC_XF = 2 * RMAX * RMAX, SC_BV = SC_XF + RMAX, SC_VT = SC_BV + RMAX,
+              SC_VLO_T = SC_VT + 3 * RMAX;  // T offset where the FP32 low parts start
+constexpr int TAB_LANE = SOLVE_TAB_LANE;
 
 struct SolveLayout {
-    long long gik, warp, wstride, K, Ms, total;
+    long long gik, tab, warp, wstride, K, Ms, total;
 };
 
 __host__ __device__ inline SolveLayout solve_layout(int Q, int tot, int sz, bool ksm) {
     SolveLayout L;
     const long long Qa = (Q + 3) & ~3;
     L.gik = static_cast<long long>(PW) * WSD * 8;
-    L.warp = (L.gik + static_cast<long long>(tot) * sz + 15) & ~15LL;
-    L.wstride = Qa * (2 * sz + 4);
+    L.tab = (L.gik + static_cast<long long>(tot) * sz + 15) & ~15LL;
+    L.warp = (L.tab + static_cast<long long>(solve_tab_ints(Q)) * 4 + 15) & ~15LL;
+    L.wstride = Qa * 2 * sz;
     L.K = (L.warp + PW * L.wstride + 15) & ~15LL;
     L.Ms = (L.K + (ksm ? static_cast<long long>(Q) * Q * sz : 0) + 15) & ~15LL;
     L.total = L.Ms + static_cast<long long>(PW) * Q * 8;
     return L;
 }
+
+template <typename T>
+__device__ __forceinline__ T* warp_scratch_t(unsigned char* smem, int w) {
+    return reinterpret_cast<T*>(reinterpret_cast<double*>(smem) + w * WSD + SC_T);
+}
+
 
 // Butterfly reduce-scatter across the warp: v[V] per lane (V = 32 or 64) ->
 // the warp sums of value index lane (V = 32) or 2 lane, 2 lane + 1 (V = 64)
@@ -555,35 +599,55 @@ __device__ __forceinline__ void ldlt_solve_regs(const F (&A)[RI][RI], const F (&
         for (int t = r + 1; t < RI; ++t) x[r] -= A[t][r] * x[t];
 }
 
+// Error-free transformations in FP32: a + b = s + e and a * b = p + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
 // One stage (slot ti, Ri = RI values) of the column solve, by one warp:
 //   H(c, c2) = sum_{o, o2} omega(o) omega(o2) K[(o2, c2), (o, c)] + rho [c = c2]
 //   b(c)     = sum_o omega(o) M_k(j, (o, c)) + rho g_old(c)
 //   (H) g = b
 // where (o, c) is the K index with digit c in slot ti, cb[o] the index of
 // (o, 0) and sp the index step of the slot.  Lanes take (o, o2) combinations
-// and keep every pair c <= c2 (K is symmetric, so H is) and every b(c) in
-// registers; one reduce-scatter leaves value q with lane q, which writes it
-// out.  Every lane then factorises H and solves in registers (FP32 on the
-// mixed path, followed by one step of refinement with the residual formed in
-// FP64 by lane r for row r; FP64 on the FP64 path).  The new column ends in
-// gd[0..RI).  Returns false (uniformly) when H is not numerically SPD or the
-// solution is not finite.
+// (lane's first one (o_0, o2_0), then steps of 32) and keep every pair
+// c <= c2 (K is symmetric, so H is) and every b(c) in registers; one
+// reduce-scatter leaves value q with lane q, which writes it out.  Every lane
+// then factorises H and solves in registers.
+//   FP64 path: all of it in FP64; the new column goes to gd.
+//   Mixed path: FP32 factorisation and solve, then one step of refinement
+//   whose residual b - H g is formed by lane r for row r in two-float
+//   arithmetic (error-free products and sums of the FP32 sums, rho and the
+//   old value as hi + lo pairs: about 48 significant bits, no FP64
+//   instruction); the new column as a two-float pair replaces (ghi, glo).
+// Returns false (uniformly) when H is not numerically SPD or the result is
+// not finite; the old column is then left in place.
 template <typename T, int RI>
 __device__ __forceinline__ bool stage_solve(const T* __restrict__ K, const T* __restrict__ om,
                                             const int* __restrict__ cb, const T* __restrict__ mrow, int Q,
-                                            int Qo, int sp, int lane, double rho, const double* __restrict__ gold,
-                                            double* Hd, double* bd, T* Af, T* xf, double* gd) {
+                                            int Qo, int sp, int lane, int olane, int dq, int dr, T rhoT, float rhi,
+                                            float rlo, T* ghi, float* glo, T* Af, T* Hv, T* xf, T* bv, double* gd,
+                                            unsigned long long* ts) {
     constexpr bool MIXED = sizeof(T) == 4;
     constexpr int NP = RI * (RI + 1) / 2;
     constexpr int V = NP + RI <= 32 ? 32 : 64;
+    // optional sub-step timestamps (one profiled column): ts[0..3]
+    auto stamp = [&](int n) {
+        if (ts && lane == 0) ts[n] = gtimer();
+    };
     T v[V];
 #pragma unroll
     for (int q = 0; q < V; ++q) v[q] = T(0);
     const int spQ = sp * Q;
     const int n = Qo * Qo;
-    const int dq = 32 / Qo, dr = 32 - dq * Qo;
-    int o = lane / Qo;
-    int o2 = lane - o * Qo;
+    int o = olane & 0xffff;
+    int o2 = olane >> 16;
     for (int f = lane; f < n; f += 32) {
         const T w = om[o] * om[o2];
         const T* kr = K + cb[o2] * Q + cb[o];
@@ -605,6 +669,7 @@ __device__ __forceinline__ bool stage_solve(const T* __restrict__ K, const T* __
 #pragma unroll
         for (int c = 0; c < RI; ++c) v[NP + c] = fma(w, mr[c * sp], v[NP + c]);
     }
+    stamp(0);
     warp_reduce_scatter<T, V>(v, lane);
 #pragma unroll
     for (int h = 0; h < V / 32; ++h) {
@@ -614,22 +679,21 @@ __device__ __forceinline__ bool stage_solve(const T* __restrict__ K, const T* __
             int c2 = 0;
             while ((c2 + 1) * (c2 + 2) / 2 <= idx) ++c2;
             const int c = idx - c2 * (c2 + 1) / 2;
-            const T hv = val + (c == c2 ? static_cast<T>(rho) : T(0));
+            const T hv = c == c2 ? val + rhoT : val;
             Af[c2 * RI + c] = hv;
             Af[c * RI + c2] = hv;
             if (MIXED) {
-                const double hdv = static_cast<double>(val) + (c == c2 ? rho : 0.0);
-                Hd[c2 * RI + c] = hdv;
-                Hd[c * RI + c2] = hdv;
+                Hv[c2 * RI + c] = val;
+                Hv[c * RI + c2] = val;
             }
         } else if (idx < NP + RI) {
             const int c = idx - NP;
-            const double bb = static_cast<double>(val) + rho * gold[c];
-            bd[c] = bb;
-            xf[c] = static_cast<T>(bb);
+            bv[c] = val;
+            xf[c] = fma(rhoT, ghi[c], val);
         }
     }
     __syncwarp();
+    stamp(1);
     T A[RI][RI], id[RI], x[RI];
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
@@ -639,35 +703,58 @@ __device__ __forceinline__ bool stage_solve(const T* __restrict__ K, const T* __
     }
     bool ok = ldlt_regs<T, RI>(A, id);
     ldlt_solve_regs<T, RI>(A, id, x);
+    stamp(2);
     T xl = T(0);
 #pragma unroll
     for (int r = 0; r < RI; ++r)
         if (lane == r) xl = x[r];
-    double g = static_cast<double>(xl);
-    if (MIXED) {
-        // residual of row r in FP64 (lane r), the correction solved in FP32
-        T rr = T(0);
+    if constexpr (MIXED) {
+        // residual of row r: b_r - sum_t H(r, t) x_t, with b_r = bv_r + rho g_old(r)
+        // and H(r, r) = Hv(r, r) + rho, in two-float arithmetic
+        float rr = 0.f;
         if (lane < RI) {
-            double res = bd[lane];
+            float sum = bv[lane], err = 0.f, p, pe, se;
+            const float gh = ghi[lane], gl = glo[lane];
+            two_prod(rhi, gh, p, pe);
+            two_sum(sum, p, sum, se);
+            err += pe + se + fmaf(rhi, gl, rlo * gh);
 #pragma unroll
-            for (int t = 0; t < RI; ++t) res -= Hd[lane * RI + t] * static_cast<double>(x[t]);
-            rr = static_cast<T>(res);
+            for (int t = 0; t < RI; ++t) {
+                two_prod(-Hv[lane * RI + t], x[t], p, pe);
+                two_sum(sum, p, sum, se);
+                err += pe + se;
+            }
+            two_prod(-rhi, xl, p, pe);
+            two_sum(sum, p, sum, se);
+            err += pe + se - rlo * xl;
+            rr = sum + err;
         }
-        T cr[RI];
+        float cr[RI];
 #pragma unroll
         for (int t = 0; t < RI; ++t) cr[t] = __shfl_sync(0xffffffffu, rr, t);
-        ldlt_solve_regs<T, RI>(A, id, cr);
-        T cl = T(0);
+        ldlt_solve_regs<float, RI>(A, id, cr);
+        float cl = 0.f;
 #pragma unroll
         for (int r = 0; r < RI; ++r)
             if (lane == r) cl = cr[r];
-        g += static_cast<double>(cl);
+        float nh, nl;
+        two_sum(xl, cl, nh, nl);
+        if (lane < RI && !isfinite(nh)) ok = false;
+        const bool all = __all_sync(0xffffffffu, ok) != 0;
+        if (all && lane < RI) {
+            ghi[lane] = nh;
+            glo[lane] = nl;
+        }
+        stamp(3);
+        return all;
+    } else {
+        if (lane < RI) {
+            gd[lane] = xl;
+            if (!isfinite(xl)) ok = false;
+        }
+        stamp(3);
+        return __all_sync(0xffffffffu, ok) != 0;
     }
-    if (lane < RI) {
-        gd[lane] = g;
-        if (!isfinite(g)) ok = false;
-    }
-    return __all_sync(0xffffffffu, ok) != 0;
 }
 
 template <typename T>
@@ -697,23 +784,25 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
     const bool ksm = p.solve_k_in_smem != 0;
     const SolveLayout L = solve_layout(Q, tot, static_cast<int>(sizeof(T)), ksm);
     double* my = reinterpret_cast<double*>(smem) + warp * WSD;
-    double* Hd = my;                      // RMAX*RMAX: H (FP64)
-    double* vs = Hd + RMAX * RMAX;        // 3 x RMAX current columns
-    double* bd = vs + 3 * RMAX;           // RMAX rhs (FP64)
-    double* gd = bd + RMAX;               // RMAX solution (FP64)
-    double* rd = gd + RMAX;               // RMAX (spare)
-    T* Af = reinterpret_cast<T*>(rd + RMAX);  // RMAX*RMAX: H in the factorisation's precision
-    T* xf = Af + RMAX * RMAX + RMAX;            // RMAX: b in that precision
-    T* vt = reinterpret_cast<T*>(my + 2 * RMAX * RMAX + 8 * RMAX);  // 3 x RMAX columns in T
+    double* vs = my + SC_VS;  // 3 x RMAX current columns (FP64, fetched)
+    double* gd = my + SC_GD;  // RMAX: new column (FP64 path)
+    T* sc = warp_scratch_t<T>(smem, warp);
+    T* Af = sc + SC_AF;  // RMAX*RMAX: H + rho I
+    T* Hv = sc + SC_HV;  // RMAX*RMAX: H's sums (mixed path)
+    T* xf = sc + SC_XF;  // RMAX: b
+    T* bv = sc + SC_BV;  // RMAX: b's sums (mixed path)
+    T* vt = sc + SC_VT;  // 3 x RMAX: current columns in T (high parts on the mixed path)
+    float* vlo = reinterpret_cast<float*>(sc + SC_VLO_T);  // 3 x RMAX: low parts (mixed path)
     T* gik = reinterpret_cast<T*>(smem + L.gik);
+    int* cbt = reinterpret_cast<int*>(smem + L.tab);  // [nm][Q] K index of (o, 0)
+    int* dgt = cbt + 3 * Q;                            // [nm][Q] digits of o, 3 bits per slot
+    int* lnt = dgt + 3 * Q;                            // [nm][TAB_LANE]: lane's first (o, o2); steps
     const int Qa = (Q + 3) & ~3;
     T* om = reinterpret_cast<T*>(smem + L.warp + warp * L.wstride);
     T* mf = om + Qa;
-    int* cb = reinterpret_cast<int*>(mf + Qa);
     T* Ks = reinterpret_cast<T*>(smem + L.K);
     double* Ms = reinterpret_cast<double*>(smem + L.Ms) + static_cast<size_t>(warp) * Q;
     const T* mrow = MIXED ? mf : reinterpret_cast<const T*>(Ms);
-    for (int t = 0; t < nm; ++t) stage_async(gik + gko[t], p.Gt + s.goff[m[t]][k], Rm[t] * s.I[m[t]]);
     // the current columns G_{k,m}(:, j) and the row M_k(j, :) of a column,
     // copied asynchronously (the first column's together with the tables)
     auto fetch_column = [&](int j) {
@@ -726,56 +815,78 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
         for (int q = lane; q < Q; q += 32)
             asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(Ms + q)), "l"(Mj + q) : "memory");
     };
+    // what the first column needs (its data, K, the index tables) in one
+    // cp.async group; the tables G_{i,k}, read only by the W refresh, in a
+    // second group that is waited for before the refresh
     const int j0 = warp * gridDim.x + blockIdx.x;
     if (j0 < Ik) fetch_column(j0);
     if (ksm) stage_async(Ks, p.Kk, Q * Q);
+    stage_async(cbt, p.stab[k], solve_tab_ints(Q));
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int t = 0; t < nm; ++t) stage_async(gik + gko[t], p.Gt + s.goff[m[t]][k], Rm[t] * s.I[m[t]]);
+    asm volatile("cp.async.commit_group;" ::: "memory");
     const T* K = ksm ? Ks : p.Kk;
-    stage_wait();
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncthreads();
     IFCTN_SSTAMP(1);
     const double rho = p.rho;
+    const T rhoT = static_cast<T>(rho);
+    const float rhi = static_cast<float>(rho);
+    const float rlo = static_cast<float>(rho - static_cast<double>(rhi));
     // W refresh by the whole CTA when every warp has at most one column
     const bool cta_refresh = static_cast<long long>(gridDim.x) * PW >= Ik;
+    if (!cta_refresh) {  // every warp refreshes its columns: the tables first
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+    }
     for (int j = j0; j < Ik; j += gridDim.x * PW) {
         if (j != j0) {
             fetch_column(j);
             asm volatile("cp.async.wait_all;" ::: "memory");
             __syncwarp();
         }
-        // the column vectors and the M_k row in T, converted once per column
+        // the column vectors (two-float pairs on the mixed path) and the M_k
+        // row in T, converted once per column
         for (int idx = lane; idx < nm * RMAX; idx += 32) {
             const int t = idx / RMAX, r = idx - t * RMAX;
-            if (r < Rm[t]) vt[idx] = static_cast<T>(vs[idx]);
+            if (r < Rm[t]) {
+                const double g = vs[idx];
+                const T h = static_cast<T>(g);
+                vt[idx] = h;
+                if (MIXED) vlo[idx] = static_cast<float>(g - static_cast<double>(h));
+            }
         }
         if (MIXED)
             for (int q = lane; q < Q; q += 32) mf[q] = static_cast<T>(Ms[q]);
         __syncwarp();
         IFCTN_SSTAMP(2);
+        unsigned changed = 0;  // slots whose column was updated
         for (int ti = 0; ti < nm; ++ti) {
             const int i = m[ti], Ri = Rm[ti], sp = st[ti];
             const int Qo = Q / Ri;
-            // omega(o) = prod over slots t != ti of v_t(digit_t(o)), and the
-            // K index of (o, c = 0)
+            // omega(o) = prod over slots t != ti of v_t(digit_t(o))
             for (int o = lane; o < Qo; o += 32) {
+                const int pk = dgt[ti * Q + o];
                 T w = T(1);
-                int rem = o;
-                for (int t = nm - 1; t >= 0; --t) {
-                    if (t == ti) continue;
-                    const int d = rem % Rm[t];
-                    rem /= Rm[t];
-                    w *= vt[t * RMAX + d];
-                }
+                for (int t = 0; t < nm; ++t)
+                    if (t != ti) w *= vt[t * RMAX + ((pk >> (3 * t)) & 7)];
                 om[o] = w;
-                const int hi = o / sp;
-                cb[o] = hi * Ri * sp + (o - hi * sp);
             }
             __syncwarp();
             if (ti == 0) IFCTN_SSTAMP(3);
-            const double* gold = vs + ti * RMAX;
+            const int* cb = cbt + ti * Q;
+            const int olane = lnt[ti * TAB_LANE + lane];
+            const int steps = lnt[ti * TAB_LANE + 32];
+            const int dq = steps & 0xffff, dr = steps >> 16;
+            T* gh = vt + ti * RMAX;
+            float* gl = vlo + ti * RMAX;
+            unsigned long long* sts = (stamp_col && ti == 0) ? p.tstamp + 44 : nullptr;
             bool okc;
             switch (Ri) {
 #define IFCTN_SOLVE_CASE(R)                                                                                     \
     case R:                                                                                                     \
-        okc = stage_solve<T, R>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd, Af, xf, gd);               \
+        okc = stage_solve<T, R>(K, om, cb, mrow, Q, Qo, sp, lane, olane, dq, dr, rhoT, rhi, rlo, gh, gl, Af, Hv, \
+                                xf, bv, gd, sts);                                                               \
         break;
                 IFCTN_SOLVE_CASE(1)
                 IFCTN_SOLVE_CASE(2)
@@ -785,30 +896,40 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
                 IFCTN_SOLVE_CASE(6)
                 IFCTN_SOLVE_CASE(7)
                 default:
-                    okc = stage_solve<T, 8>(K, om, cb, mrow, Q, Qo, sp, lane, rho, gold, Hd, bd, Af, xf, gd);
+                    okc = stage_solve<T, 8>(K, om, cb, mrow, Q, Qo, sp, lane, olane, dq, dr, rhoT, rhi, rlo, gh, gl,
+                                            Af, Hv, xf, bv, gd, sts);
                     break;
 #undef IFCTN_SOLVE_CASE
             }
-            if (ti == 0) IFCTN_SSTAMP(4);
-            if (ti == 0) IFCTN_SSTAMP(5);
-            if (ti == 0) IFCTN_SSTAMP(6);
-            if (ti == 0) IFCTN_SSTAMP(7);
-            if (!okc) {
-                if (lane == 0) atomicOr(p.flags, FLAG_NOTSPD);
-                if (lane < Ri) gd[lane] = vs[ti * RMAX + lane];
-            }
-            __syncwarp();
+            if (!okc && lane == 0) atomicOr(p.flags, FLAG_NOTSPD);  // the old column stays
             if (ti == 0) IFCTN_SSTAMP(8);
-            for (int r = lane; r < Ri; r += 32) {
-                const double g = gd[r];
-                const T gt = static_cast<T>(g);
-                vs[ti * RMAX + r] = g;
-                vt[ti * RMAX + r] = gt;
-                p.Gd[s.goff[k][i] + r * Ik + j] = g;
-                p.Gt[s.goff[k][i] + r * Ik + j] = gt;
+            if (okc) {
+                changed |= 1u << ti;
+                for (int r = lane; r < Ri; r += 32) {
+                    if (MIXED) {
+                        p.Gt[s.goff[k][i] + r * Ik + j] = gh[r];
+                    } else {
+                        const double g = gd[r];
+                        vs[ti * RMAX + r] = g;
+                        vt[ti * RMAX + r] = static_cast<T>(g);
+                        p.Gd[s.goff[k][i] + r * Ik + j] = g;
+                        p.Gt[s.goff[k][i] + r * Ik + j] = static_cast<T>(g);
+                    }
+                }
             }
             __syncwarp();
             if (ti == 0) IFCTN_SSTAMP(9);
+        }
+        if (MIXED) {
+            // FP64 master copy of the updated slots: hi + lo
+            for (int idx = lane; idx < nm * RMAX; idx += 32) {
+                const int t = idx / RMAX, r = idx - t * RMAX;
+                if (r < Rm[t] && ((changed >> t) & 1u)) {
+                    const double g = static_cast<double>(vt[idx]) + static_cast<double>(vlo[idx]);
+                    vs[idx] = g;
+                    p.Gd[s.goff[k][m[t]] + r * Ik + j] = g;
+                }
+            }
         }
         IFCTN_SSTAMP(10);
         if (cta_refresh) continue;  // done below by the whole CTA
@@ -834,6 +955,7 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
         IFCTN_SSTAMP(11);
         stamp_col = false;
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     if (cta_refresh) {
         // columns of this CTA: j = w * gridDim.x + blockIdx.x, their new
@@ -846,9 +968,7 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
             for (int idx = tid; idx < ncol * Ii; idx += PT) {
                 const int w = idx / Ii, b = idx - w * Ii;
                 const int j = w * gridDim.x + blockIdx.x;
-                const T* vtw =
-                    reinterpret_cast<const T*>(reinterpret_cast<double*>(smem) + w * WSD + 2 * RMAX * RMAX + 8 * RMAX) +
-                    t * RMAX;
+                const T* vtw = warp_scratch_t<T>(smem, w) + SC_VT + t * RMAX;
                 T acc = T(0);
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r)
@@ -1275,10 +1395,10 @@ __global__ void __launch_bounds__(PT) k_solve_cols(const __grid_constant__ Sweep
 }
 
 
-// CTA 0 stamps the end of every phase of the first sweep (profiling aid)
+// CTA 0 stamps the end of every phase of one sweep of the launch (profiling aid)
 #define IFCTN_STAMP(p, sw, slot)                                                        \
     do {                                                                              \
-        if ((p).tstamp && (sw) == 0 && blockIdx.x == 0 && threadIdx.x == 0 &&         \
+        if ((p).tstamp && (sw) == (p).stamp_sweep && blockIdx.x == 0 && threadIdx.x == 0 &&         \
             (slot) < 64)                                                              \
             (p).tstamp[(slot)] = gtimer();                                            \
     } while (0)
@@ -1326,15 +1446,15 @@ __global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const __grid_constan
                 }
             }
             IFCTN_STAMP(p, sw, 1 + 6 * k);
-            if (p.tstamp && sw == 0 && threadIdx.x == 0 && k < 4 && blockIdx.x < 512)
+            if (p.tstamp && sw == p.stamp_sweep && threadIdx.x == 0 && k < 4 && blockIdx.x < 512)
                 p.tstamp[64 + k * 512 + blockIdx.x] = gtimer();
             if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
             IFCTN_STAMP(p, sw, 2 + 6 * k);
-            reduce_phase<T>(p, k, work);
+            reduce_phase<T>(p, k, work, sw == p.stamp_sweep && k == p.stamp_mode);
             IFCTN_STAMP(p, sw, 3 + 6 * k);
             if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
             IFCTN_STAMP(p, sw, 4 + 6 * k);
-            solve_phase<T>(p, k, work, sw == 0 && k == s.N - 1);
+            solve_phase<T>(p, k, work, sw == p.stamp_sweep && k == p.stamp_mode);
             IFCTN_STAMP(p, sw, 5 + 6 * k);
             if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
             IFCTN_STAMP(p, sw, 6 + 6 * k);
