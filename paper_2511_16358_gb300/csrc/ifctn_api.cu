@@ -438,6 +438,36 @@ ContractPlan plan_contract(const Shape& s, int k, int sz, std::vector<UnitDesc>&
 // Plan of the warp-pipelined kernels (one CTA of 8 warps per SM, a TMA ring
 // per warp).  Returns warp = 0 when the shape does not fit their shared-memory
 // layout; the CTA kernels then run the mode.
+// Chunk count for splitting S slabs (t tasks each) into the units of a
+// warp-pipelined contraction, `outer` units per chunk.  A unit ends in a CTA
+// barrier, so its tasks should split evenly over the NW warps, and the
+// units evenly over the SMs.  Cost model, in task times: the most units a
+// CTA runs times (tasks a warp runs per unit + per-unit overhead E).  The
+// candidates are c0 (the balance-driven default) and every divisor c of S
+// whose units give each warp the same number of tasks; the default is left
+// only for a predicted gain above 3 %.
+int warp_unit_chunks(int S, int t, long long outer, int c0, int NW, int sms) {
+    constexpr double E = 0.4;
+    auto cost = [&](int c) {
+        const long long nu = outer * c;
+        const long long per_cta = (nu + sms - 1) / sms;
+        const long long tasks = static_cast<long long>((S + c - 1) / c) * t;
+        return static_cast<double>(per_cta) * (static_cast<double>((tasks + NW - 1) / NW) + E);
+    };
+    int best = c0;
+    double bc = cost(c0);
+    for (int c = 1; c <= S; ++c) {
+        if (S % c != 0 || (static_cast<long long>(S / c) * t) % NW != 0) continue;
+        if (outer * c > 64LL * sms) break;
+        const double v = cost(c);
+        if (v < bc && v < 0.97 * cost(c0)) {  // leave the default only for a clear gain
+            bc = v;
+            best = c;
+        }
+    }
+    return best;
+}
+
 ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitDesc>& units) {
     constexpr int NW = 16;
     ContractPlan pl;
@@ -497,8 +527,9 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
         const int nrb = cdiv(IA, RBK);
         if (N == 4) {
             const int I0 = s.I[0], I1 = s.I[1];
-            const int nC = std::max(1, std::min(std::min(cdiv(target, static_cast<long long>(I0) * nbc),
-                                                         std::max(1, I1 * nrb / NW)), I1));
+            int nC = std::max(1, std::min(std::min(cdiv(target, static_cast<long long>(I0) * nbc),
+                                                   std::max(1, I1 * nrb / NW)), I1));
+            nC = warp_unit_chunks(I1, nrb, static_cast<long long>(I0) * nbc, nC, NW, sms);
             for (int i0 = 0; i0 < I0; ++i0)
                 for (int c = 0; c < nC; ++c)
                     for (int bc = 0; bc < nbc; ++bc) {
@@ -601,7 +632,8 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
         const int nrc = cdiv(IA, RBK);
         if (isF && N == 4) {
             const int o = 1 - k, Io = s.I[o], Ik = s.I[k], I1 = s.I[1];
-            const int nOC = std::max(1, std::min(cdiv(target, static_cast<long long>(Ik) * nrc), std::max(1, Io / NW)));
+            int nOC = std::max(1, std::min(cdiv(target, static_cast<long long>(Ik) * nrc), std::max(1, Io / NW)));
+            nOC = warp_unit_chunks(Io, 1, static_cast<long long>(Ik) * nrc, nOC, NW, sms);
             for (int j = 0; j < Ik; ++j)
                 for (int oc = 0; oc < nOC; ++oc)
                     for (int rc = 0; rc < nrc; ++rc) {
@@ -631,7 +663,8 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
             pl.xr = round_up(RBK * IB + 32 / sz, VN);
         } else if (N == 4) {
             const int I0 = s.I[0], I1 = s.I[1];
-            const int nC = std::max(1, std::min(cdiv(target, static_cast<long long>(I0) * nrc), std::max(1, I1 / NW)));
+            int nC = std::max(1, std::min(cdiv(target, static_cast<long long>(I0) * nrc), std::max(1, I1 / NW)));
+            nC = warp_unit_chunks(I1, 1, static_cast<long long>(I0) * nrc, nC, NW, sms);
             for (int i0 = 0; i0 < I0; ++i0)
                 for (int c = 0; c < nC; ++c)
                     for (int rc = 0; rc < nrc; ++rc) {
@@ -1015,9 +1048,10 @@ struct Engine : ifctn_ctx {
         pp.stamp_sweep = 0;
         if (const char* e = getenv("IFCTN_STAMP_SWEEP")) pp.stamp_sweep = std::max(0, atoi(e));
         {
-            // X-update work units: row ranges of slabs, about 4 per CTA
-            // contiguous row ranges of 2K..16K entries, about 4 units per CTA
-            const long long target_units = 4LL * 2 * num_sms();
+            // X-update work units: contiguous row ranges of 2K..16K entries,
+            // about one per CTA of the persistent grid (each unit pays the
+            // latency of building its row and slab factors)
+            const long long target_units = 2LL * num_sms();
             const long long rows_total = static_cast<long long>(sh.nF) * sh.IA;
             long long rows = std::max<long long>(1, rows_total / target_units);
             rows = std::max<long long>(rows, std::max(1, 2048 / sh.IB));
