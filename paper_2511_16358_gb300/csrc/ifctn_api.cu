@@ -986,7 +986,19 @@ struct Engine : ifctn_ctx {
             int nm = 0;
             for (int q = 0; q < sh.N; ++q)
                 if (q != k) m[nm++] = q;
-            pp.gunits[k] = nm == 2 ? (sh.I[m[0]] + 1) / 2 : nm == 3 ? sh.I[m[0]] : 0;
+            // order 3: a Gram unit takes iob values of i_o, one output per thread
+            // (iob R^2 <= threads); enough of them per unit that the Gram units fit on
+            // the CTAs the contraction units leave free (one work item per CTA)
+            pp.gram_iob[k] = 2;
+            if (nm == 2) {
+                const int Io = sh.I[m[0]], Rl = sh.R[k][m[1]];
+                const int free_ctas = 2 * num_sms() - plan[k].nunits;
+                const int cap = std::max(2, PERSISTENT_THREADS / (Rl * Rl));
+                if (free_ctas > 0) pp.gram_iob[k] = std::max(2, std::min(cap, cdiv(Io, free_ctas)));
+                pp.gunits[k] = cdiv(Io, pp.gram_iob[k]);
+            } else {
+                pp.gunits[k] = nm == 3 ? sh.I[m[0]] : 0;
+            }
             const long long Q = mode_q(sh, k);
             if (Q * Q * static_cast<long long>(sizeof(T)) > 96 * 1024) k_fits = false;
         }

@@ -4,12 +4,15 @@
 
 namespace ifctn {
 
+constexpr int PERSISTENT_THREADS = 256;  // threads per CTA of the persistent kernel
+
 template <typename T>
 struct SweepParams {
     Shape sh;
     ContractPlan pl[MAXN];
     const UnitDesc* units[MAXN];
     int gunits[MAXN];        // Gram work units of phase 1, per mode
+    int gram_iob[MAXN];      // io values per Gram unit (order 3), per mode
     T* X;
     const uint32_t* mb;
     const T* Xt;             // ground truth for RSE/RMSE, or null

@@ -33,9 +33,8 @@ namespace {
 using cdev::contract_col_unit;
 using cdev::contract_row_unit;
 
-constexpr int PT = 256;  // threads per CTA
+constexpr int PT = PERSISTENT_THREADS;
 constexpr int PW = PT / 32;
-constexpr int GRAM_IOB = 2;  // io values per Gram unit (N = 3)
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -180,18 +179,23 @@ __device__ void gram_unit(const SweepParams<T>& p, int k, int gu, unsigned char*
     if (s.N == 3) {
         const int o = m[0], l = m[1];
         const int Io = s.I[o], Il = s.I[l], Rl = s.R[k][l];
-        const int io0 = gu * GRAM_IOB, io1 = min(Io, io0 + GRAM_IOB);
-        T* gl = sm;  // Rl x Il
-        stage_async(gl, p.Gt + s.goff[l][k], Rl * Il);
-        T* wr = gl + Rl * Il;  // (io1-io0) x Il
-        stage_async(wr, p.W + s.woff[o][l] + static_cast<long long>(io0) * Il, (io1 - io0) * Il);
+        const int iob = p.gram_iob[k];
+        const int io0 = gu * iob, io1 = min(Io, io0 + iob);
+        // rows at an odd stride: the threads of a warp read different rows at
+        // the same il without bank conflicts
+        const int ld = Il | 1;
+        T* gl = sm;  // Rl x ld
+        for (int r = 0; r < Rl; ++r) stage_async(gl + r * ld, p.Gt + s.goff[l][k] + r * Il, Il);
+        T* wr = gl + Rl * ld;  // (io1-io0) x ld
+        for (int r = 0; r < io1 - io0; ++r)
+            stage_async(wr + r * ld, p.W + s.woff[o][l] + static_cast<long long>(io0 + r) * Il, Il);
         stage_wait();
         const int nout = (io1 - io0) * Rl * Rl;
         for (int idx = tid; idx < nout; idx += PT) {
             const int y = idx % Rl, x = (idx / Rl) % Rl, ir = idx / (Rl * Rl);
-            const T* gx = gl + x * Il;
-            const T* gy = gl + y * Il;
-            const T* w2 = wr + ir * Il;
+            const T* gx = gl + x * ld;
+            const T* gy = gl + y * ld;
+            const T* w2 = wr + ir * ld;
             T a0 = T(0), a1 = T(0);
             int il = 0;
             for (; il + 1 < Il; il += 2) {
@@ -1545,7 +1549,7 @@ int persistent_smem_bytes(const SweepParams<T>& p) {
                                           static_cast<long long>(PW) * RMAX * 32) * sizeof(T));
         if (nm == 2) {
             const int l = m[1];
-            need = std::max<long long>(need, static_cast<long long>(s.R[k][l] * s.I[l] + GRAM_IOB * s.I[l]) * sizeof(T));
+            need = std::max<long long>(need, static_cast<long long>(s.R[k][l] + p.gram_iob[k]) * (s.I[l] | 1) * sizeof(T));
         } else if (nm == 3) {
             const int c = m[1], l = m[2];
             const long long Q2 = static_cast<long long>(s.R[k][c]) * s.R[k][l];
