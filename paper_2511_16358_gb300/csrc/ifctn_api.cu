@@ -1032,7 +1032,6 @@ struct Engine : ifctn_ctx {
         pp.flags = flags();
         pp.tol = tol.p;
         pp.bar_count = bar.p;
-        pp.bar_gen = bar.p + 1;
         pp.rho = prob.rho;
         pp.inv1p = 1.0 / (1.0 + prob.rho);
         pp.nmiss = nmiss;
@@ -1089,11 +1088,16 @@ struct Engine : ifctn_ctx {
     ifctn_status launch_run(int n) {
         if (n <= 0) return IFCTN_OK;
         if (persistent) {
-            pp.nsweeps = n;
-            pp.tolv = cur_tol;
-            pp.Xt = (logm && truth) ? Xt.p : nullptr;
-            CK(launch_persistent<T>(pp, pgrid, psmem, st));
-            ++launch_count;
+            // at most 65536 sweeps a launch: the grid barrier's arrival counter
+            // (zeroed before each launch) then stays far below 2^32
+            for (int s0 = 0; s0 < n; s0 += 65536) {
+                pp.nsweeps = std::min(65536, n - s0);
+                pp.tolv = cur_tol;
+                pp.Xt = (logm && truth) ? Xt.p : nullptr;
+                CK(cudaMemsetAsync(bar.p, 0, 4 * sizeof(unsigned), st));
+                CK(launch_persistent<T>(pp, pgrid, psmem, st));
+                ++launch_count;
+            }
         } else {
             for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(gexec, st));
             launch_count += static_cast<long long>(n) * launches;

@@ -31,7 +31,6 @@ struct SweepParams {
     int* flags;
     const double* tol;
     unsigned* bar_count;
-    unsigned* bar_gen;
     double rho;
     long long nmiss;
     int nsweeps;

@@ -48,36 +48,31 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     return v;
 }
 
-__device__ __forceinline__ unsigned atom_add_acqrel_u32(unsigned* p, unsigned v) {
-    unsigned old;
-    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
+
+
+// Software grid barrier (the grid is co-resident: cooperative launch).  The
+// arrival counter only grows during a launch (the host zeroes it before each
+// launch): barrier number b of the launch is passed once it reaches
+// b * gridDim.x.  Thread 0 of a CTA arrives with a release reduction and
+// spins with acquire loads until the target, bounded by a clock budget (on
+// expiry: timeout flag, and the kernel returns).  Every CTA passes the same
+// sequence of barriers, so `nb` (this CTA's count of barriers passed) agrees.
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Software grid barrier (the grid is co-resident: cooperative launch).
-// Arrival is an acq_rel add on a counter; the last CTA resets the counter and
-// publishes the next generation with a release store; the others spin with
-// acquire loads, bounded by a clock budget.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* flags) {
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& nb, int* flags) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
+    ++nb;
     if (threadIdx.x == 0) {
-        const unsigned g = ld_acquire_u32(gen);
-        const unsigned arrived = atom_add_acqrel_u32(count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            *reinterpret_cast<volatile unsigned*>(count) = 0u;
-            st_release_u32(gen, g + 1u);
-        } else {
-            const long long t0 = clock64();
-            while (ld_acquire_u32(gen) == g) {
-                if (clock64() - t0 > 4000000000LL) {
-                    atomicOr(flags, FLAG_TIMEOUT);
-                    break;
-                }
+        const unsigned target = nb * gridDim.x;
+        red_release_add_u32(count, 1u);
+        const long long t0 = clock64();
+        while (ld_acquire_u32(count) < target) {
+            if (clock64() - t0 > 4000000000LL) {
+                atomicOr(flags, FLAG_TIMEOUT);
+                break;
             }
         }
     }
@@ -1421,6 +1416,7 @@ __global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const __grid_constan
     __syncthreads();
     if (*reinterpret_cast<volatile const int*>(p.done)) return;
     int pipe = 0;
+    unsigned nbar = 0;  // grid barriers passed in this launch
     const Shape& s = p.sh;
     __shared__ int redc;
     __shared__ int wtag;
@@ -1452,21 +1448,21 @@ __global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const __grid_constan
             IFCTN_STAMP(p, sw, 1 + 6 * k);
             if (p.tstamp && sw == p.stamp_sweep && threadIdx.x == 0 && k < 4 && blockIdx.x < 512)
                 p.tstamp[64 + k * 512 + blockIdx.x] = gtimer();
-            if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
+            if (!grid_barrier(p.bar_count, nbar, p.flags)) return;
             IFCTN_STAMP(p, sw, 2 + 6 * k);
             reduce_phase<T>(p, k, work, sw == p.stamp_sweep && k == p.stamp_mode);
             IFCTN_STAMP(p, sw, 3 + 6 * k);
-            if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
+            if (!grid_barrier(p.bar_count, nbar, p.flags)) return;
             IFCTN_STAMP(p, sw, 4 + 6 * k);
             solve_phase<T>(p, k, work, sw == p.stamp_sweep && k == p.stamp_mode);
             IFCTN_STAMP(p, sw, 5 + 6 * k);
-            if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
+            if (!grid_barrier(p.bar_count, nbar, p.flags)) return;
             IFCTN_STAMP(p, sw, 6 + 6 * k);
         }
         double* xp = p.xpart + 8LL * gridDim.x * (sw & 1);
         xupdate_phase<T>(p, xp + 8 * blockIdx.x, work);
         IFCTN_STAMP(p, sw, 25);
-        if (!grid_barrier(p.bar_count, p.bar_gen, p.flags)) return;
+        if (!grid_barrier(p.bar_count, nbar, p.flags)) return;
         IFCTN_STAMP(p, sw, 26);
         // Stop decision (only when a tolerance is set): every CTA sums the
         // per-CTA values in the same order, so all take the same
