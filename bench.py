@@ -102,12 +102,14 @@ class Clocks:
 # ---------------------------------------------------------------------------
 def make_inputs(w, b, inp):
     dims, R = w.dims, w.R
-    Gt = inp.gaussian_factors(dims, R, inp.planted_factor_seed(w))
-    P = int(np.prod(dims))
-    prob = b.make_problem(dims, R, rho=w.rho, max_sweeps=0, tol=0.0, precision=b.FP64)
-    ctx = b.create(prob, np.zeros(P), np.zeros(P, dtype=np.uint8), Gt)
-    planted = b.reconstruct(ctx, np.empty(dims, dtype=np.float64))
-    b.destroy(ctx)
+    planted = None
+    if w.planted:
+        Gt = inp.gaussian_factors(dims, R, inp.planted_factor_seed(w))
+        P = int(np.prod(dims))
+        prob = b.make_problem(dims, R, rho=w.rho, max_sweeps=0, tol=0.0, precision=b.FP64)
+        ctx = b.create(prob, np.zeros(P), np.zeros(P, dtype=np.uint8), Gt)
+        planted = b.reconstruct(ctx, np.empty(dims, dtype=np.float64))
+        b.destroy(ctx)
     xt, mask, _ = inp.workload_inputs(w, planted)
     return xt, mask
 
@@ -193,7 +195,8 @@ def cpu_baseline(w, budget_s=15.0):
     import oracle
     from paper_2511_16358_gb300 import inputs as inp
     dims, R = w.dims, w.R
-    planted = oracle.reconstruct(dims, R, inp.gaussian_factors(dims, R, inp.planted_factor_seed(w)))
+    planted = (oracle.reconstruct(dims, R, inp.gaussian_factors(dims, R, inp.planted_factor_seed(w)))
+               if w.planted else None)
     xt, mask, G0 = inp.workload_inputs(w, planted)
     X = oracle.init_x(xt, mask)
     rec = oracle.reconstruct(dims, R, G0)
@@ -218,7 +221,8 @@ def run_reference(args, w):
     import oracle
     from paper_2511_16358_gb300 import inputs as inp
     dims, R = w.dims, w.R
-    planted = oracle.reconstruct(dims, R, inp.gaussian_factors(dims, R, inp.planted_factor_seed(w)))
+    planted = (oracle.reconstruct(dims, R, inp.gaussian_factors(dims, R, inp.planted_factor_seed(w)))
+               if w.planted else None)
     xt, mask, G0 = inp.workload_inputs(w, planted)
     X = oracle.init_x(xt, mask)
     rec = oracle.reconstruct(dims, R, G0)

@@ -120,6 +120,30 @@ def fiber_mask(shape, fiber_mode: int, fiber_missing: float, p_observed: float, 
     return m
 
 
+def tucker_tensor(dims, core_ranks, seed: int) -> np.ndarray:
+    """Tucker-generated tensor of the paper's synthetic experiment (Sec. 5.1).
+
+    Core C (r_1 x ... x r_N) and factor matrices U_k (I_k x r_k) have i.i.d.
+    U(0,1) entries, drawn in that order from the one stream ``seed``; the
+    tensor is C x_1 U_1 x_2 U_2 ... x_N U_N (mode-k products), divided by its
+    largest entry so that it lies in [0, 1] (the experiments pre-normalise
+    every dataset to [0, 1]).  Its multilinear rank is (r_1, ..., r_N).  This
+    is data preparation: the completion model is iFCTN, not Tucker.
+    """
+    dims = tuple(int(d) for d in dims)
+    core_ranks = tuple(int(r) for r in core_ranks)
+    ncore = int(np.prod(core_ranks))
+    u = uniform(seed, ncore + sum(d * r for d, r in zip(dims, core_ranks)))
+    T = u[:ncore].reshape(core_ranks)
+    off = ncore
+    for k, (d, r) in enumerate(zip(dims, core_ranks)):
+        U = u[off:off + d * r].reshape(d, r)
+        off += d * r
+        # mode-k product: contract mode k of T with the columns of U, keep the axis order
+        T = np.moveaxis(np.tensordot(U, T, axes=([1], [k])), 0, k)
+    return T / T.max()
+
+
 def gaussian_noise(shape, sigma: float, seed: int) -> np.ndarray:
     return sigma * normal(seed, int(np.prod(shape))).reshape(shape)
 
@@ -168,6 +192,13 @@ class Workload:
     seed_base: int
     fiber: tuple | None = None          # (mode, fraction) for fiber-missing masks
     extra: dict = field(default_factory=dict)
+    tucker: tuple | None = None         # core ranks: the truth is Tucker-generated, not planted iFCTN
+
+    @property
+    def planted(self) -> bool:
+        """True when the truth is an iFCTN tensor of Gaussian factors, which the
+        consumer computes (oracle or library) and passes to workload_inputs."""
+        return self.tucker is None
 
     @property
     def N(self):
@@ -198,12 +229,26 @@ WORKLOADS = {
                               0.2, "raw", 0.0, "fp64", 6),
 }
 
+# The paper's synthetic experiment (Sec. 5.1, Fig. 3): a 20^4 tensor of Tucker rank
+# (5,5,5,5) with U(0,1) core and factors, completed at random-missing rates up to 90%
+# with the experiments' defaults (rho = 0.1, t_max = 1000, eps = 1e-5).  The text gives
+# no iFCTN rank for it; every R_{k,l} = 5 (the Tucker rank) is the reading taken.
+TUCKER_MISSING_RATES = (0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9)
+for _m in TUCKER_MISSING_RATES:
+    _name = f"tucker20x4_rm{int(round(100 * _m)):02d}"
+    WORKLOADS[_name] = Workload(_name, (20, 20, 20, 20), rank_matrix(4, 5), 0.1, 1000,
+                                round(1.0 - _m, 10), "raw", 0.0, "fp64", 7,
+                                extra={"tol": 1e-5}, tucker=(5, 5, 5, 5))
 
-def workload_inputs(w: Workload, planted: np.ndarray):
+
+def workload_inputs(w: Workload, planted: np.ndarray | None):
     """Given the planted tensor (computed by the caller from
-    ``gaussian_factors(w.dims, w.R, 1000 + w.seed_base)``), return
-    (X_true, mask, G0) for the workload."""
+    ``gaussian_factors(w.dims, w.R, 1000 + w.seed_base)``; None for a workload
+    whose truth is Tucker-generated), return (X_true, mask, G0) for the
+    workload."""
     shape = w.dims
+    if w.tucker is not None:
+        planted = tucker_tensor(shape, w.tucker, 1000 + w.seed_base)
     noise = gaussian_noise(shape, w.sigma, 3000 + w.seed_base) if w.sigma > 0 else None
     xt = planted if w.kind == "raw" else finalize(planted, w.kind, noise)
     if w.fiber is not None:

@@ -1,5 +1,8 @@
 """Seeded test cases shared by the parity tests (inputs only; planted tensors
 and scalings come from the oracle, never from the GPU path)."""
+import contextlib
+import os
+
 import numpy as np
 
 import oracle
@@ -40,3 +43,20 @@ def make_case(dims, edge, p_obs, seed, kind="max1", sigma=0.0, fiber=None):
     X0 = oracle.init_x(xt, mask)
     G0 = scaled_uniform_start(dims, R, X0, mask, 4000 + seed)
     return dict(dims=tuple(dims), R=R, Gtrue=Gt, xt=xt, mask=mask, G0=G0, X0=X0)
+
+
+@contextlib.contextmanager
+def path(name):
+    """Forces the execution path of contexts created inside the block:
+    "persistent" (one cooperative launch per call, the default for tensors that
+    stay in L2) or "graph" (per-stage kernels with the warp-pipelined
+    contraction, the default for HBM-sized tensors)."""
+    old = os.environ.get("IFCTN_PATH")
+    os.environ["IFCTN_PATH"] = name
+    try:
+        yield
+    finally:
+        if old is None:
+            del os.environ["IFCTN_PATH"]
+        else:
+            os.environ["IFCTN_PATH"] = old

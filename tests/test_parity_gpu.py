@@ -5,8 +5,6 @@ FP64 path: every factor and the completed tensor within 1e-10 relative
 state, and after whole runs.  Mixed path (FP32 tensor and contractions, FP64
 solves): RSE within 1e-3 relative of the oracle's.
 """
-import contextlib
-import os
 
 import numpy as np
 import pytest
@@ -14,7 +12,7 @@ import pytest
 import oracle
 from paper_2511_16358_gb300 import binding as b
 from paper_2511_16358_gb300 import inputs as inp
-from tests._cases import make_case, rel_err
+from tests._cases import make_case, path, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -24,19 +22,6 @@ TOL64 = 1e-10
 # stay in L2); "graph": per-stage kernels with the warp-pipelined contraction
 # (the default for HBM-sized tensors), forced here on small shapes.
 PATHS = ["persistent", "graph"]
-
-
-@contextlib.contextmanager
-def path(name):
-    old = os.environ.get("IFCTN_PATH")
-    os.environ["IFCTN_PATH"] = name
-    try:
-        yield
-    finally:
-        if old is None:
-            del os.environ["IFCTN_PATH"]
-        else:
-            os.environ["IFCTN_PATH"] = old
 
 
 def _ctx(case, precision=b.FP64, rho=0.1, max_sweeps=10, tol=0.0):
