@@ -141,7 +141,7 @@ def tucker_tensor(dims, core_ranks, seed: int) -> np.ndarray:
         off += d * r
         # mode-k product: contract mode k of T with the columns of U, keep the axis order
         T = np.moveaxis(np.tensordot(U, T, axes=([1], [k])), 0, k)
-    return T / T.max()
+    return np.ascontiguousarray(T / T.max())
 
 
 def gaussian_noise(shape, sigma: float, seed: int) -> np.ndarray:

@@ -1,0 +1,159 @@
+"""Batched iFCTN-rank grid search on the completion server.
+
+The experiments choose the iFCTN ranks R_{k,l} per dataset from a grid and
+report the best result, and the times they report include that tuning
+(Sec. 5; the multispectral grid is R_{1,2} in {3,6,9,15,30,36},
+R_{1,3} = R_{2,3} in {3,6,9}, Sec. 5.2).  Every grid point is an independent
+completion job, so the search submits all of them to one server at once; the
+server's continuous batching keeps as many resident as slots and the device
+budget allow and overlaps their kernels.  The completions run in the
+library's kernels; this module only builds the jobs, splits the mask and
+scores the returned tensors.
+
+Scoring:
+  * with a ground truth (the experiments' protocol, synthetic data):
+    RSE = ||X_true - X|| / ||X_true|| of each completed tensor;
+  * without one: a seeded share of the observed entries is held out of every
+    job, and the score is the relative error on those held-out entries.
+The lowest score wins; ties go to the point with fewer parameters
+(sum_k I_k sum_{l != k} R_{k,l}), then to the earlier grid point.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# per-edge rank limit of the library (its stage systems are held in registers)
+MAX_EDGE_RANK = 8
+
+
+def rank_matrix(N: int, edges: dict) -> np.ndarray:
+    """4x4 symmetric rank matrix from {(k, l): R_{k,l}} over the pairs k < l."""
+    R = np.zeros((4, 4), dtype=np.int32)
+    for (k, l), r in edges.items():
+        R[k, l] = R[l, k] = int(r)
+    return R
+
+
+def msi_grid(max_rank: int = MAX_EDGE_RANK) -> list:
+    """The multispectral grid of Sec. 5.2 for an order-3 tensor, without the
+    points that need an edge rank above ``max_rank``."""
+    out = []
+    for r12 in (3, 6, 9, 15, 30, 36):
+        for r13 in (3, 6, 9):
+            if max(r12, r13) <= max_rank:
+                out.append(rank_matrix(3, {(0, 1): r12, (0, 2): r13, (1, 2): r13}))
+    return out
+
+
+def edge_grid(N: int, choices: dict) -> list:
+    """Every combination of per-edge choices {(k, l): [R, ...]}, pairs k < l;
+    edges not named take the first value of ``choices['default']``."""
+    pairs = [(k, l) for k in range(N) for l in range(k + 1, N)]
+    lists = [list(choices.get(p, choices.get("default", [1]))) for p in pairs]
+    out = []
+    for combo in np.array(np.meshgrid(*lists, indexing="ij")).reshape(len(pairs), -1).T:
+        out.append(rank_matrix(N, dict(zip(pairs, combo.tolist()))))
+    return out
+
+
+def param_count(dims, R) -> int:
+    """Number of iFCTN parameters, sum_k I_k sum_{l != k} R_{k,l} (Sec. 4.3)."""
+    N = len(dims)
+    return int(sum(int(dims[k]) * int(R[k][l]) for k in range(N) for l in range(N) if l != k))
+
+
+def holdout_split(mask, fraction: float, seed: int):
+    """Splits the observed set into (fit mask as uint8, held-out boolean mask)
+    by a seeded Bernoulli(fraction) draw per observed entry."""
+    obs = np.asarray(mask).astype(bool)
+    draw = np.random.default_rng(seed).random(obs.shape) < fraction
+    held = obs & draw
+    return (obs & ~held).astype(np.uint8), held
+
+
+@dataclass
+class SearchResult:
+    criterion: str                 # "rse" (against a ground truth) or "holdout"
+    grid: list                     # the rank matrices searched, in submission order
+    scores: list                   # one score per grid point (lower is better)
+    stats: list                    # the server's per-job stats (sweeps_done, converged, ...)
+    best_index: int
+    best_ranks: np.ndarray
+    best_x: np.ndarray             # completed tensor of the best point
+    seconds: float                 # wall time of the whole search (submit to last result)
+    params: list = field(default_factory=list)
+
+
+def search(obs, mask, grid, *, rho=0.1, max_sweeps=1000, tol=1e-5, precision=None, xtrue=None,
+           holdout=0.1, seed=0, hbm_budget_bytes=100 << 30, slots=16, backend=None) -> SearchResult:
+    """Completes ``obs`` (observed where ``mask`` is 1) once per rank matrix of
+    ``grid`` on one server and returns the best point (see module docstring).
+
+    ``backend`` defaults to the library binding; it must provide the binding's
+    server_create / submit / poll / server_destroy / make_problem /
+    tensor_dtype and its FP64 and OK constants.
+    """
+    if backend is None:
+        from paper_2511_16358_gb300 import binding as backend
+    b = backend
+    if not grid:
+        raise ValueError("empty rank grid")
+    precision = b.FP64 if precision is None else precision
+    dims = tuple(int(d) for d in np.shape(obs))
+    for R in grid:
+        N = len(dims)
+        for k in range(N):
+            for l in range(N):
+                if k != l and not 1 <= int(R[k][l]) <= MAX_EDGE_RANK:
+                    raise ValueError(f"edge rank R[{k},{l}] = {int(R[k][l])} outside 1..{MAX_EDGE_RANK}")
+    dt = b.tensor_dtype(precision)
+    obs_h = np.ascontiguousarray(obs, dtype=dt)
+    if xtrue is None:
+        if not 0.0 < holdout < 1.0:
+            raise ValueError("holdout must lie in (0, 1) when no ground truth is given")
+        fit_mask, held = holdout_split(mask, holdout, seed)
+        if not held.any():
+            raise ValueError("no observed entry was held out")
+        criterion = "holdout"
+    else:
+        fit_mask, held = np.ascontiguousarray(mask, dtype=np.uint8), None
+        criterion = "rse"
+
+    t0 = time.perf_counter()
+    srv = b.server_create(int(hbm_budget_bytes), int(slots))
+    outs, stats = [], []
+    try:
+        # every job is queued before the first result is awaited: the server
+        # batches them as slots and budget allow
+        tickets = [b.submit(srv, b.make_problem(dims, R, rho=rho, max_sweeps=max_sweeps, tol=tol,
+                                                precision=precision, seed=seed),
+                            obs_h, fit_mask, None) for R in grid]
+        for t in tickets:
+            out = np.empty(dims, dtype=dt)
+            rc, st = b.poll(srv, t, out, timeout_us=-1)
+            if rc != b.OK:
+                raise RuntimeError(f"rank-search job {t} ended with status {rc}")
+            outs.append(out)
+            stats.append(st)
+    finally:
+        b.server_destroy(srv)
+    seconds = time.perf_counter() - t0
+
+    scores = []
+    if criterion == "rse":
+        xt = np.asarray(xtrue, dtype=np.float64)
+        den = np.linalg.norm(xt)
+        for X in outs:
+            scores.append(float(np.linalg.norm(xt - X.astype(np.float64)) / den))
+    else:
+        ref = np.asarray(obs, dtype=np.float64)[held]
+        den = np.linalg.norm(ref)
+        for X in outs:
+            scores.append(float(np.linalg.norm(X.astype(np.float64)[held] - ref) / den))
+    params = [param_count(dims, R) for R in grid]
+    best = min(range(len(grid)), key=lambda i: (scores[i], params[i], i))
+    return SearchResult(criterion, list(grid), scores, stats, best, np.asarray(grid[best]), outs[best],
+                        seconds, params)
