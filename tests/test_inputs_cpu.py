@@ -74,3 +74,31 @@ def test_small_workloads_value_ranges_and_mask(name):
         assert abs(resid.std() - w.sigma) < 0.1 * w.sigma
     assert abs(mask.mean() - w.p_observed) < 0.01
     assert G0.size == inp.factor_size(w.dims, w.R) and G0.min() >= 0.0 and G0.max() < 1.0
+
+
+def test_served_stream_requests_follow_the_stream_recipe():
+    """512 requests, Poisson arrivals at 200/s, order 3 or 4 uniformly, modes
+    uniform in [32, 128], per-edge ranks uniform in [2, 6], observed fraction
+    uniform in [0.1, 0.5], 50 sweeps each."""
+    from paper_2511_16358_gb300.serve_bench import draw_requests
+    reqs = draw_requests(512, 200.0, 5000, 32, 128, 2, 6, 0.1, 0.5, 50)
+    assert len(reqs) == 512
+    t = np.array([r["t"] for r in reqs])
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert (gaps > 0).all()
+    assert abs(gaps.mean() - 1 / 200) < 0.15 / 200          # exponential: mean 1/rate
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.15       # and coefficient of variation 1
+    orders = np.array([len(r["dims"]) for r in reqs])
+    assert set(orders.tolist()) == {3, 4} and abs((orders == 4).mean() - 0.5) < 0.07
+    dims = np.concatenate([r["dims"] for r in reqs])
+    assert dims.min() == 32 and dims.max() == 128
+    ranks = []
+    for r in reqs:
+        N = len(r["dims"])
+        R = r["R"]
+        assert (R == R.T).all()
+        ranks += [int(R[k, l]) for k in range(N) for l in range(k + 1, N)]
+    assert set(ranks) == {2, 3, 4, 5, 6}
+    p = np.array([r["p"] for r in reqs])
+    assert p.min() >= 0.1 and p.max() <= 0.5 and abs(p.mean() - 0.3) < 0.02
+    assert all(r["sweeps"] == 50 for r in reqs)
