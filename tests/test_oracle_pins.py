@@ -277,6 +277,66 @@ def test_block_system_equals_dense_normal_equations(k, i, j):
     np.testing.assert_allclose(b, A.T @ x, rtol=1e-12, atol=1e-12)
 
 
+def _prop1_Z(dims, R, F, k):
+    """Z_k of Prop. 1 (P_{-k} x Q_k): rows in the little-endian order of the
+    remaining modes, columns the Kronecker order of kron_{m=N..1, m!=k} G_{m,k}^T."""
+    N = len(dims)
+    rest = [m for m in range(N) if m != k]
+    S = np.ones([dims[m] for m in rest])
+    for a_, p_ in enumerate(rest):
+        for b_, q_ in enumerate(rest):
+            if b_ <= a_:
+                continue
+            shp = [1] * len(rest)
+            shp[a_], shp[b_] = dims[p_], dims[q_]
+            S = S * (F[(p_, q_)].T @ F[(q_, p_)]).reshape(shp)
+    K = None
+    for m in range(N - 1, -1, -1):
+        if m != k:
+            K = F[(m, k)].T if K is None else np.kron(K, F[(m, k)].T)
+    return S.reshape(-1, order="F")[:, None] * K
+
+
+def _E(dims, R, F, k, i, j):
+    """E_j: the Kronecker product, in Z_k's column order, of G_{k,m}(:, j) for
+    m not in {k, i} and the identity at position i, so that Z_k E_j g is the
+    slice i_k = j of the model as a function of column j of G_{k,i}."""
+    N = len(dims)
+    E = None
+    for m in range(N - 1, -1, -1):
+        if m == k:
+            continue
+        f = np.eye(int(R[k][i])) if m == i else F[(k, m)][:, j][:, None]
+        E = f if E is None else np.kron(E, f)
+    return E
+
+
+@pytest.mark.parametrize("dims,edge", [
+    ((3, 4, 5, 2), {(0, 1): 2, (0, 2): 3, (0, 3): 2, (1, 2): 2, (1, 3): 3, (2, 3): 1}),
+    ((4, 3, 5), {(0, 1): 3, (0, 2): 2, (1, 2): 4}),
+])
+def test_regrouped_mode_systems_equal_block_systems(dims, edge):
+    """The regrouping the GPU path relies on (Prop. 1 applied to eq. (updateG)):
+    with M_k = X_(k) Z_k and K_k = Z_k^T Z_k, every block system of mode k is
+    H = E_j^T K_k E_j and b = E_j^T M_k(j,:)^T, for every i != k and every j."""
+    R, G = _problem(dims, edge, 90 + len(dims))
+    X = inp.normal(91, int(np.prod(dims))).reshape(dims)
+    F = inp.unpack_factors(G, dims, R)
+    N = len(dims)
+    for k in range(N):
+        Z = _prop1_Z(dims, R, F, k)
+        M = _unfold_littleendian(X, k) @ Z
+        K = Z.T @ Z
+        for i in range(N):
+            if i == k:
+                continue
+            for j in range(dims[k]):
+                E = _E(dims, R, F, k, i, j)
+                H, b = oracle.block_system(dims, R, G, X, k, i, j)
+                np.testing.assert_allclose(E.T @ K @ E, H, rtol=1e-12, atol=1e-12)
+                np.testing.assert_allclose(E.T @ M[j], b, rtol=1e-12, atol=1e-12)
+
+
 def _numpy_sweep(dims, R, rho, G, X, mask):
     """Algorithm 1, one sweep, from explicit dense systems (tiny sizes only)."""
     N = len(dims)
