@@ -122,38 +122,41 @@ def search(obs, mask, grid, *, rho=0.1, max_sweeps=1000, tol=1e-5, precision=Non
         fit_mask, held = np.ascontiguousarray(mask, dtype=np.uint8), None
         criterion = "rse"
 
+    if criterion == "rse":
+        xt = np.asarray(xtrue, dtype=np.float64)
+        den = np.linalg.norm(xt)
+
+        def score(X):
+            return float(np.linalg.norm(xt - X.astype(np.float64)) / den)
+    else:
+        ref = np.asarray(obs, dtype=np.float64)[held]
+        den = np.linalg.norm(ref)
+
+        def score(X):
+            return float(np.linalg.norm(X.astype(np.float64)[held] - ref) / den)
+
+    params = [param_count(dims, R) for R in grid]
     t0 = time.perf_counter()
     srv = b.server_create(int(hbm_budget_bytes), int(slots))
-    outs, stats = [], []
+    scores, stats, best, best_x = [], [], None, None
     try:
         # every job is queued before the first result is awaited: the server
         # batches them as slots and budget allow
         tickets = [b.submit(srv, b.make_problem(dims, R, rho=rho, max_sweeps=max_sweeps, tol=tol,
                                                 precision=precision, seed=seed),
                             obs_h, fit_mask, None) for R in grid]
-        for t in tickets:
+        for n, t in enumerate(tickets):
             out = np.empty(dims, dtype=dt)
             rc, st = b.poll(srv, t, out, timeout_us=-1)
             if rc != b.OK:
                 raise RuntimeError(f"rank-search job {t} ended with status {rc}")
-            outs.append(out)
             stats.append(st)
+            scores.append(score(out))
+            # only the best completed tensor so far is kept
+            if best is None or (scores[n], params[n]) < (scores[best], params[best]):
+                best, best_x = n, out
     finally:
         b.server_destroy(srv)
     seconds = time.perf_counter() - t0
-
-    scores = []
-    if criterion == "rse":
-        xt = np.asarray(xtrue, dtype=np.float64)
-        den = np.linalg.norm(xt)
-        for X in outs:
-            scores.append(float(np.linalg.norm(xt - X.astype(np.float64)) / den))
-    else:
-        ref = np.asarray(obs, dtype=np.float64)[held]
-        den = np.linalg.norm(ref)
-        for X in outs:
-            scores.append(float(np.linalg.norm(X.astype(np.float64)[held] - ref) / den))
-    params = [param_count(dims, R) for R in grid]
-    best = min(range(len(grid)), key=lambda i: (scores[i], params[i], i))
-    return SearchResult(criterion, list(grid), scores, stats, best, np.asarray(grid[best]), outs[best],
+    return SearchResult(criterion, list(grid), scores, stats, best, np.asarray(grid[best]), best_x,
                         seconds, params)
