@@ -156,6 +156,95 @@ def test_three_way_remark_formula():
     np.testing.assert_allclose(oracle.reconstruct(dims, R, G), ref, rtol=1e-13, atol=1e-14)
 
 
+def _cherry_tensor(mats, k, Ik):
+    """Def. 1 written out entry by entry: a mode-k cherry tensor with cherry
+    factors mats[i] (P_i x I_k, i != k) has entry prod_{i != k} mats[i](p_i, i_k)."""
+    N = len(mats)
+    shape = [Ik if i == k else mats[i].shape[0] for i in range(N)]
+    T = np.zeros(shape)
+    for idx in itertools.product(*[range(d) for d in shape]):
+        T[idx] = np.prod([mats[i][idx[i], idx[k]] for i in range(N) if i != k])
+    return T
+
+
+def _cherry_product(A, k, B, t, alpha, beta):
+    """Def. 3 entry by entry (brute force): A = CT_k({A_i}), B = CT_t({B_j});
+    the result has the modes of A without alpha, then those of B without beta,
+    and entry prod_{i != k, alpha} A_i(., i_k) * prod_{j != t, beta} B_j(., j_t)
+    * (A_alpha^T B_beta)(i_k, j_t)."""
+    N, M = len(A), len(B)
+    Ik = next(A[i].shape[1] for i in range(N) if i != k)
+    Jt = next(B[j].shape[1] for j in range(M) if j != t)
+    nA = [i for i in range(N) if i != alpha]
+    mB = [j for j in range(M) if j != beta]
+    dimA = [Ik if i == k else A[i].shape[0] for i in nA]
+    dimB = [Jt if j == t else B[j].shape[0] for j in mB]
+    AB = A[alpha].T @ B[beta]
+    C = np.zeros(dimA + dimB)
+    for ia in itertools.product(*[range(d) for d in dimA]):
+        a = dict(zip(nA, ia))
+        for jb in itertools.product(*[range(d) for d in dimB]):
+            b = dict(zip(mB, jb))
+            v = AB[a[k], b[t]]
+            for i in nA:
+                if i != k:
+                    v *= A[i][a[i], a[k]]
+            for j in mB:
+                if j != t:
+                    v *= B[j][b[j], b[t]]
+            C[ia + jb] = v
+    return C
+
+
+def test_cherry_product_is_the_contraction_of_the_shared_mode():
+    """Def. 3: the cherry product equals summing the product of the two cherry
+    tensors over the connected mode (alpha of A, beta of B)."""
+    rng = np.random.default_rng(5)
+    Ik, Jt = 3, 4
+    A = [rng.standard_normal((2, Ik)), None, rng.standard_normal((3, Ik)), rng.standard_normal((2, Ik))]
+    B = [rng.standard_normal((3, Jt)), rng.standard_normal((2, Jt)), None]
+    k, t, alpha, beta = 1, 2, 2, 0
+    TA = _cherry_tensor(A, k, Ik)
+    TB = _cherry_tensor(B, t, Jt)
+    ref = np.tensordot(TA, TB, axes=([alpha], [beta]))
+    np.testing.assert_allclose(_cherry_product(A, k, B, t, alpha, beta), ref, rtol=1e-13, atol=1e-14)
+
+
+def test_cherry_product_remark_forms():
+    """The N = M = 3 remark after Def. 3: a mode-2 cherry tensor (P x I x R) and a
+    mode-3 cherry tensor (Q x R x J) give C(p,i,q,j) = A_1(p,i) B_1(q,j) (A_3^T B_2)_{ij};
+    matricised, C = diag(vec(A_3^T B_2)) (B_1 kron A_1)^T with rows (i,j), i fastest,
+    and columns (p,q), p fastest (the printed column size R_1 R_3 is read as P Q)."""
+    rng = np.random.default_rng(6)
+    P, I, R, Q, J = 2, 3, 4, 3, 2
+    A1, A3 = rng.standard_normal((P, I)), rng.standard_normal((R, I))
+    B1, B2 = rng.standard_normal((Q, J)), rng.standard_normal((R, J))
+    C = _cherry_product([A1, None, A3], 1, [B1, B2, None], 2, 2, 1)
+    assert C.shape == (P, I, Q, J)
+    np.testing.assert_allclose(C, np.einsum("pi,qj,ij->piqj", A1, B1, A3.T @ B2), rtol=1e-13, atol=1e-14)
+    Cmat = np.diag((A3.T @ B2).reshape(-1, order="F")) @ np.kron(B1, A1).T
+    ref = np.transpose(C, (1, 3, 0, 2)).reshape(I * J, P * Q, order="F")
+    np.testing.assert_allclose(Cmat, ref, rtol=1e-13, atol=1e-14)
+
+
+def test_cherry_products_pack_the_subnetwork_and_rebuild_the_tensor():
+    """Packing by cherry products (Sec. 3): G_1 * G_2 over r_{1,2} is the
+    sub-network of the remaining cherries (its unfolding is Z_3 of Prop. 1),
+    and contracting it with G_3 over r_{1,3}, r_{2,3} gives iFCTN(G)."""
+    dims = (3, 4, 2)
+    R, G = _problem(dims, {(0, 1): 2, (0, 2): 3, (1, 2): 2}, 81)
+    F = inp.unpack_factors(G, dims, R)
+    c = [[F[(k, m)] if m != k else None for m in range(3)] for k in range(3)]
+    C12 = _cherry_product(c[0], 0, c[1], 1, 1, 0)            # modes (i1, r13, i2, r23)
+    assert C12.shape == (dims[0], R[0, 2], dims[1], R[1, 2])
+    T3 = _cherry_tensor(c[2], 2, dims[2])                      # modes (r13, r23, i3)
+    X = np.einsum("asbt,sti->abi", C12, T3)
+    np.testing.assert_allclose(X, oracle.reconstruct(dims, R, G), rtol=1e-12, atol=1e-13)
+    # rows (i1, i2) with i1 fastest, columns (r13, r23) with r23 slowest: Z_3
+    Z3 = np.transpose(C12, (0, 2, 1, 3)).reshape(dims[0] * dims[1], -1, order="F")
+    np.testing.assert_allclose(Z3, _prop1_Z(dims, R, F, 2), rtol=1e-12, atol=1e-13)
+
+
 @pytest.mark.parametrize("k", [0, 1, 2, 3])
 def test_prop1_subnetwork_unfolding(k):
     """Prop. 1: (X_(k))^T = Z_k (G_(k))^T, Z_k = diag(vec S_k) (kron_{i=N..1, i!=k} G_{i,k}^T),
