@@ -294,6 +294,32 @@ def test_prop3_transposition_invariance():
                                    rtol=1e-13, atol=1e-14)
 
 
+def test_reconstruction_invariant_under_edge_gauge():
+    """Each rank index r_{k,l} appears only in G_{k,l} and G_{l,k} (eq. (iFCTN)), so
+    G_{k,l} -> A G_{k,l}, G_{l,k} -> A^{-T} G_{l,k} with any invertible A leaves the
+    tensor unchanged; the permutation-and-scaling ambiguity of Prop. 2 is the
+    special case A = Pi Lambda.  A mispaired or transposed factor breaks it."""
+    dims = (3, 4, 2, 3)
+    edge = {(0, 1): 2, (0, 2): 3, (0, 3): 2, (1, 2): 3, (1, 3): 1, (2, 3): 2}
+    R, G = _problem(dims, edge, 64)
+    X = oracle.reconstruct(dims, R, G)
+    rng = np.random.default_rng(65)
+    G2 = G.copy()
+    F2 = inp.unpack_factors(G2, dims, R)
+    for (k, l), r in edge.items():
+        A = rng.standard_normal((r, r)) + 2.0 * np.eye(r)
+        F2[(k, l)][:, :] = A @ F2[(k, l)]
+        F2[(l, k)][:, :] = np.linalg.inv(A).T @ F2[(l, k)]
+    assert np.max(np.abs(G2 - G)) > 1e-2
+    np.testing.assert_allclose(oracle.reconstruct(dims, R, G2), X, rtol=1e-11, atol=1e-12 * np.abs(X).max())
+    # the same (not the inverse) scaling on both ends of an edge scales the tensor
+    G3 = G.copy()
+    F3 = inp.unpack_factors(G3, dims, R)
+    F3[(0, 2)][:, :] = 2.0 * F3[(0, 2)]
+    F3[(2, 0)][:, :] = 2.0 * F3[(2, 0)]
+    assert np.max(np.abs(oracle.reconstruct(dims, R, G3) - X)) > 1e-3 * np.abs(X).max()
+
+
 def test_rank_one_is_cp_outer_product():
     dims = (3, 4, 5, 2)
     R, G = _problem(dims, 1, 61)
