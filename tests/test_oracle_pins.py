@@ -587,6 +587,38 @@ def test_perturbed_planted_start_converges_monotonically():
     assert obj[-1] < 1e-3 * obj[0]
 
 
+def test_theorem1_limit_is_a_critical_point():
+    """Theorem 1 (with Lemmas 2 and 3): the bounded PAM sequence has finite
+    length and converges to a critical point of F(G, X) = 1/2 ||X - iFCTN(G)||^2
+    over X with P_Omega(X) = P_Omega(O).  On a noisy problem whose observed
+    entries the model cannot fit (F > 0 at the limit), run to a tight
+    tolerance: the partial gradient of F in every factor column,
+    A_j^T (A_j g - x_j), vanishes, X equals the reconstruction off Omega, and
+    the steps ||X^{s+1} - X^s|| have a vanishing tail sum."""
+    from tests._cases import make_case
+    case = make_case((6, 5, 4), 2, 0.8, seed=111, kind="minmax01", sigma=0.05)
+    dims, R, mask = case["dims"], case["R"], case["mask"]
+    G, X = case["G0"].copy(), case["X0"].copy()
+    log = oracle.complete(dims, R, 0.1, G, X, mask, max_sweeps=20000, tol=1e-12)
+    assert len(log) < 20000 and log[-1]["rel_change"] < 1e-12
+    assert log[-1]["objective"] > 1e-3                      # not an exact fit: a non-trivial critical point
+    rec = oracle.reconstruct(dims, R, G)
+    off = ~mask.astype(bool)
+    assert np.linalg.norm((X - rec)[off]) < 1e-10 * np.linalg.norm(X)
+    assert (X[~off] == case["X0"][~off]).all()
+    F = inp.unpack_factors(G, dims, R)
+    for k in range(3):
+        for i in range(3):
+            if i == k:
+                continue
+            for j in range(dims[k]):
+                H, b = oracle.block_system(dims, R, G, X, k, i, j)
+                g = F[(k, i)][:, j]
+                assert np.linalg.norm(H @ g - b) <= 1e-9 * np.linalg.norm(b)
+    steps = np.sqrt([s["dx2"] for s in log])
+    assert steps[len(steps) // 2:].sum() < 1e-3 * steps.sum()
+
+
 def test_observed_entries_unchanged_and_update_closed_form():
     dims = (5, 4, 6)
     R, G = _problem(dims, 2, 141)
