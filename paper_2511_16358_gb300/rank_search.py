@@ -10,6 +10,11 @@ budget allow and overlaps their kernels.  The completions run in the
 library's kernels; this module only builds the jobs, splits the mask and
 scores the returned tensors.
 
+Command line (one GPU): ``python -m paper_2511_16358_gb300.rank_search
+--workload msi256x256x31_r6`` searches the multispectral grid on that
+workload and prints one JSON line (scores, best ranks, wall time of the whole
+search).
+
 Scoring:
   * with a ground truth (the experiments' protocol, synthetic data):
     RSE = ||X_true - X|| / ||X_true|| of each completed tensor;
@@ -20,6 +25,8 @@ The lowest score wins; ties go to the point with fewer parameters
 """
 from __future__ import annotations
 
+import argparse
+import json
 import time
 from dataclasses import dataclass, field
 
@@ -160,3 +167,59 @@ def search(obs, mask, grid, *, rho=0.1, max_sweeps=1000, tol=1e-5, precision=Non
     seconds = time.perf_counter() - t0
     return SearchResult(criterion, list(grid), scores, stats, best, np.asarray(grid[best]), best_x,
                         seconds, params)
+
+
+def _planted(b, inp, w):
+    """The workload's truth: iFCTN of its Gaussian factors, reconstructed by
+    the library (None for a Tucker-generated truth, which inputs builds)."""
+    if not w.planted:
+        return None
+    dims = w.dims
+    Gt = inp.gaussian_factors(dims, w.R, inp.planted_factor_seed(w))
+    P = int(np.prod(dims))
+    ctx = b.create(b.make_problem(dims, w.R, rho=w.rho, max_sweeps=0, tol=0.0, precision=b.FP64),
+                   np.zeros(P), np.zeros(P, dtype=np.uint8), Gt)
+    try:
+        return b.reconstruct(ctx, np.empty(dims, dtype=np.float64))
+    finally:
+        b.destroy(ctx)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description="batched iFCTN-rank grid search on one GPU")
+    ap.add_argument("--workload", default="msi256x256x31_r6")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--sweeps", type=int, default=None, help="t_max per job (default: the workload's)")
+    ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--criterion", default="rse", choices=["rse", "holdout"])
+    ap.add_argument("--slots", type=int, default=16)
+    args = ap.parse_args(argv)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from . import binding as b
+    from . import inputs as inp
+
+    w = inp.WORKLOADS[args.workload]
+    N = len(w.dims)
+    xt, mask, _ = inp.workload_inputs(w, _planted(b, inp, w))
+    grid = msi_grid() if N == 3 else [rank_matrix(N, {(k, l): r for k in range(N) for l in range(k + 1, N)})
+                                      for r in (3, 5, 8)]
+    prec = b.MIXED if args.precision == "mixed" else b.FP64
+    res = search(xt * mask, mask, grid, rho=w.rho, max_sweeps=args.sweeps or w.sweeps, tol=args.tol,
+                 precision=prec, xtrue=xt if args.criterion == "rse" else None, slots=args.slots)
+
+    def edges(R):
+        return {f"R{k + 1}{l + 1}": int(R[k][l]) for k in range(N) for l in range(k + 1, N)}
+
+    print(json.dumps({
+        "workload": w.name, "criterion": res.criterion, "precision": args.precision,
+        "points": [dict(edges(R), score=sc, sweeps=st.get("sweeps_done"), params=pc)
+                   for R, sc, st, pc in zip(res.grid, res.scores, res.stats, res.params)],
+        "best": dict(edges(res.best_ranks), score=res.scores[res.best_index]),
+        "seconds_including_tuning": res.seconds}), flush=True)
+
+
+if __name__ == "__main__":
+    main()
+
