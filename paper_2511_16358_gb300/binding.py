@@ -122,10 +122,12 @@ def ptr(a):
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        assert a.flags.c_contiguous
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays passed to the library must be C-contiguous (np.ascontiguousarray)")
         return a.ctypes.data
     if hasattr(a, "data_ptr"):
-        assert a.is_contiguous()
+        if not a.is_contiguous():
+            raise ValueError("tensors passed to the library must be contiguous (.contiguous())")
         return a.data_ptr()
     raise TypeError(type(a))
 

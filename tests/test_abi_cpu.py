@@ -102,3 +102,21 @@ def test_oracle_and_cuda_path_share_no_code():
     assert "#include \"" not in osrc  # only system headers
     opy = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
     assert "paper_2511_16358_gb300" not in opy
+
+
+def test_binding_refuses_non_contiguous_buffers():
+    """The library takes plain pointers with C-order layouts: a strided view
+    would be read as the wrong elements, so the binding refuses it."""
+    import torch
+
+    from paper_2511_16358_gb300 import binding as b
+    a = np.zeros((4, 6))
+    assert b.ptr(a) == a.ctypes.data and b.ptr(None) is None
+    with pytest.raises(ValueError):
+        b.ptr(a[:, ::2])
+    with pytest.raises(ValueError):
+        b.ptr(np.zeros((4, 6)).T)
+    with pytest.raises(ValueError):
+        b.ptr(torch.zeros(4, 6).t())
+    with pytest.raises(TypeError):
+        b.ptr([1.0, 2.0])
