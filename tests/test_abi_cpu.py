@@ -64,6 +64,9 @@ def _prob(**kw):
     dict(ranks=np.array([[0, 2, 3], [2, 0, 2], [2, 2, 0]])),  # not symmetric
     dict(rho=0.0),
     dict(rho=-1.0),
+    dict(rho=float("nan")),
+    dict(rho=float("inf")),
+    dict(tol=-1.0),
     dict(max_sweeps=-1),
     dict(dims=(4,)),
     dict(dims=(4, 0, 3)),
@@ -88,6 +91,27 @@ def test_null_context_and_server_arguments(lib):
     assert lib.ifctn_kernels_per_sweep(None) == 0
     lib.ifctn_destroy(None)
     lib.ifctn_server_destroy(None)
+
+
+def test_server_and_noalloc_arguments_rejected_before_gpu_work(lib):
+    import ctypes
+
+    from paper_2511_16358_gb300 import binding as b
+    srv = ctypes.c_void_p()
+    assert lib.ifctn_server_create(0, 4, ctypes.byref(srv)) == b.EINVAL
+    assert lib.ifctn_server_create(1 << 30, 0, ctypes.byref(srv)) == b.EINVAL
+    assert lib.ifctn_submit(None, None, None, None, None, None) == b.EINVAL
+    assert lib.ifctn_reconstruct_noalloc(3, None, None, 0, None, None, None) == b.EINVAL
+    R2 = np.array([[0, 2], [2, 0]])
+    host = np.zeros(8)
+    # pair matrices of 2048 x 2048 FP64 entries exceed the fixed scratch array: refused
+    # from the sizes alone, before the buffers are looked at
+    with pytest.raises(b.IfctnError) as ei:
+        b.reconstruct_noalloc((2048, 2048), R2, b.FP64, host, host)
+    assert ei.value.status == b.EINVAL and "scratch" in b.last_error()
+    with pytest.raises(b.IfctnError) as ei:
+        b.reconstruct_noalloc((4, 5), np.array([[0, 9], [9, 0]]), b.FP64, host, host)
+    assert ei.value.status == b.EINVAL
 
 
 def test_oracle_and_cuda_path_share_no_code():
