@@ -122,6 +122,12 @@ def test_oracle_and_cuda_path_share_no_code():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
                 assert "ifctn_oracle" not in src and "ifo_" not in src, f
+    # and the oracle uses nothing of the package or the CUDA library
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            src = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "paper_2511_16358_gb300" not in src and "libifctn.so" not in src, f
+            assert not re.search(r"#include\s*[<\"]cuda|^\s*(import|from)\s+(torch|cupy)\b", src, re.M), f
     osrc = open(os.path.join(ROOT, "oracle", "ifctn_oracle.c")).read()
     assert "#include \"" not in osrc  # only system headers
     opy = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
