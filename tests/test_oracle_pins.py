@@ -647,3 +647,42 @@ def test_thread_count_does_not_change_results():
         outs.append((Gw, Xw))
     np.testing.assert_array_equal(outs[0][0], outs[1][0])
     np.testing.assert_array_equal(outs[0][1], outs[1][1])
+
+
+# ---------------------------------------------------------------------------
+# the objective of Sec. 4.1, eq. (iFCTN-TC): F = 1/2 ||X - iFCTN(G)||_F^2
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,edge,seed", [
+    ((5, 4, 6), {(0, 1): 2, (0, 2): 3, (1, 2): 2}, 131),
+    ((3, 4, 2, 3), {(0, 1): 2, (0, 2): 1, (0, 3): 2, (1, 2): 3, (1, 3): 2, (2, 3): 1}, 132),
+])
+def test_objective_is_half_squared_misfit_of_the_fctn_contraction(dims, edge, seed):
+    """The objective of eq. (iFCTN-TC) written out independently of the oracle:
+    the reconstruction is the eq. (FCTN) contraction of the Def. 1 cherry
+    cores, the misfit is taken against the tensor after the X block of the
+    sweep (X^{s+1}) and the factors after it (G^{s+1}), and the weight is 1/2.
+    A dropped 1/2, a misfit against X^s or against the factors before the
+    sweep each moves the value by far more than the tolerance."""
+    N = len(dims)
+    R, Gt = _problem(dims, edge, seed)
+    xt = oracle.reconstruct(dims, R, Gt) + 0.05 * inp.normal(seed + 1, int(np.prod(dims))).reshape(dims)
+    mask = inp.uniform_mask(dims, 0.5, seed + 2)
+    G = inp.uniform_factors(dims, R, seed + 3)
+    X = oracle.init_x(xt, mask)
+
+    def f_ref(Gv, Xv):
+        F = inp.unpack_factors(Gv, dims, R)
+        rec = _fctn_contract(dims, [_cherry_core(dims, R, F, m) for m in range(N)])
+        return 0.5 * float(np.sum((Xv - rec) ** 2))
+
+    assert oracle.objective(dims, R, G, X) == pytest.approx(f_ref(G, X), rel=1e-12)
+    for _ in range(2):
+        Gs, Xs = G.copy(), X.copy()
+        st = oracle.sweep(dims, R, 0.1, G, X, mask)
+        want = f_ref(G, X)
+        assert st["objective"] == pytest.approx(want, rel=1e-12)
+        assert oracle.objective(dims, R, G, X) == pytest.approx(want, rel=1e-12)
+        # the pin separates the readings it rules out
+        assert abs(f_ref(G, Xs) - want) > 1e-6 * want
+        assert abs(f_ref(Gs, X) - want) > 1e-6 * want
