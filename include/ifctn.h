@@ -50,9 +50,13 @@ typedef enum {
 
 typedef enum {
     IFCTN_FP64 = 0,   /* tensor, contractions, solves, reductions all FP64 */
-    IFCTN_MIXED = 1   /* FP32 tensor and contractions (FP32 accumulate);
-                         FP64 factor master copy, normal-equation right-hand
-                         sides, Cholesky solves and cross-block reductions */
+    IFCTN_MIXED = 1   /* FP32 tensor, contractions and Gram (FP32 accumulate);
+                         FP64 factor master copy, M_k reduction, stop-test,
+                         objective and RSE sums.  The small proximal systems
+                         are factorised in FP32 (LDL^T) and refined once with
+                         a residual formed in two-float arithmetic (about 48
+                         significant bits from FP32 instructions): no FP64
+                         instruction runs in a solve stage. */
 } ifctn_precision;
 
 /* Algorithm 1's inputs (Sec. 4.2): order N, sizes, iFCTN ranks, proximal
@@ -147,6 +151,19 @@ ifctn_status ifctn_mode_system(ifctn_ctx* ctx, int32_t k, double* Mk, double* Kk
    k is ignored by stage 3. */
 ifctn_status ifctn_launch_stage(ifctn_ctx* ctx, int32_t stage, int32_t k);
 
+/* Diagnostic of the failure path (no counterpart in the paper; it checks this
+   library's error handling).  Every device wait of the library's kernels is
+   bounded: on expiry the kernel records a timeout in the context's flag word
+   and returns, and the call reports IFCTN_ETIMEOUT.  This runs, on the
+   context's stream, one grid barrier that a CTA never joins and one mbarrier
+   phase that no copy completes, each with a budget of budget_cycles SM clock
+   cycles (1000..4e9), and returns what a real expiry returns: IFCTN_ETIMEOUT.
+   The flag word is cleared after it is reported (by this call and by every
+   other call that reports a device failure), so the context stays usable;
+   this call does not touch the problem's state (G, X).  IFCTN_EINVAL for a
+   budget out of range. */
+ifctn_status ifctn_wait_selftest(ifctn_ctx* ctx, int64_t budget_cycles);
+
 /* Number of kernel launches one sweep issues when sweeps run as a CUDA graph
    of per-stage kernels (for launch accounting). */
 int32_t ifctn_kernels_per_sweep(const ifctn_ctx* ctx);
@@ -212,14 +229,20 @@ ifctn_status ifctn_submit(ifctn_server* srv, const ifctn_problem* prob, const vo
 ifctn_status ifctn_poll(ifctn_server* srv, uint64_t ticket, void* out_X, ifctn_stats* out,
                         int64_t timeout_us);
 
-/* Server counters: jobs queued, resident, done; device bytes in use;
-   latency (submit to completion, seconds) of the i-th completed job. */
+/* Server counters: jobs queued, resident and completed; device bytes in use;
+   the largest number of jobs resident at once. */
 typedef struct {
     int64_t queued, resident, completed;
     int64_t bytes_in_use;
     int64_t peak_resident;
 } ifctn_server_info;
 ifctn_status ifctn_server_info_get(ifctn_server* srv, ifctn_server_info* out);
+
+/* Latency of the job with this ticket, in seconds from its ifctn_submit to the
+   end of its last sweep on the device (the result copied to pinned host
+   memory).  IFCTN_ENOTFOUND while the job has not finished, or for a ticket
+   the server never issued.  Still readable after ifctn_poll has released the
+   ticket. */
 ifctn_status ifctn_server_latency(ifctn_server* srv, uint64_t ticket, double* seconds);
 
 void ifctn_server_destroy(ifctn_server* srv);

@@ -29,7 +29,7 @@ EXPORTED = [
     "ifctn_mode_system", "ifctn_kernels_per_sweep", "ifctn_destroy", "ifctn_server_create",
     "ifctn_submit", "ifctn_poll", "ifctn_server_info_get", "ifctn_server_latency",
     "ifctn_server_destroy", "ifctn_last_error", "ifctn_sweep_async", "ifctn_launch_stage",
-    "ifctn_launch_count", "ifctn_phase_times", "ifctn_reconstruct_noalloc",
+    "ifctn_launch_count", "ifctn_phase_times", "ifctn_reconstruct_noalloc", "ifctn_wait_selftest",
 ]
 
 
@@ -99,6 +99,7 @@ def load(path: str | None = None):
         "ifctn_launch_count": (i64, [vp]),
         "ifctn_phase_times": (i32, [vp, P(dp), i32, P(i32)]),
         "ifctn_reconstruct_noalloc": (i32, [i32, P(i64), P(i32), i32, vp, vp, vp]),
+        "ifctn_wait_selftest": (i32, [vp, i64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -223,6 +224,12 @@ def mode_system(ctx, k, Mk, Kk):
     return Mk, Kk
 
 
+def wait_selftest(ctx, budget_cycles):
+    """Runs the library's bounded device waits on conditions nothing satisfies;
+    returns the status (IFCTN_ETIMEOUT when the waits expired as designed)."""
+    return int(load().ifctn_wait_selftest(ctx, int(budget_cycles)))
+
+
 def kernels_per_sweep(ctx) -> int:
     return int(load().ifctn_kernels_per_sweep(ctx))
 
@@ -238,12 +245,44 @@ def phase_times(ctx) -> list:
     return [arr[i] for i in range(n.value)]
 
 
+def _noalloc_check(name, t, dtype_name, numel):
+    """The C entry point receives no buffer lengths, so the binding checks
+    every buffer it passes: a torch tensor of the right dtype and size,
+    contiguous, in CUDA memory of the current device (a short or mistyped
+    buffer would be read or written past its end on the GPU)."""
+    if not hasattr(t, "data_ptr"):
+        raise ValueError(f"{name} must be a CUDA torch tensor, got {type(t).__name__}")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise ValueError(f"{name} must be {dtype_name}, got {t.dtype}")
+    if t.numel() != numel:
+        raise ValueError(f"{name} must hold {numel} elements, got {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _noalloc_device_check(name, t):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be in CUDA memory of the current device")
+    import torch
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+
+
 def reconstruct_noalloc(dims, ranks, precision, factors_dev, out_dev, stream=None):
-    """Allocation-free reconstruction: factors_dev / out_dev are device buffers
-    (e.g. CUDA torch tensors); nothing is allocated by the library."""
+    """Allocation-free reconstruction: factors_dev / out_dev are CUDA tensors
+    of the current device (factors FP64, out in the precision's tensor dtype);
+    nothing is allocated by the library."""
+    R = np.asarray(ranks)
+    N = len(dims)
+    nfac = sum(int(R[k, l]) * int(dims[k]) for k in range(N) for l in range(N) if l != k)
+    _noalloc_check("factors_dev", factors_dev, "float64", nfac)
+    _noalloc_check("out_dev", out_dev, "float64" if precision == FP64 else "float32",
+                   int(np.prod([int(x) for x in dims])))
+    _noalloc_device_check("factors_dev", factors_dev)
+    _noalloc_device_check("out_dev", out_dev)
     d = (ctypes.c_int64 * 4)(*([int(x) for x in dims] + [0] * (4 - len(dims))))
     r = (ctypes.c_int32 * 16)()
-    R = np.asarray(ranks)
     for k in range(R.shape[0]):
         for l in range(R.shape[1]):
             r[k * 4 + l] = int(R[k, l])

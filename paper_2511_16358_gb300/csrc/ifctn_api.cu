@@ -6,6 +6,7 @@
 // Gram chain of mode k runs on a side branch of the graph, concurrently with
 // the HBM-streaming contraction of the same mode.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -73,14 +74,23 @@ ifctn_status build_shape(const ifctn_problem* p, Shape& s) {
         set_error("order must be 2..4");
         return IFCTN_EINVAL;
     }
+    // Every size the kernels index with 32-bit integers (I_k, the slab count,
+    // the packed factor and pair-matrix arrays) must stay below 2^31, and the
+    // entry count below 2^40 (far beyond device memory), so that no product
+    // below overflows.
+    constexpr long long MAX_ENTRIES = 1LL << 40;
     s.P = 1;
     for (int k = 0; k < s.N; ++k) {
         if (p->dims[k] < 1 || p->dims[k] > (1 << 30)) {
-            set_error("dims must be >= 1");
+            set_error("dims must be in 1..2^30");
             return IFCTN_EINVAL;
         }
         s.I[k] = static_cast<int>(p->dims[k]);
         s.P *= p->dims[k];
+        if (s.P > MAX_ENTRIES) {
+            set_error("tensor has more than 2^40 entries");
+            return IFCTN_EINVAL;
+        }
     }
     for (int k = 0; k < s.N; ++k)
         for (int l = 0; l < s.N; ++l) {
@@ -110,6 +120,10 @@ ifctn_status build_shape(const ifctn_problem* p, Shape& s) {
             if (k == l) continue;
             s.goff[k][l] = static_cast<int>(off);
             off += static_cast<long long>(s.R[k][l]) * s.I[k];
+            if (off > INT_MAX) {
+                set_error("packed factor array has 2^31 or more entries");
+                return IFCTN_EINVAL;
+            }
         }
     s.gsize = static_cast<int>(off);
     off = 0;
@@ -117,16 +131,21 @@ ifctn_status build_shape(const ifctn_problem* p, Shape& s) {
         for (int q = p2 + 1; q < s.N; ++q) {
             s.woff[p2][q] = static_cast<int>(off);
             off += static_cast<long long>(s.I[p2]) * s.I[q];
+            if (off > INT_MAX) {
+                set_error("pair matrices have 2^31 or more entries");
+                return IFCTN_EINVAL;
+            }
         }
-    if (off > (1LL << 31)) {
-        set_error("pair matrices too large");
-        return IFCTN_EINVAL;
-    }
     s.wsize = static_cast<int>(off);
     s.IA = s.I[s.N - 2];
     s.IB = s.I[s.N - 1];
-    s.nF = 1;
-    for (int m = 0; m < s.N - 2; ++m) s.nF *= s.I[m];
+    long long nf = 1;
+    for (int m = 0; m < s.N - 2; ++m) nf *= s.I[m];
+    if (nf > INT_MAX) {
+        set_error("more than 2^31 - 1 slabs (product of all but the last two sizes)");
+        return IFCTN_EINVAL;
+    }
+    s.nF = static_cast<int>(nf);
     return IFCTN_OK;
 }
 
@@ -775,6 +794,7 @@ struct ifctn_ctx {
     virtual size_t device_bytes() const = 0;
     virtual ifctn_status enqueue(int n, double tol, bool reset) = 0;
     virtual ifctn_status launch_stage(int stage, int k) = 0;
+    virtual ifctn_status wait_selftest(long long budget) = 0;
     virtual long long launch_total() const = 0;
     virtual ifctn_status phase_times(double* out, int max, int* n) = 0;
     virtual void set_grid_cap(int g) = 0;
@@ -1229,10 +1249,17 @@ struct Engine : ifctn_ctx {
         return IFCTN_OK;
     }
 
+    // Reports a failure recorded by a kernel once: the flag word is cleared
+    // when it is read, so the context can be used again (its state is that of
+    // the interrupted call; set_factors / set_x restore a checkpoint).
     ifctn_status check_flags() {
         int f[3];
         CK(cudaMemcpyAsync(f, ints.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        if (f[2] & (FLAG_TIMEOUT | FLAG_NOTSPD)) {
+            CK(cudaMemsetAsync(flags(), 0, sizeof(int), st));
+            CK(cudaStreamSynchronize(st));
+        }
         if (f[2] & FLAG_TIMEOUT) {
             set_error("a bounded device wait expired");
             return IFCTN_ETIMEOUT;
@@ -1354,6 +1381,13 @@ struct Engine : ifctn_ctx {
             default: set_error("unknown stage"); return IFCTN_EINVAL;
         }
         return IFCTN_OK;
+    }
+
+    ifctn_status wait_selftest(long long budget) override {
+        CK(cudaMemsetAsync(bar.p, 0, sizeof(unsigned), st));
+        CK(launch_wait_selftest(flags(), bar.p, budget, st));
+        CK(cudaStreamSynchronize(st));
+        return check_flags();
     }
 
     ifctn_status complete(void* out_X, ifctn_stats* out) override {
@@ -1554,6 +1588,13 @@ ifctn_status ifctn_sweep_async(ifctn_ctx* ctx, int32_t n) {
 }
 ifctn_status ifctn_launch_stage(ifctn_ctx* ctx, int32_t stage, int32_t k) {
     IFCTN_CTX_CALL(ctx, launch_stage(stage, k));
+}
+ifctn_status ifctn_wait_selftest(ifctn_ctx* ctx, int64_t budget_cycles) {
+    if (budget_cycles < 1000 || budget_cycles > ifctn::WAIT_BUDGET_CYCLES) {
+        set_error("budget_cycles must be in 1000..4e9");
+        return IFCTN_EINVAL;
+    }
+    IFCTN_CTX_CALL(ctx, wait_selftest(budget_cycles));
 }
 void ifctn_destroy(ifctn_ctx* ctx) { delete ctx; }
 const char* ifctn_last_error(void) { return g_last_error.c_str(); }

@@ -125,13 +125,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     return ok != 0;
 }
 
-// Waits for phase `parity` of the barrier with a clock budget (about 2 s at
-// 2 GHz).  On expiry it records FLAG_TIMEOUT and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* flags) {
+// Clock budget of every bounded device wait (about 2 s at 2 GHz).
+constexpr long long WAIT_BUDGET_CYCLES = 4000000000LL;
+
+// Waits for phase `parity` of the barrier with a clock budget (WAIT_BUDGET_CYCLES
+// unless a shorter one is given).  On expiry it records FLAG_TIMEOUT and
+// returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* flags,
+                                                  long long budget = WAIT_BUDGET_CYCLES) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > 4000000000LL) {
+        if (clock64() - t0 > budget) {
             atomicOr(flags, FLAG_TIMEOUT);
             return false;
         }

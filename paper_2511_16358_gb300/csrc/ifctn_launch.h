@@ -112,5 +112,9 @@ cudaError_t launch_sumsq(long long P, const T* X, double* part, int nblocks, cud
 cudaError_t launch_count_bits(long long nwords, const uint32_t* bits, double* part, int nblocks,
                               cudaStream_t st);
 cudaError_t launch_to_double(long long n, const float* a, double* b, cudaStream_t st);
+// Failure-path diagnostic: a grid barrier one CTA never joins and an mbarrier
+// phase no copy completes, each bounded by `budget` clock cycles (sets
+// FLAG_TIMEOUT in *flags; *count must be zero).
+cudaError_t launch_wait_selftest(int* flags, unsigned* count, long long budget, cudaStream_t st);
 
 }  // namespace ifctn

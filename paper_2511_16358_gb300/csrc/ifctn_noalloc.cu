@@ -54,13 +54,18 @@ ifctn_status scratch_for_current_device(void** out) {
     return IFCTN_OK;
 }
 
-bool is_device_pointer(const void* p) {
+// True when p is device (or managed) memory that the current device owns.
+// Memory of another GPU is refused: the scratch array and the launches are
+// on the current device, and reaching another GPU's memory from there either
+// faults or crosses the interconnect.
+bool is_current_device_pointer(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 template <typename T>
@@ -101,8 +106,15 @@ extern "C" ifctn_status ifctn_reconstruct_noalloc(int32_t order, const int64_t* 
                          std::to_string(NOALLOC_SCRATCH_BYTES) + "-byte static array of the allocation-free path");
         return IFCTN_EINVAL;
     }
-    if (!is_device_pointer(factors) || !is_device_pointer(out)) {
-        ifctn::set_error("the allocation-free path needs device pointers for factors and out");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        ifctn::set_error("no usable current CUDA device");
+        return IFCTN_ECUDA;
+    }
+    if (!is_current_device_pointer(factors, dev) || !is_current_device_pointer(out, dev)) {
+        ifctn::set_error("the allocation-free path needs factors and out in memory of the current device (" +
+                         std::to_string(dev) + ")");
         return IFCTN_EINVAL;
     }
     void* scratch = nullptr;

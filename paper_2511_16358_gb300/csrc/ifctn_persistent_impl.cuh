@@ -61,7 +61,8 @@ __device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& nb, int* flags) {
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& nb, int* flags,
+                                             long long budget = WAIT_BUDGET_CYCLES) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
     ++nb;
@@ -70,7 +71,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& nb, int*
         red_release_add_u32(count, 1u);
         const long long t0 = clock64();
         while (ld_acquire_u32(count) < target) {
-            if (clock64() - t0 > 4000000000LL) {
+            if (clock64() - t0 > budget) {
                 atomicOr(flags, FLAG_TIMEOUT);
                 break;
             }
@@ -1465,23 +1466,23 @@ __global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const __grid_constan
         if (!grid_barrier(p.bar_count, nbar, p.flags)) return;
         IFCTN_STAMP(p, sw, 26);
         // Stop decision (only when a tolerance is set): every CTA sums the
-        // per-CTA values in the same order, so all take the same
-        // decision without another barrier.  The FP64 log record is written
+        // per-CTA FP64 values in the same order as the log record below and
+        // applies the same formula, so all CTAs take the decision the log
+        // reports, without another barrier.  The FP64 log record is written
         // by the last CTA, which carries the least work in the next phases.
         bool conv = false;
         if (p.tolv > 0) {
             if (threadIdx.x < 32) {
-                // in the tensor dtype: FP64 on the FP64 path, FP32 on the mixed one
-                T a0 = T(0), a1 = T(0);
+                double a0 = 0.0, a1 = 0.0;
                 for (int b = threadIdx.x; b < gridDim.x; b += 32) {
-                    a0 += static_cast<T>(reinterpret_cast<volatile double*>(xp)[8 * b + 0]);
-                    a1 += static_cast<T>(reinterpret_cast<volatile double*>(xp)[8 * b + 1]);
+                    a0 += reinterpret_cast<volatile double*>(xp)[8 * b + 0];
+                    a1 += reinterpret_cast<volatile double*>(xp)[8 * b + 1];
                 }
                 a0 = warp_sum(a0);
                 a1 = warp_sum(a1);
                 if (threadIdx.x == 0) {
-                    const T tf = static_cast<T>(p.tolv);
-                    redc = (a1 > T(0) && a0 < tf * tf * a1) ? 1 : 0;
+                    const double rel = a1 > 0 ? sqrt(a0) / sqrt(a1) : (a0 > 0 ? INFINITY : 0.0);
+                    redc = rel < p.tolv ? 1 : 0;
                 }
             }
             __syncthreads();

@@ -102,16 +102,46 @@ def test_server_and_noalloc_arguments_rejected_before_gpu_work(lib):
     assert lib.ifctn_server_create(1 << 30, 0, ctypes.byref(srv)) == b.EINVAL
     assert lib.ifctn_submit(None, None, None, None, None, None) == b.EINVAL
     assert lib.ifctn_reconstruct_noalloc(3, None, None, 0, None, None, None) == b.EINVAL
-    R2 = np.array([[0, 2], [2, 0]])
+    R2 = (ctypes.c_int32 * 16)(*([0, 2, 0, 0, 2, 0] + [0] * 10))
+    dims = (ctypes.c_int64 * 4)(2048, 2048, 0, 0)
     host = np.zeros(8)
+    hp = ctypes.c_void_p(host.ctypes.data)
     # pair matrices of 2048 x 2048 FP64 entries exceed the fixed scratch array: refused
     # from the sizes alone, before the buffers are looked at
-    with pytest.raises(b.IfctnError) as ei:
-        b.reconstruct_noalloc((2048, 2048), R2, b.FP64, host, host)
-    assert ei.value.status == b.EINVAL and "scratch" in b.last_error()
-    with pytest.raises(b.IfctnError) as ei:
-        b.reconstruct_noalloc((4, 5), np.array([[0, 9], [9, 0]]), b.FP64, host, host)
-    assert ei.value.status == b.EINVAL
+    assert lib.ifctn_reconstruct_noalloc(2, dims, R2, b.FP64, hp, hp, None) == b.EINVAL
+    assert "scratch" in b.last_error()
+    R9 = (ctypes.c_int32 * 16)(*([0, 9, 0, 0, 9, 0] + [0] * 10))
+    dims = (ctypes.c_int64 * 4)(4, 5, 0, 0)
+    assert lib.ifctn_reconstruct_noalloc(2, dims, R9, b.FP64, hp, hp, None) == b.EINVAL
+
+
+def test_noalloc_binding_refuses_mistyped_and_missized_buffers():
+    """The allocation-free entry point takes no buffer lengths, so the binding
+    refuses, before any call into the library, factors that are not FP64 or
+    not exactly the packed size, and an output of the wrong dtype or size."""
+    import torch
+
+    from paper_2511_16358_gb300 import binding as b
+    from paper_2511_16358_gb300 import inputs as inp
+    dims = (5, 4, 3)
+    R = inp.rank_matrix(3, 2)
+    nf = inp.factor_size(dims, R)
+    good_f = torch.zeros(nf, dtype=torch.float64)
+    good_o = torch.zeros(dims, dtype=torch.float64)
+    cases = [
+        (torch.zeros(nf, dtype=torch.float32), good_o, "float64"),        # FP32 factors
+        (torch.zeros(nf - 1, dtype=torch.float64), good_o, "elements"),  # short factors
+        (good_f, torch.zeros((5, 4, 2), dtype=torch.float64), "elements"),  # mis-shaped out
+        (good_f, torch.zeros(dims, dtype=torch.float32), "float64"),     # out dtype vs FP64
+        (good_f, torch.zeros(60, dtype=torch.float64)[::1].view(5, 12).t(), "contiguous"),
+        (np.zeros(nf), good_o, "torch tensor"),                          # host numpy buffer
+        (good_f, good_o, "CUDA memory"),                                 # right sizes, host memory
+    ]
+    for f, o, word in cases:
+        with pytest.raises(ValueError, match=word):
+            b.reconstruct_noalloc(dims, R, b.FP64, f, o)
+    with pytest.raises(ValueError, match="float32"):
+        b.reconstruct_noalloc(dims, R, b.MIXED, good_f, good_o)
 
 
 def test_oracle_and_cuda_path_share_no_code():
