@@ -1,16 +1,26 @@
 #!/usr/bin/env python
 """Benchmark of the iFCTN PAM sweep on one GB300 (or N replicas, one per GPU).
 
-Workload (default): the multispectral-image shaped problem, 256 x 256 x 31
-FP32 in [0,1], planted iFCTN with all ranks 6 plus N(0, 0.01^2) noise, 10%
-uniformly observed, rho = 0.1, 100 sweeps per job, mixed precision.  One
-"step" is one whole completion job (100 PAM sweeps) starting from the job's
-initial state, which is restored from device-resident copies before the step;
-L2 is flushed (a 256 MiB write) before every timed step.  The metric is PAM
-sweeps per second over the whole job (all ranks).
+Workload (default): the traffic-shaped problem, 288 x 400 x 60 x 24 FP32
+(166M entries, 663.6 MB), planted iFCTN with all ranks 5, |x| scaled to
+[0, 1] plus N(0, 0.05^2) noise clipped at 0, 5 % of the entries observed and
+20 % of the mode-1 fibers missing entirely; rho = 0.1, 200 PAM sweeps per job,
+mixed precision.  One "step" is one whole completion job (200 sweeps) from
+the job's initial state, which is restored from device-resident copies before
+the step; the tensor is larger than L2 and L2 is also flushed (a 256 MiB
+write) before every timed step.  The metric is PAM sweeps per second over the
+whole job (all ranks).
+
+Besides the metric the line carries: the plain FP64 GPU path on the same job,
+time-to-RSE of both paths, each path's RSE error against the FP64 oracle's
+(stored values written by tests/golden/make_workload_rse.py), the end-to-end
+rate through the C ABI with host buffers, the roofline of the dominant
+kernel, the oracle timed on the host cores, the served stream (p50/p99
+latency and jobs/s at three settings) and a second workload
+(``--extra-workloads``).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle instead (the reference arm of this benchmark).
+oracle instead (the reference arm of this benchmark) on the same workload.
 """
 from __future__ import annotations
 
@@ -30,6 +40,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PAM sweeps/s"
 UNIT = "sweeps/s"
+DEFAULT_WORKLOAD = "traffic288x400x60x24_r5"
+PRECISION_LABEL = {
+    "mixed": ("mixed: FP32 tensor, contractions and Gram with FP32 accumulation; FP64 M_k reduction, stop-test, "
+              "objective and RSE sums; proximal systems factorised in FP32 (LDL^T) and refined once with a "
+              "two-float residual (no FP64 instruction in a solve)"),
+    "fp64": "fp64: every step in FP64",
+}
 
 
 def parse():
@@ -38,10 +55,27 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="msi256x256x31_r6")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64"])
-    ap.add_argument("--quick", action="store_true", help="skip the FP64-path, time-to-RSE and e2e extras")
+    ap.add_argument("--extra-workloads", default="msi256x256x31_r6",
+                    help="comma-separated workloads also timed (metric, FP64 path, roofline, RSE error)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-stream entry")
+    ap.add_argument("--quick", action="store_true",
+                    help="only the metric: no FP64 path, time-to-RSE, e2e, oracle, serving or extra workloads")
     return ap.parse_args()
+
+
+def workload_config(w, world):
+    """The workload as both arms report it (identical dicts)."""
+    N = len(w.dims)
+    return {"workload": w.name, "dims": [int(d) for d in w.dims],
+            "ranks": {f"{k}-{l}": int(w.R[k][l]) for k in range(N) for l in range(k + 1, N)},
+            "observed": w.p_observed,
+            "mask": (f"{int(100 * w.fiber[1])}% of mode-{w.fiber[0]} fibers missing, elsewhere uniform"
+                     if w.fiber else "uniform"),
+            "sweeps_per_job": w.sweeps, "rho": w.rho,
+            "l2": "flushed (256 MiB write) before every timed step",
+            "parallelism": f"replicas x{world}"}
 
 
 # ---------------------------------------------------------------------------
@@ -149,6 +183,7 @@ def rse_curve(b, ctx, xt, sweeps):
     b.set_truth(ctx, xt, log=True)
     b.sweep(ctx, sweeps)
     log = b.get_log(ctx)
+    b.set_truth(ctx, xt, log=False)
     return [r["rse"] for r in log[-sweeps:]]
 
 
@@ -191,27 +226,55 @@ def committed_traffic(kernel: str, workload: str):
     return None
 
 
-def cpu_baseline(w, budget_s=15.0):
+def oracle_rse(name):
+    """{sweep: (rse, rmse)} of the FP64 oracle on the workload's job, from the
+    stored values (tests/golden/workload_rse.txt), or {}."""
+    path = os.path.join(ROOT, "tests", "golden", "workload_rse.txt")
+    rows = {}
+    try:
+        for line in open(path):
+            line = line.strip()
+            if line and not line.startswith("#"):
+                nm, s, rse, rmse = line.split()
+                if nm == name:
+                    rows[int(s)] = (float(rse), float(rmse))
+    except OSError:
+        pass
+    return rows
+
+
+def oracle_start(w):
+    """The oracle's inputs and initial state of the workload's job (the
+    benchmark's reference arm and CPU baseline)."""
     import oracle
     from paper_2511_16358_gb300 import inputs as inp
     dims, R = w.dims, w.R
     planted = (oracle.reconstruct(dims, R, inp.gaussian_factors(dims, R, inp.planted_factor_seed(w)))
                if w.planted else None)
     xt, mask, G0 = inp.workload_inputs(w, planted)
+    del planted
     X = oracle.init_x(xt, mask)
     rec = oracle.reconstruct(dims, R, G0)
     N = len(dims)
-    G = G0 * (np.linalg.norm(X) / np.sqrt(w.p_observed) / np.linalg.norm(rec)) ** (1.0 / (N * (N - 1)))
+    nobs = max(int(mask.sum()), 1)
+    G = G0 * (np.linalg.norm(X) * np.sqrt(mask.size / nobs) / np.linalg.norm(rec)) ** (1.0 / (N * (N - 1)))
+    return G, X, mask
+
+
+def cpu_baseline(w, budget_s=15.0):
+    import oracle
+    G, X, mask = oracle_start(w)
     cores = os.cpu_count() or 1
     n, t0 = 0, time.perf_counter()
     while True:
-        oracle.sweep(dims, R, w.rho, G, X, mask, nthreads=cores)
+        oracle.sweep(w.dims, w.R, w.rho, G, X, mask, nthreads=cores)
         n += 1
         el = time.perf_counter() - t0
         if el > budget_s or n >= 2000:
             break
     return {"value": n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} FP64 oracle sweeps of {w.name} on {cores} host threads ({el:.1f} s)"}
+            "sample": f"the first {n} FP64 oracle sweeps of the {w.name} job ({w.sweeps} sweeps) on {cores} "
+                      f"host threads, {el:.1f} s, reported per sweep"}
 
 
 def run_reference(args, w):
@@ -219,33 +282,233 @@ def run_reference(args, w):
     if rank != 0:
         return
     import oracle
-    from paper_2511_16358_gb300 import inputs as inp
-    dims, R = w.dims, w.R
-    planted = (oracle.reconstruct(dims, R, inp.gaussian_factors(dims, R, inp.planted_factor_seed(w)))
-               if w.planted else None)
-    xt, mask, G0 = inp.workload_inputs(w, planted)
-    X = oracle.init_x(xt, mask)
-    rec = oracle.reconstruct(dims, R, G0)
-    N = len(dims)
-    G = G0 * (np.linalg.norm(X) / np.sqrt(w.p_observed) / np.linalg.norm(rec)) ** (1.0 / (N * (N - 1)))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    G, X, mask = oracle_start(w)
     cores = os.cpu_count() or 1
     per = []
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.sweep(dims, R, w.rho, G, X, mask, nthreads=cores)
+        oracle.sweep(w.dims, w.R, w.rho, G, X, mask, nthreads=cores)
         if it >= args.warmup:
             per.append(time.perf_counter() - t0)
     tot = sum(per)
     v = len(per) / tot
+    sample = (f"one FP64 oracle sweep of the {w.name} job per step (sweeps {args.warmup + 1}.."
+              f"{args.warmup + args.steps} after {args.warmup} warm-up sweeps), {cores} host threads")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(per),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "dims": list(dims), "sweeps_per_step": 1,
-                                             "implementation": "FP64 CPU oracle (C, OpenMP)"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"1 oracle sweep of {w.name} per step, {cores} host threads"},
+            "data": "synthetic", "config": workload_config(w, world),
+            "implementation": "FP64 CPU oracle (C, OpenMP over independent columns)",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+class Job:
+    """One workload on the device: inputs, a timed context and its restore copies."""
+
+    def __init__(self, b, torch, inp, w, prec, stream):
+        self.b, self.torch, self.w, self.prec, self.stream = b, torch, w, prec, stream
+        self.dt = b.tensor_dtype(prec)
+        self.xt, self.mask = make_inputs(w, b, inp)
+        self.P = self.xt.size
+        self.N = len(w.dims)
+
+    def new_ctx(self, precision, n=None):
+        b, w = self.b, self.w
+        return b.create(b.make_problem(w.dims, w.R, rho=w.rho, max_sweeps=n or w.sweeps, tol=0.0,
+                                       precision=precision, seed=4000 + w.seed_base),
+                        self.xt.astype(b.tensor_dtype(precision)), self.mask, None, self.stream.cuda_stream)
+
+    def state(self, ctx, precision):
+        torch, b = self.torch, self.b
+        from paper_2511_16358_gb300 import inputs as inp
+        G0 = torch.empty(inp.factor_size(self.w.dims, self.w.R), dtype=torch.float64, device="cuda")
+        b.get_factors(ctx, G0)
+        X0 = torch.empty(self.w.dims, dtype=torch.float32 if precision == b.MIXED else torch.float64,
+                         device="cuda")
+        b.get_x(ctx, X0)
+        return G0, X0
+
+
+def roofline_of(b, torch, job, prec, stream, tot, steps, launches_timed):
+    """Dominant kernel of the timed path, its algorithmic bytes per launch and
+    CUDA-event seconds per launch; per-stage device times of one sweep."""
+    w, N, P = job.w, job.N, job.P
+    pctx = job.new_ctx(prec)  # stages mutate the state: a context of their own
+    stt = stage_times(b, torch, pctx, stream, N)
+    b.destroy(pctx)
+    sz = np.dtype(b.tensor_dtype(prec)).itemsize
+    per_sweep = {}
+    for key, v in stt.items():
+        base = key.rstrip("0123456789")
+        per_sweep[base] = per_sweep.get(base, 0.0) + v
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    src = "measured" if "hbm_gbs" in peaks else "fallback"
+    mask_bytes = (P + 7) // 8
+    sweep_bytes = (N + 2) * P * sz + mask_bytes  # N contraction reads, X read + write, mask
+    persistent = launches_timed == steps  # one launch per step
+    if persistent:
+        kname = "k_sweep_persistent"
+        desc = "all phases of all sweeps of a job, one cooperative launch"
+        alg = w.sweeps * sweep_bytes
+        t_launch = tot / steps
+    else:
+        kname = "k_contract_roww/k_contract_colw"
+        desc = "mode-k streaming contraction M_k = X_(k) Z_k, one read of X per launch"
+        alg = P * sz
+        t_launch = sum(v for kk, v in stt.items() if kk.startswith("contract")) / N
+    achieved = alg / t_launch / 1e9
+    r = {"bound": "hbm", "kernel": kname, "kernel_role": desc, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+         "frac": achieved / hbm, "peak_source": src,
+         "algorithmic_bytes_per_launch": alg, "seconds_per_launch": t_launch,
+         "traffic": committed_traffic(kname, w.name),
+         "stage_seconds_per_launch": stt,
+         "stage_share_per_sweep": {k: v / sum(per_sweep.values()) for k, v in per_sweep.items()},
+         "dominant_stage": max(per_sweep, key=per_sweep.get)}
+    if not persistent and "xupdate" in stt:
+        xu_bytes = 2 * P * sz + mask_bytes
+        r["xupdate"] = {"kernel": "k_xupdate_slab", "algorithmic_bytes_per_launch": xu_bytes,
+                        "seconds_per_launch": stt["xupdate"],
+                        "achieved": xu_bytes / stt["xupdate"] / 1e9,
+                        "frac": xu_bytes / stt["xupdate"] / 1e9 / hbm}
+    if persistent:
+        r["note"] = ("tensor resident in L2 (%.1f MB): the sweep is bound by the latency of its dependent phases, "
+                     "not by HBM" % (P * sz / 1e6))
+    return r
+
+
+def rse_errors(w, r_mixed, r_fp64):
+    """RSE of the GPU paths after the job's sweeps against the stored FP64
+    oracle RSE of the same job (relative difference)."""
+    gold = oracle_rse(w.name)
+    if w.sweeps not in gold:
+        return {"oracle": None, "note": "no stored oracle RSE for this workload"}
+    g = gold[w.sweeps][0]
+    out = {"sweeps": w.sweeps, "oracle_fp64_rse": g,
+           "source": "tests/golden/workload_rse.txt (FP64 oracle, written by tests/golden/make_workload_rse.py)"}
+    if r_mixed is not None:
+        out["mixed_rse"] = r_mixed
+        out["mixed_rel_err"] = abs(r_mixed - g) / g
+    if r_fp64 is not None:
+        out["fp64_gpu_rse"] = r_fp64
+        out["fp64_gpu_rel_err"] = abs(r_fp64 - g) / g
+    out["bound"] = 1e-3
+    return out
+
+
+def fp64_and_rse(b, torch, job, ctx, G0, X0, value, stream, flush, steps):
+    """Plain FP64 GPU path on the same job, time-to-RSE of both paths, and the
+    RSE errors against the oracle."""
+    w = job.w
+    sweeps = w.sweeps
+    out = {}
+    c64 = job.new_ctx(b.FP64)
+    G064, X064 = job.state(c64, b.FP64)
+    t64, _ = time_steps(b, torch, c64, stream, X064, G064, sweeps, max(1, min(steps, 3)), 1, flush)
+    v64 = sweeps * len(t64) / sum(t64)
+    out["fp64_path"] = {"value": v64, "unit": UNIT, "speedup_mixed_over_fp64": value / v64,
+                        "precision": PRECISION_LABEL["fp64"]}
+    # time-to-RSE: RSE* = FP64 RSE after the job's sweeps x (1 + 1e-3)
+    b.set_factors(c64, G064)
+    b.set_x(c64, X064)
+    r64 = rse_curve(b, c64, job.xt.astype(np.float64), sweeps)
+    b.destroy(c64)
+    del G064, X064
+    b.set_factors(ctx, G0)
+    b.set_x(ctx, X0)
+    r32 = rse_curve(b, ctx, job.xt.astype(np.float32), sweeps)
+    target = r64[-1] * (1 + 1e-3)
+    s32 = next((i + 1 for i, r in enumerate(r32) if r <= target), None)
+    s64 = next((i + 1 for i, r in enumerate(r64) if r <= target), None)
+    out["time_to_rse"] = {
+        "rse_target": target, "rse_fp64_final": r64[-1], "rse_mixed_final": r32[-1],
+        "sweeps_mixed": s32, "sweeps_fp64": s64,
+        "seconds_mixed": (s32 / value) if s32 else None,
+        "seconds_fp64": (s64 / v64) if s64 else None,
+        "speedup": ((s64 / v64) / (s32 / value)) if (s32 and s64) else None}
+    out["rse_vs_oracle"] = rse_errors(w, r32[-1], r64[-1])
+    return out
+
+
+def e2e_rate(b, torch, job, prec, steps):
+    """Same metric through the public API with host buffers: every step
+    creates a context from pinned host inputs (copied to the device), runs the
+    job and copies the completed tensor back."""
+    w = job.w
+    dt = b.tensor_dtype(prec)
+    sz = np.dtype(dt).itemsize
+    obs_h = torch.from_numpy(job.xt.astype(dt)).pin_memory()
+    mask_h = torch.from_numpy(job.mask.astype(np.uint8)).pin_memory()
+    out_h = torch.empty(w.dims, dtype=obs_h.dtype).pin_memory()
+    e2e = []
+    for it in range(2 + steps):
+        t0 = time.perf_counter()
+        c = b.create(b.make_problem(w.dims, w.R, rho=w.rho, max_sweeps=w.sweeps, tol=0.0, precision=prec,
+                                    seed=4000 + w.seed_base), obs_h, mask_h, None, None)
+        b.complete(c, out_h)
+        b.destroy(c)
+        if it >= 2:
+            e2e.append(time.perf_counter() - t0)
+    return {"value": w.sweeps * len(e2e) / sum(e2e), "unit": UNIT,
+            "h2d_bytes_per_step": int(job.P * (sz + 1)), "d2h_bytes_per_step": int(job.P * sz)}
+
+
+def served_entry():
+    """The served stream at three settings: the configured stream (512
+    requests, Poisson 200 req/s, 100 GB budget), a rate the GPU sustains, and
+    a 2 GB budget that makes admission wait."""
+    from paper_2511_16358_gb300 import serve_bench as sb
+    runs = {}
+    for key, argv in (("stream_200rps_100GB", ["--requests", "512", "--rate", "200"]),
+                      ("sustainable_15rps", ["--requests", "160", "--rate", "15"]),
+                      ("admission_2GB", ["--requests", "96", "--rate", "200", "--budget-gb", "2"])):
+        r = sb.run(sb.parse(argv))
+        runs[key] = {"requests": r["requests"], "rate_req_s": r["rate_req_s"], "budget_gb": r["budget_gb"],
+                     "p50_s": r["latency_from_arrival_s"]["p50"], "p99_s": r["latency_from_arrival_s"]["p99"],
+                     "server_p50_s": r["server_latency_s"]["p50"], "server_p99_s": r["server_latency_s"]["p99"],
+                     "jobs_per_s": r["jobs_per_s"], "sweeps_per_s": r["sweeps_per_s"],
+                     "peak_resident": r["peak_resident"], "client_submit_lag_p50_s": r["client_submit_lag_s"]["p50"]}
+    runs["config"] = ("order 3/4, I_k in [32,128], R_{k,l} in [2,6], p in [0.1,0.5], 50 sweeps each, FP32 mixed, "
+                      "16 slots; latency from the scheduled Poisson arrival to completion")
+    return runs
+
+
+def bench_workload(b, torch, inp, w, prec, stream, flush, steps, warmup, world, full, rank, with_e2e=True):
+    """Times one workload; returns (value, line fields)."""
+    job = Job(b, torch, inp, w, prec, stream)
+    ctx = job.new_ctx(prec)
+    G0, X0 = job.state(ctx, prec)
+    local = torch.cuda.current_device()
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    lc0 = b.launch_count(ctx)
+    times, _ = time_steps(b, torch, ctx, stream, X0, G0, w.sweeps, steps, warmup, flush)
+    ck = clocks.stop()
+    launches_timed = (b.launch_count(ctx) - lc0) * steps // (steps + warmup)
+    tot = sum(times)
+    fields = {"ms_per_step": 1000 * tot / steps, "gpu_launches": launches_timed, "clocks": ck,
+              "config": workload_config(w, world), "precision": PRECISION_LABEL["mixed" if prec == b.MIXED else "fp64"],
+              "dtype": "f32" if prec == b.MIXED else "f64"}
+    value_rank = steps * w.sweeps / tot
+    fields["roofline"] = roofline_of(b, torch, job, prec, stream, tot, steps, launches_timed)
+    if full and rank == 0:
+        if prec == b.MIXED:
+            fields.update(fp64_and_rse(b, torch, job, ctx, G0, X0, value_rank, stream, flush, steps))
+        if with_e2e:
+            fields["e2e"] = e2e_rate(b, torch, job, prec, steps)
+    b.destroy(ctx)
+    return tot, fields, job
 
 
 def main():
@@ -256,9 +519,6 @@ def main():
         run_reference(args, w)
         return
     import torch
-    # the persistent kernel timestamps the phases of one sweep of every launch:
-    # a sweep from the middle of the step (steady state), unless set otherwise
-    os.environ.setdefault("IFCTN_STAMP_SWEEP", str(max(0, w.sweeps // 2)))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -273,169 +533,42 @@ def main():
     from paper_2511_16358_gb300 import binding as b
 
     prec = b.MIXED if (args.precision or w.precision) == "mixed" else b.FP64
-    dt = b.tensor_dtype(prec)
-    sweeps = w.sweeps
-    xt, mask = make_inputs(w, b, inp)
-    P = xt.size
-    dims = w.dims
-    N = len(dims)
     stream = torch.cuda.Stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
-
-    def new_ctx(precision, n):
-        return b.create(b.make_problem(dims, w.R, rho=w.rho, max_sweeps=n, tol=0.0, precision=precision,
-                                       seed=4000 + w.seed_base),
-                        xt.astype(b.tensor_dtype(precision)), mask, None, stream.cuda_stream)
-
-    ctx = new_ctx(prec, sweeps)
-    G0 = torch.empty(inp.factor_size(dims, w.R), dtype=torch.float64, device="cuda")
-    b.get_factors(ctx, G0)
-    X0 = torch.empty(dims, dtype=torch.float32 if dt == np.float32 else torch.float64, device="cuda")
-    b.get_x(ctx, X0)
-    kps = b.kernels_per_sweep(ctx)
-
-    clocks = Clocks(local)
+    full = not args.quick
     if dist:
         dist.barrier()
+    tot, fields, job = bench_workload(b, torch, inp, w, prec, stream, flush, args.steps, args.warmup, world, full,
+                                      rank)
     torch.cuda.synchronize()
-    clocks.start()
-    lc0 = b.launch_count(ctx)
-    times, st_last = time_steps(b, torch, ctx, stream, X0, G0, sweeps, args.steps, args.warmup, flush)
-    ck = clocks.stop()
-    launches_timed = (b.launch_count(ctx) - lc0) * args.steps // (args.steps + args.warmup)
-    ph = b.phase_times(ctx)
-    names = []
-    for k in range(len(w.dims)):
-        names += [f"m{k}_contract", f"m{k}_bar1", f"m{k}_reduce", f"m{k}_bar2", f"m{k}_solve", f"m{k}_bar3"]
-    names = names[: 6 * len(w.dims)]
-    phases = {}
-    prev = 0.0
-    for nm, t in zip(names, ph[: 6 * len(w.dims)]):
-        phases[nm] = t - prev
-        prev = t
-    if len(ph) >= 26:
-        phases["xupdate"] = ph[24] - prev
-        phases["xupdate_bar"] = ph[25] - ph[24]
-    for k in range(len(w.dims)):
-        if len(ph) >= 28 + 2 * k:
-            phases[f"m{k}_contract_cta_max_end"] = ph[26 + 2 * k]
-            phases[f"m{k}_contract_cta_mean_end"] = ph[27 + 2 * k]
-    sub = ph[26 + 2 * N: 26 + 2 * N + 12]
-    if len(sub) == 12:
-        names_sub = ["start", "staged", "column_loaded", "omega", "H_b_sums", "reduced", "ldlt_solve", "refined",
-                     "checked", "stored", "stages_done", "W_refreshed"]
-        mode = int(os.environ.get("IFCTN_STAMP_MODE", len(w.dims) - 1))
-        phases["solve_first_column_s"] = {nm: (t - sub[0]) for nm, t in zip(names_sub, sub)}
-        phases["solve_first_column_s"]["mode"] = mode
-    red = ph[26 + 2 * N + 12: 26 + 2 * N + 16]
-    if len(red) == 4 and red[0] == red[0]:
-        phases["reduce_substeps_s"] = {"K_done": red[1] - red[0], "coef_done": red[2] - red[0],
-                                       "M_done": red[3] - red[0]}
-    torch.cuda.synchronize()
-    tot, value = aggregate_ranks(torch, dist, sum(times), world, args.steps * sweeps, "cuda")
-
+    tot, value = aggregate_ranks(torch, dist, tot, world, args.steps * w.sweeps, "cuda")
     extras = {}
-    # per-stage device times (separate context: stages mutate the state)
-    pctx = new_ctx(prec, sweeps)
-    stt = stage_times(b, torch, pctx, stream, N)
-    b.destroy(pctx)
-    sz = np.dtype(dt).itemsize
-    per_sweep = {}
-    for key, v in stt.items():
-        base = key.rstrip("0123456789")
-        per_sweep[base] = per_sweep.get(base, 0.0) + v
-    dominant = max(per_sweep, key=per_sweep.get)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    src = "measured" if "hbm_gbs" in peaks else "fallback"
-    mask_bytes = (P + 7) // 8
-    sweep_bytes = (N + 2) * P * sz + mask_bytes  # N contraction reads, X read + write, mask
-    persistent = launches_timed == args.steps  # one launch per step
-    if persistent:
-        # one cooperative launch runs the whole step (all sweeps); its device
-        # time is the CUDA-event time of the step on the context's stream
-        kname = "k_sweep_persistent (all phases of all sweeps, one cooperative launch)"
-        alg = sweeps * sweep_bytes
-        t_launch = tot / args.steps
-    else:
-        kname = "k_contract_roww/k_contract_colw (mode-k streaming contraction, warp-pipelined)"
-        alg = P * sz  # one read of X per contraction launch
-        t_launch = sum(v for kk, v in stt.items() if kk.startswith("contract")) / N
-    achieved = alg / t_launch / 1e9
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_source": src,
-                "algorithmic_bytes_per_launch": alg, "seconds_per_launch": t_launch,
-                "traffic": committed_traffic(kname.split()[0], w.name),
-                "stage_seconds_per_launch": stt,
-                "stage_share_per_sweep": {k: v / sum(per_sweep.values()) for k, v in per_sweep.items()},
-                "dominant_stage": dominant}
-    if persistent:
-        roofline["note"] = ("tensor resident in L2 (%.1f MB): the sweep is bound by the latency of its "
-                            "dependent phases, not by HBM" % (P * sz / 1e6))
-
-    if not args.quick and rank == 0:
-        # plain FP64 GPU path on the same job
-        if prec == b.MIXED:
-            c64 = new_ctx(b.FP64, sweeps)
-            G064 = torch.empty_like(G0)
-            b.get_factors(c64, G064)
-            X064 = torch.empty(dims, dtype=torch.float64, device="cuda")
-            b.get_x(c64, X064)
-            t64, _ = time_steps(b, torch, c64, stream, X064, G064, sweeps, max(1, min(args.steps, 3)), 1, flush)
-            v64 = sweeps * len(t64) / sum(t64)
-            extras["fp64_path"] = {"value": v64, "unit": UNIT, "speedup_mixed_over_fp64": value / world / v64}
-            # time-to-RSE: RSE* = FP64 RSE after the job's sweeps x (1 + 1e-3)
-            b.set_factors(c64, G064)
-            b.set_x(c64, X064)
-            r64 = rse_curve(b, c64, xt.astype(np.float64), sweeps)
-            b.set_factors(ctx, G0)
-            b.set_x(ctx, X0)
-            r32 = rse_curve(b, ctx, xt.astype(np.float32), sweeps)
-            target = r64[-1] * (1 + 1e-3)
-            s32 = next((i + 1 for i, r in enumerate(r32) if r <= target), None)
-            s64 = next((i + 1 for i, r in enumerate(r64) if r <= target), None)
-            extras["time_to_rse"] = {
-                "rse_target": target, "rse_fp64_final": r64[-1], "rse_mixed_final": r32[-1],
-                "sweeps_mixed": s32, "sweeps_fp64": s64,
-                "seconds_mixed": (s32 / (value / world)) if s32 else None,
-                "seconds_fp64": (s64 / v64) if s64 else None}
-            b.destroy(c64)
-        # end to end through the public API with host buffers
-        import torch as _t
-        obs_h = _t.from_numpy(xt.astype(dt)).pin_memory()
-        mask_h = _t.from_numpy(mask.astype(np.uint8)).pin_memory()
-        out_h = _t.empty(dims, dtype=obs_h.dtype).pin_memory()
-        e2e = []
-        for it in range(2 + args.steps):
-            t0 = time.perf_counter()
-            c = b.create(b.make_problem(dims, w.R, rho=w.rho, max_sweeps=sweeps, tol=0.0, precision=prec,
-                                        seed=4000 + w.seed_base), obs_h, mask_h, None, None)
-            b.complete(c, out_h)
-            b.destroy(c)
-            if it >= 2:
-                e2e.append(time.perf_counter() - t0)
-        extras["e2e"] = {"value": sweeps * len(e2e) / sum(e2e), "unit": UNIT,
-                         "h2d_bytes_per_step": int(P * (sz + 1)), "d2h_bytes_per_step": int(P * sz)}
+    if full and rank == 0:
         extras["cpu_baseline"] = cpu_baseline(w)
-    b.destroy(ctx)
+        del job
+        if not args.no_serve:
+            extras["served"] = served_entry()
+        others = {}
+        for name in [x for x in args.extra_workloads.split(",") if x and x != w.name]:
+            w2 = inp.WORKLOADS[name]
+            p2 = b.MIXED if w2.precision == "mixed" else b.FP64
+            t2, f2, j2 = bench_workload(b, torch, inp, w2, p2, stream, flush, args.steps, args.warmup, 1, True, 0,
+                                        with_e2e=False)
+            del j2
+            others[name] = dict(value=args.steps * w2.sweeps / t2, unit=UNIT, **f2)
+        if others:
+            extras["extra_workloads"] = others
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == b.MIXED else "f64",
-                "data": "synthetic",
-                "config": {"workload": w.name, "dims": list(dims), "ranks": int(w.R[0][1]),
-                           "observed": w.p_observed, "sweeps_per_step": sweeps,
-                           "precision": "mixed (FP32 tensor/contractions, FP64 solves)" if prec == b.MIXED else "fp64",
-                           "l2": "flushed (256 MiB write) before every timed step",
-                           "parallelism": f"replicas x{world}"},
-                "gpu_launches": launches_timed,
-                "persistent_phases_s": dict(phases, sweep=int(os.environ["IFCTN_STAMP_SWEEP"])),
-                "clocks": ck, "roofline": roofline}
+                "scaling": "weak", "vs_baseline": None, "dtype": fields["dtype"], "data": "synthetic",
+                "config": fields["config"], "precision": fields["precision"],
+                "gpu_launches": fields["gpu_launches"], "clocks": fields["clocks"],
+                "roofline": fields["roofline"]}
+        for key in ("fp64_path", "time_to_rse", "rse_vs_oracle", "e2e"):
+            if key in fields:
+                line[key] = fields[key]
         line.update(extras)
         line.setdefault("e2e", None)
         print(json.dumps(line), flush=True)

@@ -66,7 +66,7 @@ def make_inputs(torch, b, inp, rq, stream):
     return x, mask
 
 
-def main(argv=None):
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -77,8 +77,16 @@ def main(argv=None):
     ap.add_argument("--dmin", type=int, default=32)
     ap.add_argument("--dmax", type=int, default=128)
     ap.add_argument("--pinned-cap-gb", type=float, default=32.0)
-    args = ap.parse_args(argv)
+    return ap.parse_args(argv)
 
+
+def main(argv=None):
+    print(json.dumps(run(parse(argv))), flush=True)
+
+
+def run(args) -> dict:
+    """Serves one stream with the settings of ``args`` (see ``parse``) and
+    returns the JSON record."""
     import torch
 
     import __graft_entry__
@@ -172,7 +180,7 @@ def main(argv=None):
                    "entries_mean": float(entries.mean()), "entries_max": float(entries.max()),
                    "seed": args.seed, "data": "synthetic planted iFCTN + N(0,0.01^2) noise"},
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 if __name__ == "__main__":
