@@ -472,8 +472,14 @@ def served_entry():
     for key, argv in (("stream_200rps_100GB", ["--requests", "512", "--rate", "200"]),
                       ("sustainable_15rps", ["--requests", "160", "--rate", "15"]),
                       ("admission_2GB", ["--requests", "96", "--rate", "200", "--budget-gb", "2"])):
-        r = sb.run(sb.parse(argv))
-        runs[key] = {"requests": r["requests"], "rate_req_s": r["rate_req_s"], "budget_gb": r["budget_gb"],
+        try:
+            r = sb.run(sb.parse(argv))
+        except Exception as e:  # keep the line: report the failure in its entry
+            runs[key] = {"error": f"{type(e).__name__}: {e}"}
+            continue
+        runs[key] = {"requests": r["requests"], "served": r["served"],
+                     "refused_larger_than_budget": r["refused_larger_than_budget"],
+                     "rate_req_s": r["rate_req_s"], "budget_gb": r["budget_gb"],
                      "p50_s": r["latency_from_arrival_s"]["p50"], "p99_s": r["latency_from_arrival_s"]["p99"],
                      "server_p50_s": r["server_latency_s"]["p50"], "server_p99_s": r["server_latency_s"]["p99"],
                      "jobs_per_s": r["jobs_per_s"], "sweeps_per_s": r["sweeps_per_s"],

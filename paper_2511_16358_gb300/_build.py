@@ -27,18 +27,42 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _digest() -> str:
+def _includes(path, seen):
+    """The in-tree files `path` includes (#include "..."), transitively."""
+    import re
+    if path in seen:
+        return
+    seen.add(path)
+    with open(path) as f:
+        for name in re.findall(r'^\s*#\s*include\s+"([^"]+)"', f.read(), re.M):
+            dep = os.path.normpath(os.path.join(os.path.dirname(path), name))
+            if os.path.exists(dep):
+                _includes(dep, seen)
+
+
+def _tu_digest(src) -> str:
+    """Digest of one translation unit: its source, every in-tree header it
+    includes and the compiler flags."""
+    seen = set()
+    _includes(os.path.join(CSRC, src), seen)
     h = hashlib.sha256()
-    for name in sorted(os.listdir(CSRC)):
-        with open(os.path.join(CSRC, name), "rb") as f:
-            h.update(name.encode() + f.read())
-    with open(os.path.join(ROOT, "include", "ifctn.h"), "rb") as f:
-        h.update(f.read())
+    for path in sorted(seen):
+        with open(path, "rb") as f:
+            h.update(os.path.relpath(path, ROOT).encode() + f.read())
     h.update(" ".join(ARCH + FLAGS).encode())
     return h.hexdigest()
 
 
+def _digest() -> str:
+    h = hashlib.sha256()
+    for src in SOURCES:
+        h.update(_tu_digest(src).encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles the translation units whose sources or headers changed (each
+    object keeps the digest it was built from) and links libifctn.so."""
     stamp = os.path.join(BUILD, "stamp")
     dig = _digest()
     if not force and os.path.exists(LIB) and os.path.exists(stamp):
@@ -50,12 +74,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def comp(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        ostamp = obj + ".digest"
+        d = _tu_digest(src)
+        if not force and os.path.exists(obj) and os.path.exists(ostamp):
+            with open(ostamp) as f:
+                if f.read().strip() == d:
+                    return obj
         cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
         if verbose and r.stderr:
             print(r.stderr)
+        with open(ostamp, "w") as f:
+            f.write(d)
         return obj
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:

@@ -487,7 +487,15 @@ int warp_unit_chunks(int S, int t, long long outer, int c0, int NW, int sms) {
     return best;
 }
 
-ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitDesc>& units) {
+// IFCTN_CW_RPL=1 keeps the warp contraction at one row per lane (timing and
+// tuning); otherwise two rows per lane are used where the plan allows them.
+bool rows_per_lane_allowed() {
+    const char* e = getenv("IFCTN_CW_RPL");
+    return !(e && strcmp(e, "1") == 0);
+}
+
+ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitDesc>& units,
+                                bool rpl_allowed) {
     constexpr int NW = 16;
     ContractPlan pl;
     memset(&pl, 0, sizeof(pl));
@@ -640,12 +648,23 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
         if ((ldx / VN) % 2 == 0) ldx += VN;
         pl.ldx = ldx;
         // a lane owns one row: tasks of up to 32 rows; rows too long for 16 of
-        // them in a task leave the mode to the CTA kernels
-        const int RBK = balanced(IA, std::min(32, XBYTES / (sz * IB)));
+        // them in a task leave the mode to the CTA kernels.  Order 4 with equal
+        // ranks R_{k,B} = R_{k,l2} (2..5) and more than 32 rows: two rows per
+        // lane, tasks of up to 64 rows (IFCTN_CW_RPL=1 or 2 forces the choice
+        // where both are possible).
+        int RBK = balanced(IA, std::min(32, XBYTES / (sz * IB)));
         if (RBK < std::min(IA, 16)) {
             units.clear();
             pl.warp = 0;
             return pl;
+        }
+        pl.rpl = 1;
+        if (rpl_allowed && N == 4 && pl.Rl2 == pl.R1 && pl.R1 >= 2 && pl.R1 <= 5) {
+            const int RBK2 = balanced(IA, std::min(64, 2 * XBYTES / (sz * IB)));
+            if (RBK2 > 32) {
+                RBK = RBK2;
+                pl.rpl = 2;
+            }
         }
         pl.TAc = RBK;
         const int nrc = cdiv(IA, RBK);
@@ -715,7 +734,7 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
         xregion = round_up(RBK * IB + 32 / sz, VN);
         if (foldA) xregion *= 2;
         const int RBP = round_up(pl.R1, VN);
-        tab_elems = static_cast<long long>(NW) * IB * RBP;
+        tab_elems = static_cast<long long>(NW) * IB * (pl.vec ? pl.R1 : RBP);
         gtab_elems = static_cast<long long>(pl.R1) * IB +
                      (pl.l2 >= 0 ? static_cast<long long>(pl.Rl2) * s.I[pl.l2] : 0) +
                      (isF ? static_cast<long long>(pl.RA) * IA : 0);
@@ -728,15 +747,23 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
     pl.sub_elems = static_cast<int>(tc);
     auto r128 = [](long long b) { return (b + 127) / 128 * 128; };
     const long long limit = 225 * 1024;
-    // per-warp ring of a task's W entries (cp.async), ROW 160, COL 96 elements a stage
-    const long long auxw = (k == Bm) ? 96 : 160;
+    // per-warp ring of a task's W entries (cp.async), elements a stage: COL 96
+    // (row weights of two F modes, W_{0,1}(i0, i1)); ROW one row W_{p,B}(i_p, :)
+    // (two for N = 4, k = 2) padded to whole warps, then the fold weights of up
+    // to 32 rows per lane row
+    const long long auxw = (k == Bm) ? 96 : (N == 4 && k == 2 ? 2LL : 1LL) * round_up(IB, 32) + 32LL * std::max(1, pl.rpl);
+    pl.auxw = static_cast<int>(auxw);
+    // with two rows per lane the unit-end sums (zs) share the per-warp
+    // coefficient tables' space: those are rewritten only by the next unit's
+    // tasks, after the unit end's last CTA barrier
+    const bool zs_in_tab = pl.rpl == 2 && zs_elems <= tab_elems;
     for (int S = 4; S >= 2; --S) {
         const long long off_tile = 640;
         const long long off_tab = off_tile + r128(static_cast<long long>(NW) * S * tc * sz);
         const long long off_gtab = off_tab + r128(tab_elems * sz);
         const long long off_wab = off_gtab + r128(gtab_elems * sz);
-        const long long off_zs = off_wab + r128(wab_elems * sz);
-        const long long off_aux = off_zs + r128(zs_elems * sz);
+        const long long off_zs = zs_in_tab ? off_tab : off_wab + r128(wab_elems * sz);
+        const long long off_aux = zs_in_tab ? off_wab + r128(wab_elems * sz) : off_zs + r128(zs_elems * sz);
         const long long total = off_aux + static_cast<long long>(NW) * S * auxw * sz;
         if (total <= limit) {
             pl.nstages = S;
@@ -751,6 +778,7 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
             break;
         }
     }
+    if (!pl.warp && pl.rpl == 2) return plan_contract_warp(s, k, sz, units, false);
     pl.grid = std::max(1, std::min(pl.nunits, sms));
     if (!pl.warp) units.clear();
     return pl;
@@ -903,7 +931,7 @@ struct Engine : ifctn_ctx {
         for (int k = 0; k < sh.N; ++k) {
             std::vector<UnitDesc> u;
             plan[k].warp = 0;
-            if (graph_only) plan[k] = plan_contract_warp(sh, k, sz, u);
+            if (graph_only) plan[k] = plan_contract_warp(sh, k, sz, u, rows_per_lane_allowed());
             if (!plan[k].warp) plan[k] = plan_contract(sh, k, sz, u);
             if (plan[k].smem > SMEM_LIMIT && !plan[k].warp) {
                 set_error("tensor shape needs more shared memory than available");

@@ -138,13 +138,21 @@ __device__ __forceinline__ Task task_at(const UnitCur& c, int t, int rbk) {
 // them, one task ahead, into registers.
 // ---------------------------------------------------------------------------
 
-template <typename T, int RB>
+// RPL rows per lane (1, or 2 for tasks of up to 64 rows: twice the independent
+// work per coefficient-table load and per task overhead); RCT the rank of the
+// register fold when fixed at compile time (0: any, up to RMAX; the z
+// registers are then sized for RMAX).
+template <typename T, int RB, int RPL, int RCT>
 __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_constant__ ContractArgs<T> A) {
+    static_assert(RPL == 1 || RPL == 2, "one or two rows per lane");
     if (*A.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int VN = 16 / static_cast<int>(sizeof(T));
     constexpr int RBP = (RB + VN - 1) / VN * VN;
-    constexpr bool SPLIT = RB <= 5;  // two accumulator sets (shorter FMA chains) while registers allow
+    constexpr int ZR = RCT > 0 ? RCT : RMAX;
+    // two accumulator sets (shorter FMA chains) while registers allow; with two
+    // rows per lane the rows are the independent chains
+    constexpr bool SPLIT = RPL == 1 && RB <= 5;
     const Shape& s = A.sh;
     const ContractPlan& pl = A.pl;
     const int N = s.N, k = A.k, IA = s.IA, IB = s.IB, Am = N - 2, Bm = N - 1;
@@ -156,7 +164,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
     const int S = pl.nstages, TC = pl.sub_elems;
     const int RBK = pl.TAc, LDX = pl.ldx, XR = pl.xr, ZW = pl.zw;
     const int l2 = pl.l2;
-    const int RC = foldA ? pl.RA : pl.Rl2;
+    const int RC = RCT > 0 ? RCT : (foldA ? pl.RA : pl.Rl2);
     // F modes p != k whose rows W_{p,B}(i_p, :) enter the coefficient table
     const int p0 = (N == 4) ? (k == 0 ? 1 : 0) : (N == 3 && k != 0 ? 0 : -1);
     const bool two_psi = N == 4 && k == 2;
@@ -165,7 +173,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
     int* misc = reinterpret_cast<int*>(smem + MISC_OFF);  // [0] abort, [1 + w] z slot of warp w
     volatile int* abortf = misc;
     T* tiles = reinterpret_cast<T*>(smem + pl.off_tile);
-    T* psi = reinterpret_cast<T*>(smem + pl.off_tab) + static_cast<size_t>(warp) * IB * RBP;
+    T* psi = reinterpret_cast<T*>(smem + pl.off_tab) + static_cast<size_t>(warp) * IB * PS;
     T* gtab = reinterpret_cast<T*>(smem + pl.off_gtab);
     T* wab = reinterpret_cast<T*>(smem + pl.off_wab);
     T* zs = reinterpret_cast<T*>(smem + pl.off_zs);
@@ -187,9 +195,13 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
     stage_wait();
 
     // per-warp ring of the W entries each task needs besides its tile, filled
-    // by cp.async at issue time (lane-owned: w0/w1 at b = lane, lane + 32; the
-    // fold weight at row = lane) and waited for with the stage
-    constexpr int AUXW = 160;
+    // by cp.async at issue time and waited for with the stage.  Slot layout:
+    // [0, IBP) the row W_{p0,B}(i_p0, :), [IBP, 2 IBP) the row W_{1,B}(i1, :)
+    // (N = 4, k = 2), then the fold weights of the task's rows (32 RPL; b =
+    // lane + 32 m and row = lane + 32 q are lane-owned).
+    const int IBP = (IB + 31) & ~31;
+    const int AUXW = pl.auxw;
+    const int AUX_W1 = IBP, AUX_FW = two_psi ? 2 * IBP : IBP;
     T* auxr = reinterpret_cast<T*>(smem + pl.off_aux) + static_cast<size_t>(warp) * S * AUXW;
 
     // issue path: the task's rows of X (and, N = 3 k = 0, of W_{A,B}) by TMA
@@ -216,20 +228,21 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
             T* ax = auxr + st * AUXW;
             if (p0 >= 0) {
                 const T* r = A.W + s.woff[p0][Bm] + static_cast<long long>(p0 == 0 ? i0 : i1) * IB;
-                if (lane < IB) cp_async_elem(ax + lane, r + lane);
-                if (lane + 32 < IB) cp_async_elem(ax + 32 + lane, r + lane + 32);
+                for (int b = lane; b < IB; b += 32) cp_async_elem(ax + b, r + b);
             }
             if (two_psi) {
                 const T* r = A.W + s.woff[1][Bm] + static_cast<long long>(i1) * IB;
-                if (lane < IB) cp_async_elem(ax + 64 + lane, r + lane);
-                if (lane + 32 < IB) cp_async_elem(ax + 96 + lane, r + lane + 32);
+                for (int b = lane; b < IB; b += 32) cp_async_elem(ax + AUX_W1 + b, r + b);
             }
             if (isF && N == 4) {
                 const int o = 1 - k, io = o == 0 ? i0 : i1;
-                if (lane < tk.na)
-                    cp_async_elem(ax + 128 + lane, A.W + s.woff[o][Am] + static_cast<long long>(io) * IA + tk.a0 + lane);
+#pragma unroll
+                for (int q = 0; q < RPL; ++q)
+                    if (lane + 32 * q < tk.na)
+                        cp_async_elem(ax + AUX_FW + 32 * q + lane,
+                                      A.W + s.woff[o][Am] + static_cast<long long>(io) * IA + tk.a0 + 32 * q + lane);
             } else if (!isF && N == 4) {
-                cp_async_elem(ax + 128 + lane, A.W + s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1);
+                cp_async_elem(ax + AUX_FW + lane, A.W + s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1);
             }
             cp_async_commit();
         }
@@ -272,11 +285,13 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
         }
         stage_wait();
 
-        T z[RMAX][RB];
+        T z[RPL][ZR][RB];
 #pragma unroll
-        for (int r2 = 0; r2 < RMAX; ++r2)
+        for (int q = 0; q < RPL; ++q)
 #pragma unroll
-            for (int r = 0; r < RB; ++r) z[r2][r] = T(0);
+            for (int r2 = 0; r2 < ZR; ++r2)
+#pragma unroll
+                for (int r = 0; r < RB; ++r) z[q][r2][r] = T(0);
 
         int zslot = -1;
         for (int t = warp; t < nt; t += NWARP, ++it) {
@@ -291,30 +306,34 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
                 int i0, i1;
                 decode_f(s, tk.f, i0, i1);
                 // coefficient table psi(b, r) = prod_{p in F, p != k} W_{p,B}(i_p, b) G_{B,k}(r, b)
+                for (int b = lane; b < IB; b += 32) {
+                    const T om = (p0 >= 0 ? ax[b] : T(1)) * (two_psi ? ax[AUX_W1 + b] : T(1));
 #pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    const int b = lane + 32 * m;
-                    if (b < IB) {
-                        const T om = (p0 >= 0 ? ax[32 * m + lane] : T(1)) * (two_psi ? ax[64 + 32 * m + lane] : T(1));
-#pragma unroll
-                        for (int r = 0; r < RBP; ++r)
-                            if (r < RB) psi[b * PS + r] = om * gB[r * IB + b];
-                            else if (!vec) psi[b * PS + r] = T(0);
-                    }
+                    for (int r = 0; r < RBP; ++r)
+                        if (r < RB) psi[b * PS + r] = om * gB[r * IB + b];
+                        else if (!vec) psi[b * PS + r] = T(0);
                 }
                 __syncwarp();
-                const bool va = lane < tk.na;
-                const int row = va ? lane : 0;
-                const T* xr = buf + shift16(A.X + (tk.f * IA + tk.a0) * IB) + static_cast<size_t>(row) * IB;
-                const T* wr = nullptr;
-                if (foldA)
-                    wr = buf + XR + shift16(A.W + s.woff[Am][Bm] + static_cast<long long>(tk.a0) * IB) +
-                         static_cast<size_t>(row) * IB;
-                else if (isF)
-                    wr = wab + static_cast<size_t>(tk.a0 - uc.a0 + row) * LDX;
-                T u0[RB], u1[RB];
+                bool va[RPL];
+                const T* xr[RPL];
+                const T* wr[RPL];
 #pragma unroll
-                for (int r = 0; r < RB; ++r) u0[r] = u1[r] = T(0);
+                for (int q = 0; q < RPL; ++q) {
+                    va[q] = lane + 32 * q < tk.na;
+                    const int row = va[q] ? lane + 32 * q : 0;
+                    xr[q] = buf + shift16(A.X + (tk.f * IA + tk.a0) * IB) + static_cast<size_t>(row) * IB;
+                    wr[q] = nullptr;
+                    if (foldA)
+                        wr[q] = buf + XR + shift16(A.W + s.woff[Am][Bm] + static_cast<long long>(tk.a0) * IB) +
+                                static_cast<size_t>(row) * IB;
+                    else if (isF)
+                        wr[q] = wab + static_cast<size_t>(tk.a0 - uc.a0 + row) * LDX;
+                }
+                T u0[RPL][RB], u1[RPL][RB];
+#pragma unroll
+                for (int q = 0; q < RPL; ++q)
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) u0[q][r] = u1[q][r] = T(0);
                 if (vec) {
                     // 16-byte chunks of the row; with pl.skew each lane starts at
                     // its own chunk so rows that share banks are read apart
@@ -323,66 +342,84 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
 #pragma unroll 2
                     for (int ic2 = 0; ic2 < nch; ++ic2, c = (c + 1 == nch) ? 0 : c + 1) {
                         const int b = c * VN;
-                        T xa[VN];
-                        ld_row<T, VN>(xr + b, xa);
-                        if (wr) {
-                            T wa[VN];
-                            ld_row<T, VN>(wr + b, wa);
-#pragma unroll
-                            for (int j = 0; j < VN; ++j) xa[j] *= wa[j];
-                        }
                         T p[VN * RB];
                         ld_row<T, VN * RB>(psi + b * RB, p);
 #pragma unroll
-                        for (int j = 0; j < VN; ++j)
+                        for (int q = 0; q < RPL; ++q) {
+                            T xa[VN];
+                            ld_row<T, VN>(xr[q] + b, xa);
+                            if (wr[q]) {
+                                T wa[VN];
+                                ld_row<T, VN>(wr[q] + b, wa);
 #pragma unroll
-                            for (int r = 0; r < RB; ++r) {
-                                if (SPLIT && (j & 1)) u1[r] = fma(xa[j], p[j * RB + r], u1[r]);
-                                else u0[r] = fma(xa[j], p[j * RB + r], u0[r]);
+                                for (int j = 0; j < VN; ++j) xa[j] *= wa[j];
                             }
+#pragma unroll
+                            for (int j = 0; j < VN; ++j)
+#pragma unroll
+                                for (int r = 0; r < RB; ++r) {
+                                    if (SPLIT && (j & 1)) u1[q][r] = fma(xa[j], p[j * RB + r], u1[q][r]);
+                                    else u0[q][r] = fma(xa[j], p[j * RB + r], u0[q][r]);
+                                }
+                        }
                     }
                 } else {
 #pragma unroll 4
                     for (int b = 0; b < IB; ++b) {
                         T p[RBP];
                         ld_row<T, RBP>(psi + b * RBP, p);
-                        T xa = xr[b];
-                        if (wr) xa *= wr[b];
 #pragma unroll
-                        for (int r = 0; r < RB; ++r) {
-                            if (SPLIT && (b & 1)) u1[r] = fma(xa, p[r], u1[r]);
-                            else u0[r] = fma(xa, p[r], u0[r]);
+                        for (int q = 0; q < RPL; ++q) {
+                            T xa = xr[q][b];
+                            if (wr[q]) xa *= wr[q][b];
+#pragma unroll
+                            for (int r = 0; r < RB; ++r) {
+                                if (SPLIT && (b & 1)) u1[q][r] = fma(xa, p[r], u1[q][r]);
+                                else u0[q][r] = fma(xa, p[r], u0[q][r]);
+                            }
                         }
                     }
                 }
+                if constexpr (SPLIT) {
 #pragma unroll
-                for (int r = 0; r < RB; ++r) u0[r] += u1[r];
-                // fold the row into z
+                    for (int q = 0; q < RPL; ++q)
+#pragma unroll
+                        for (int r = 0; r < RB; ++r) u0[q][r] += u1[q][r];
+                }
+                // fold the rows into z
                 if (foldA) {
-                    const T* ga = gA + tk.a0 + row;
 #pragma unroll
-                    for (int r2 = 0; r2 < RMAX; ++r2)
-                        if (r2 < RC) {
-                            const T c0 = va ? ga[r2 * IA] : T(0);
+                    for (int q = 0; q < RPL; ++q) {
+                        const T* ga = gA + tk.a0 + (va[q] ? lane + 32 * q : 0);
 #pragma unroll
-                            for (int r = 0; r < RB; ++r) z[r2][r] = fma(c0, u0[r], z[r2][r]);
-                        }
+                        for (int r2 = 0; r2 < ZR; ++r2)
+                            if (r2 < RC) {
+                                const T c0 = va[q] ? ga[r2 * IA] : T(0);
+#pragma unroll
+                                for (int r = 0; r < RB; ++r) z[0][r2][r] = fma(c0, u0[q][r], z[0][r2][r]);
+                            }
+                    }
                 } else if (l2 < 0) {
 #pragma unroll
-                    for (int r = 0; r < RB; ++r) z[0][r] += va ? u0[r] : T(0);
+                    for (int q = 0; q < RPL; ++q)
+#pragma unroll
+                        for (int r = 0; r < RB; ++r) z[q][0][r] += va[q] ? u0[q][r] : T(0);
                 } else {
-                    const T sc = va ? ((N == 4) ? ax[128 + lane] : T(1)) : T(0);
                     // coefficient G_{l2,k}(r2, i_l2) times the fold weight
                     const int il2 = isF ? (l2 == 0 ? i0 : i1) : (N == 4 ? i1 : i0);
                     const T* gl = gL + il2;
                     const int Il2 = s.I[l2];
 #pragma unroll
-                    for (int r2 = 0; r2 < RMAX; ++r2)
-                        if (r2 < RC) {
-                            const T c0 = gl[r2 * Il2] * sc;
+                    for (int q = 0; q < RPL; ++q) {
+                        const T sc = va[q] ? ((N == 4) ? ax[AUX_FW + (isF ? 32 * q : 0) + lane] : T(1)) : T(0);
 #pragma unroll
-                            for (int r = 0; r < RB; ++r) z[r2][r] = fma(c0, u0[r], z[r2][r]);
-                        }
+                        for (int r2 = 0; r2 < ZR; ++r2)
+                            if (r2 < RC) {
+                                const T c0 = gl[r2 * Il2] * sc;
+#pragma unroll
+                                for (int r = 0; r < RB; ++r) z[q][r2][r] = fma(c0, u0[q][r], z[q][r2][r]);
+                            }
+                    }
                 }
             }
             __syncwarp();
@@ -398,19 +435,25 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
             T* zb = tiles + (static_cast<size_t>(warp) * S + zslot) * TC;
             if (foldA) {
 #pragma unroll
-                for (int r2 = 0; r2 < RMAX; ++r2)
+                for (int r2 = 0; r2 < ZR; ++r2)
                     if (r2 < RC)
 #pragma unroll
                         for (int r = 0; r < RB; ++r) {
-                            const T v = warp_sum(z[r2][r]);
+                            const T v = warp_sum(z[0][r2][r]);
                             if (lane == 0) zb[r2 * RB + r] = v;
                         }
-            } else if (lane < nru) {
+            } else {
 #pragma unroll
-                for (int r2 = 0; r2 < RMAX; ++r2)
-                    if (r2 < RC)
+                for (int q = 0; q < RPL; ++q) {
+                    const int row = lane + 32 * q;
+                    if (row < nru) {
 #pragma unroll
-                        for (int r = 0; r < RB; ++r) zb[lane * ZW + r2 * RB + r] = z[r2][r];
+                        for (int r2 = 0; r2 < ZR; ++r2)
+                            if (r2 < RC)
+#pragma unroll
+                                for (int r = 0; r < RB; ++r) zb[row * ZW + r2 * RB + r] = z[q][r2][r];
+                    }
+                }
             }
             if (lane == 0) misc[1 + warp] = zslot;
         }
@@ -490,7 +533,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
     const T* gL = gtab + nAg;
     // per-warp ring of the W entries of a task (phi row weights at a = lane,
     // and W_{0,1}(i0, i1)), filled by cp.async at issue time
-    constexpr int AUXW = 96;
+    const int AUXW = pl.auxw;
     T* auxr = reinterpret_cast<T*>(smem + pl.off_aux) + static_cast<size_t>(warp) * S * AUXW;
 
     if (tid == 0) {
@@ -656,9 +699,9 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
     }
 }
 
-template <typename T, int R>
+template <typename T, int R, int RPL = 1, int RCT = 0>
 cudaError_t launch_roww_r(const ContractArgs<T>& a, int grid, cudaStream_t st) {
-    auto kern = k_contract_roww<T, R>;
+    auto kern = k_contract_roww<T, R, RPL, RCT>;
     cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(kern), a.pl.smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, NWARP * 32, a.pl.smem, st>>>(a);
@@ -679,6 +722,15 @@ cudaError_t launch_colw_r(const ContractArgs<T>& a, int grid, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_contract_warp(const ContractArgs<T>& a, int grid, cudaStream_t st) {
     const bool col = a.pl.kcase == CASE_COL;
+    if (!col && a.pl.rpl == 2) {  // two rows per lane: instantiated for equal ranks R_{k,B} = R_{k,l2}
+        switch (a.pl.R1) {
+            case 2: return wdev::launch_roww_r<T, 2, 2, 2>(a, grid, st);
+            case 3: return wdev::launch_roww_r<T, 3, 2, 3>(a, grid, st);
+            case 4: return wdev::launch_roww_r<T, 4, 2, 4>(a, grid, st);
+            case 5: return wdev::launch_roww_r<T, 5, 2, 5>(a, grid, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (a.pl.R1) {
 #define IFCTN_CASE(R) \
     case R:           \

@@ -82,6 +82,8 @@ struct ContractPlan {
     int grid;        // CTAs (one per SM)
     int off_tile, off_tab, off_gtab, off_wab, off_zs, off_aux;  // shared-memory carve-up (bytes)
     int fin_div, fin_mod;  // > 0: the units covering output row r are r / fin_div + n * fin_mod
+    int auxw;        // warp kernels: elements of a warp's per-stage ring slot of W entries
+    int rpl;         // ROW warp kernel: rows per lane (1, or 2 for tasks of up to 64 rows)
     long long part_elems;
 };
 

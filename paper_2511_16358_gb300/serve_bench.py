@@ -110,6 +110,7 @@ def run(args) -> dict:
     del x, m
 
     pending = {}  # ticket -> (request, bytes)
+    refused = []  # requests refused at submit (a job larger than the budget)
     done_at, server_lat, lag = {}, [], []
     held = 0
     cap = args.pinned_cap_gb * (1 << 30)
@@ -142,7 +143,14 @@ def run(args) -> dict:
                               seed=rq["seed"])
         ts = time.perf_counter()
         lag.append(ts - t0 - rq["t"])
-        tk = b.submit(srv, prob, x, m, None)
+        try:
+            tk = b.submit(srv, prob, x, m, None)
+        except b.IfctnError as e:
+            if e.status != b.ENOMEM:
+                raise
+            refused.append(rq["i"])  # larger than the whole budget: refused at submit
+            del x, m
+            continue
         nb = x.numel() * 9
         pending[tk] = (rq, nb, ts)
         held += nb
@@ -154,22 +162,25 @@ def run(args) -> dict:
     info = b.server_info_get(srv)
     b.server_destroy(srv)
 
-    lat = np.array([done_at[rq["i"]] - t0 - rq["t"] for rq in reqs])
+    served = [rq for rq in reqs if rq["i"] in done_at]
+    lat = np.array([done_at[rq["i"]] - t0 - rq["t"] for rq in served])
     slat = np.array(server_lat)
     span = max(done_at.values()) - t0  # first arrival (t = 0) to last completion
     del t_end
-    sweeps_total = sum(rq["sweeps"] for rq in reqs)
+    sweeps_total = sum(rq["sweeps"] for rq in served)
     entries = np.array([float(np.prod(rq["dims"])) for rq in reqs])
     line = {
         "metric": "served completion latency (p50/p99)",
         "unit": "s",
         "requests": len(reqs),
+        "served": len(served),
+        "refused_larger_than_budget": len(refused),
         "rate_req_s": args.rate,
         "latency_from_arrival_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                    "max": float(lat.max())},
         "server_latency_s": {"p50": float(np.percentile(slat, 50)), "p99": float(np.percentile(slat, 99))},
         "client_submit_lag_s": {"p50": float(np.percentile(lag, 50)), "max": float(np.max(lag))},
-        "jobs_per_s": len(reqs) / span,
+        "jobs_per_s": len(served) / span,
         "sweeps_per_s": sweeps_total / span,
         "span_s": span,
         "peak_resident": int(info["peak_resident"]),

@@ -15,9 +15,10 @@ Algorithm 1) -- and the two results are compared.
   two-float residual.  The error against the FP64 solve of the same FP64
   systems is then set by the FP32 assembly: about Q_k FP32 roundings per
   entry of H and b (relative 2^-24 each) amplified by the condition number of
-  H + rho I (at most (lambda_max + rho) / rho).  The bound asserted, 2e-4, is
-  what that estimate gives for these shapes with a margin; the measured value
-  is printed so the stated error can be read off a run.
+  H + rho I (at most (lambda_max + rho) / rho).  Measured on a GB300: 2.2e-7
+  (order 3) and 1.2e-7 (order 4); the bound asserted, 2e-6, leaves a factor of
+  ten.  The measured value is printed so the stated error can be read off a
+  run.
 """
 import numpy as np
 import pytest
@@ -46,7 +47,7 @@ def _host_solves(dims, R, G, Mk, Kk, k, rho):
     return G
 
 
-@pytest.mark.parametrize("precision,tol", [(b.FP64, 1e-12), (b.MIXED, 2e-4)])
+@pytest.mark.parametrize("precision,tol", [(b.FP64, 1e-12), (b.MIXED, 2e-6)])
 @pytest.mark.parametrize("dims,edge", [
     ((40, 36, 30), 4),
     ((14, 12, 10, 9), {(0, 1): 3, (0, 2): 4, (0, 3): 2, (1, 2): 3, (1, 3): 4, (2, 3): 2}),

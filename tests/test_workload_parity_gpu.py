@@ -98,3 +98,48 @@ def test_traffic_one_fp64_sweep_on_the_graph_path_matches_oracle():
     c.close()
     assert rel_err(Xg, X1) < 1e-10
     np.testing.assert_array_equal(Xg[mask.astype(bool)], X0[mask.astype(bool)])
+
+
+@pytest.mark.parametrize("dims,edge", [
+    ((6, 7, 3, 100), {(0, 1): 4, (0, 3): 4, (1, 3): 4, (0, 2): 3, (1, 2): 3, (2, 3): 3}),
+    ((9, 5, 70), {(0, 1): 3, (0, 2): 5, (1, 2): 2}),
+    ((5, 6, 4, 133), 2),
+])
+def test_graph_path_long_contiguous_mode_one_sweep_matches_oracle(dims, edge):
+    """Contiguous modes longer than two warps (64): every lane of the streaming
+    contraction covers several columns of the coefficient table."""
+    from tests._cases import make_case
+    case = make_case(dims, edge, 0.3, seed=451, kind="max1", sigma=0.02)
+    with path("graph"):
+        c = b.Completion(dims, case["R"], case["xt"], case["mask"], rho=0.1, max_sweeps=1, tol=0.0,
+                         precision=b.FP64, init_factors=case["G0"].copy())
+    c.sweep(1)
+    G1, X1 = case["G0"].copy(), case["X0"].copy()
+    oracle.sweep(dims, case["R"], 0.1, G1, X1, case["mask"])
+    assert rel_err(c.factors(), G1) < 1e-10
+    assert rel_err(c.x(), X1) < 1e-10
+    c.close()
+
+
+@pytest.mark.parametrize("rows_per_lane", ["1", "2"])
+@pytest.mark.parametrize("dims,edge", [
+    ((7, 6, 50, 12), 3),
+    ((5, 9, 61, 8), 5),
+    ((6, 5, 40, 16), {(0, 1): 4, (0, 2): 2, (0, 3): 4, (1, 2): 4, (1, 3): 4, (2, 3): 4}),
+])
+def test_graph_path_two_rows_per_lane_one_sweep_matches_oracle(dims, edge, rows_per_lane, monkeypatch):
+    """The streaming contraction of the modes k < N - 1 with one row per lane
+    and with two (tasks of up to 64 rows; used for order 4, R_{k,B} = R_{k,l2}
+    and more than 32 rows): one FP64 sweep equals the oracle's."""
+    from tests._cases import make_case
+    monkeypatch.setenv("IFCTN_CW_RPL", rows_per_lane)
+    case = make_case(dims, edge, 0.3, seed=461, kind="max1", sigma=0.02)
+    with path("graph"):
+        c = b.Completion(dims, case["R"], case["xt"], case["mask"], rho=0.1, max_sweeps=2, tol=0.0,
+                         precision=b.FP64, init_factors=case["G0"].copy())
+    c.sweep(2)
+    G1, X1 = case["G0"].copy(), case["X0"].copy()
+    oracle.complete(dims, case["R"], 0.1, G1, X1, case["mask"], max_sweeps=2)
+    assert rel_err(c.factors(), G1) < 1e-10
+    assert rel_err(c.x(), X1) < 1e-10
+    c.close()
