@@ -164,6 +164,31 @@ ifctn_status ifctn_launch_stage(ifctn_ctx* ctx, int32_t stage, int32_t k);
    budget out of range. */
 ifctn_status ifctn_wait_selftest(ifctn_ctx* ctx, int64_t budget_cycles);
 
+/* Autotuning of the streaming contraction (no counterpart in the paper: it
+   picks launch shapes for this GPU).  For every mode whose contraction runs
+   the warp-pipelined HBM-streaming kernels, the planner leaves four choices
+   open: two rows per lane or one, the ring stages per warp, the task size and
+   the grouping of slabs into work units.  This call takes each mode's choice
+   from the cache file at cache_path (nullable) when the file holds the key
+   (library source digest, dtype, shape, ranks, mode, SM count); otherwise it
+   times the distinct candidate plans on the context's stream (CUDA events,
+   the median of five launches of the contraction, on the context's own
+   tensor), keeps the fastest by the rule of ifctn_tune_choose, and appends
+   the choice to the cache.  The results of the sweep do not depend on the
+   choice beyond the order of floating-point sums within a mode's partials.
+   *timed (nullable) receives the number of candidate plans timed (0 when the
+   cache answered every mode).  Contexts created while the environment
+   variable IFCTN_TUNE_CACHE names a file tune themselves this way at
+   creation.  Contexts whose sweeps run as one persistent launch have no
+   choices to make (*timed = 0). */
+ifctn_status ifctn_tune(ifctn_ctx* ctx, const char* cache_path, int32_t* timed);
+
+/* The tuner's selection rule, exposed for callers that time candidates
+   themselves: given n > 0 timings with the planner's default first, returns
+   the index of the fastest, or 0 unless the fastest beats the default by 2 %
+   or more; -1 for n <= 0 or a null array.  Host only. */
+int32_t ifctn_tune_choose(int32_t n, const double* seconds);
+
 /* Number of kernel launches one sweep issues when sweeps run as a CUDA graph
    of per-stage kernels (for launch accounting). */
 int32_t ifctn_kernels_per_sweep(const ifctn_ctx* ctx);

@@ -40,6 +40,24 @@ def _includes(path, seen):
                 _includes(dep, seen)
 
 
+def _sources_digest() -> str:
+    """Digest of every library source and the public header (the tuning
+    cache keys carry it, so a changed library never reuses stale choices)."""
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    with open(os.path.join(ROOT, "include", "ifctn.h"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _tu_flags(src):
+    if src == "ifctn_api.cu":
+        return [f'-DIFCTN_SOURCE_DIGEST="{_sources_digest()}"']
+    return []
+
+
 def _tu_digest(src) -> str:
     """Digest of one translation unit: its source, every in-tree header it
     includes and the compiler flags."""
@@ -49,7 +67,7 @@ def _tu_digest(src) -> str:
     for path in sorted(seen):
         with open(path, "rb") as f:
             h.update(os.path.relpath(path, ROOT).encode() + f.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(" ".join(ARCH + FLAGS + _tu_flags(src)).encode())
     return h.hexdigest()
 
 
@@ -80,7 +98,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             with open(ostamp) as f:
                 if f.read().strip() == d:
                     return obj
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *_tu_flags(src), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

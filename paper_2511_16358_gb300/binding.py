@@ -30,6 +30,7 @@ EXPORTED = [
     "ifctn_submit", "ifctn_poll", "ifctn_server_info_get", "ifctn_server_latency",
     "ifctn_server_destroy", "ifctn_last_error", "ifctn_sweep_async", "ifctn_launch_stage",
     "ifctn_launch_count", "ifctn_phase_times", "ifctn_reconstruct_noalloc", "ifctn_wait_selftest",
+    "ifctn_tune", "ifctn_tune_choose",
 ]
 
 
@@ -100,6 +101,8 @@ def load(path: str | None = None):
         "ifctn_phase_times": (i32, [vp, P(dp), i32, P(i32)]),
         "ifctn_reconstruct_noalloc": (i32, [i32, P(i64), P(i32), i32, vp, vp, vp]),
         "ifctn_wait_selftest": (i32, [vp, i64]),
+        "ifctn_tune": (i32, [vp, ctypes.c_char_p, P(i32)]),
+        "ifctn_tune_choose": (i32, [i32, P(dp)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -228,6 +231,20 @@ def wait_selftest(ctx, budget_cycles):
     """Runs the library's bounded device waits on conditions nothing satisfies;
     returns the status (IFCTN_ETIMEOUT when the waits expired as designed)."""
     return int(load().ifctn_wait_selftest(ctx, int(budget_cycles)))
+
+
+def tune(ctx, cache_path=None) -> int:
+    """Autotunes the streaming contraction's launch shapes (cache_path: the
+    tuning cache file, or None); returns the number of candidate plans timed."""
+    n = ctypes.c_int32(0)
+    _check(load().ifctn_tune(ctx, None if cache_path is None else str(cache_path).encode(), ctypes.byref(n)))
+    return n.value
+
+
+def tune_choose(seconds) -> int:
+    """The tuner's selection rule on a list of timings (default first)."""
+    a = (ctypes.c_double * max(len(seconds), 1))(*[float(x) for x in seconds])
+    return int(load().ifctn_tune_choose(len(seconds), a))
 
 
 def kernels_per_sweep(ctx) -> int:

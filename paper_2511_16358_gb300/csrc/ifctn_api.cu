@@ -494,9 +494,16 @@ bool rows_per_lane_allowed() {
     return !(e && strcmp(e, "1") == 0);
 }
 
+WarpKnobs default_warp_knobs() {
+    WarpKnobs kn;
+    kn.rpl = rows_per_lane_allowed() ? 1 : 0;
+    return kn;
+}
+
 ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitDesc>& units,
-                                bool rpl_allowed) {
-    constexpr int NW = 16;
+                                const WarpKnobs& kn) {
+    const bool rpl_allowed = kn.rpl != 0;
+    int NW = 16;  // warps of a CTA (12 for the COL kernel with tasks of up to 64 rows)
     ContractPlan pl;
     memset(&pl, 0, sizeof(pl));
     const int N = s.N, Am = N - 2, Bm = N - 1, IA = s.IA, IB = s.IB;
@@ -505,7 +512,7 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
     // work units: enough for balance; where the partials are kept per unit
     // (CASE_A, COL) fewer, since the finisher sums over them
     const int target = (k < N - 2) ? 8 * sms : 4 * sms;
-    const int XBYTES = 4 * 1024;  // at most this many X bytes in one task (per warp, per stage)
+    const int XBYTES = kn.xbytes;  // at most this many X bytes in a one-row-per-lane task
     // rows per task: at most cap, split evenly
     auto balanced = [](int rows, int cap) {
         cap = std::max(1, std::min(rows, cap));
@@ -548,15 +555,26 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
         const int nbc = cdiv(IB, 32);
         pl.vec = 0;
         pl.ldx = IB;
-        // a lane builds one row of the coefficient table: at most 32 rows a task
-        const int RBK = balanced(IA, std::min(32, std::max(1, XBYTES / (sz * IB))));
+        // a lane builds one row of the coefficient table: at most 32 rows a task,
+        // or 64 (two rows a lane, 12 warps so that their rings fit) when the
+        // rows are short enough (IFCTN_CW_RPL=1 keeps 32)
+        int RBK = balanced(IA, std::min(32, std::max(1, XBYTES / (sz * IB))));
+        pl.rpl = 1;
+        if (rpl_allowed) {
+            const int RBK2 = balanced(IA, std::min(64, std::max(1, 2 * XBYTES / (sz * IB))));
+            if (RBK2 > 32) {
+                RBK = RBK2;
+                pl.rpl = 2;
+                NW = 12;
+            }
+        }
         pl.TAc = RBK;
         const int nrb = cdiv(IA, RBK);
         if (N == 4) {
             const int I0 = s.I[0], I1 = s.I[1];
             int nC = std::max(1, std::min(std::min(cdiv(target, static_cast<long long>(I0) * nbc),
                                                    std::max(1, I1 * nrb / NW)), I1));
-            nC = warp_unit_chunks(I1, nrb, static_cast<long long>(I0) * nbc, nC, NW, sms);
+            if (kn.chunking == 0) nC = warp_unit_chunks(I1, nrb, static_cast<long long>(I0) * nbc, nC, NW, sms);
             for (int i0 = 0; i0 < I0; ++i0)
                 for (int c = 0; c < nC; ++c)
                     for (int bc = 0; bc < nbc; ++bc) {
@@ -591,7 +609,7 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
         pl.fin_div = 32;  // units covering column b: b / 32, b / 32 + nbc, ...
         pl.fin_mod = nbc;
         xregion = round_up(RBK * IB + 32 / sz, VN);
-        tab_elems = static_cast<long long>(NW) * (32 + VN) * pl.R1;
+        tab_elems = static_cast<long long>(NW) * (32 * pl.rpl + VN) * pl.R1;
         gtab_elems = static_cast<long long>(pl.R1) * IA + (pl.l2 >= 0 ? static_cast<long long>(pl.Rl2) * s.I[pl.l2] : 0);
         zmin = 32LL * pl.zw;
         pl.aux_slot = 0;
@@ -671,7 +689,7 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
         if (isF && N == 4) {
             const int o = 1 - k, Io = s.I[o], Ik = s.I[k], I1 = s.I[1];
             int nOC = std::max(1, std::min(cdiv(target, static_cast<long long>(Ik) * nrc), std::max(1, Io / NW)));
-            nOC = warp_unit_chunks(Io, 1, static_cast<long long>(Ik) * nrc, nOC, NW, sms);
+            if (kn.chunking == 0) nOC = warp_unit_chunks(Io, 1, static_cast<long long>(Ik) * nrc, nOC, NW, sms);
             for (int j = 0; j < Ik; ++j)
                 for (int oc = 0; oc < nOC; ++oc)
                     for (int rc = 0; rc < nrc; ++rc) {
@@ -702,7 +720,7 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
         } else if (N == 4) {
             const int I0 = s.I[0], I1 = s.I[1];
             int nC = std::max(1, std::min(cdiv(target, static_cast<long long>(I0) * nrc), std::max(1, I1 / NW)));
-            nC = warp_unit_chunks(I1, 1, static_cast<long long>(I0) * nrc, nC, NW, sms);
+            if (kn.chunking == 0) nC = warp_unit_chunks(I1, 1, static_cast<long long>(I0) * nrc, nC, NW, sms);
             for (int i0 = 0; i0 < I0; ++i0)
                 for (int c = 0; c < nC; ++c)
                     for (int rc = 0; rc < nrc; ++rc) {
@@ -747,17 +765,19 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
     pl.sub_elems = static_cast<int>(tc);
     auto r128 = [](long long b) { return (b + 127) / 128 * 128; };
     const long long limit = 225 * 1024;
-    // per-warp ring of a task's W entries (cp.async), elements a stage: COL 96
-    // (row weights of two F modes, W_{0,1}(i0, i1)); ROW one row W_{p,B}(i_p, :)
+    // per-warp ring of a task's W entries (cp.async), elements a stage: COL the
+    // row weights of two F modes (32 or 64 rows each), W_{0,1}(i0, i1); ROW one row W_{p,B}(i_p, :)
     // (two for N = 4, k = 2) padded to whole warps, then the fold weights of up
     // to 32 rows per lane row
-    const long long auxw = (k == Bm) ? 96 : (N == 4 && k == 2 ? 2LL : 1LL) * round_up(IB, 32) + 32LL * std::max(1, pl.rpl);
+    const long long auxw = (k == Bm) ? 64LL * std::max(1, pl.rpl) + 32
+                                     : (N == 4 && k == 2 ? 2LL : 1LL) * round_up(IB, 32) + 32LL * std::max(1, pl.rpl);
     pl.auxw = static_cast<int>(auxw);
     // with two rows per lane the unit-end sums (zs) share the per-warp
     // coefficient tables' space: those are rewritten only by the next unit's
     // tasks, after the unit end's last CTA barrier
     const bool zs_in_tab = pl.rpl == 2 && zs_elems <= tab_elems;
     for (int S = 4; S >= 2; --S) {
+        if (kn.stages > 0 && S != kn.stages) continue;
         const long long off_tile = 640;
         const long long off_tab = off_tile + r128(static_cast<long long>(NW) * S * tc * sz);
         const long long off_gtab = off_tab + r128(tab_elems * sz);
@@ -778,7 +798,12 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
             break;
         }
     }
-    if (!pl.warp && pl.rpl == 2) return plan_contract_warp(s, k, sz, units, false);
+    pl.nwarp = NW;
+    if (!pl.warp && pl.rpl == 2) {
+        WarpKnobs k1 = kn;
+        k1.rpl = 0;
+        return plan_contract_warp(s, k, sz, units, k1);
+    }
     pl.grid = std::max(1, std::min(pl.nunits, sms));
     if (!pl.warp) units.clear();
     return pl;
@@ -823,6 +848,7 @@ struct ifctn_ctx {
     virtual ifctn_status enqueue(int n, double tol, bool reset) = 0;
     virtual ifctn_status launch_stage(int stage, int k) = 0;
     virtual ifctn_status wait_selftest(long long budget) = 0;
+    virtual ifctn_status tune(const char* path, int* ntimed) = 0;
     virtual long long launch_total() const = 0;
     virtual ifctn_status phase_times(double* out, int max, int* n) = 0;
     virtual void set_grid_cap(int g) = 0;
@@ -839,6 +865,22 @@ bool choose_graph_only(const Shape& sh, int sz) {
     if (e && strcmp(e, "graph") == 0) return true;
     if (e && strcmp(e, "persistent") == 0) return false;
     return sh.P * static_cast<long long>(sz) > L2_RESIDENT_BYTES;
+}
+
+#ifndef IFCTN_SOURCE_DIGEST
+#define IFCTN_SOURCE_DIGEST "unversioned"
+#endif
+
+// The autotuner's selection rule: the fastest candidate, except that the
+// planner's default (candidate 0) is kept unless the fastest beats it by 2 %
+// or more (timings of nearly equal shapes differ by noise, and the default
+// is what every other context of the shape runs when no cache is used).
+int tune_choose(int n, const double* secs) {
+    if (n <= 0) return -1;
+    int best = 0;
+    for (int i = 1; i < n; ++i)
+        if (secs[i] < secs[best]) best = i;
+    return secs[best] <= 0.98 * secs[0] ? best : 0;
 }
 
 template <typename T>
@@ -931,7 +973,7 @@ struct Engine : ifctn_ctx {
         for (int k = 0; k < sh.N; ++k) {
             std::vector<UnitDesc> u;
             plan[k].warp = 0;
-            if (graph_only) plan[k] = plan_contract_warp(sh, k, sz, u, rows_per_lane_allowed());
+            if (graph_only) plan[k] = plan_contract_warp(sh, k, sz, u, default_warp_knobs());
             if (!plan[k].warp) plan[k] = plan_contract(sh, k, sz, u);
             if (plan[k].smem > SMEM_LIMIT && !plan[k].warp) {
                 set_error("tensor shape needs more shared memory than available");
@@ -1018,6 +1060,202 @@ struct Engine : ifctn_ctx {
         if (rs != IFCTN_OK) return rs;
         CK(cudaStreamSynchronize(st));
         setup_persistent();
+        // launch shapes from the tuning cache named by IFCTN_TUNE_CACHE (timed
+        // and added to it where the cache has no entry for this shape)
+        if (const char* path = getenv("IFCTN_TUNE_CACHE")) {
+            if (*path && graph_only) {
+                rs = tune(path, nullptr);
+                if (rs != IFCTN_OK) return rs;
+                return IFCTN_OK;  // tune() rebuilt the graph
+            }
+        }
+        return build_graph();
+    }
+
+    // ---- autotuning of the streaming contraction's launch shape ----------
+    // Key of mode k of this problem in the tuning cache: the library's source
+    // digest, the dtype, the shape and ranks, the mode and the SM count.
+    std::string tune_key(int k) const {
+        std::string key = std::string("ifctn-tune-v1 ") + IFCTN_SOURCE_DIGEST + (sizeof(T) == 4 ? " f32 " : " f64 ");
+        key += "N" + std::to_string(sh.N);
+        for (int m = 0; m < sh.N; ++m) key += "," + std::to_string(sh.I[m]);
+        key += " R";
+        for (int p2 = 0; p2 < sh.N; ++p2)
+            for (int q = p2 + 1; q < sh.N; ++q) key += std::to_string(sh.R[p2][q]) + ".";
+        key += " k" + std::to_string(k) + " sms" + std::to_string(num_sms());
+        return key;
+    }
+
+    // Device seconds of one launch of the mode-k contraction with plan pl and
+    // units u (the median of 5 launches after one warm-up, CUDA events on the
+    // context's stream); unit descriptors and partials in scratch buffers.
+    ifctn_status time_contract(int k, const ContractPlan& pl, const std::vector<UnitDesc>& u, double* sec) {
+        DevBuf<UnitDesc> du;
+        DevBuf<T> dp;
+        if (du.alloc(u.size()) != cudaSuccess || dp.alloc(std::max<long long>(pl.part_elems, 1)) != cudaSuccess) {
+            du.release();
+            dp.release();
+            cudaGetLastError();
+            set_error("device allocation failed while tuning");
+            return IFCTN_ENOMEM;
+        }
+        ContractArgs<T> a = cargs(k);
+        a.pl = pl;
+        a.units = du.p;
+        a.part = dp.p;
+        cudaEvent_t e[6];
+        for (auto& ev : e) cudaEventCreate(&ev);
+        cudaError_t err = cudaMemcpyAsync(du.p, u.data(), u.size() * sizeof(UnitDesc), cudaMemcpyHostToDevice, st);
+        if (err == cudaSuccess) err = launch_contract<T>(a, st);
+        for (int i = 0; i < 5 && err == cudaSuccess; ++i) {
+            err = cudaEventRecord(e[i], st);
+            if (err == cudaSuccess) err = launch_contract<T>(a, st);
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(e[5], st);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+        std::vector<double> t;
+        for (int i = 0; i < 5 && err == cudaSuccess; ++i) {
+            float ms = 0.f;
+            err = cudaEventElapsedTime(&ms, e[i], e[i + 1]);
+            t.push_back(1e-3 * ms);
+        }
+        for (auto& ev : e) cudaEventDestroy(ev);
+        du.release();
+        dp.release();
+        if (err != cudaSuccess) {
+            set_error(std::string("tuning launch failed: ") + cudaGetErrorString(err));
+            return IFCTN_ECUDA;
+        }
+        std::sort(t.begin(), t.end());
+        *sec = t[t.size() / 2];
+        return IFCTN_OK;
+    }
+
+    // For every mode whose contraction runs the warp-pipelined kernels: takes
+    // the launch shape from the cache at `path` (nullable) when it holds this
+    // key, else times the planner's candidates (rows per lane, ring stages,
+    // task size, unit chunking), keeps the fastest by the rule of
+    // tune_choose(), and appends it to the cache.  Then re-lays the unit
+    // descriptors and rebuilds the sweep graph.
+    ifctn_status tune(const char* path, int* ntimed) {
+        int timed = 0;
+        std::vector<std::string> lines;
+        if (path && *path) {
+            if (FILE* f = fopen(path, "r")) {
+                char buf[1024];
+                while (fgets(buf, sizeof(buf), f)) lines.emplace_back(buf);
+                fclose(f);
+            }
+        }
+        const int sz = sizeof(T);
+        CK(cudaMemsetAsync(done(), 0, sizeof(int), st));
+        std::vector<UnitDesc> all;
+        long long maxpart = 1;
+        ContractPlan np[MAXN];
+        int noff[MAXN] = {};
+        for (int k = 0; k < sh.N; ++k) {
+            std::vector<UnitDesc> u;
+            np[k] = plan[k];
+            if (plan[k].warp) {
+                const std::string key = tune_key(k);
+                WarpKnobs chosen = default_warp_knobs();
+                bool cached = false;
+                for (const std::string& ln : lines) {
+                    if (ln.compare(0, key.size(), key) == 0 && ln.size() > key.size() && ln[key.size()] == ' ') {
+                        int v[4];
+                        if (sscanf(ln.c_str() + key.size(), " rpl=%d stages=%d xbytes=%d chunking=%d", &v[0], &v[1],
+                                   &v[2], &v[3]) == 4) {
+                            chosen.rpl = v[0];
+                            chosen.stages = v[1];
+                            chosen.xbytes = v[2];
+                            chosen.chunking = v[3];
+                            cached = true;
+                        }
+                    }
+                }
+                if (!cached) {
+                    std::vector<WarpKnobs> cands(1, default_warp_knobs());
+                    for (int rpl : {1, 0})
+                        for (int stg : {0, 2, 3})
+                            for (int xb : {4096, 2048, 8192})
+                                for (int ch : {0, 1}) {
+                                    WarpKnobs w;
+                                    w.rpl = rpl;
+                                    w.stages = stg;
+                                    w.xbytes = xb;
+                                    w.chunking = ch;
+                                    cands.push_back(w);
+                                }
+                    std::vector<ContractPlan> cp;
+                    std::vector<std::vector<UnitDesc>> cu;
+                    std::vector<double> secs;
+                    std::vector<int> which;
+                    for (size_t c = 0; c < cands.size(); ++c) {
+                        std::vector<UnitDesc> uc;
+                        ContractPlan pc = plan_contract_warp(sh, k, sz, uc, cands[c]);
+                        if (!pc.warp) continue;
+                        bool dup = false;  // the same plan and units as a candidate timed already
+                        for (size_t j = 0; j < cp.size() && !dup; ++j)
+                            dup = memcmp(&cp[j], &pc, sizeof(pc)) == 0 && cu[j].size() == uc.size() &&
+                                  memcmp(cu[j].data(), uc.data(), uc.size() * sizeof(UnitDesc)) == 0;
+                        if (dup) continue;
+                        double t = 0;
+                        ifctn_status rs = time_contract(k, pc, uc, &t);
+                        if (rs != IFCTN_OK) return rs;
+                        ++timed;
+                        cp.push_back(pc);
+                        cu.push_back(uc);
+                        secs.push_back(t);
+                        which.push_back(static_cast<int>(c));
+                    }
+                    const int pick = which.empty() ? 0 : which[tune_choose(static_cast<int>(secs.size()), secs.data())];
+                    chosen = cands[pick];
+                    if (path && *path && !which.empty()) {
+                        if (FILE* f = fopen(path, "a")) {
+                            const int pi = tune_choose(static_cast<int>(secs.size()), secs.data());
+                            fprintf(f, "%s rpl=%d stages=%d xbytes=%d chunking=%d seconds=%.9g default_seconds=%.9g\n",
+                                    key.c_str(), chosen.rpl, chosen.stages, chosen.xbytes, chosen.chunking, secs[pi],
+                                    secs[0]);
+                            fclose(f);
+                        }
+                    }
+                }
+                np[k] = plan_contract_warp(sh, k, sz, u, chosen);
+                if (!np[k].warp) np[k] = plan_contract(sh, k, sz, u);
+            } else {
+                np[k] = plan_contract(sh, k, sz, u);
+            }
+            noff[k] = static_cast<int>(all.size());
+            all.insert(all.end(), u.begin(), u.end());
+            maxpart = std::max(maxpart, np[k].part_elems);
+        }
+        CK(cudaStreamSynchronize(st));
+        if (all.size() > units.n) {
+            units.release();
+            if (units.alloc(all.size()) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("device allocation failed");
+                return IFCTN_ENOMEM;
+            }
+        }
+        if (static_cast<size_t>(maxpart) > part.n) {
+            part.release();
+            if (part.alloc(maxpart) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("device allocation failed");
+                return IFCTN_ENOMEM;
+            }
+        }
+        CK(cudaMemcpyAsync(units.p, all.data(), all.size() * sizeof(UnitDesc), cudaMemcpyHostToDevice, st));
+        for (int k = 0; k < sh.N; ++k) {
+            plan[k] = np[k];
+            unit_off[k] = noff[k];
+            pp.pl[k] = plan[k];
+            pp.units[k] = units.p + unit_off[k];
+        }
+        pp.part = part.p;
+        CK(cudaStreamSynchronize(st));
+        if (ntimed) *ntimed = timed;
         return build_graph();
     }
 
@@ -1113,8 +1351,11 @@ struct Engine : ifctn_ctx {
             const long long target_units = 2LL * num_sms();
             const long long rows_total = static_cast<long long>(sh.nF) * sh.IA;
             long long rows = std::max<long long>(1, rows_total / target_units);
+            // IFCTN_XU_ENTRIES overrides the 16K-entry cap (timing and tuning)
+            long long cap = 16384;
+            if (const char* e = getenv("IFCTN_XU_ENTRIES")) cap = std::max(1024LL, atoll(e));
             rows = std::max<long long>(rows, std::max(1, 2048 / sh.IB));
-            rows = std::min<long long>(rows, std::max(1, 16384 / sh.IB));
+            rows = std::min<long long>(rows, std::max<long long>(1, cap / sh.IB));
             rows = std::min<long long>(rows, rows_total);
             pp.xu_rows = static_cast<int>(std::max<long long>(rows, 1));
             pp.xu_wab_smem = static_cast<long long>(sh.IA) * sh.IB * sizeof(T) <= 64 * 1024 ? 1 : 0;
@@ -1616,6 +1857,20 @@ ifctn_status ifctn_sweep_async(ifctn_ctx* ctx, int32_t n) {
 }
 ifctn_status ifctn_launch_stage(ifctn_ctx* ctx, int32_t stage, int32_t k) {
     IFCTN_CTX_CALL(ctx, launch_stage(stage, k));
+}
+ifctn_status ifctn_tune(ifctn_ctx* ctx, const char* cache_path, int32_t* timed) {
+    int t = 0;
+    if (!ctx) {
+        set_error("null context");
+        return IFCTN_EINVAL;
+    }
+    const ifctn_status rs = ctx->tune(cache_path, &t);
+    if (timed) *timed = t;
+    return rs;
+}
+int32_t ifctn_tune_choose(int32_t n, const double* seconds) {
+    if (n <= 0 || !seconds) return -1;
+    return ifctn::tune_choose(n, seconds);
 }
 ifctn_status ifctn_wait_selftest(ifctn_ctx* ctx, int64_t budget_cycles) {
     if (budget_cycles < 1000 || budget_cycles > ifctn::WAIT_BUDGET_CYCLES) {

@@ -142,8 +142,8 @@ __device__ __forceinline__ Task task_at(const UnitCur& c, int t, int rbk) {
 // work per coefficient-table load and per task overhead); RCT the rank of the
 // register fold when fixed at compile time (0: any, up to RMAX; the z
 // registers are then sized for RMAX).
-template <typename T, int RB, int RPL, int RCT>
-__global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_constant__ ContractArgs<T> A) {
+template <typename T, int RB, int RPL, int RCT, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_constant__ ContractArgs<T> A) {
     static_assert(RPL == 1 || RPL == 2, "one or two rows per lane");
     if (*A.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
     const T* gA = gtab + nB + nL;
 
     if (tid == 0) {
-        for (int i = 0; i < NWARP * S; ++i) mbar_init(&bars[i], 1);
+        for (int i = 0; i < NW * S; ++i) mbar_init(&bars[i], 1);
         misc[0] = 0;
         fence_mbar_init();
     }
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
             bulk_g2s(buf, reinterpret_cast<const void*>(xlo), static_cast<unsigned>(xhi - xlo), bar);
             if (foldA) bulk_g2s(buf + XR, reinterpret_cast<const void*>(wlo), static_cast<unsigned>(whi - wlo), bar);
         }
-        ct += NWARP;
+        ct += NW;
         settle();
     };
     ic.ui = blockIdx.x;
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
                 for (int r = 0; r < RB; ++r) z[q][r2][r] = T(0);
 
         int zslot = -1;
-        for (int t = warp; t < nt; t += NWARP, ++it) {
+        for (int t = warp; t < nt; t += NW, ++it) {
             const int st = it % S;
             const unsigned par = static_cast<unsigned>((it / S) & 1);
             T* buf = tiles + (static_cast<size_t>(warp) * S + st) * TC;
@@ -423,14 +423,14 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
                 }
             }
             __syncwarp();
-            if (t + NWARP < nt) {
+            if (t + NW < nt) {
                 issue_next(st);  // the stage is free again
             } else {
                 zslot = st;  // keeps z for the unit reduction; refilled after it
             }
         }
         // ---- unit end: reduce over warps (fixed order) ----
-        const int nwk = min(NWARP, nt);
+        const int nwk = min(NW, nt);
         if (zslot >= 0) {
             T* zb = tiles + (static_cast<size_t>(warp) * S + zslot) * TC;
             if (foldA) {
@@ -505,8 +505,8 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_roww(const __grid_co
 // G_{0,k}(r2, i0)).
 // ---------------------------------------------------------------------------
 
-template <typename T, int RA>
-__global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_constant__ ContractArgs<T> A) {
+template <typename T, int RA, int RPL, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) k_contract_colw(const __grid_constant__ ContractArgs<T> A) {
     if (*A.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int VN = 16 / static_cast<int>(sizeof(T));
@@ -524,20 +524,23 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
     int* misc = reinterpret_cast<int*>(smem + MISC_OFF);
     volatile int* abortf = misc;
     T* tiles = reinterpret_cast<T*>(smem + pl.off_tile);
-    // phi rows of a task, RA values each, padded to a multiple of VN rows
-    T* phi = reinterpret_cast<T*>(smem + pl.off_tab) + static_cast<size_t>(warp) * (32 + VN) * RA;
+    // phi rows of a task (up to 32 RPL, lane-owned: a = lane + 32 q), RA values
+    // each, plus VN zero rows of padding
+    constexpr int PR = 32 * RPL;
+    T* phi = reinterpret_cast<T*>(smem + pl.off_tab) + static_cast<size_t>(warp) * (PR + VN) * RA;
     T* gtab = reinterpret_cast<T*>(smem + pl.off_gtab);
     const int nAg = pl.R1 * IA;
     const int nL = l2 >= 0 ? RC * s.I[l2] : 0;
     const T* gAt = gtab;
     const T* gL = gtab + nAg;
-    // per-warp ring of the W entries of a task (phi row weights at a = lane,
-    // and W_{0,1}(i0, i1)), filled by cp.async at issue time
+    // per-warp ring of the W entries of a task (phi row weights W_{0,A}(i0, a)
+    // at [0, PR) and W_{1,A}(i1, a) at [PR, 2 PR), a = lane + 32 q; W_{0,1}(i0,
+    // i1) at [2 PR, 2 PR + 32)), filled by cp.async at issue time
     const int AUXW = pl.auxw;
     T* auxr = reinterpret_cast<T*>(smem + pl.off_aux) + static_cast<size_t>(warp) * S * AUXW;
 
     if (tid == 0) {
-        for (int i = 0; i < NWARP * S; ++i) mbar_init(&bars[i], 1);
+        for (int i = 0; i < NW * S; ++i) mbar_init(&bars[i], 1);
         misc[0] = 0;
         fence_mbar_init();
     }
@@ -565,12 +568,16 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
             int i0, i1;
             decode_f(s, tk.f, i0, i1);
             T* ax = auxr + st * AUXW;
-            if (lane < tk.na) {
-                if (N >= 3) cp_async_elem(ax + lane, A.W + s.woff[0][Am] + static_cast<long long>(i0) * IA + tk.a0 + lane);
-                if (N == 4)
-                    cp_async_elem(ax + 32 + lane, A.W + s.woff[1][Am] + static_cast<long long>(i1) * IA + tk.a0 + lane);
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                const int a = lane + 32 * q;
+                if (a < tk.na) {
+                    if (N >= 3) cp_async_elem(ax + a, A.W + s.woff[0][Am] + static_cast<long long>(i0) * IA + tk.a0 + a);
+                    if (N == 4)
+                        cp_async_elem(ax + PR + a, A.W + s.woff[1][Am] + static_cast<long long>(i1) * IA + tk.a0 + a);
+                }
             }
-            if (N == 4) cp_async_elem(ax + 64 + lane, A.W + s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1);
+            if (N == 4) cp_async_elem(ax + 2 * PR + lane, A.W + s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1);
             cp_async_commit();
         }
         if (lane == 0) {
@@ -583,7 +590,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
             fence_proxy_async();
             bulk_g2s(buf, reinterpret_cast<const void*>(lo), static_cast<unsigned>(hi - lo), bar);
         }
-        ct += NWARP;
+        ct += NW;
         settle();
     };
     ic.ui = blockIdx.x;
@@ -605,7 +612,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
 #pragma unroll
             for (int r = 0; r < RA; ++r) z[r2][r] = T(0);
         int zslot = -1;
-        for (int t = warp; t < nt; t += NWARP, ++it) {
+        for (int t = warp; t < nt; t += NW, ++it) {
             const int st = it % S;
             const unsigned par = static_cast<unsigned>((it / S) & 1);
             T* buf = tiles + (static_cast<size_t>(warp) * S + st) * TC;
@@ -616,17 +623,18 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
             if (ok) {
                 int i0, i1;
                 decode_f(s, tk.f, i0, i1);
-                // phi rows (lane = row); rows past na are zero
-                {
-                    const int a = lane;
-                    const T om = (a < tk.na) ? (N >= 3 ? ax[a] : T(1)) * (N == 4 ? ax[32 + a] : T(1)) : T(0);
+                // phi rows (lane-owned rows a = lane + 32 q); rows past na are zero
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) {
+                    const int a = lane + 32 * q;
+                    const T om = (a < tk.na) ? (N >= 3 ? ax[a] : T(1)) * (N == 4 ? ax[PR + a] : T(1)) : T(0);
 #pragma unroll
                     for (int r = 0; r < RA; ++r)
                         phi[a * RA + r] = a < tk.na ? om * gAt[r * IA + tk.a0 + a] : T(0);
-                    if (lane < VN) {  // padding rows RBK.. of the last chunk
+                }
+                if (lane < VN) {  // padding rows PR.. of the last chunk
 #pragma unroll
-                        for (int r = 0; r < RA; ++r) phi[(32 + lane) * RA + r] = T(0);
-                    }
+                    for (int r = 0; r < RA; ++r) phi[(PR + lane) * RA + r] = T(0);
                 }
                 __syncwarp();
                 const T* xt = buf + shift16(A.X + (tk.f * IA + tk.a0) * IB) + u.b0 + (colok ? lane : 0);
@@ -654,7 +662,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
 #pragma unroll
                     for (int r = 0; r < RA; ++r) z[0][r] += colok ? u0[r] : T(0);
                 } else {
-                    const T scale = colok ? (N == 4 ? ax[64 + lane] : T(1)) : T(0);
+                    const T scale = colok ? (N == 4 ? ax[2 * PR + lane] : T(1)) : T(0);
                     const int il2 = N == 4 ? i1 : i0;
                     const T* gl = gL + il2;
                     const int Il2 = s.I[l2];
@@ -668,12 +676,12 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
                 }
             }
             __syncwarp();
-            if (t + NWARP < nt)
+            if (t + NW < nt)
                 issue_next(st);
             else
                 zslot = st;
         }
-        const int nwk = min(NWARP, nt);
+        const int nwk = min(NW, nt);
         if (zslot >= 0) {
             T* zb = tiles + (static_cast<size_t>(warp) * S + zslot) * TC;
             if (colok)
@@ -699,21 +707,21 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_contract_colw(const __grid_co
     }
 }
 
-template <typename T, int R, int RPL = 1, int RCT = 0>
+template <typename T, int R, int RPL = 1, int RCT = 0, int NW = NWARP>
 cudaError_t launch_roww_r(const ContractArgs<T>& a, int grid, cudaStream_t st) {
-    auto kern = k_contract_roww<T, R, RPL, RCT>;
+    auto kern = k_contract_roww<T, R, RPL, RCT, NW>;
     cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(kern), a.pl.smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, NWARP * 32, a.pl.smem, st>>>(a);
+    kern<<<grid, NW * 32, a.pl.smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T, int R>
+template <typename T, int R, int RPL = 1, int NW = NWARP>
 cudaError_t launch_colw_r(const ContractArgs<T>& a, int grid, cudaStream_t st) {
-    auto kern = k_contract_colw<T, R>;
+    auto kern = k_contract_colw<T, R, RPL, NW>;
     cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(kern), a.pl.smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, NWARP * 32, a.pl.smem, st>>>(a);
+    kern<<<grid, NW * 32, a.pl.smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -729,6 +737,24 @@ cudaError_t launch_contract_warp(const ContractArgs<T>& a, int grid, cudaStream_
             case 4: return wdev::launch_roww_r<T, 4, 2, 4>(a, grid, st);
             case 5: return wdev::launch_roww_r<T, 5, 2, 5>(a, grid, st);
             default: return cudaErrorInvalidValue;
+        }
+    }
+    if (col && a.pl.rpl == 2) {  // tasks of up to 64 rows: 12 warps (their rings fit shared memory)
+        switch (a.pl.R1) {
+#define IFCTN_CASE(R) \
+    case R:           \
+        return wdev::launch_colw_r<T, R, 2, 12>(a, grid, st);
+            IFCTN_CASE(1)
+            IFCTN_CASE(2)
+            IFCTN_CASE(3)
+            IFCTN_CASE(4)
+            IFCTN_CASE(5)
+            IFCTN_CASE(6)
+            IFCTN_CASE(7)
+            IFCTN_CASE(8)
+#undef IFCTN_CASE
+            default:
+                return cudaErrorInvalidValue;
         }
     }
     switch (a.pl.R1) {

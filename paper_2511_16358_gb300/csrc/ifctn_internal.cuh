@@ -83,8 +83,21 @@ struct ContractPlan {
     int off_tile, off_tab, off_gtab, off_wab, off_zs, off_aux;  // shared-memory carve-up (bytes)
     int fin_div, fin_mod;  // > 0: the units covering output row r are r / fin_div + n * fin_mod
     int auxw;        // warp kernels: elements of a warp's per-stage ring slot of W entries
-    int rpl;         // ROW warp kernel: rows per lane (1, or 2 for tasks of up to 64 rows)
+    int rpl;         // warp kernels: rows per lane (1, or 2 for tasks of up to 64 rows)
+    int nwarp;       // warp kernels: warps per CTA
     long long part_elems;
+};
+
+// Launch-shape choices of the warp-pipelined contraction that the planner
+// leaves open (the autotuner times them): rows per lane allowed (1) or not,
+// ring stages per warp (0 = as many as fit, else 2..4), X bytes of a
+// one-row-per-lane task, and the unit chunking (0 = the cost model that gives
+// every warp of a unit the same number of tasks, 1 = balance across SMs only).
+struct WarpKnobs {
+    int rpl = 1;
+    int stages = 0;
+    int xbytes = 4096;
+    int chunking = 0;
 };
 
 // ---------------------------------------------------------------------------
