@@ -164,6 +164,37 @@ ifctn_status ifctn_launch_stage(ifctn_ctx* ctx, int32_t stage, int32_t k);
    budget out of range. */
 ifctn_status ifctn_wait_selftest(ifctn_ctx* ctx, int64_t budget_cycles);
 
+/* Slab-sharded sweeps: one tensor split along its first mode across several
+   processes, one GPU each (the paper's column independence, Sec. 4.2: the
+   columns of G_{1,l} are solved independently, and every other quantity a
+   mode needs is a sum over tensor entries).
+   Each process creates an ordinary context for its slab X[lo:hi, ...]: a
+   problem with dims (hi - lo, I_2, ..., I_N) and the full ranks, whose
+   factors G_{1,l} are the columns lo..hi-1 of the whole problem's G_{1,l}
+   and whose other factors are the whole problem's.  ifctn_sweep_exchange
+   then runs n sweeps of Algorithm 1 with the per-stage kernels and calls
+   allreduce(user, values, count) on host memory wherever the slabs' results
+   must be combined:
+     - for every mode k >= 2, before its column solves: the slab's partial
+       M_k (I_k x Q_k) followed by its partial K_k (Q_k x Q_k), count =
+       I_k Q_k + Q_k^2 doubles;
+     - after the X update: the slab's ||X^{s+1} - X^s||^2, ||X^s||^2 and
+       ||X^{s+1} - iFCTN(G^{s+1})||^2 (count = 3).
+   allreduce must replace every value by its sum over the processes, the same
+   bits on every process (e.g. an all-gather summed in process order), and
+   return 0; a nonzero return stops the call with IFCTN_EINVAL.  Mode 1 needs
+   no exchange: its M_1 rows and its columns are the slab's own, and K_1 does
+   not depend on i_1.  The factors G_{k,l} of the modes k >= 2 then come out
+   the same on every process and the slab's G_{1,l} columns and X entries are
+   those of the whole problem's sweep (up to the order of the partial sums).
+   tol is ignored; out (nullable) receives sweeps_done (counted per context),
+   rel_change and objective of the last sweep from the combined sums (rse and
+   rmse NaN).  No data-path collective runs on the device: the caller's
+   allreduce may use any transport. */
+typedef int32_t (*ifctn_allreduce_fn)(void* user, double* values, int64_t count);
+ifctn_status ifctn_sweep_exchange(ifctn_ctx* ctx, int32_t n, ifctn_allreduce_fn allreduce, void* user,
+                                  ifctn_stats* out);
+
 /* Autotuning of the streaming contraction (no counterpart in the paper: it
    picks launch shapes for this GPU).  For every mode whose contraction runs
    the warp-pipelined HBM-streaming kernels, the planner leaves four choices

@@ -30,7 +30,7 @@ EXPORTED = [
     "ifctn_submit", "ifctn_poll", "ifctn_server_info_get", "ifctn_server_latency",
     "ifctn_server_destroy", "ifctn_last_error", "ifctn_sweep_async", "ifctn_launch_stage",
     "ifctn_launch_count", "ifctn_phase_times", "ifctn_reconstruct_noalloc", "ifctn_wait_selftest",
-    "ifctn_tune", "ifctn_tune_choose",
+    "ifctn_tune", "ifctn_tune_choose", "ifctn_sweep_exchange",
 ]
 
 
@@ -52,6 +52,10 @@ class Stats(ctypes.Structure):
 class ServerInfo(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int64), ("resident", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("bytes_in_use", ctypes.c_int64), ("peak_resident", ctypes.c_int64)]
+
+
+# int32_t (*)(void* user, double* values, int64_t count)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64)
 
 
 class IfctnError(RuntimeError):
@@ -103,6 +107,7 @@ def load(path: str | None = None):
         "ifctn_wait_selftest": (i32, [vp, i64]),
         "ifctn_tune": (i32, [vp, ctypes.c_char_p, P(i32)]),
         "ifctn_tune_choose": (i32, [i32, P(dp)]),
+        "ifctn_sweep_exchange": (i32, [vp, i32, ALLREDUCE_FN, vp, P(Stats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -231,6 +236,29 @@ def wait_selftest(ctx, budget_cycles):
     """Runs the library's bounded device waits on conditions nothing satisfies;
     returns the status (IFCTN_ETIMEOUT when the waits expired as designed)."""
     return int(load().ifctn_wait_selftest(ctx, int(budget_cycles)))
+
+
+def sweep_exchange(ctx, n, allreduce) -> dict:
+    """n sweeps of a slab context (ifctn_sweep_exchange); ``allreduce(values)``
+    receives a float64 numpy view of host memory and must replace it in place
+    by the sum over the processes (the same bits everywhere)."""
+    err = []
+
+    def cb(_user, ptr_, count):
+        try:
+            allreduce(np.ctypeslib.as_array(ptr_, shape=(int(count),)))
+            return 0
+        except Exception as e:  # reported after the call returns
+            err.append(e)
+            return 1
+
+    fn = ALLREDUCE_FN(cb)
+    st = Stats()
+    rc = load().ifctn_sweep_exchange(ctx, int(n), fn, None, ctypes.byref(st))
+    if err:
+        raise err[0]
+    _check(rc)
+    return st.as_dict()
 
 
 def tune(ctx, cache_path=None) -> int:

@@ -849,6 +849,7 @@ struct ifctn_ctx {
     virtual ifctn_status launch_stage(int stage, int k) = 0;
     virtual ifctn_status wait_selftest(long long budget) = 0;
     virtual ifctn_status tune(const char* path, int* ntimed) = 0;
+    virtual ifctn_status sweep_exchange(int n, ifctn_allreduce_fn fn, void* user, ifctn_stats* out) = 0;
     virtual long long launch_total() const = 0;
     virtual ifctn_status phase_times(double* out, int max, int* n) = 0;
     virtual void set_grid_cap(int g) = 0;
@@ -914,6 +915,7 @@ struct Engine : ifctn_ctx {
     DevBuf<unsigned> bar;
     DevBuf<unsigned long long> tstamp;  // [0,64): phase ends; [64 + k*512 + cta]: per-CTA phase-1 ends
     long long launch_count = 0;
+    int ex_sweeps = 0;  // sweeps run by sweep_exchange
     double cur_tol = 0.0;
 
     int* counter() { return ints.p; }
@@ -1652,6 +1654,86 @@ struct Engine : ifctn_ctx {
         return IFCTN_OK;
     }
 
+    // n sweeps of a slab of a tensor split along its first mode (see
+    // ifctn_sweep_exchange): the per-stage kernels, with the partial M_k and
+    // K_k of every mode k >= 1 and the stop-test sums combined by `fn`.
+    ifctn_status sweep_exchange(int n, ifctn_allreduce_fn fn, void* user, ifctn_stats* out) override {
+        if (n < 0 || !fn) {
+            set_error(n < 0 ? "n must be >= 0" : "null allreduce function");
+            return IFCTN_EINVAL;
+        }
+        CK(cudaMemsetAsync(done(), 0, sizeof(int), st));
+        long long need = 8;
+        for (int k = 1; k < sh.N; ++k) {
+            const long long Q = mode_q(sh, k);
+            need = std::max(need, static_cast<long long>(sh.I[k]) * Q + Q * Q);
+        }
+        if (tmpD.n < static_cast<size_t>(need)) {
+            tmpD.release();
+            if (tmpD.alloc(need) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("device allocation failed");
+                return IFCTN_ENOMEM;
+            }
+        }
+        std::vector<double> hb(need);
+        std::vector<T> kt;
+        double sums[3] = {0, 0, 0};
+        for (int s_ = 0; s_ < n; ++s_) {
+            for (int k = 0; k < sh.N; ++k) {
+                CK(launch_contract<T>(cargs(k), st));
+                CK(launch_contract_finish<T>(sh, k, plan[k], units.p + unit_off[k], part.p, Gt.p, Mk[k].p, done(),
+                                             st));
+                CK(launch_gram<T>(sh, k, Gt.p, W.p, t1.p, t2.p, Kk.p, done(), st));
+                launch_count += 3;
+                if (k > 0) {  // M_k and K_k are sums over the slab's entries: combine them
+                    const long long Q = mode_q(sh, k), nm = static_cast<long long>(sh.I[k]) * Q;
+                    CK(cudaMemcpyAsync(hb.data(), Mk[k].p, nm * sizeof(double), cudaMemcpyDeviceToHost, st));
+                    if (sizeof(T) == sizeof(double)) {
+                        CK(cudaMemcpyAsync(hb.data() + nm, Kk.p, Q * Q * sizeof(double), cudaMemcpyDeviceToHost, st));
+                    } else {
+                        CK(launch_to_double(Q * Q, reinterpret_cast<const float*>(Kk.p), tmpD.p, st));
+                        CK(cudaMemcpyAsync(hb.data() + nm, tmpD.p, Q * Q * sizeof(double), cudaMemcpyDeviceToHost, st));
+                        ++launch_count;
+                    }
+                    CK(cudaStreamSynchronize(st));
+                    if (fn(user, hb.data(), nm + Q * Q) != 0) {
+                        set_error("the allreduce function failed");
+                        return IFCTN_EINVAL;
+                    }
+                    CK(cudaMemcpyAsync(Mk[k].p, hb.data(), nm * sizeof(double), cudaMemcpyHostToDevice, st));
+                    kt.assign(Q * Q, T(0));
+                    for (long long i = 0; i < Q * Q; ++i) kt[i] = static_cast<T>(hb[nm + i]);
+                    CK(cudaMemcpyAsync(Kk.p, kt.data(), Q * Q * sizeof(T), cudaMemcpyHostToDevice, st));
+                    CK(cudaStreamSynchronize(st));  // kt and hb are reused
+                }
+                CK(launch_solve_cols<T>(pp, k, st));
+                ++launch_count;
+            }
+            CK(launch_xupdate_slab<T>(pp, xpart.p, slab_xblocks(), st));
+            for (int t = 0; t < 3; ++t) CK(launch_sum_partials(xpart.p, slab_xblocks(), 8, t, scal.p + t, st));
+            launch_count += 4;
+            CK(cudaMemcpyAsync(sums, scal.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (fn(user, sums, 3) != 0) {
+                set_error("the allreduce function failed");
+                return IFCTN_EINVAL;
+            }
+            ++ex_sweeps;
+        }
+        ifctn_status rs = check_flags();
+        if (rs != IFCTN_OK) return rs;
+        if (out) {
+            memset(out, 0, sizeof(*out));
+            out->sweeps_done = ex_sweeps;
+            out->rel_change = sums[1] > 0 ? std::sqrt(sums[0]) / std::sqrt(sums[1]) : (sums[0] > 0 ? INFINITY : 0.0);
+            out->objective = 0.5 * sums[2];
+            out->rse = out->rmse = NAN;
+            if (n == 0) out->rel_change = out->objective = NAN;
+        }
+        return IFCTN_OK;
+    }
+
     ifctn_status wait_selftest(long long budget) override {
         CK(cudaMemsetAsync(bar.p, 0, sizeof(unsigned), st));
         CK(launch_wait_selftest(flags(), bar.p, budget, st));
@@ -1857,6 +1939,10 @@ ifctn_status ifctn_sweep_async(ifctn_ctx* ctx, int32_t n) {
 }
 ifctn_status ifctn_launch_stage(ifctn_ctx* ctx, int32_t stage, int32_t k) {
     IFCTN_CTX_CALL(ctx, launch_stage(stage, k));
+}
+ifctn_status ifctn_sweep_exchange(ifctn_ctx* ctx, int32_t n, ifctn_allreduce_fn allreduce, void* user,
+                                  ifctn_stats* out) {
+    IFCTN_CTX_CALL(ctx, sweep_exchange(n, allreduce, user, out));
 }
 ifctn_status ifctn_tune(ifctn_ctx* ctx, const char* cache_path, int32_t* timed) {
     int t = 0;
