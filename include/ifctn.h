@@ -203,8 +203,10 @@ ifctn_status ifctn_sweep_exchange(ifctn_ctx* ctx, int32_t n, ifctn_allreduce_fn 
    from the cache file at cache_path (nullable) when the file holds the key
    (library source digest, dtype, shape, ranks, mode, SM count); otherwise it
    times the distinct candidate plans on the context's stream (CUDA events,
-   the median of five launches of the contraction, on the context's own
-   tensor), keeps the fastest by the rule of ifctn_tune_choose, and appends
+   the median of five runs of the contraction on the context's own
+   tensor, together with the reduction of its partials into M_k, which
+   depends on the plan too), keeps the fastest by the rule of
+   ifctn_tune_choose, and appends
    the choice to the cache.  The results of the sweep do not depend on the
    choice beyond the order of floating-point sums within a mode's partials.
    *timed (nullable) receives the number of candidate plans timed (0 when the

@@ -575,6 +575,7 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
             int nC = std::max(1, std::min(std::min(cdiv(target, static_cast<long long>(I0) * nbc),
                                                    std::max(1, I1 * nrb / NW)), I1));
             if (kn.chunking == 0) nC = warp_unit_chunks(I1, nrb, static_cast<long long>(I0) * nbc, nC, NW, sms);
+            if (kn.chunking == 2) nC = 1;
             for (int i0 = 0; i0 < I0; ++i0)
                 for (int c = 0; c < nC; ++c)
                     for (int bc = 0; bc < nbc; ++bc) {
@@ -690,6 +691,7 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
             const int o = 1 - k, Io = s.I[o], Ik = s.I[k], I1 = s.I[1];
             int nOC = std::max(1, std::min(cdiv(target, static_cast<long long>(Ik) * nrc), std::max(1, Io / NW)));
             if (kn.chunking == 0) nOC = warp_unit_chunks(Io, 1, static_cast<long long>(Ik) * nrc, nOC, NW, sms);
+            if (kn.chunking == 2) nOC = 1;
             for (int j = 0; j < Ik; ++j)
                 for (int oc = 0; oc < nOC; ++oc)
                     for (int rc = 0; rc < nrc; ++rc) {
@@ -721,6 +723,7 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
             const int I0 = s.I[0], I1 = s.I[1];
             int nC = std::max(1, std::min(cdiv(target, static_cast<long long>(I0) * nrc), std::max(1, I1 / NW)));
             if (kn.chunking == 0) nC = warp_unit_chunks(I1, 1, static_cast<long long>(I0) * nrc, nC, NW, sms);
+            if (kn.chunking == 2) nC = 1;
             for (int i0 = 0; i0 < I0; ++i0)
                 for (int c = 0; c < nC; ++c)
                     for (int rc = 0; rc < nrc; ++rc) {
@@ -1088,8 +1091,8 @@ struct Engine : ifctn_ctx {
         return key;
     }
 
-    // Device seconds of one launch of the mode-k contraction with plan pl and
-    // units u (the median of 5 launches after one warm-up, CUDA events on the
+    // Device seconds of the mode-k contraction and its finisher with plan pl
+    // and units u (the median of 5 runs after one warm-up, CUDA events on the
     // context's stream); unit descriptors and partials in scratch buffers.
     ifctn_status time_contract(int k, const ContractPlan& pl, const std::vector<UnitDesc>& u, double* sec) {
         DevBuf<UnitDesc> du;
@@ -1107,11 +1110,19 @@ struct Engine : ifctn_ctx {
         a.part = dp.p;
         cudaEvent_t e[6];
         for (auto& ev : e) cudaEventCreate(&ev);
+        // the contraction and the finisher that reduces its per-unit partials
+        // into M_k: both change with the plan
+        auto pair = [&]() {
+            cudaError_t r = launch_contract<T>(a, st);
+            if (r == cudaSuccess)
+                r = launch_contract_finish<T>(sh, k, pl, du.p, dp.p, Gt.p, Mk[k].p, done(), st);
+            return r;
+        };
         cudaError_t err = cudaMemcpyAsync(du.p, u.data(), u.size() * sizeof(UnitDesc), cudaMemcpyHostToDevice, st);
-        if (err == cudaSuccess) err = launch_contract<T>(a, st);
+        if (err == cudaSuccess) err = pair();
         for (int i = 0; i < 5 && err == cudaSuccess; ++i) {
             err = cudaEventRecord(e[i], st);
-            if (err == cudaSuccess) err = launch_contract<T>(a, st);
+            if (err == cudaSuccess) err = pair();
         }
         if (err == cudaSuccess) err = cudaEventRecord(e[5], st);
         if (err == cudaSuccess) err = cudaStreamSynchronize(st);
@@ -1180,7 +1191,7 @@ struct Engine : ifctn_ctx {
                     for (int rpl : {1, 0})
                         for (int stg : {0, 2, 3})
                             for (int xb : {4096, 2048, 8192})
-                                for (int ch : {0, 1}) {
+                                for (int ch : {0, 1, 2}) {
                                     WarpKnobs w;
                                     w.rpl = rpl;
                                     w.stages = stg;
@@ -1361,6 +1372,8 @@ struct Engine : ifctn_ctx {
             rows = std::min<long long>(rows, rows_total);
             pp.xu_rows = static_cast<int>(std::max<long long>(rows, 1));
             pp.xu_wab_smem = static_cast<long long>(sh.IA) * sh.IB * sizeof(T) <= 64 * 1024 ? 1 : 0;
+            pp.xu_variant = 0;
+            if (const char* e = getenv("IFCTN_XU_VARIANT")) pp.xu_variant = std::max(0, std::min(3, atoi(e)));
         }
         psmem = persistent_smem_bytes<T>(pp);
         persistent = false;

@@ -92,7 +92,9 @@ struct ContractPlan {
 // leaves open (the autotuner times them): rows per lane allowed (1) or not,
 // ring stages per warp (0 = as many as fit, else 2..4), X bytes of a
 // one-row-per-lane task, and the unit chunking (0 = the cost model that gives
-// every warp of a unit the same number of tasks, 1 = balance across SMs only).
+// every warp of a unit the same number of tasks, 1 = balance across SMs only,
+// 2 = the fewest units: one per output row or deferred index, which leaves
+// the finisher the fewest partials to reduce).
 struct WarpKnobs {
     int rpl = 1;
     int stages = 0;

@@ -45,6 +45,7 @@ struct SweepParams {
     double tolv;                 // stop tolerance of this launch (0 = none)
     int xu_rows;                 // X update: rows of a slab per work unit
     int xu_wab_smem;             // X update: W_{A,B} kept in shared memory
+    int xu_variant;              // X update (per-stage path): batch / residency variant
 };
 
 // Index tables of the column solves of mode k (the same for every column):

@@ -12,5 +12,4 @@ template int persistent_smem_bytes<float>(const SweepParams<float>&);
 template cudaError_t launch_persistent<float>(const SweepParams<float>&, int, int, cudaStream_t);
 template int persistent_max_grid<float>(int);
 template cudaError_t launch_solve_cols<float>(const SweepParams<float>&, int, cudaStream_t);
-template cudaError_t launch_xupdate_slab<float>(const SweepParams<float>&, double*, int, cudaStream_t);
 }  // namespace ifctn

@@ -12,5 +12,4 @@ template int persistent_smem_bytes<double>(const SweepParams<double>&);
 template cudaError_t launch_persistent<double>(const SweepParams<double>&, int, int, cudaStream_t);
 template int persistent_max_grid<double>(int);
 template cudaError_t launch_solve_cols<double>(const SweepParams<double>&, int, cudaStream_t);
-template cudaError_t launch_xupdate_slab<double>(const SweepParams<double>&, double*, int, cudaStream_t);
 }  // namespace ifctn

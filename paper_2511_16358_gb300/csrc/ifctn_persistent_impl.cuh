@@ -1139,7 +1139,11 @@ __device__ __forceinline__ void xacc(const SweepParams<T>& p, const T rho, const
 // (N = 4) are built in shared memory, and W_{A,B} is kept in shared memory
 // when it fits, so that iFCTN(G)(i) = alpha(row) beta(f, b) W_{A,B}(a, b)
 // costs three shared loads per entry.
-template <typename T>
+// XB4: 16-byte vectors of X a thread holds in flight per batch (the loads of
+// a batch are all issued before its stores).
+// VEC_ONLY: compiled for the 16-byte path alone (the caller guarantees it
+// applies), which leaves the registers of the element-wise path unused.
+template <typename T, int XB4 = 4, bool VEC_ONLY = false>
 __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned char* smem) {
     const Shape& s = p.sh;
     const int N = s.N, IA = s.IA, IB = s.IB, Am = N - 2, Bm = N - 1;
@@ -1206,7 +1210,7 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
         (void)SU;
         const long long e0 = r0 * IB;
         const int n = nr * IB;
-        if (vec) {
+        if (VEC_ONLY || vec) {
             const int nch = IB / VN;
             const int n4 = nr * nch;
             int rl4 = threadIdx.x / nch, c4 = threadIdx.x - rl4 * nch;
@@ -1216,7 +1220,6 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
                 ++sl4;
             }
             const int drl4 = PT / nch, dc4 = PT - drl4 * nch;
-            constexpr int XB4 = 4;
             for (int ob = 0; ob < n4; ob += XB4 * PT) {
                 T xo[XB4][VN], rec[XB4][VN];
                 uint32_t wd[XB4];
@@ -1375,12 +1378,15 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
     __syncthreads();
 }
 
-// Standalone form of the X update for the per-stage (graph) path.
-template <typename T>
-__global__ void __launch_bounds__(PT) k_xupdate_slab(const __grid_constant__ SweepParams<T> p, double* __restrict__ xpart) {
+// Standalone form of the X update for the per-stage (graph) path.  XB4
+// vectors in flight per thread and MINB resident CTAs per SM set the bytes in
+// flight per SM (XB4 x 16 B x 256 threads x MINB).
+template <typename T, int XB4, int MINB, bool VEC_ONLY>
+__global__ void __launch_bounds__(PT, MINB) k_xupdate_slab(const __grid_constant__ SweepParams<T> p,
+                                                           double* __restrict__ xpart) {
     if (*reinterpret_cast<volatile const int*>(p.done)) return;
     extern __shared__ __align__(128) unsigned char xsm[];
-    xupdate_phase<T>(p, xpart + 8 * blockIdx.x, xsm);
+    xupdate_phase<T, XB4, VEC_ONLY>(p, xpart + 8 * blockIdx.x, xsm);
 }
 
 
@@ -1570,15 +1576,32 @@ cudaError_t launch_persistent(const SweepParams<T>& p, int grid, int smem, cudaS
                                        smem, st);
 }
 
-template <typename T>
-cudaError_t launch_xupdate_slab(const SweepParams<T>& p, double* xpart, int nblocks, cudaStream_t st) {
+template <typename T, int XB4, int MINB, bool VEC_ONLY>
+cudaError_t launch_xupdate_slab_v(const SweepParams<T>& p, double* xpart, int nblocks, cudaStream_t st) {
     const int smem = static_cast<int>((static_cast<long long>(p.xu_wab_smem ? p.sh.IA * p.sh.IB : 0) + p.xu_rows +
                                        static_cast<long long>((p.xu_rows + p.sh.IA - 1) / p.sh.IA + 1) * p.sh.IB) *
                                       sizeof(T)) + 64;
-    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_xupdate_slab<T>), smem);
+    auto kern = k_xupdate_slab<T, XB4, MINB, VEC_ONLY>;
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess) return e;
-    k_xupdate_slab<T><<<nblocks, PT, smem, st>>>(p, xpart);
+    kern<<<nblocks, PT, smem, st>>>(p, xpart);
     return cudaGetLastError();
+}
+
+// p.xu_variant picks the batch and residency of the 16-byte path (1: 8
+// vectors, 2 CTAs/SM; 2: 4 vectors, 3 CTAs/SM; 3: 4 vectors, 4 CTAs/SM);
+// 0, and every shape the 16-byte path does not apply to, runs the generic
+// kernel (4 vectors, 2 CTAs/SM).
+template <typename T>
+cudaError_t launch_xupdate_slab(const SweepParams<T>& p, double* xpart, int nblocks, cudaStream_t st) {
+    constexpr int VN = 16 / static_cast<int>(sizeof(T));
+    const bool vec = p.xu_wab_smem != 0 && p.sh.IB % VN == 0;
+    switch (vec ? p.xu_variant : 0) {
+        case 1: return launch_xupdate_slab_v<T, 8, 2, true>(p, xpart, nblocks, st);
+        case 2: return launch_xupdate_slab_v<T, 4, 3, true>(p, xpart, nblocks, st);
+        case 3: return launch_xupdate_slab_v<T, 4, 4, true>(p, xpart, nblocks, st);
+        default: return launch_xupdate_slab_v<T, 4, 2, false>(p, xpart, nblocks, st);
+    }
 }
 
 template <typename T>
