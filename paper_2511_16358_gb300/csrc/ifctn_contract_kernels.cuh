@@ -34,6 +34,7 @@ using namespace cdev;
 
 template <typename T, int RB>
 __global__ void __launch_bounds__(256) k_contract_row(const __grid_constant__ ContractArgs<T> A) {
+    pdl_begin();
     if (*A.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
@@ -48,6 +49,7 @@ __global__ void __launch_bounds__(256) k_contract_row(const __grid_constant__ Co
 
 template <typename T, int RA>
 __global__ void __launch_bounds__(256) k_contract_col(const __grid_constant__ ContractArgs<T> A) {
+    pdl_begin();
     if (*A.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(256) k_contract_finish(const __grid_constant__
                                                          const T* __restrict__ Gt,
                                                          double* __restrict__ Mk,
                                                          const int* __restrict__ done) {
+    pdl_begin();
     if (*done) return;
     const int Ik = s.I[k], Q = pl.Q, Qp = pl.Qp;
     const long long total = static_cast<long long>(Ik) * Q;
@@ -149,6 +152,7 @@ __global__ void __launch_bounds__(256) k_contract_finish_rows(const __grid_const
                                                               const UnitDesc* __restrict__ units,
                                                               const T* __restrict__ part, const T* __restrict__ Gt,
                                                               double* __restrict__ Mk, const int* __restrict__ done) {
+    pdl_begin();
     if (*done) return;
     __shared__ T red[256 * RMAX];
     const int row = blockIdx.x;

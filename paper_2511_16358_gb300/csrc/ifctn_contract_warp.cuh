@@ -144,6 +144,7 @@ __device__ __forceinline__ Task task_at(const UnitCur& c, int t, int rbk) {
 // registers are then sized for RMAX).
 template <typename T, int RB, int RPL, int RCT, int NW>
 __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_constant__ ContractArgs<T> A) {
+    pdl_begin();
     static_assert(RPL == 1 || RPL == 2, "one or two rows per lane");
     if (*A.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -507,6 +508,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
 
 template <typename T, int RA, int RPL, int NW>
 __global__ void __launch_bounds__(NW * 32, 1) k_contract_colw(const __grid_constant__ ContractArgs<T> A) {
+    pdl_begin();
     if (*A.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int VN = 16 / static_cast<int>(sizeof(T));

@@ -107,6 +107,17 @@ struct WarpKnobs {
 // ---------------------------------------------------------------------------
 #ifdef __CUDACC__
 
+// Programmatic dependent launch: the sweep graph's kernel-to-kernel edges let a
+// kernel be launched while its predecessor still runs.  Every kernel that can
+// sit in that graph first waits until its predecessors have completed and
+// their writes are visible (a no-op for an ordinary launch), then lets its own
+// dependents launch, so their launch latency and block scheduling overlap
+// this kernel's run instead of following it.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }

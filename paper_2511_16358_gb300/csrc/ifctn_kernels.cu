@@ -28,6 +28,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_gram_t1(const __grid_constant__ Shape s, const int k, const T* __restrict__ Gt,
                                                  const T* __restrict__ W, T* __restrict__ out,
                                                  const int* __restrict__ done) {
+    pdl_begin();
     if (*done) return;
     int m[3];
     nonk_modes(s, k, m);
@@ -70,6 +71,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_gram_t2(const __grid_constant__ Shape s, const int k, const T* __restrict__ Gt,
                                                  const T* __restrict__ t1, T* __restrict__ t2,
                                                  const int* __restrict__ done) {
+    pdl_begin();
     if (*done) return;
     int m[3];
     nonk_modes(s, k, m);
@@ -155,6 +157,7 @@ template <typename T, int RL>
 __global__ void __launch_bounds__(GRAM_WARPS * 32) k_gram_io(const __grid_constant__ Shape s, const int k,
                                                              const T* __restrict__ Gt, const T* __restrict__ W,
                                                              T* __restrict__ t2, const int* __restrict__ done) {
+    pdl_begin();
     if (*done) return;
     extern __shared__ __align__(16) unsigned char gsm[];
     constexpr int NP = RL * (RL + 1) / 2;
@@ -249,6 +252,7 @@ template <typename T>
 __global__ void __launch_bounds__(GRAM_WARPS * 32) k_gram_fin(const __grid_constant__ Shape s, const int k,
                                                               const T* __restrict__ Gt, const T* __restrict__ t2,
                                                               T* __restrict__ K, const int* __restrict__ done) {
+    pdl_begin();
     if (*done) return;
     __shared__ T red[GRAM_WARPS][32];
     int m[3];
@@ -447,6 +451,7 @@ __global__ void __launch_bounds__(256) k_xupdate(const __grid_constant__ Shape s
                                                  T* __restrict__ X, const uint32_t* __restrict__ mb,
                                                  const T* __restrict__ W, double* __restrict__ xpart,
                                                  const int* __restrict__ done) {
+    pdl_begin();
     if (*done) return;
     using V = typename Vec<T>::type;
     constexpr int NV = Vec<T>::n;
@@ -513,6 +518,7 @@ __global__ void __launch_bounds__(256) k_xupdate(const __grid_constant__ Shape s
 template <typename T>
 __global__ void __launch_bounds__(256) k_reconstruct(const __grid_constant__ Shape s, const T* __restrict__ W,
                                                      T* __restrict__ out, double* __restrict__ xpart) {
+    pdl_begin();
     const long long P = s.P;
     const long long gtid = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     const long long gstr = static_cast<long long>(gridDim.x) * blockDim.x;
@@ -544,6 +550,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_metrics(const long long P, const T* __restrict__ X,
                                                  const T* __restrict__ Xt, const uint32_t* __restrict__ mb,
                                                  double* __restrict__ mpart, const int* __restrict__ done) {
+    pdl_begin();
     if (*done) return;
     const long long gtid = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     const long long gstr = static_cast<long long>(gridDim.x) * blockDim.x;
@@ -570,6 +577,7 @@ __global__ void __launch_bounds__(256) k_metrics(const long long P, const T* __r
 
 template <typename T>
 __global__ void k_pairs(const __grid_constant__ Shape s, const double* __restrict__ Gd, T* __restrict__ W) {
+    pdl_begin();
     const long long gtid = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     const long long gstr = static_cast<long long>(gridDim.x) * blockDim.x;
     for (long long idx = gtid; idx < s.wsize; idx += gstr) {
@@ -594,12 +602,14 @@ __global__ void k_pairs(const __grid_constant__ Shape s, const double* __restric
 template <typename T>
 __global__ void k_init_x(const long long P, const T* __restrict__ O, const uint8_t* __restrict__ mask,
                          T* __restrict__ X) {
+    pdl_begin();
     const long long gstr = static_cast<long long>(gridDim.x) * blockDim.x;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < P; e += gstr)
         X[e] = mask[e] ? O[e] : T(0);
 }
 
 __global__ void k_pack_mask(const long long P, const uint8_t* __restrict__ mask, uint32_t* __restrict__ bits) {
+    pdl_begin();
     const long long nw = (P + 31) / 32;
     const long long gstr = static_cast<long long>(gridDim.x) * blockDim.x;
     for (long long wd = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; wd < nw; wd += gstr) {
@@ -614,6 +624,7 @@ __global__ void k_pack_mask(const long long P, const uint8_t* __restrict__ mask,
 
 template <typename T>
 __global__ void k_cast(const int n, const double* __restrict__ a, T* __restrict__ b) {
+    pdl_begin();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = to_t<T>(a[i]);
 }
 
@@ -621,6 +632,7 @@ __global__ void k_finalize(const double* __restrict__ xpart, const int nblocks, 
                            const int mblocks, const long long nmiss, const double* __restrict__ tolp,
                            SweepStat* __restrict__ log, const int cap, int* __restrict__ counter,
                            int* __restrict__ done, const int* __restrict__ flags) {
+    pdl_begin();
     if (*done) return;
     __shared__ double sh[256][6];
     const int t = threadIdx.x;
@@ -669,6 +681,7 @@ __global__ void k_finalize(const double* __restrict__ xpart, const int nblocks, 
 __global__ void k_finalize8(const double* __restrict__ xpart, const int nblocks, const int met, const long long nmiss,
                             const double* __restrict__ tolp, SweepStat* __restrict__ log, const int cap,
                             int* __restrict__ counter, int* __restrict__ done, const int* __restrict__ flags) {
+    pdl_begin();
     if (*done) return;
     __shared__ double sh[256][6];
     const int t = threadIdx.x;
@@ -711,6 +724,7 @@ __global__ void k_finalize8(const double* __restrict__ xpart, const int nblocks,
 
 __global__ void k_sum_partials(const double* __restrict__ xpart, const int nblocks, const int stride,
                                const int slot, double* __restrict__ out) {
+    pdl_begin();
     __shared__ double sh[256];
     double a = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) a += xpart[stride * b + slot];
@@ -724,6 +738,7 @@ __global__ void k_sum_partials(const double* __restrict__ xpart, const int nbloc
 }
 
 __global__ void k_scale(const int n, double* __restrict__ Gd, const double* __restrict__ ratio, const double expo) {
+    pdl_begin();
     const double sc = pow(*ratio, expo);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) Gd[i] *= sc;
 }
@@ -882,6 +897,7 @@ namespace ifctn {
 namespace {
 template <typename T>
 __global__ void __launch_bounds__(256) k_sumsq(const long long P, const T* __restrict__ X, double* __restrict__ part) {
+    pdl_begin();
     const long long gstr = static_cast<long long>(gridDim.x) * blockDim.x;
     double acc[3] = {0.0, 0.0, 0.0};
     T fa = T(0);
@@ -900,6 +916,7 @@ __global__ void __launch_bounds__(256) k_sumsq(const long long P, const T* __res
 
 __global__ void __launch_bounds__(256) k_count_bits(const long long nwords, const uint32_t* __restrict__ bits,
                                                     double* __restrict__ part) {
+    pdl_begin();
     const long long gstr = static_cast<long long>(gridDim.x) * blockDim.x;
     double acc[3] = {0.0, 0.0, 0.0};
     long long c = 0;
@@ -910,6 +927,7 @@ __global__ void __launch_bounds__(256) k_count_bits(const long long nwords, cons
 }
 
 __global__ void k_to_double_f(const long long n, const float* __restrict__ a, double* __restrict__ b) {
+    pdl_begin();
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<long long>(gridDim.x) * blockDim.x)
         b[i] = static_cast<double>(a[i]);

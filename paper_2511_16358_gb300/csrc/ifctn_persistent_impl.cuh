@@ -1384,6 +1384,7 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
 template <typename T, int XB4, int MINB, bool VEC_ONLY>
 __global__ void __launch_bounds__(PT, MINB) k_xupdate_slab(const __grid_constant__ SweepParams<T> p,
                                                            double* __restrict__ xpart) {
+    pdl_begin();
     if (*reinterpret_cast<volatile const int*>(p.done)) return;
     extern __shared__ __align__(128) unsigned char xsm[];
     xupdate_phase<T, XB4, VEC_ONLY>(p, xpart + 8 * blockIdx.x, xsm);
@@ -1395,6 +1396,7 @@ __global__ void __launch_bounds__(PT, MINB) k_xupdate_slab(const __grid_constant
 // CTA refreshes the W_{k,.} entries of its columns before it exits.
 template <typename T>
 __global__ void __launch_bounds__(PT) k_solve_cols(const __grid_constant__ SweepParams<T> p, const int k) {
+    pdl_begin();
     if (*reinterpret_cast<volatile const int*>(p.done)) return;
     extern __shared__ __align__(128) unsigned char ssm[];
     solve_phase<T>(p, k, ssm);

@@ -87,6 +87,8 @@ def test_two_slabs_match_the_whole_problem(dims, edge, exec_path):
     assert rel_err(sh.merge_factors(slabs, dims, R, bounds), G) < 1e-10
     assert rel_err(np.concatenate(xs, axis=0), X) < 1e-10
     st = res[0][2]
-    assert st["sweeps_done"] == SWEEPS and res[1][2] == st
+    assert st["sweeps_done"] == SWEEPS
+    for key in ("sweeps_done", "rel_change", "objective"):  # rse / rmse are NaN without a truth
+        assert res[1][2][key] == st[key]
     assert st["rel_change"] == pytest.approx(log[-1]["rel_change"], rel=1e-9)
     assert st["objective"] == pytest.approx(log[-1]["objective"], rel=1e-9)
