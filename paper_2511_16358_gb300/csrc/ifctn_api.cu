@@ -1372,10 +1372,10 @@ struct Engine : ifctn_ctx {
             rows = std::min<long long>(rows, rows_total);
             pp.xu_rows = static_cast<int>(std::max<long long>(rows, 1));
             pp.xu_wab_smem = static_cast<long long>(sh.IA) * sh.IB * sizeof(T) <= 64 * 1024 ? 1 : 0;
-            // 16-byte path: 4 vectors a thread in flight, 4 CTAs per SM (measured
-            // on the 288x400x60x24 shape: 307 us against 341 us for the generic
-            // kernel's 2 CTAs per SM); IFCTN_XU_VARIANT overrides (timing)
-            pp.xu_variant = 3;
+            // 16-byte path, FP32: 4 vectors a thread in flight, 4 CTAs per SM
+            // (measured on the 288x400x60x24 shape: 307 us against 341 us for the
+            // generic kernel's 2 CTAs per SM); IFCTN_XU_VARIANT overrides (timing)
+            pp.xu_variant = sizeof(T) == 4 ? 3 : 1;  // FP64: 8 vectors, 2 CTAs/SM (no register spill)
             if (const char* e = getenv("IFCTN_XU_VARIANT")) pp.xu_variant = std::max(0, std::min(3, atoi(e)));
         }
         psmem = persistent_smem_bytes<T>(pp);

@@ -121,25 +121,32 @@ def test_graph_path_long_contiguous_mode_one_sweep_matches_oracle(dims, edge):
     c.close()
 
 
+@pytest.mark.parametrize("precision,tol", [(b.FP64, 1e-10), (b.MIXED, 2e-4)])
 @pytest.mark.parametrize("rows_per_lane", ["1", "2"])
 @pytest.mark.parametrize("dims,edge", [
     ((7, 6, 50, 12), 3),
     ((5, 9, 61, 8), 5),
     ((6, 5, 40, 16), {(0, 1): 4, (0, 2): 2, (0, 3): 4, (1, 2): 4, (1, 3): 4, (2, 3): 4}),
+    ((6, 7, 70, 24), 5),
 ])
-def test_graph_path_two_rows_per_lane_one_sweep_matches_oracle(dims, edge, rows_per_lane, monkeypatch):
-    """The streaming contraction of the modes k < N - 1 with one row per lane
-    and with two (tasks of up to 64 rows; used for order 4, R_{k,B} = R_{k,l2}
-    and more than 32 rows): one FP64 sweep equals the oracle's."""
+def test_graph_path_rows_per_lane_two_sweeps_match_oracle(dims, edge, rows_per_lane, precision, tol, monkeypatch):
+    """The streaming contraction with one row per lane and with two (tasks of
+    up to 64 rows; order 4, R_{k,B} = R_{k,l2}, more than 32 rows), for the
+    modes k < N - 1 and for the last mode; FP64 (1e-10) and the mixed path,
+    whose FP32 inner loops run on packed f32x2 pairs (relative error against
+    the FP64 oracle after two sweeps below 2e-4; FP32 contractions with
+    about 1e-6 relative error per mode system)."""
     from tests._cases import make_case
     monkeypatch.setenv("IFCTN_CW_RPL", rows_per_lane)
     case = make_case(dims, edge, 0.3, seed=461, kind="max1", sigma=0.02)
+    dt = b.tensor_dtype(precision)
     with path("graph"):
-        c = b.Completion(dims, case["R"], case["xt"], case["mask"], rho=0.1, max_sweeps=2, tol=0.0,
-                         precision=b.FP64, init_factors=case["G0"].copy())
+        c = b.Completion(dims, case["R"], case["xt"].astype(dt), case["mask"], rho=0.1, max_sweeps=2, tol=0.0,
+                         precision=precision, init_factors=case["G0"].copy())
     c.sweep(2)
-    G1, X1 = case["G0"].copy(), case["X0"].copy()
+    xin = case["xt"].astype(dt).astype(np.float64)
+    G1, X1 = case["G0"].copy(), oracle.init_x(xin, case["mask"])
     oracle.complete(dims, case["R"], 0.1, G1, X1, case["mask"], max_sweeps=2)
-    assert rel_err(c.factors(), G1) < 1e-10
-    assert rel_err(c.x(), X1) < 1e-10
+    assert rel_err(c.factors(), G1) < tol
+    assert rel_err(c.x().astype(np.float64), X1) < tol
     c.close()
