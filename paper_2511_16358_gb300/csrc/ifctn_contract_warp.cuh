@@ -56,33 +56,6 @@ __device__ __forceinline__ void ld_row(const T* __restrict__ p, T (&o)[NP]) {
     }
 }
 
-// Packed FP32 pairs (Blackwell's f32x2 instructions): one instruction does the
-// two IEEE round-to-nearest operations of a pair, which halves the FP32
-// instruction count of the inner loops (the kernels are issue-bound).  A pair
-// accumulates the even and the odd elements of a run separately and the two
-// are added at the end -- the same arithmetic as two scalar accumulators.
-using f2x = unsigned long long;
-__device__ __forceinline__ f2x pk2(float a, float b) {
-    f2x r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ float sum2(f2x v) {
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-    return lo + hi;
-}
-__device__ __forceinline__ f2x ffma2(f2x a, f2x b, f2x c) {
-    f2x r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-__device__ __forceinline__ f2x fmul2(f2x a, f2x b) {
-    f2x r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-
 // Bounded wait, uniform across the warp.  After the first expiry (abort flag
 // set) later waits give in-flight copies only a short grace period.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned par, volatile int* abortf, int* flags) {
@@ -181,7 +154,6 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
     // two accumulator sets (shorter FMA chains) while registers allow; with two
     // rows per lane the rows are the independent chains
     constexpr bool SPLIT = RPL == 1 && RB <= 5;
-    constexpr bool F32X2 = sizeof(T) == 4;  // packed pairs on the FP32 16-byte path
     const Shape& s = A.sh;
     const ContractPlan& pl = A.pl;
     const int N = s.N, k = A.k, IA = s.IA, IB = s.IB, Am = N - 2, Bm = N - 1;
@@ -335,21 +307,12 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
                 int i0, i1;
                 decode_f(s, tk.f, i0, i1);
                 // coefficient table psi(b, r) = prod_{p in F, p != k} W_{p,B}(i_p, b) G_{B,k}(r, b)
-                // (FP32 16-byte path: pairs of columns interleaved, (b, b + 1) of
-                // every r side by side, for the packed inner loop)
                 for (int b = lane; b < IB; b += 32) {
                     const T om = (p0 >= 0 ? ax[b] : T(1)) * (two_psi ? ax[AUX_W1 + b] : T(1));
 #pragma unroll
-                    for (int r = 0; r < RBP; ++r) {
-                        if constexpr (F32X2) {
-                            if (vec) {
-                                if (r < RB) psi[(b >> 1) * 2 * RB + 2 * r + (b & 1)] = om * gB[r * IB + b];
-                                continue;
-                            }
-                        }
+                    for (int r = 0; r < RBP; ++r)
                         if (r < RB) psi[b * PS + r] = om * gB[r * IB + b];
                         else if (!vec) psi[b * PS + r] = T(0);
-                    }
                 }
                 __syncwarp();
                 bool va[RPL];
@@ -372,50 +335,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
                 for (int q = 0; q < RPL; ++q)
 #pragma unroll
                     for (int r = 0; r < RB; ++r) u0[q][r] = u1[q][r] = T(0);
-                bool packed = false;
-                if constexpr (F32X2) {
-                  if (vec) {
-                    // the 16-byte path with packed pairs (even / odd columns of a
-                    // row accumulate in the two halves)
-                    packed = true;
-                    f2x U[RPL][RB];
-#pragma unroll
-                    for (int q = 0; q < RPL; ++q)
-#pragma unroll
-                        for (int r = 0; r < RB; ++r) U[q][r] = 0ull;
-                    const int nch = IB / VN;
-                    int c = pl.skew ? lane % nch : 0;
-#pragma unroll 2
-                    for (int ic2 = 0; ic2 < nch; ++ic2, c = (c + 1 == nch) ? 0 : c + 1) {
-                        const int b = c * VN;
-                        float p[VN * RB];
-                        ld_row<float, VN * RB>(reinterpret_cast<const float*>(psi) + b * RB, p);
-#pragma unroll
-                        for (int q = 0; q < RPL; ++q) {
-                            float xa[VN];
-                            ld_row<float, VN>(reinterpret_cast<const float*>(xr[q]) + b, xa);
-                            f2x x01 = pk2(xa[0], xa[1]), x23 = pk2(xa[2], xa[3]);
-                            if (wr[q]) {
-                                float wa[VN];
-                                ld_row<float, VN>(reinterpret_cast<const float*>(wr[q]) + b, wa);
-                                x01 = fmul2(x01, pk2(wa[0], wa[1]));
-                                x23 = fmul2(x23, pk2(wa[2], wa[3]));
-                            }
-#pragma unroll
-                            for (int r = 0; r < RB; ++r) {
-                                U[q][r] = ffma2(x01, pk2(p[2 * r], p[2 * r + 1]), U[q][r]);
-                                U[q][r] = ffma2(x23, pk2(p[2 * RB + 2 * r], p[2 * RB + 2 * r + 1]), U[q][r]);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < RPL; ++q)
-#pragma unroll
-                        for (int r = 0; r < RB; ++r) u0[q][r] = static_cast<T>(sum2(U[q][r]));
-                  }
-                }
-                if (packed) {
-                } else if (vec) {
+                if (vec) {
                     // 16-byte chunks of the row; with pl.skew each lane starts at
                     // its own chunk so rows that share banks are read apart
                     const int nch = IB / VN;
@@ -461,18 +381,11 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
                         }
                     }
                 }
-                if constexpr (SPLIT && !F32X2) {
+                if constexpr (SPLIT) {
 #pragma unroll
                     for (int q = 0; q < RPL; ++q)
 #pragma unroll
                         for (int r = 0; r < RB; ++r) u0[q][r] += u1[q][r];
-                } else if constexpr (SPLIT) {
-                    if (!vec) {
-#pragma unroll
-                        for (int q = 0; q < RPL; ++q)
-#pragma unroll
-                            for (int r = 0; r < RB; ++r) u0[q][r] += u1[q][r];
-                    }
                 }
                 // fold the rows into z
                 if (foldA) {
@@ -600,7 +513,6 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_colw(const __grid_const
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int VN = 16 / static_cast<int>(sizeof(T));
     constexpr bool SPLIT = RA <= 5;
-    constexpr bool F32X2 = sizeof(T) == 4;  // packed pairs of rows (even / odd rows in the two halves)
     const Shape& s = A.sh;
     const ContractPlan& pl = A.pl;
     const int N = s.N, k = A.k, IA = s.IA, IB = s.IB, Am = N - 2;
@@ -618,9 +530,6 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_colw(const __grid_const
     // each, plus VN zero rows of padding
     constexpr int PR = 32 * RPL;
     T* phi = reinterpret_cast<T*>(smem + pl.off_tab) + static_cast<size_t>(warp) * (PR + VN) * RA;
-    // table index of (row a, rank r): FP32 interleaves pairs of rows, (a, a + 1)
-    // of every r side by side, for the packed inner loop
-    auto phi_at = [](int a, int r) { return F32X2 ? (a >> 1) * 2 * RA + 2 * r + (a & 1) : a * RA + r; };
     T* gtab = reinterpret_cast<T*>(smem + pl.off_gtab);
     const int nAg = pl.R1 * IA;
     const int nL = l2 >= 0 ? RC * s.I[l2] : 0;
@@ -723,11 +632,11 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_colw(const __grid_const
                     const T om = (a < tk.na) ? (N >= 3 ? ax[a] : T(1)) * (N == 4 ? ax[PR + a] : T(1)) : T(0);
 #pragma unroll
                     for (int r = 0; r < RA; ++r)
-                        phi[phi_at(a, r)] = a < tk.na ? om * gAt[r * IA + tk.a0 + a] : T(0);
+                        phi[a * RA + r] = a < tk.na ? om * gAt[r * IA + tk.a0 + a] : T(0);
                 }
                 if (lane < VN) {  // padding rows PR.. of the last chunk
 #pragma unroll
-                    for (int r = 0; r < RA; ++r) phi[phi_at(PR + lane, r)] = T(0);
+                    for (int r = 0; r < RA; ++r) phi[(PR + lane) * RA + r] = T(0);
                 }
                 __syncwarp();
                 const T* xt = buf + shift16(A.X + (tk.f * IA + tk.a0) * IB) + u.b0 + (colok ? lane : 0);
@@ -735,44 +644,22 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_colw(const __grid_const
 #pragma unroll
                 for (int r = 0; r < RA; ++r) u0[r] = u1[r] = T(0);
                 const int nav = (tk.na + VN - 1) / VN * VN;
-                if constexpr (F32X2) {
-                    f2x U[RA];
+                for (int a = 0; a < nav; a += VN) {
+                    T p[VN * RA];
+                    ld_row<T, VN * RA>(phi + a * RA, p);
 #pragma unroll
-                    for (int r = 0; r < RA; ++r) U[r] = 0ull;
-                    for (int a = 0; a < nav; a += VN) {
-                        float p[VN * RA];
-                        ld_row<float, VN * RA>(reinterpret_cast<const float*>(phi) + a * RA, p);
-                        float xv[VN];
-#pragma unroll
-                        for (int j = 0; j < VN; ++j)
-                            xv[j] = static_cast<float>(xt[static_cast<size_t>(min(a + j, tk.na - 1)) * IB]);
-                        const f2x x01 = pk2(xv[0], xv[1]), x23 = pk2(xv[2], xv[3]);
+                    for (int j = 0; j < VN; ++j) {
+                        const int ar = min(a + j, tk.na - 1);
+                        const T x = xt[static_cast<size_t>(ar) * IB];
 #pragma unroll
                         for (int r = 0; r < RA; ++r) {
-                            U[r] = ffma2(x01, pk2(p[2 * r], p[2 * r + 1]), U[r]);
-                            U[r] = ffma2(x23, pk2(p[2 * RA + 2 * r], p[2 * RA + 2 * r + 1]), U[r]);
+                            if (SPLIT && (j & 1)) u1[r] = fma(x, p[j * RA + r], u1[r]);
+                            else u0[r] = fma(x, p[j * RA + r], u0[r]);
                         }
                     }
-#pragma unroll
-                    for (int r = 0; r < RA; ++r) u0[r] = static_cast<T>(sum2(U[r]));
-                } else {
-                    for (int a = 0; a < nav; a += VN) {
-                        T p[VN * RA];
-                        ld_row<T, VN * RA>(phi + a * RA, p);
-#pragma unroll
-                        for (int j = 0; j < VN; ++j) {
-                            const int ar = min(a + j, tk.na - 1);
-                            const T x = xt[static_cast<size_t>(ar) * IB];
-#pragma unroll
-                            for (int r = 0; r < RA; ++r) {
-                                if (SPLIT && (j & 1)) u1[r] = fma(x, p[j * RA + r], u1[r]);
-                                else u0[r] = fma(x, p[j * RA + r], u0[r]);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int r = 0; r < RA; ++r) u0[r] += u1[r];
                 }
+#pragma unroll
+                for (int r = 0; r < RA; ++r) u0[r] += u1[r];
                 if (l2 < 0) {
 #pragma unroll
                     for (int r = 0; r < RA; ++r) z[0][r] += colok ? u0[r] : T(0);

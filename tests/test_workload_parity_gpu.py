@@ -132,10 +132,9 @@ def test_graph_path_long_contiguous_mode_one_sweep_matches_oracle(dims, edge):
 def test_graph_path_rows_per_lane_two_sweeps_match_oracle(dims, edge, rows_per_lane, precision, tol, monkeypatch):
     """The streaming contraction with one row per lane and with two (tasks of
     up to 64 rows; order 4, R_{k,B} = R_{k,l2}, more than 32 rows), for the
-    modes k < N - 1 and for the last mode; FP64 (1e-10) and the mixed path,
-    whose FP32 inner loops run on packed f32x2 pairs (relative error against
-    the FP64 oracle after two sweeps below 2e-4; FP32 contractions with
-    about 1e-6 relative error per mode system)."""
+    modes k < N - 1 and for the last mode; FP64 (1e-10) and the mixed path
+    (relative error against the FP64 oracle after two sweeps below 2e-4; its
+    FP32 contractions carry about 1e-6 relative error per mode system)."""
     from tests._cases import make_case
     monkeypatch.setenv("IFCTN_CW_RPL", rows_per_lane)
     case = make_case(dims, edge, 0.3, seed=461, kind="max1", sigma=0.02)
