@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64"])
-    ap.add_argument("--extra-workloads", default="msi256x256x31_r6",
+    ap.add_argument("--extra-workloads", default="msi256x256x31_r6,video144x176x3x100",
                     help="comma-separated workloads also timed (metric, FP64 path, roofline, RSE error)")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream entry")
     ap.add_argument("--quick", action="store_true",

@@ -212,7 +212,8 @@ ifctn_status ifctn_sweep_exchange(ifctn_ctx* ctx, int32_t n, ifctn_allreduce_fn 
    *timed (nullable) receives the number of candidate plans timed (0 when the
    cache answered every mode).  Contexts created while the environment
    variable IFCTN_TUNE_CACHE names a file tune themselves this way at
-   creation.  Contexts whose sweeps run as one persistent launch have no
+   creation; the contexts of a server's jobs only read that cache (a job
+   never waits for timing), and shapes it lacks keep the planner's default.  Contexts whose sweeps run as one persistent launch have no
    choices to make (*timed = 0). */
 ifctn_status ifctn_tune(ifctn_ctx* ctx, const char* cache_path, int32_t* timed);
 

@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ifctn.h"
 #include "ifctn_api_internal.h"
 #include "ifctn_launch.h"
@@ -871,6 +873,21 @@ bool choose_graph_only(const Shape& sh, int sz) {
     return sh.P * static_cast<long long>(sz) > L2_RESIDENT_BYTES;
 }
 
+// NVTX range over a scope (header-only NVTX3: free unless a profiler injects a
+// tool).  The host-side enqueue of each stage is named, so that a timeline shows
+// the stages of the per-stage path, the exchange of the sharded sweep, tuning
+// and graph or persistent sweep launches.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+const char* const kModeSystems[MAXN] = {"ifctn mode 1 contraction+Gram", "ifctn mode 2 contraction+Gram",
+                                        "ifctn mode 3 contraction+Gram", "ifctn mode 4 contraction+Gram"};
+const char* const kModeSolves[MAXN] = {"ifctn mode 1 solves", "ifctn mode 2 solves", "ifctn mode 3 solves",
+                                       "ifctn mode 4 solves"};
+
 #ifndef IFCTN_SOURCE_DIGEST
 #define IFCTN_SOURCE_DIGEST "unversioned"
 #endif
@@ -919,6 +936,9 @@ struct Engine : ifctn_ctx {
     DevBuf<unsigned long long> tstamp;  // [0,64): phase ends; [64 + k*512 + cta]: per-CTA phase-1 ends
     long long launch_count = 0;
     int ex_sweeps = 0;  // sweeps run by sweep_exchange
+    // creation-time tuning (IFCTN_TUNE_CACHE) may time candidates; contexts
+    // of served jobs only read the cache, so a job never pays for timing
+    bool tune_timing = true;
     double cur_tol = 0.0;
 
     int* counter() { return ints.p; }
@@ -1069,7 +1089,7 @@ struct Engine : ifctn_ctx {
         // and added to it where the cache has no entry for this shape)
         if (const char* path = getenv("IFCTN_TUNE_CACHE")) {
             if (*path && graph_only) {
-                rs = tune(path, nullptr);
+                rs = tune(path, nullptr, !tune_timing);
                 if (rs != IFCTN_OK) return rs;
                 return IFCTN_OK;  // tune() rebuilt the graph
             }
@@ -1150,7 +1170,10 @@ struct Engine : ifctn_ctx {
     // task size, unit chunking), keeps the fastest by the rule of
     // tune_choose(), and appends it to the cache.  Then re-lays the unit
     // descriptors and rebuilds the sweep graph.
-    ifctn_status tune(const char* path, int* ntimed) {
+    ifctn_status tune(const char* path, int* ntimed) override { return tune(path, ntimed, false); }
+
+    ifctn_status tune(const char* path, int* ntimed, bool lookup_only) {
+        NvtxRange nr("ifctn tune");
         int timed = 0;
         std::vector<std::string> lines;
         if (path && *path) {
@@ -1186,7 +1209,7 @@ struct Engine : ifctn_ctx {
                         }
                     }
                 }
-                if (!cached) {
+                if (!cached && !lookup_only) {
                     std::vector<WarpKnobs> cands(1, default_warp_knobs());
                     for (int rpl : {1, 0})
                         for (int stg : {0, 2, 3})
@@ -1393,6 +1416,7 @@ struct Engine : ifctn_ctx {
     }
 
     ifctn_status launch_run(int n) {
+        NvtxRange nr("ifctn sweeps");
         if (n <= 0) return IFCTN_OK;
         if (persistent) {
             // at most 65536 sweeps a launch: the grid barrier's arrival counter
@@ -1468,6 +1492,7 @@ struct Engine : ifctn_ctx {
 
     // mode-k systems: Gram on the side stream, contraction on the main one
     cudaError_t enqueue_mode_systems(int k) {
+        NvtxRange r(kModeSystems[k]);
         cudaError_t e;
         if ((e = cudaEventRecord(ev_fork[k], st)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(side, ev_fork[k], 0)) != cudaSuccess) return e;
@@ -1484,9 +1509,11 @@ struct Engine : ifctn_ctx {
         cudaError_t e;
         for (int k = 0; k < sh.N; ++k) {
             if ((e = enqueue_mode_systems(k)) != cudaSuccess) return e;
+            NvtxRange r(kModeSolves[k]);
             if ((e = launch_solve_cols<T>(pp, k, st)) != cudaSuccess)
                 return e;
         }
+        NvtxRange r("ifctn X update");
         pp.Xt = (logm && truth) ? Xt.p : nullptr;
         const int xb = slab_xblocks();
         if ((e = launch_xupdate_slab<T>(pp, xpart.p, xb, st)) != cudaSuccess) return e;
@@ -1744,8 +1771,10 @@ struct Engine : ifctn_ctx {
         std::vector<double> hb(need);
         std::vector<T> kt;
         double sums[3] = {0, 0, 0};
+        NvtxRange nr("ifctn sharded sweeps");
         for (int s_ = 0; s_ < n; ++s_) {
             for (int k = 0; k < sh.N; ++k) {
+                NvtxRange mr(kModeSystems[k]);
                 CK(launch_contract<T>(cargs(k), st));
                 CK(launch_contract_finish<T>(sh, k, plan[k], units.p + unit_off[k], part.p, Gt.p, Mk[k].p, done(),
                                              st));
@@ -1762,6 +1791,7 @@ struct Engine : ifctn_ctx {
                         ++launch_count;
                     }
                     CK(cudaStreamSynchronize(st));
+                    NvtxRange xr("ifctn exchange");
                     if (fn(user, hb.data(), nm + Q * Q) != 0) {
                         set_error("the allreduce function failed");
                         return IFCTN_EINVAL;
@@ -1925,7 +1955,7 @@ template struct Engine<float>;
 template struct Engine<double>;
 
 ifctn_status create_ctx(const ifctn_problem* prob, const void* obs, const uint8_t* mask, const double* init,
-                        void* stream, ifctn_ctx** out) {
+                        void* stream, ifctn_ctx** out, bool tune_timing) {
     if (!out || !prob) {
         set_error("null argument");
         return IFCTN_EINVAL;
@@ -1935,10 +1965,12 @@ ifctn_status create_ctx(const ifctn_problem* prob, const void* obs, const uint8_
     ifctn_status rs;
     if (prob->precision == IFCTN_FP64) {
         auto* e = new Engine<double>();
+        e->tune_timing = tune_timing;
         rs = e->init(prob, obs, mask, init, stream);
         c = e;
     } else {
         auto* e = new Engine<float>();
+        e->tune_timing = tune_timing;
         rs = e->init(prob, obs, mask, init, stream);
         c = e;
     }
@@ -1962,7 +1994,7 @@ extern "C" {
 ifctn_status ifctn_create(const ifctn_problem* prob, const void* obs, const uint8_t* mask,
                           const double* init_factors, void* cuda_stream, ifctn_ctx** out) {
     g_last_error.clear();
-    return create_ctx(prob, obs, mask, init_factors, cuda_stream, out);
+    return create_ctx(prob, obs, mask, init_factors, cuda_stream, out, true);
 }
 
 #define IFCTN_CTX_CALL(ctx, expr)          \

@@ -12,8 +12,10 @@ namespace ifctn {
 void set_error(const std::string& m);
 ifctn_status build_shape(const ifctn_problem* p, Shape& s);
 int mode_q(const Shape& s, int k);
+// tune_timing: a context created while IFCTN_TUNE_CACHE names a file may time
+// launch-shape candidates for shapes the cache lacks (false: cache lookups only)
 ifctn_status create_ctx(const ifctn_problem* prob, const void* obs, const uint8_t* mask, const double* init,
-                        void* stream, ifctn_ctx** out);
+                        void* stream, ifctn_ctx** out, bool tune_timing);
 size_t ctx_device_bytes(const ifctn_ctx* c);
 // asynchronous use by the server: enqueue n sweeps (tolerance tol) on the
 // context's stream without waiting.

@@ -98,7 +98,7 @@ void ifctn_server::run() {
             in_use += j->bytes;
             lk.unlock();
             ifctn_ctx* c = nullptr;
-            ifctn_status rs = create_ctx(&j->prob, j->obs, j->mask, j->init, nullptr, &c);
+            ifctn_status rs = create_ctx(&j->prob, j->obs, j->mask, j->init, nullptr, &c, false);
             if (rs == IFCTN_OK) rs = ctx_enqueue(c, 0, j->prob.tol, true);
             if (rs == IFCTN_OK && cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming) != cudaSuccess)
                 rs = IFCTN_ECUDA;
