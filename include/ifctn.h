@@ -268,10 +268,17 @@ ifctn_status ifctn_reconstruct_noalloc(int32_t order, const int64_t* dims, const
    A server owns a device-memory budget and up to max_slots resident jobs.
    ifctn_submit copies the job's inputs to pinned host memory and queues it;
    a scheduler thread admits queued jobs in arrival order as slots and budget
-   free up, runs the resident jobs' sweeps interleaved on separate CUDA streams
-   (so their kernels overlap on the device), and copies each result to pinned
-   host memory when its job finishes.  Every job runs exactly the kernels it
-   would run alone, so its result does not depend on the mix.
+   free up and keeps every resident job's sweeps in flight:
+     - jobs whose sweeps run as one persistent launch (tensors that stay in
+       L2) are batched: one cooperative launch per round runs a few sweeps of
+       each such job (one dtype per round), every job on its own slice of the
+       grid with its own barriers, stop test and logs;
+     - larger jobs run their sweep graphs on separate CUDA streams, so their
+       kernels overlap on the device.
+   Each result is copied to pinned host memory when its job finishes.  A job
+   runs the same kernel code and the same fixed-order reductions alone or in
+   a mix (the persistent kernel's results do not depend on its grid), so its
+   result does not depend on the mix.
    --------------------------------------------------------------------------- */
 ifctn_status ifctn_server_create(size_t hbm_budget_bytes, int32_t max_slots, ifctn_server** out);
 
@@ -289,11 +296,13 @@ ifctn_status ifctn_poll(ifctn_server* srv, uint64_t ticket, void* out_X, ifctn_s
                         int64_t timeout_us);
 
 /* Server counters: jobs queued, resident and completed; device bytes in use;
-   the largest number of jobs resident at once. */
+   the largest number of jobs resident at once; the shared persistent launches
+   run so far and the job rounds they carried (see the serving notes above). */
 typedef struct {
     int64_t queued, resident, completed;
     int64_t bytes_in_use;
     int64_t peak_resident;
+    int64_t batch_launches, batched_jobs;
 } ifctn_server_info;
 ifctn_status ifctn_server_info_get(ifctn_server* srv, ifctn_server_info* out);
 

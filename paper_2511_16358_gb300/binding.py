@@ -51,7 +51,8 @@ class Stats(ctypes.Structure):
 
 class ServerInfo(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int64), ("resident", ctypes.c_int64), ("completed", ctypes.c_int64),
-                ("bytes_in_use", ctypes.c_int64), ("peak_resident", ctypes.c_int64)]
+                ("bytes_in_use", ctypes.c_int64), ("peak_resident", ctypes.c_int64),
+                ("batch_launches", ctypes.c_int64), ("batched_jobs", ctypes.c_int64)]
 
 
 # int32_t (*)(void* user, double* values, int64_t count)

@@ -859,6 +859,9 @@ struct ifctn_ctx {
     virtual ifctn_status phase_times(double* out, int max, int* n) = 0;
     virtual void set_grid_cap(int g) = 0;
     virtual cudaStream_t stream() const = 0;
+    // batched persistent launches (serving): the element size of the context's
+    // dtype when its sweeps run as one persistent launch, else 0
+    virtual int batch_kind() const = 0;
 };
 
 namespace ifctn {
@@ -1721,6 +1724,23 @@ struct Engine : ifctn_ctx {
         if (n) *n = persistent ? cnt : 0;
         return IFCTN_OK;
     }
+    int batch_kind() const override { return persistent ? static_cast<int>(sizeof(T)) : 0; }
+
+    // Prepares n sweeps of this context for a launch shared with other jobs:
+    // the per-launch state (grid-barrier counter) is reset on stream bst, and
+    // *out receives the launch parameters for the CTA slice [cta0, cta0 + ncta).
+    ifctn_status batch_prepare(int n, cudaStream_t bst, int cta0, int ncta, SweepParams<T>* out) {
+        pp.nsweeps = n;
+        pp.tolv = cur_tol;
+        pp.Xt = (logm && truth) ? Xt.p : nullptr;
+        CK(cudaMemsetAsync(bar.p, 0, 4 * sizeof(unsigned), bst));
+        *out = pp;
+        out->cta0 = cta0;
+        out->ncta = ncta;
+        ++launch_count;
+        return IFCTN_OK;
+    }
+
     void set_grid_cap(int g) override {
         grid_cap = g;
         setup_persistent();
@@ -1983,6 +2003,81 @@ ifctn_status create_ctx(const ifctn_problem* prob, const void* obs, const uint8_
 }
 
 size_t ctx_device_bytes(const ifctn_ctx* c) { return c ? c->device_bytes() : 0; }
+int ctx_batch_kind(const ifctn_ctx* c) { return c ? c->batch_kind() : 0; }
+
+namespace {
+
+// One cooperative launch that runs ns[i] sweeps of each persistent-path
+// context ctxs[i] (all of the same dtype) on its own slice of the grid.  Every
+// job gets at least one CTA and at most its own full-launch grid, the rest in
+// proportion to its tensor size; the kernel and the per-job arithmetic are
+// those of the job's own launch, whose results do not depend on the grid size.
+template <typename T>
+ifctn_status run_batch_t(ifctn_ctx* const* ctxs, const int* ns, int nj, cudaStream_t bst) {
+    std::vector<Engine<T>*> es(nj);
+    int smem = 0;
+    double wsum = 0;
+    for (int i = 0; i < nj; ++i) {
+        es[i] = static_cast<Engine<T>*>(ctxs[i]);
+        smem = std::max(smem, es[i]->psmem);
+        wsum += static_cast<double>(es[i]->sh.P);
+    }
+    const int gmax = persistent_multi_max_grid<T>(smem);
+    if (gmax < nj) {
+        set_error("a batched launch cannot give every job a CTA");
+        return IFCTN_ECUDA;
+    }
+    std::vector<int> nc(nj);
+    int used = 0;
+    for (int i = 0; i < nj; ++i) {
+        const double share = static_cast<double>(es[i]->sh.P) / wsum;
+        nc[i] = std::max(1, std::min(es[i]->pgrid, static_cast<int>(share * (gmax - nj)) + 1));
+        used += nc[i];
+    }
+    while (used > gmax) {  // the +1 floors can overshoot by a few CTAs
+        int big = 0;
+        for (int i = 1; i < nj; ++i)
+            if (nc[i] > nc[big]) big = i;
+        --nc[big];
+        --used;
+    }
+    std::vector<SweepParams<T>> hp(nj);
+    int c0 = 0;
+    for (int i = 0; i < nj; ++i) {
+        ifctn_status rs = es[i]->batch_prepare(ns[i], bst, c0, nc[i], &hp[i]);
+        if (rs != IFCTN_OK) return rs;
+        c0 += nc[i];
+    }
+    SweepParams<T>* dp = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&dp), nj * sizeof(SweepParams<T>), bst));
+    CK(cudaMemcpyAsync(dp, hp.data(), nj * sizeof(SweepParams<T>), cudaMemcpyHostToDevice, bst));
+    const cudaError_t e = launch_persistent_multi<T>(dp, nj, c0, smem, bst);
+    cudaFreeAsync(dp, bst);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("batched persistent launch failed: ") + cudaGetErrorString(e));
+        return IFCTN_ECUDA;
+    }
+    // the host copy of the parameters must outlive the asynchronous upload
+    CK(cudaStreamSynchronize(bst));
+    return IFCTN_OK;
+}
+
+}  // namespace
+
+ifctn_status ctx_run_batch(ifctn_ctx* const* ctxs, const int* nsweeps, int njobs, cudaStream_t bst) {
+    if (njobs <= 0) return IFCTN_OK;
+    const int kind = ctxs[0]->batch_kind();
+    for (int i = 1; i < njobs; ++i)
+        if (ctxs[i]->batch_kind() != kind) {
+            set_error("a batched launch needs jobs of one dtype on the persistent path");
+            return IFCTN_EINVAL;
+        }
+    if (kind == 4) return run_batch_t<float>(ctxs, nsweeps, njobs, bst);
+    if (kind == 8) return run_batch_t<double>(ctxs, nsweeps, njobs, bst);
+    set_error("a batched launch needs contexts on the persistent path");
+    return IFCTN_EINVAL;
+}
 ifctn_status ctx_enqueue(ifctn_ctx* c, int n, double tol, bool reset) { return c->enqueue(n, tol, reset); }
 void ctx_set_grid_cap(ifctn_ctx* c, int g) { c->set_grid_cap(g); }
 cudaStream_t ctx_stream(ifctn_ctx* c) { return c->stream(); }

@@ -17,6 +17,12 @@ int mode_q(const Shape& s, int k);
 ifctn_status create_ctx(const ifctn_problem* prob, const void* obs, const uint8_t* mask, const double* init,
                         void* stream, ifctn_ctx** out, bool tune_timing);
 size_t ctx_device_bytes(const ifctn_ctx* c);
+// serving: element size of a context whose sweeps run as one persistent
+// launch (4 or 8), else 0; and one cooperative launch running nsweeps[i]
+// sweeps of every ctxs[i] (same kind) on a slice of the grid each, on stream
+// bst (returns once the launch is enqueued)
+int ctx_batch_kind(const ifctn_ctx* c);
+ifctn_status ctx_run_batch(ifctn_ctx* const* ctxs, const int* nsweeps, int njobs, cudaStream_t bst);
 // asynchronous use by the server: enqueue n sweeps (tolerance tol) on the
 // context's stream without waiting.
 ifctn_status ctx_enqueue(ifctn_ctx* c, int n, double tol, bool reset);

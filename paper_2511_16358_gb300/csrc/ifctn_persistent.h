@@ -46,6 +46,7 @@ struct SweepParams {
     int xu_rows;                 // X update: rows of a slab per work unit
     int xu_wab_smem;             // X update: W_{A,B} kept in shared memory
     int xu_variant;              // X update (per-stage path): batch / residency variant
+    int cta0, ncta;              // the job's slice of the launch's grid (first CTA, CTA count)
 };
 
 // Index tables of the column solves of mode k (the same for every column):
@@ -93,6 +94,12 @@ template <typename T>
 int persistent_max_grid(int smem);
 template <typename T>
 cudaError_t launch_persistent(const SweepParams<T>& p, int grid, int smem, cudaStream_t st);
+// several jobs in one cooperative launch (jobs: device array, slices in
+// ascending cta0 covering [0, grid)); the occupancy-limited grid of that kernel
+template <typename T>
+cudaError_t launch_persistent_multi(const SweepParams<T>* jobs, int njobs, int grid, int smem, cudaStream_t st);
+template <typename T>
+int persistent_multi_max_grid(int smem);
 // the column solves of mode k with the W_{k,.} refresh (per-stage path)
 template <typename T>
 cudaError_t launch_solve_cols(const SweepParams<T>& p, int k, cudaStream_t st);

@@ -11,5 +11,7 @@ template cudaError_t launch_contract_finish<float>(const Shape&, int, const Cont
 template int persistent_smem_bytes<float>(const SweepParams<float>&);
 template cudaError_t launch_persistent<float>(const SweepParams<float>&, int, int, cudaStream_t);
 template int persistent_max_grid<float>(int);
+template cudaError_t launch_persistent_multi<float>(const SweepParams<float>*, int, int, int, cudaStream_t);
+template int persistent_multi_max_grid<float>(int);
 template cudaError_t launch_solve_cols<float>(const SweepParams<float>&, int, cudaStream_t);
 }  // namespace ifctn

@@ -11,5 +11,7 @@ template cudaError_t launch_contract_finish<double>(const Shape&, int, const Con
 template int persistent_smem_bytes<double>(const SweepParams<double>&);
 template cudaError_t launch_persistent<double>(const SweepParams<double>&, int, int, cudaStream_t);
 template int persistent_max_grid<double>(int);
+template cudaError_t launch_persistent_multi<double>(const SweepParams<double>*, int, int, int, cudaStream_t);
+template int persistent_multi_max_grid<double>(int);
 template cudaError_t launch_solve_cols<double>(const SweepParams<double>&, int, cudaStream_t);
 }  // namespace ifctn

@@ -50,10 +50,11 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 
 
 
-// Software grid barrier (the grid is co-resident: cooperative launch).  The
-// arrival counter only grows during a launch (the host zeroes it before each
-// launch): barrier number b of the launch is passed once it reaches
-// b * gridDim.x.  Thread 0 of a CTA arrives with a release reduction and
+// Software grid barrier over the nctas CTAs of one job (the grid is
+// co-resident: cooperative launch; several jobs can share a launch, each with
+// its own counter).  The arrival counter only grows during a launch (the host
+// zeroes it before each launch): barrier number b of the launch is passed
+// once it reaches b * nctas.  Thread 0 of a CTA arrives with a release reduction and
 // spins with acquire loads until the target, bounded by a clock budget (on
 // expiry: timeout flag, and the kernel returns).  Every CTA passes the same
 // sequence of barriers, so `nb` (this CTA's count of barriers passed) agrees.
@@ -61,13 +62,13 @@ __device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& nb, int* flags,
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& nb, int* flags, unsigned nctas,
                                              long long budget = WAIT_BUDGET_CYCLES) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
     ++nb;
     if (threadIdx.x == 0) {
-        const unsigned target = nb * gridDim.x;
+        const unsigned target = nb * nctas;
         red_release_add_u32(count, 1u);
         const long long t0 = clock64();
         while (ld_acquire_u32(count) < target) {
@@ -258,12 +259,20 @@ __device__ void gram_unit(const SweepParams<T>& p, int k, int gu, unsigned char*
 // Phase 2: K_k and M_k from the partials.  A group of L lanes reduces one
 // output; the groups of the whole grid share the outputs.
 // ---------------------------------------------------------------------------
+// The CTA's index within its job and the job's CTA count: a launch can run
+// several jobs on consecutive slices of its grid (cta0 = the slice's first CTA).
+template <typename T>
+__device__ __forceinline__ int vbid(const SweepParams<T>& p) {
+    return static_cast<int>(blockIdx.x) - p.cta0;
+}
+
 template <typename T>
 __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem, bool stamp = false) {
+    const int VB = vbid(p), VG = p.ncta;  // this job's CTA index and grid size
     const Shape& s = p.sh;
     // sub-step timestamps (slots 52..55) of CTA 0, thread 0, when `stamp` is set
     auto rstamp = [&](int n) {
-        if (stamp && p.tstamp && blockIdx.x == 0 && threadIdx.x == 0) p.tstamp[52 + n] = gtimer();
+        if (stamp && p.tstamp && VB == 0 && threadIdx.x == 0) p.tstamp[52 + n] = gtimer();
     };
     rstamp(0);
     const ContractPlan& pl = p.pl[k];
@@ -274,8 +283,8 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
     for (int t = 1; t < nm; ++t) Q2 *= s.R[k][m[t]];
     const int Q = Ro * Q2;
     const int lane = threadIdx.x & 31;
-    const long long gwarp = static_cast<long long>(blockIdx.x) * PW + (threadIdx.x >> 5);
-    const long long nwarps = static_cast<long long>(gridDim.x) * PW;
+    const long long gwarp = static_cast<long long>(VB) * PW + (threadIdx.x >> 5);
+    const long long nwarps = static_cast<long long>(VG) * PW;
     // --- K (upper triangle, mirrored) ---
     {
         const int L = pow2_at_least((Io + 3) / 4);
@@ -327,14 +336,14 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
         const int Qp = pl.Qp;
         const int ncol = pl.nrow * Qp;
         int TW = 32;
-        while (TW > 8 && (ncol + TW - 1) / TW < static_cast<int>(gridDim.x)) TW >>= 1;
+        while (TW > 8 && (ncol + TW - 1) / TW < VG) TW >>= 1;
         const int SUBS = 32 / TW;
         const int ntile = (ncol + TW - 1) / TW;
         const int Rd = pl.dmode >= 0 ? s.R[k][pl.dmode] : 1;
         const int nu = pl.nunits;
         T* coef = reinterpret_cast<T*>(smem);      // Rd x nu
         T* red = coef + ((Rd * nu + 3) & ~3);      // PW x RMAX x 32
-        if (static_cast<int>(blockIdx.x) < ntile) {
+        if (VB < ntile) {
             if (pl.dmode >= 0 && pl.key_div == 1 && nu == s.I[pl.dmode]) {
                 // coef(rd, u) = G_{d,k}(rd, u): the whole table, one copy
                 stage_async(coef, p.Gt + s.goff[pl.dmode][k], Rd * nu);
@@ -350,7 +359,7 @@ __device__ void reduce_phase(const SweepParams<T>& p, int k, unsigned char* smem
             rstamp(2);
             const int warp = threadIdx.x >> 5;
             const int cl = lane % TW, sub = lane / TW;
-            for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+            for (int tile = VB; tile < ntile; tile += VG) {
                 const int c = tile * TW + cl;
                 const bool valid = c < ncol;
                 T acc[RMAX];
@@ -759,12 +768,13 @@ __device__ __forceinline__ bool stage_solve(const T* __restrict__ K, const T* __
 
 template <typename T>
 __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem, bool stamp = false) {
+    const int VB = vbid(p), VG = p.ncta;  // this job's CTA index and grid size
     const Shape& s = p.sh;
     const int Ik = s.I[k];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    bool stamp_col = stamp && p.tstamp && blockIdx.x == 0 && warp == 0;
+    bool stamp_col = stamp && p.tstamp && VB == 0 && warp == 0;
     IFCTN_SSTAMP(0);
-    if (static_cast<int>(blockIdx.x) >= Ik) return;  // no columns for this CTA
+    if (VB >= Ik) return;  // no columns for this CTA
     constexpr bool MIXED = sizeof(T) == 4;
     int m[3];
     const int nm = nonk(s, k, m);
@@ -818,7 +828,7 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
     // what the first column needs (its data, K, the index tables) in one
     // cp.async group; the tables G_{i,k}, read only by the W refresh, in a
     // second group that is waited for before the refresh
-    const int j0 = warp * gridDim.x + blockIdx.x;
+    const int j0 = warp * VG + VB;
     if (j0 < Ik) fetch_column(j0);
     if (ksm) stage_async(Ks, p.Kk, Q * Q);
     stage_async(cbt, p.stab[k], solve_tab_ints(Q));
@@ -834,12 +844,12 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
     const float rhi = static_cast<float>(rho);
     const float rlo = static_cast<float>(rho - static_cast<double>(rhi));
     // W refresh by the whole CTA when every warp has at most one column
-    const bool cta_refresh = static_cast<long long>(gridDim.x) * PW >= Ik;
+    const bool cta_refresh = static_cast<long long>(VG) * PW >= Ik;
     if (!cta_refresh) {  // every warp refreshes its columns: the tables first
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
     }
-    for (int j = j0; j < Ik; j += gridDim.x * PW) {
+    for (int j = j0; j < Ik; j += VG * PW) {
         if (j != j0) {
             fetch_column(j);
             asm volatile("cp.async.wait_all;" ::: "memory");
@@ -958,16 +968,16 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     if (cta_refresh) {
-        // columns of this CTA: j = w * gridDim.x + blockIdx.x, their new
+        // columns of this CTA: j = w * VG + VB, their new
         // G_{k,i}(:, j) in warp w's scratch (same arithmetic as per warp)
-        const int ncol = min(PW, (Ik - static_cast<int>(blockIdx.x) + static_cast<int>(gridDim.x) - 1) /
-                                     static_cast<int>(gridDim.x));
+        const int ncol = min(PW, (Ik - VB + VG - 1) /
+                                     VG);
         for (int t = 0; t < nm; ++t) {
             const int i = m[t], Ri = Rm[t], Ii = s.I[i];
             const T* gk = gik + gko[t];
             for (int idx = tid; idx < ncol * Ii; idx += PT) {
                 const int w = idx / Ii, b = idx - w * Ii;
-                const int j = w * gridDim.x + blockIdx.x;
+                const int j = w * VG + VB;
                 const T* vtw = warp_scratch_t<T>(smem, w) + SC_VT + t * RMAX;
                 T acc = T(0);
 #pragma unroll
@@ -979,7 +989,7 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
                     p.W[s.woff[i][k] + static_cast<long long>(b) * Ik + j] = acc;
             }
         }
-        if (stamp && p.tstamp && blockIdx.x == 0 && threadIdx.x == 0) p.tstamp[40 + 11] = gtimer();
+        if (stamp && p.tstamp && VB == 0 && threadIdx.x == 0) p.tstamp[40 + 11] = gtimer();
     }
 }
 #undef IFCTN_SSTAMP
@@ -1145,6 +1155,7 @@ __device__ __forceinline__ void xacc(const SweepParams<T>& p, const T rho, const
 // applies), which leaves the registers of the element-wise path unused.
 template <typename T, int XB4 = 4, bool VEC_ONLY = false>
 __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned char* smem) {
+    const int VB = vbid(p), VG = p.ncta;  // this job's CTA index and grid size
     const Shape& s = p.sh;
     const int N = s.N, IA = s.IA, IB = s.IB, Am = N - 2, Bm = N - 1;
     const T rho = static_cast<T>(p.rho), inv1p = static_cast<T>(p.inv1p);
@@ -1168,7 +1179,7 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
     T run2[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     const long long rows_total = static_cast<long long>(s.nF) * IA;
     const long long nunit = (rows_total + RU - 1) / RU;
-    for (long long un = blockIdx.x; un < nunit; un += gridDim.x) {
+    for (long long un = VB; un < nunit; un += VG) {
         const long long r0 = un * RU;
         const int nr = static_cast<int>(min(static_cast<long long>(RU), rows_total - r0));
         const long long f0 = r0 / IA;
@@ -1406,14 +1417,15 @@ __global__ void __launch_bounds__(PT) k_solve_cols(const __grid_constant__ Sweep
 // CTA 0 stamps the end of every phase of one sweep of the launch (profiling aid)
 #define IFCTN_STAMP(p, sw, slot)                                                        \
     do {                                                                              \
-        if ((p).tstamp && (sw) == (p).stamp_sweep && blockIdx.x == 0 && threadIdx.x == 0 &&         \
+        if ((p).tstamp && (sw) == (p).stamp_sweep && vbid(p) == 0 && threadIdx.x == 0 &&            \
             (slot) < 64)                                                              \
             (p).tstamp[(slot)] = gtimer();                                            \
     } while (0)
 
+// All sweeps of one job on the CTAs [p.cta0, p.cta0 + p.ncta) of the launch.
 template <typename T>
-__global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const __grid_constant__ SweepParams<T> p) {
-    extern __shared__ __align__(128) unsigned char smem[];
+__device__ __forceinline__ void sweep_body(const SweepParams<T>& p, unsigned char* smem) {
+    const int VB = vbid(p), VG = p.ncta;  // this job's CTA index and grid size
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     unsigned char* work = smem + 128;
     __shared__ ContractArgs<T> cargs[MAXN];
@@ -1435,43 +1447,41 @@ __global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const __grid_constan
             const int nU = p.pl[k].nunits, nG = p.gunits[k];
             if (threadIdx.x == 0) wtag = 0;  // W_{A,B} changes between modes
             __syncthreads();
-            // contraction units first, then the Gram units (they clobber the
-            // shared W_{A,B} cache, so the tag is cleared before them)
             // Gram units first (they start the longest dependency-free work),
             // then the contraction units; a Gram unit clobbers the shared
             // W_{A,B} cache, so the tag is cleared around it
-            for (int w = blockIdx.x; w < nU + nG; w += gridDim.x) {
+            for (int w = VB; w < nU + nG; w += VG) {
                 if (w < nG) {
                     if (threadIdx.x == 0) wtag = 0;
                     gram_unit<T>(p, k, w, work);
-                    if (threadIdx.x == 0 && w + static_cast<int>(gridDim.x) >= nG &&
-                        w + static_cast<int>(gridDim.x) < nU + nG)
-                        prefetch_unit<T>(p, k, w + gridDim.x - nG);
+                    if (threadIdx.x == 0 && w + VG >= nG &&
+                        w + VG < nU + nG)
+                        prefetch_unit<T>(p, k, w + VG - nG);
                 } else {
                     const int cu = w - nG;
-                    if (threadIdx.x == 0 && cu + static_cast<int>(gridDim.x) < nU)
-                        prefetch_unit<T>(p, k, cu + gridDim.x);
+                    if (threadIdx.x == 0 && cu + VG < nU)
+                        prefetch_unit<T>(p, k, cu + VG);
                     if (!contract_dispatch<T>(cargs[k], cu, work, bars, pipe, &wtag)) return;
                 }
             }
             IFCTN_STAMP(p, sw, 1 + 6 * k);
-            if (p.tstamp && sw == p.stamp_sweep && threadIdx.x == 0 && k < 4 && blockIdx.x < 512)
-                p.tstamp[64 + k * 512 + blockIdx.x] = gtimer();
-            if (!grid_barrier(p.bar_count, nbar, p.flags)) return;
+            if (p.tstamp && sw == p.stamp_sweep && threadIdx.x == 0 && k < 4 && VB < 512)
+                p.tstamp[64 + k * 512 + VB] = gtimer();
+            if (!grid_barrier(p.bar_count, nbar, p.flags, VG)) return;
             IFCTN_STAMP(p, sw, 2 + 6 * k);
             reduce_phase<T>(p, k, work, sw == p.stamp_sweep && k == p.stamp_mode);
             IFCTN_STAMP(p, sw, 3 + 6 * k);
-            if (!grid_barrier(p.bar_count, nbar, p.flags)) return;
+            if (!grid_barrier(p.bar_count, nbar, p.flags, VG)) return;
             IFCTN_STAMP(p, sw, 4 + 6 * k);
             solve_phase<T>(p, k, work, sw == p.stamp_sweep && k == p.stamp_mode);
             IFCTN_STAMP(p, sw, 5 + 6 * k);
-            if (!grid_barrier(p.bar_count, nbar, p.flags)) return;
+            if (!grid_barrier(p.bar_count, nbar, p.flags, VG)) return;
             IFCTN_STAMP(p, sw, 6 + 6 * k);
         }
-        double* xp = p.xpart + 8LL * gridDim.x * (sw & 1);
-        xupdate_phase<T>(p, xp + 8 * blockIdx.x, work);
+        double* xp = p.xpart + 8LL * VG * (sw & 1);
+        xupdate_phase<T>(p, xp + 8 * VB, work);
         IFCTN_STAMP(p, sw, 25);
-        if (!grid_barrier(p.bar_count, nbar, p.flags)) return;
+        if (!grid_barrier(p.bar_count, nbar, p.flags, VG)) return;
         IFCTN_STAMP(p, sw, 26);
         // Stop decision (only when a tolerance is set): every CTA sums the
         // per-CTA FP64 values in the same order as the log record below and
@@ -1482,7 +1492,7 @@ __global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const __grid_constan
         if (p.tolv > 0) {
             if (threadIdx.x < 32) {
                 double a0 = 0.0, a1 = 0.0;
-                for (int b = threadIdx.x; b < gridDim.x; b += 32) {
+                for (int b = threadIdx.x; b < VG; b += 32) {
                     a0 += reinterpret_cast<volatile double*>(xp)[8 * b + 0];
                     a1 += reinterpret_cast<volatile double*>(xp)[8 * b + 1];
                 }
@@ -1496,9 +1506,9 @@ __global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const __grid_constan
             __syncthreads();
             conv = redc != 0;
         }
-        if (blockIdx.x == gridDim.x - 1 && threadIdx.x < 32) {
+        if (VB == VG - 1 && threadIdx.x < 32) {
             double a[6] = {0, 0, 0, 0, 0, 0};
-            for (int b = threadIdx.x; b < gridDim.x; b += 32)
+            for (int b = threadIdx.x; b < VG; b += 32)
                 for (int t = 0; t < 6; ++t) a[t] += reinterpret_cast<volatile double*>(xp)[8 * b + t];
             for (int t = 0; t < 6; ++t) a[t] = warp_sum(a[t]);
             if (threadIdx.x == 0) {
@@ -1530,6 +1540,32 @@ __global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const __grid_constan
         // xpart is double-buffered by sweep parity: the buffer read here is
         // rewritten two sweeps later, after many more grid barriers.
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PT, 2) k_sweep_persistent(const __grid_constant__ SweepParams<T> p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    sweep_body<T>(p, smem);
+}
+
+// Several jobs in one cooperative launch: job j runs on the CTAs
+// [jobs[j].cta0, jobs[j].cta0 + jobs[j].ncta) (slices in ascending order,
+// covering the grid), exactly as it would run alone on a grid of that size;
+// its parameters are copied to shared memory once.
+template <typename T>
+__global__ void __launch_bounds__(PT, 2) k_sweep_multi(const SweepParams<T>* __restrict__ jobs, const int njobs) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(16) SweepParams<T> sp;
+    int j = 0;
+    while (j + 1 < njobs && jobs[j + 1].cta0 <= static_cast<int>(blockIdx.x)) ++j;
+    {
+        const int* src = reinterpret_cast<const int*>(jobs + j);
+        int* dst = reinterpret_cast<int*>(&sp);
+        for (int i = threadIdx.x; i < static_cast<int>(sizeof(SweepParams<T>) / sizeof(int)); i += blockDim.x)
+            dst[i] = src[i];
+    }
+    __syncthreads();
+    sweep_body<T>(sp, smem);
 }
 
 }  // namespace
@@ -1572,14 +1608,47 @@ int persistent_smem_bytes(const SweepParams<T>& p) {
 }
 
 template <typename T>
-cudaError_t launch_persistent(const SweepParams<T>& p, int grid, int smem, cudaStream_t st) {
-    void* args[] = {const_cast<SweepParams<T>*>(&p)};
+cudaError_t launch_persistent(const SweepParams<T>& p0, int grid, int smem, cudaStream_t st) {
+    SweepParams<T> p = p0;
+    p.cta0 = 0;
+    p.ncta = grid;
+    void* args[] = {&p};
     return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_sweep_persistent<T>), dim3(grid), dim3(PT), args,
                                        smem, st);
 }
 
+template <typename T>
+cudaError_t launch_persistent_multi(const SweepParams<T>* jobs, int njobs, int grid, int smem, cudaStream_t st) {
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_sweep_multi<T>), smem);
+    if (e != cudaSuccess) return e;
+    void* args[] = {const_cast<SweepParams<T>**>(&jobs), &njobs};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_sweep_multi<T>), dim3(grid), dim3(PT), args, smem,
+                                       st);
+}
+
+template <typename T>
+int persistent_multi_max_grid(int smem) {
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_sweep_multi<T>), smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_multi<T>, PT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return per * sms;
+}
+
 template <typename T, int XB4, int MINB, bool VEC_ONLY>
-cudaError_t launch_xupdate_slab_v(const SweepParams<T>& p, double* xpart, int nblocks, cudaStream_t st) {
+cudaError_t launch_xupdate_slab_v(const SweepParams<T>& p0, double* xpart, int nblocks, cudaStream_t st) {
+    SweepParams<T> p = p0;
+    p.cta0 = 0;
+    p.ncta = nblocks;
     const int smem = static_cast<int>((static_cast<long long>(p.xu_wab_smem ? p.sh.IA * p.sh.IB : 0) + p.xu_rows +
                                        static_cast<long long>((p.xu_rows + p.sh.IA - 1) / p.sh.IA + 1) * p.sh.IB) *
                                       sizeof(T)) + 64;
@@ -1621,7 +1690,9 @@ cudaError_t launch_solve_cols(const SweepParams<T>& p0, int k, cudaStream_t st) 
     const int smem = static_cast<int>(solve_layout(Q, tot, sz, p.solve_k_in_smem != 0).total + 64);
     cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_solve_cols<T>), smem);
     if (e != cudaSuccess) return e;
-    k_solve_cols<T><<<(s.I[k] + PW - 1) / PW, PT, smem, st>>>(p, k);
+    p.cta0 = 0;
+    p.ncta = (s.I[k] + PW - 1) / PW;
+    k_solve_cols<T><<<p.ncta, PT, smem, st>>>(p, k);
     return cudaGetLastError();
 }
 

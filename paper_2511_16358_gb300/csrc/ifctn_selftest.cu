@@ -17,7 +17,7 @@ __global__ void k_wait_selftest(int* flags, unsigned* count, long long budget) {
     __shared__ __align__(8) uint64_t bar;
     if (blockIdx.x != 0) return;  // CTA 1 never arrives at the barrier
     unsigned nb = 0;
-    grid_barrier(count, nb, flags, budget);  // waits for 2 arrivals, 1 comes
+    grid_barrier(count, nb, flags, gridDim.x, budget);  // waits for 2 arrivals, 1 comes
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();

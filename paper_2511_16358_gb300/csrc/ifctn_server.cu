@@ -41,6 +41,7 @@ struct Job {
     ifctn_ctx* ctx = nullptr;
     cudaEvent_t ev = nullptr;
     int enqueued = 0;
+    bool batch_pending = false;  // part of the shared launch in flight
     size_t bytes = 0;
     JobState state = QUEUED;
     ifctn_status err = IFCTN_OK;
@@ -78,8 +79,15 @@ struct ifctn_server {
     uint64_t next_ticket = 1;
     size_t in_use = 0;
     int64_t completed = 0, peak_resident = 0;
+    int64_t batch_launches = 0, batched_jobs = 0;
     bool stop = false;
     std::thread worker;
+    // jobs whose sweeps run as one persistent launch share one cooperative
+    // launch per round, on this stream, each on its own slice of the grid
+    cudaStream_t bst = nullptr;
+    cudaEvent_t bev = nullptr;
+    bool batch_inflight = false;
+    std::vector<std::shared_ptr<Job>> batch_members;
 
     void run();
     void admit_locked_unlock(std::unique_lock<std::mutex>& lk);
@@ -88,6 +96,9 @@ struct ifctn_server {
 void ifctn_server::run() {
     cudaSetDevice(device);
     const int kInflight = 4;  // sweeps kept queued per resident job
+    const int kRound = 4;     // sweeps of every job in one shared persistent launch
+    cudaStreamCreateWithFlags(&bst, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&bev, cudaEventDisableTiming);
     std::unique_lock<std::mutex> lk(mu);
     while (!stop) {
         // 1. admission, in arrival order
@@ -100,6 +111,10 @@ void ifctn_server::run() {
             ifctn_ctx* c = nullptr;
             ifctn_status rs = create_ctx(&j->prob, j->obs, j->mask, j->init, nullptr, &c, false);
             if (rs == IFCTN_OK) rs = ctx_enqueue(c, 0, j->prob.tol, true);
+            // a job of the shared launches runs on the server's stream: its own
+            // stream's set-up must be complete first
+            if (rs == IFCTN_OK && ctx_batch_kind(c) && cudaStreamSynchronize(ctx_stream(c)) != cudaSuccess)
+                rs = IFCTN_ECUDA;
             if (rs == IFCTN_OK && cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming) != cudaSuccess)
                 rs = IFCTN_ECUDA;
             lk.lock();
@@ -135,10 +150,56 @@ void ifctn_server::run() {
         std::vector<std::shared_ptr<Job>> snap = resident;
         lk.unlock();
         bool progressed = false;
+        // 2a. jobs on the persistent path: one shared cooperative launch per
+        // round (kRound sweeps of each, one dtype per round)
+        if (batch_inflight && cudaEventQuery(bev) == cudaSuccess) {
+            batch_inflight = false;
+            for (auto& j : batch_members) j->batch_pending = false;
+            batch_members.clear();
+            progressed = true;
+        }
+        if (!batch_inflight) {
+            std::vector<std::shared_ptr<Job>> mem;
+            std::vector<ifctn_ctx*> cs;
+            std::vector<int> ns;
+            int kind = 0;
+            for (auto& j : snap) {
+                if (j->state != RESIDENT || j->err != IFCTN_OK || j->enqueued >= j->prob.max_sweeps) continue;
+                const int k = ctx_batch_kind(j->ctx);
+                if (!k) continue;
+                if (!kind) kind = k;
+                if (k != kind) continue;
+                mem.push_back(j);
+                cs.push_back(j->ctx);
+                ns.push_back(std::min(kRound, j->prob.max_sweeps - j->enqueued));
+            }
+            if (!mem.empty()) {
+                ifctn_status rs = ctx_run_batch(cs.data(), ns.data(), static_cast<int>(cs.size()), bst);
+                if (rs == IFCTN_OK && cudaEventRecord(bev, bst) != cudaSuccess) rs = IFCTN_ECUDA;
+                for (size_t i = 0; i < mem.size(); ++i) {
+                    mem[i]->enqueued += ns[i];
+                    if (rs != IFCTN_OK) {
+                        mem[i]->err = rs;
+                        mem[i]->msg = ifctn_last_error();
+                    } else {
+                        mem[i]->batch_pending = true;
+                    }
+                }
+                if (rs == IFCTN_OK) {
+                    batch_members = mem;
+                    batch_inflight = true;
+                    ++batch_launches;
+                    batched_jobs += static_cast<int64_t>(mem.size());
+                }
+                progressed = true;
+            }
+        }
         for (auto& j : snap) {
             if (j->state == RESIDENT) {
                 const int total = j->prob.max_sweeps;
-                if (j->enqueued < total) {
+                const bool shared = ctx_batch_kind(j->ctx) != 0;
+                if (shared && (j->batch_pending || (j->enqueued < total && j->err == IFCTN_OK))) continue;
+                if (j->enqueued < total && !shared) {
                     // only top up when the previous batch has drained
                     if (j->enqueued == 0 || cudaEventQuery(j->ev) == cudaSuccess) {
                         const int n = std::min(kInflight, total - j->enqueued);
@@ -151,7 +212,7 @@ void ifctn_server::run() {
                             j->msg = ifctn_last_error();
                         }
                     }
-                } else if (cudaEventQuery(j->ev) == cudaSuccess || total == 0) {
+                } else if (shared || cudaEventQuery(j->ev) == cudaSuccess || total == 0) {
                     // 3. result to pinned host memory
                     ifctn_status rs = j->err;
                     if (rs == IFCTN_OK) rs = ifctn_sweep(j->ctx, 0, &j->stats);
@@ -311,6 +372,8 @@ ifctn_status ifctn_server_info_get(ifctn_server* srv, ifctn_server_info* out) {
     out->completed = srv->completed;
     out->bytes_in_use = static_cast<int64_t>(srv->in_use);
     out->peak_resident = srv->peak_resident;
+    out->batch_launches = srv->batch_launches;
+    out->batched_jobs = srv->batched_jobs;
     return IFCTN_OK;
 }
 
@@ -331,6 +394,11 @@ void ifctn_server_destroy(ifctn_server* srv) {
     }
     srv->cv_work.notify_all();
     if (srv->worker.joinable()) srv->worker.join();
+    if (srv->bst) {
+        cudaStreamSynchronize(srv->bst);
+        cudaStreamDestroy(srv->bst);
+    }
+    if (srv->bev) cudaEventDestroy(srv->bev);
     for (auto& j : srv->resident) {
         if (j->ctx) ifctn_destroy(j->ctx);
         if (j->ev) cudaEventDestroy(j->ev);

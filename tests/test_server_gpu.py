@@ -2,7 +2,9 @@
 
 - A job's result is the same alone and in a mix of jobs of other orders,
   sizes, ranks and precisions that are resident at the same time (bitwise:
-  every job runs the kernels it would run alone, in the same order).
+  every job runs the kernel code it would run alone, in the same order; jobs
+  whose tensors stay in L2 share cooperative launches, each on its own slice
+  of the grid, and the persistent kernel's results do not depend on the grid).
 - Its result equals the oracle's (FP64 path within 1e-10).
 - Admission follows the device-memory budget: with room for one job at a
   time, jobs run one after another and all complete.
@@ -67,6 +69,9 @@ def test_result_same_alone_and_in_the_mix_and_matches_oracle():
     b.server_destroy(srv)
     assert info["completed"] == len(JOBS)
     assert info["peak_resident"] >= 2
+    # these tensors stay in L2: their sweeps ran in shared persistent launches,
+    # several jobs a launch
+    assert info["batch_launches"] > 0 and info["batched_jobs"] > info["batch_launches"]
     for a, m in zip(alone, mixed):
         np.testing.assert_array_equal(a, m)
     # FP64 jobs against the oracle
