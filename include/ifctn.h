@@ -212,8 +212,13 @@ ifctn_status ifctn_sweep_exchange(ifctn_ctx* ctx, int32_t n, ifctn_allreduce_fn 
    *timed (nullable) receives the number of candidate plans timed (0 when the
    cache answered every mode).  Contexts created while the environment
    variable IFCTN_TUNE_CACHE names a file tune themselves this way at
-   creation; the contexts of a server's jobs only read that cache (a job
-   never waits for timing), and shapes it lacks keep the planner's default.  Contexts whose sweeps run as one persistent launch have no
+   creation.  Such a creation also picks the execution path of a tensor small
+   enough for the one-launch persistent path: unless the cache holds the
+   choice for the shape, both paths are built, ten sweeps of each are timed
+   from the same initial state, the faster context is returned (its state
+   restored to the initial one) and the choice is appended to the cache.  The
+   contexts of a server's jobs only read that cache (a job never waits for
+   timing); shapes it lacks keep the planner's defaults.  Contexts whose sweeps run as one persistent launch have no
    choices to make (*timed = 0). */
 ifctn_status ifctn_tune(ifctn_ctx* ctx, const char* cache_path, int32_t* timed);
 

@@ -942,6 +942,56 @@ struct Engine : ifctn_ctx {
     // creation-time tuning (IFCTN_TUNE_CACHE) may time candidates; contexts
     // of served jobs only read the cache, so a job never pays for timing
     bool tune_timing = true;
+    int force_path = 0;  // 1: sweep graph of per-stage kernels, 2: persistent launch, 0: by size
+    DevBuf<T> snapX;
+    DevBuf<double> snapG;
+
+    // Saves the initial state (X, G) so that sweeps timed to choose the
+    // execution path can be undone by restore_snapshot().
+    ifctn_status snapshot() {
+        if (snapX.alloc(sh.P) != cudaSuccess || snapG.alloc(sh.gsize) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("device allocation failed");
+            return IFCTN_ENOMEM;
+        }
+        CK(cudaMemcpyAsync(snapX.p, X.p, sh.P * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(snapG.p, Gd.p, sh.gsize * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        return IFCTN_OK;
+    }
+    // Back to the saved state, with the sweep counter, log and flags as at creation.
+    ifctn_status restore_snapshot() {
+        CK(cudaMemcpyAsync(X.p, snapX.p, sh.P * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(Gd.p, snapG.p, sh.gsize * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        ifctn_status rs = refresh_factors();
+        if (rs != IFCTN_OK) return rs;
+        CK(cudaMemsetAsync(ints.p, 0, 4 * sizeof(int), st));
+        CK(cudaStreamSynchronize(st));
+        snapX.release();
+        snapG.release();
+        return IFCTN_OK;
+    }
+    // Device seconds of m sweeps after m warm-up sweeps (CUDA events on the
+    // context's stream), from and back to the saved state.
+    ifctn_status time_sweeps(int m, double* sec) {
+        ifctn_status rs = snapshot();
+        if (rs != IFCTN_OK) return rs;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        rs = enqueue(m, 0.0, true);
+        if (rs == IFCTN_OK && cudaEventRecord(e0, st) != cudaSuccess) rs = IFCTN_ECUDA;
+        if (rs == IFCTN_OK) rs = enqueue(m, 0.0, true);
+        if (rs == IFCTN_OK && cudaEventRecord(e1, st) != cudaSuccess) rs = IFCTN_ECUDA;
+        float ms = 0.f;
+        if (rs == IFCTN_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rs = IFCTN_ECUDA;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rs == IFCTN_OK) rs = check_flags();
+        if (rs != IFCTN_OK) return rs;
+        *sec = 1e-3 * ms;
+        return restore_snapshot();
+    }
     double cur_tol = 0.0;
 
     int* counter() { return ints.p; }
@@ -997,7 +1047,7 @@ struct Engine : ifctn_ctx {
         const int sz = sizeof(T);
         std::vector<UnitDesc> all;
         long long maxpart = 1, maxt1 = 1, maxt2 = 1, maxK = 1;
-        graph_only = choose_graph_only(sh, sz);
+        graph_only = force_path == 1 ? true : force_path == 2 ? false : choose_graph_only(sh, sz);
         for (int k = 0; k < sh.N; ++k) {
             std::vector<UnitDesc> u;
             plan[k].warp = 0;
@@ -1974,6 +2024,108 @@ struct Engine : ifctn_ctx {
 template struct Engine<float>;
 template struct Engine<double>;
 
+namespace {
+
+template <typename T>
+ifctn_status make_engine(const ifctn_problem* prob, const void* obs, const uint8_t* mask, const double* init,
+                         void* stream, bool tune_timing, int force_path, Engine<T>** out) {
+    auto* e = new Engine<T>();
+    e->tune_timing = tune_timing;
+    e->force_path = force_path;
+    const ifctn_status rs = e->init(prob, obs, mask, init, stream);
+    if (rs != IFCTN_OK) {
+        delete e;
+        *out = nullptr;
+        return rs;
+    }
+    *out = e;
+    return IFCTN_OK;
+}
+
+// Cache key of the execution-path choice of a shape (see create_ctx).
+std::string path_key(const Shape& sh, int sz) {
+    std::string key = std::string("ifctn-tune-v1 ") + IFCTN_SOURCE_DIGEST + (sz == 4 ? " f32 " : " f64 ");
+    key += "N" + std::to_string(sh.N);
+    for (int m = 0; m < sh.N; ++m) key += "," + std::to_string(sh.I[m]);
+    key += " R";
+    for (int p2 = 0; p2 < sh.N; ++p2)
+        for (int q = p2 + 1; q < sh.N; ++q) key += std::to_string(sh.R[p2][q]) + ".";
+    key += " path sms" + std::to_string(num_sms());
+    return key;
+}
+
+// The execution path of a tensor that fits the persistent launch's L2 rule:
+// with a tuning cache (IFCTN_TUNE_CACHE), the cached choice for the shape, or,
+// where the cache has none and timing is allowed, both paths are built, 10
+// sweeps of each are timed from the same initial state after 10 warm-up
+// ones, the faster context is kept (its state restored) and the choice is
+// appended to the cache.  IFCTN_PATH overrides everything.
+template <typename T>
+ifctn_status create_tuned(const ifctn_problem* prob, const void* obs, const uint8_t* mask, const double* init,
+                          void* stream, bool tune_timing, ifctn_ctx** out) {
+    Shape sh;
+    ifctn_status rs = build_shape(prob, sh);
+    if (rs != IFCTN_OK) return rs;
+    const int sz = static_cast<int>(sizeof(T));
+    const char* cache = getenv("IFCTN_TUNE_CACHE");
+    int force = 0;
+    if (!getenv("IFCTN_PATH") && cache && *cache && !choose_graph_only(sh, sz)) {
+        const std::string key = path_key(sh, sz);
+        if (FILE* f = fopen(cache, "r")) {
+            char buf[1024];
+            while (fgets(buf, sizeof(buf), f)) {
+                const std::string ln(buf);
+                if (ln.compare(0, key.size(), key) == 0 && ln.size() > key.size() && ln[key.size()] == ' ') {
+                    if (ln.find(" path=graph") != std::string::npos) force = 1;
+                    if (ln.find(" path=persistent") != std::string::npos) force = 2;
+                }
+            }
+            fclose(f);
+        }
+        if (!force && tune_timing) {
+            Engine<T>* a = nullptr;
+            Engine<T>* g = nullptr;
+            rs = make_engine<T>(prob, obs, mask, init, stream, true, 2, &a);
+            if (rs != IFCTN_OK) return rs;
+            rs = make_engine<T>(prob, obs, mask, init, stream, true, 1, &g);
+            if (rs != IFCTN_OK) {
+                delete a;
+                return rs;
+            }
+            double ta = 0, tg = 0;
+            rs = a->time_sweeps(10, &ta);
+            if (rs == IFCTN_OK) rs = g->time_sweeps(10, &tg);
+            if (rs != IFCTN_OK) {
+                delete a;
+                delete g;
+                return rs;
+            }
+            // the size rule's choice (persistent) stays unless the graph beats it by 2 %
+            const bool graph = tg <= 0.98 * ta;
+            if (FILE* f = fopen(cache, "a")) {
+                fprintf(f, "%s path=%s seconds_persistent=%.9g seconds_graph=%.9g\n", key.c_str(),
+                        graph ? "graph" : "persistent", ta / 10, tg / 10);
+                fclose(f);
+            }
+            if (graph) {
+                delete a;
+                *out = g;
+            } else {
+                delete g;
+                *out = a;
+            }
+            return IFCTN_OK;
+        }
+    }
+    Engine<T>* e = nullptr;
+    rs = make_engine<T>(prob, obs, mask, init, stream, tune_timing, force, &e);
+    if (rs != IFCTN_OK) return rs;
+    *out = e;
+    return IFCTN_OK;
+}
+
+}  // namespace
+
 ifctn_status create_ctx(const ifctn_problem* prob, const void* obs, const uint8_t* mask, const double* init,
                         void* stream, ifctn_ctx** out, bool tune_timing) {
     if (!out || !prob) {
@@ -1981,25 +2133,8 @@ ifctn_status create_ctx(const ifctn_problem* prob, const void* obs, const uint8_
         return IFCTN_EINVAL;
     }
     *out = nullptr;
-    ifctn_ctx* c = nullptr;
-    ifctn_status rs;
-    if (prob->precision == IFCTN_FP64) {
-        auto* e = new Engine<double>();
-        e->tune_timing = tune_timing;
-        rs = e->init(prob, obs, mask, init, stream);
-        c = e;
-    } else {
-        auto* e = new Engine<float>();
-        e->tune_timing = tune_timing;
-        rs = e->init(prob, obs, mask, init, stream);
-        c = e;
-    }
-    if (rs != IFCTN_OK) {
-        delete c;
-        return rs;
-    }
-    *out = c;
-    return IFCTN_OK;
+    if (prob->precision == IFCTN_FP64) return create_tuned<double>(prob, obs, mask, init, stream, tune_timing, out);
+    return create_tuned<float>(prob, obs, mask, init, stream, tune_timing, out);
 }
 
 size_t ctx_device_bytes(const ifctn_ctx* c) { return c ? c->device_bytes() : 0; }

@@ -56,3 +56,26 @@ def test_tuner_mixed_precision_and_ignores_malformed_lines(tmp_path):
     oracle.complete(case["dims"], case["R"], 0.1, G, X, case["mask"], max_sweeps=3)
     assert rel_err(c.x().astype(np.float64), X) < 2e-3
     c.close()
+
+
+def test_execution_path_choice_is_timed_once_and_cached(tmp_path, monkeypatch):
+    """A tensor small enough for the one-launch persistent path: creation with
+    a tuning cache times both execution paths, keeps the faster, records the
+    choice; a later creation of the shape reads it; both match the oracle."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("IFCTN_TUNE_CACHE", str(cache))
+    monkeypatch.delenv("IFCTN_PATH", raising=False)
+    case = make_case((16, 15, 6, 20), {(0, 1): 3, (0, 2): 2, (0, 3): 3, (1, 2): 2, (1, 3): 3, (2, 3): 2}, 0.3,
+                     seed=473, kind="max1", sigma=0.02)
+    G, X = case["G0"].copy(), case["X0"].copy()
+    oracle.complete(case["dims"], case["R"], 0.1, G, X, case["mask"], max_sweeps=3)
+    for attempt in range(2):
+        c = b.Completion(case["dims"], case["R"], case["xt"], case["mask"], rho=0.1, max_sweeps=3, tol=0.0,
+                         precision=b.FP64, init_factors=case["G0"].copy())
+        paths = [ln for ln in cache.read_text().splitlines() if " path " in ln]
+        assert len(paths) == 1 and (" path=graph " in paths[0] or " path=persistent " in paths[0])
+        st = c.sweep(3)
+        assert st["sweeps_done"] == 3  # timing sweeps left no trace in the state or the log
+        assert rel_err(c.factors(), G) < 1e-10
+        assert rel_err(c.x(), X) < 1e-10
+        c.close()
