@@ -198,12 +198,13 @@ def aggregate_ranks(torch, dist, seconds, world, units_per_rank, device):
     return seconds, world * units_per_rank / seconds
 
 
-def source_digest() -> str:
-    """Digest of the CUDA sources (as in the build stamp, without the flags)."""
+def source_digest(names=None) -> str:
+    """Digest of CUDA sources under csrc/ (as in the build stamp, without the
+    flags): the named files, or all of them."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2511_16358_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(csrc)):
+    for name in sorted(names if names else os.listdir(csrc)):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -212,16 +213,26 @@ def source_digest() -> str:
 def committed_traffic(kernel: str, workload: str):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
     ``kernel`` on ``workload`` from the committed ncu summary, or None when the
-    summary was taken on other kernel sources than the ones built here."""
+    summary was taken on other sources than the ones built here.  A line that
+    lists ``files=`` (the kernel, the headers it includes and its launch
+    planner) is matched on the digest of those files; otherwise on all of
+    csrc/."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
         lines = open(path).read().splitlines()
     except OSError:
         return None
-    dig = source_digest()
     for ln in lines:
+        if ln.startswith("#"):
+            continue
         f = dict(kv.split("=", 1) for kv in ln.split() if "=" in kv)
-        if f.get("kernel") == kernel and f.get("workload") == workload and f.get("digest") == dig:
+        if f.get("kernel") != kernel or f.get("workload") != workload:
+            continue
+        try:
+            dig = source_digest(f["files"].split(",") if "files" in f else None)
+        except OSError:
+            continue
+        if f.get("digest") == dig:
             return float(f["bytes_per_launch"])
     return None
 
@@ -380,7 +391,8 @@ def roofline_of(b, torch, job, prec, stream, tot, steps, launches_timed):
         r["xupdate"] = {"kernel": "k_xupdate_slab", "algorithmic_bytes_per_launch": xu_bytes,
                         "seconds_per_launch": stt["xupdate"],
                         "achieved": xu_bytes / stt["xupdate"] / 1e9,
-                        "frac": xu_bytes / stt["xupdate"] / 1e9 / hbm}
+                        "frac": xu_bytes / stt["xupdate"] / 1e9 / hbm,
+                        "traffic": committed_traffic("k_xupdate_slab", w.name)}
     if persistent:
         r["note"] = ("tensor resident in L2 (%.1f MB): the sweep is bound by the latency of its dependent phases, "
                      "not by HBM" % (P * sz / 1e6))

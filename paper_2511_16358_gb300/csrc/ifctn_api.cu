@@ -1375,7 +1375,7 @@ struct Engine : ifctn_ctx {
                 pp.gunits[k] = nm == 3 ? sh.I[m[0]] : 0;
             }
             const long long Q = mode_q(sh, k);
-            if (Q * Q * static_cast<long long>(sizeof(T)) > 96 * 1024) k_fits = false;
+            if (Q * k_stride(static_cast<int>(Q)) * static_cast<long long>(sizeof(T)) > 96 * 1024) k_fits = false;
         }
         pp.solve_k_in_smem = k_fits ? 1 : 0;
         int gc = 1 << 30;

@@ -4,6 +4,12 @@
 
 namespace ifctn {
 
+// Row stride of K_k when the solve holds it in shared memory: odd, so that the
+// lanes of a warp, which read K at rows a multiple of the stride apart, fall on
+// different banks (an even Q such as 36 or 192 put them on one bank: 8- to
+// 24-way conflicts).
+__host__ __device__ inline int k_stride(int Q) { return Q | 1; }
+
 constexpr int PERSISTENT_THREADS = 256;  // threads per CTA of the persistent kernel
 
 template <typename T>

@@ -534,7 +534,7 @@ __host__ __device__ inline SolveLayout solve_layout(int Q, int tot, int sz, bool
     L.warp = (L.tab + static_cast<long long>(solve_tab_ints(Q)) * 4 + 15) & ~15LL;
     L.wstride = Qa * 2 * sz;
     L.K = (L.warp + PW * L.wstride + 15) & ~15LL;
-    L.Ms = (L.K + (ksm ? static_cast<long long>(Q) * Q * sz : 0) + 15) & ~15LL;
+    L.Ms = (L.K + (ksm ? static_cast<long long>(Q) * k_stride(Q) * sz : 0) + 15) & ~15LL;
     L.total = L.Ms + static_cast<long long>(PW) * Q * 8;
     return L;
 }
@@ -639,7 +639,7 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
 // not finite; the old column is then left in place.
 template <typename T, int RI>
 __device__ __forceinline__ bool stage_solve(const T* __restrict__ K, const T* __restrict__ om,
-                                            const int* __restrict__ cb, const T* __restrict__ mrow, int Q,
+                                            const int* __restrict__ cb, const T* __restrict__ mrow, int Q, int LK,
                                             int Qo, int sp, int lane, int olane, int dq, int dr, T rhoT, float rhi,
                                             float rlo, T* ghi, float* glo, T* Af, T* Hv, T* xf, T* bv, double* gd,
                                             unsigned long long* ts) {
@@ -653,13 +653,14 @@ __device__ __forceinline__ bool stage_solve(const T* __restrict__ K, const T* __
     T v[V];
 #pragma unroll
     for (int q = 0; q < V; ++q) v[q] = T(0);
-    const int spQ = sp * Q;
+    (void)Q;
+    const int spQ = sp * LK;  // K(row, col) at row * LK + col
     const int n = Qo * Qo;
     int o = olane & 0xffff;
     int o2 = olane >> 16;
     for (int f = lane; f < n; f += 32) {
         const T w = om[o] * om[o2];
-        const T* kr = K + cb[o2] * Q + cb[o];
+        const T* kr = K + cb[o2] * LK + cb[o];
         int q = 0;
 #pragma unroll
         for (int c2 = 0; c2 < RI; ++c2)
@@ -830,12 +831,30 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
     // second group that is waited for before the refresh
     const int j0 = warp * VG + VB;
     if (j0 < Ik) fetch_column(j0);
-    if (ksm) stage_async(Ks, p.Kk, Q * Q);
+    if (ksm) {  // rows at the odd stride k_stride(Q)
+        const int LKs = k_stride(Q);
+        if (LKs == Q) {
+            stage_async(Ks, p.Kk, Q * Q);
+        } else {
+            for (int idx = threadIdx.x; idx < Q * Q; idx += blockDim.x) {
+                const int r = idx / Q, c = idx - r * Q;
+                if (sizeof(T) == 4)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(Ks + r * LKs + c)),
+                                 "l"(p.Kk + idx)
+                                 : "memory");
+                else
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(Ks + r * LKs + c)),
+                                 "l"(p.Kk + idx)
+                                 : "memory");
+            }
+        }
+    }
     stage_async(cbt, p.stab[k], solve_tab_ints(Q));
     asm volatile("cp.async.commit_group;" ::: "memory");
     for (int t = 0; t < nm; ++t) stage_async(gik + gko[t], p.Gt + s.goff[m[t]][k], Rm[t] * s.I[m[t]]);
     asm volatile("cp.async.commit_group;" ::: "memory");
     const T* K = ksm ? Ks : p.Kk;
+    const int LK = ksm ? k_stride(Q) : Q;
     asm volatile("cp.async.wait_group 1;" ::: "memory");
     __syncthreads();
     IFCTN_SSTAMP(1);
@@ -895,7 +914,7 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
             switch (Ri) {
 #define IFCTN_SOLVE_CASE(R)                                                                                     \
     case R:                                                                                                     \
-        okc = stage_solve<T, R>(K, om, cb, mrow, Q, Qo, sp, lane, olane, dq, dr, rhoT, rhi, rlo, gh, gl, Af, Hv, \
+        okc = stage_solve<T, R>(K, om, cb, mrow, Q, LK, Qo, sp, lane, olane, dq, dr, rhoT, rhi, rlo, gh, gl, Af, Hv, \
                                 xf, bv, gd, sts);                                                               \
         break;
                 IFCTN_SOLVE_CASE(1)
@@ -906,7 +925,7 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
                 IFCTN_SOLVE_CASE(6)
                 IFCTN_SOLVE_CASE(7)
                 default:
-                    okc = stage_solve<T, 8>(K, om, cb, mrow, Q, Qo, sp, lane, olane, dq, dr, rhoT, rhi, rlo, gh, gl,
+                    okc = stage_solve<T, 8>(K, om, cb, mrow, Q, LK, Qo, sp, lane, olane, dq, dr, rhoT, rhi, rlo, gh, gl,
                                             Af, Hv, xf, bv, gd, sts);
                     break;
 #undef IFCTN_SOLVE_CASE
