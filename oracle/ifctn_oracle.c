@@ -53,6 +53,7 @@
 #endif
 
 #define IFO_MAXN 4
+#define IFO_RMAX 64 /* largest R_{k,l}: the block buffers below are sized for it */
 
 /* ------------------------------------------------------------------ */
 /* compensated summation                                               */
@@ -180,23 +181,26 @@ int ifo_reconstruct(int N, const int64_t* dims, const int32_t* R, const double* 
 /* ------------------------------------------------------------------ */
 /* Accumulates H = A^T A and b = A^T x for column j of G_{k,i}, where the row
    of A for entry i (i_k = j) is a(r) = T(i) G_{i,k}(r, i_i) and x is the
-   mode-k slice X(i_k = j, :).  T multiplies every pair matrix except W_{k,i}. */
-static void block_normal_eq(int N, const int64_t* dims, const int32_t* R, const double* G,
-                            const pairset* ps, const double* X, int k, int i, long long j,
-                            double* H, double* b) {
+   mode-k slice X(i_k = j, :).  T multiplies every pair matrix except W_{k,i}.
+   H is Rki x Rki (row-major), b has Rki entries.  Returns nonzero when the
+   accumulators cannot be allocated. */
+static int block_normal_eq(int N, const int64_t* dims, const int32_t* R, const double* G,
+                           const pairset* ps, const double* X, int k, int i, long long j,
+                           double* H, double* b) {
     const int Rki = rank_of(R, k, i);
     const double* Gik = G + ifo_factor_offset(N, dims, R, i, k);
     const long long Ii = dims[i];
     long long st[IFO_MAXN];
     c_strides(N, dims, st);
-    ksum hs[64], bs[8];
-    memset(hs, 0, sizeof(hs));
-    memset(bs, 0, sizeof(bs));
+    /* lower triangle of H (row r, column c <= r at r(r+1)/2 + c) and b */
+    ksum* hs = (ksum*)calloc((size_t)Rki * (Rki + 1) / 2 + Rki, sizeof(ksum));
+    if (!hs) return 1;
+    ksum* bs = hs + (size_t)Rki * (Rki + 1) / 2;
     /* odometer over all modes except k */
     long long idx[IFO_MAXN] = {0, 0, 0, 0};
     idx[k] = j;
     const long long Pk = ifo_numel(N, dims) / dims[k];
-    double a[8];
+    double a[IFO_RMAX];
     for (long long t = 0; t < Pk; ++t) {
         double T = 1.0;
         for (int p = 0; p < N; ++p)
@@ -210,7 +214,8 @@ static void block_normal_eq(int N, const int64_t* dims, const int32_t* R, const 
         for (int r = 0; r < Rki; ++r) a[r] = T * Gik[r * Ii + idx[i]];
         for (int r = 0; r < Rki; ++r) {
             kadd(&bs[r], a[r] * x);
-            for (int c = 0; c <= r; ++c) kadd(&hs[r * 8 + c], a[r] * a[c]);
+            ksum* hr = hs + (size_t)r * (r + 1) / 2;
+            for (int c = 0; c <= r; ++c) kadd(&hr[c], a[r] * a[c]);
         }
         /* advance the odometer (last mode fastest), skipping mode k */
         for (int m = N - 1; m >= 0; --m) {
@@ -222,23 +227,25 @@ static void block_normal_eq(int N, const int64_t* dims, const int32_t* R, const 
     for (int r = 0; r < Rki; ++r) {
         b[r] = kval(&bs[r]);
         for (int c = 0; c <= r; ++c) {
-            H[r * Rki + c] = kval(&hs[r * 8 + c]);
+            H[r * Rki + c] = kval(&hs[(size_t)r * (r + 1) / 2 + c]);
             H[c * Rki + r] = H[r * Rki + c];
         }
     }
+    free(hs);
+    return 0;
 }
 
 /* Public: H = A^T A and b = A^T x (no proximal terms) for column j of G_{k,i}
-   at the given state (G, X).  R_{k,i} <= 8. */
+   at the given state (G, X).  1 <= R_{k,i} <= IFO_RMAX. */
 int ifo_block_system(int N, const int64_t* dims, const int32_t* R, const double* G,
                      const double* X, int k, int i, long long j, double* H, double* b) {
-    if (N < 2 || N > IFO_MAXN || k == i || rank_of(R, k, i) > 8) return -1;
+    if (N < 2 || N > IFO_MAXN || k == i || rank_of(R, k, i) < 1 || rank_of(R, k, i) > IFO_RMAX) return -1;
     pairset ps;
     if (pairs_alloc(N, dims, &ps)) { pairs_free(N, &ps); return -2; }
     pairs_compute(N, dims, R, G, &ps);
-    block_normal_eq(N, dims, R, G, &ps, X, k, i, j, H, b);
+    const int rc = block_normal_eq(N, dims, R, G, &ps, X, k, i, j, H, b);
     pairs_free(N, &ps);
-    return 0;
+    return rc ? -2 : 0;
 }
 
 /* textbook Cholesky H = L L^T (lower, in place) and solve H g = rhs.
@@ -284,7 +291,7 @@ int ifo_sweep(int N, const int64_t* dims, const int32_t* R, double rho, double* 
     if (N < 2 || N > IFO_MAXN || !(rho > 0.0)) return -1;
     for (int k = 0; k < N; ++k)
         for (int l = 0; l < N; ++l)
-            if (l != k && (rank_of(R, k, l) < 1 || rank_of(R, k, l) > 8 ||
+            if (l != k && (rank_of(R, k, l) < 1 || rank_of(R, k, l) > IFO_RMAX ||
                            rank_of(R, k, l) != rank_of(R, l, k))) return -1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -304,8 +311,8 @@ int ifo_sweep(int N, const int64_t* dims, const int32_t* R, double rho, double* 
             const long long Ik = dims[k];
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
             for (long long j = 0; j < Ik; ++j) {
-                double H[64], b[8];
-                block_normal_eq(N, dims, R, G, &ps, X, k, i, j, H, b);
+                double H[IFO_RMAX * IFO_RMAX], b[IFO_RMAX];
+                if (block_normal_eq(N, dims, R, G, &ps, X, k, i, j, H, b)) { bad |= 2; continue; }
                 for (int r = 0; r < Rki; ++r) {
                     H[r * Rki + r] += rho;
                     b[r] += rho * Gki[r * Ik + j];
@@ -372,7 +379,7 @@ int ifo_sweep(int N, const int64_t* dims, const int32_t* R, double rho, double* 
     stats[4] = dx2;
     stats[5] = x02;
     pairs_free(N, &ps);
-    return bad ? 1 : 0;
+    return (bad & 2) ? -2 : (bad ? 1 : 0);
 }
 
 /* X^0 = P_Omega(O): observed values kept, zero elsewhere (Algorithm 1 init). */

@@ -383,6 +383,20 @@ def _explicit_A(dims, R, G, k, i, j):
 def test_block_system_equals_dense_normal_equations(k, i, j):
     dims = (3, 4, 5, 2)
     edge = {(0, 1): 2, (0, 2): 3, (0, 3): 2, (1, 2): 2, (1, 3): 3, (2, 3): 1}
+    _check_block_system(dims, edge, k, i, j)
+
+
+@pytest.mark.parametrize("k,i,j", [(0, 1, 2), (1, 0, 0), (2, 0, 3), (1, 2, 1)])
+def test_block_system_equals_dense_normal_equations_ranks_above_eight(k, i, j):
+    """The block buffers of the oracle hold ranks up to 64: the systems of
+    edges of rank 12 and 36 (the largest R_{1,2} of the multispectral rank
+    grid, Sec. 5.2) against the dense A_j of the FCTN route."""
+    dims = (4, 3, 5)
+    edge = {(0, 1): 36, (0, 2): 12, (1, 2): 9}
+    _check_block_system(dims, edge, k, i, j)
+
+
+def _check_block_system(dims, edge, k, i, j):
     R, G = _problem(dims, edge, 70 + k)
     X = inp.normal(71, int(np.prod(dims))).reshape(dims)
     A = _explicit_A(dims, R, G, k, i, j)
@@ -429,6 +443,7 @@ def _E(dims, R, F, k, i, j):
 @pytest.mark.parametrize("dims,edge", [
     ((3, 4, 5, 2), {(0, 1): 2, (0, 2): 3, (0, 3): 2, (1, 2): 2, (1, 3): 3, (2, 3): 1}),
     ((4, 3, 5), {(0, 1): 3, (0, 2): 2, (1, 2): 4}),
+    ((4, 3, 5), {(0, 1): 12, (0, 2): 3, (1, 2): 10}),
 ])
 def test_regrouped_mode_systems_equal_block_systems(dims, edge):
     """The regrouping the GPU path relies on (Prop. 1 applied to eq. (updateG)):
@@ -490,17 +505,42 @@ def test_sweep_equals_dense_gauss_seidel_pam():
     np.testing.assert_allclose(X, Xref, rtol=1e-10, atol=1e-12)
 
 
-def test_two_way_case_is_proximal_als():
+def test_sweep_equals_dense_gauss_seidel_pam_ranks_above_eight():
+    dims = (3, 2, 4)
+    R, G0 = _problem(dims, {(0, 1): 10, (0, 2): 3, (1, 2): 12}, 84)
+    xt = inp.normal(85, int(np.prod(dims))).reshape(dims)
+    mask = inp.uniform_mask(dims, 0.6, 86)
+    X0 = oracle.init_x(xt, mask)
+    Gref, Xref = _numpy_sweep(dims, R, 0.3, G0, X0, mask)
+    G = G0.copy()
+    X = X0.copy()
+    oracle.sweep(dims, R, 0.3, G, X, mask)
+    np.testing.assert_allclose(G, Gref, rtol=1e-9, atol=1e-11)
+    np.testing.assert_allclose(X, Xref, rtol=1e-9, atol=1e-11)
+
+
+def test_rank_above_oracle_limit_is_refused():
+    dims = (3, 2, 4)
+    R, G = _problem(dims, {(0, 1): 2, (0, 2): 2, (1, 2): 2}, 87)
+    R = np.array(R)
+    R[0, 1] = R[1, 0] = 65
+    X = np.zeros(dims)
+    with pytest.raises(RuntimeError):
+        oracle.sweep(dims, R, 0.3, np.zeros(oracle.param_count(dims, R)), X, np.ones(dims, np.uint8))
+
+
+@pytest.mark.parametrize("rank", [3, 12])
+def test_two_way_case_is_proximal_als(rank):
     """N = 2: X = G_{1,2}^T G_{2,1}; each block is textbook proximal ALS."""
     dims = (6, 5)
-    R, G = _problem(dims, 3, 91)
+    R, G = _problem(dims, rank, 91)
     F = inp.unpack_factors(G, dims, R)
     A0, B0 = F[(0, 1)].copy(), F[(1, 0)].copy()
     X = inp.normal(92, 30).reshape(dims)
     mask = np.ones(dims, dtype=np.uint8)
     rho = 0.2
-    A1 = np.linalg.solve(B0 @ B0.T + rho * np.eye(3), B0 @ X.T + rho * A0)
-    B1 = np.linalg.solve(A1 @ A1.T + rho * np.eye(3), A1 @ X + rho * B0)
+    A1 = np.linalg.solve(B0 @ B0.T + rho * np.eye(rank), B0 @ X.T + rho * A0)
+    B1 = np.linalg.solve(A1 @ A1.T + rho * np.eye(rank), A1 @ X + rho * B0)
     Gw = G.copy()
     Xw = X.copy()
     oracle.sweep(dims, R, rho, Gw, Xw, mask)
@@ -510,11 +550,12 @@ def test_two_way_case_is_proximal_als():
     np.testing.assert_array_equal(Xw, X)  # fully observed: X is never changed
 
 
-def test_cholesky_solver():
-    rng = inp.normal(93, 64).reshape(8, 8)
-    H = rng @ rng.T + 0.5 * np.eye(8)
-    b = inp.normal(94, 8)
-    np.testing.assert_allclose(oracle.cholesky_solve(H, b), np.linalg.solve(H, b), rtol=1e-12)
+@pytest.mark.parametrize("n", [8, 40])
+def test_cholesky_solver(n):
+    rng = inp.normal(93, n * n).reshape(n, n)
+    H = rng @ rng.T + 0.5 * np.eye(n)
+    b = inp.normal(94, n)
+    np.testing.assert_allclose(oracle.cholesky_solve(H, b), np.linalg.solve(H, b), rtol=1e-10)
 
 
 # ---------------------------------------------------------------------------
