@@ -15,6 +15,10 @@
  *     blocks in the order k = 0..N-1, then l = 0..N-1 (l != k), as FP64.
  *   - ranks[k*4+l] is the symmetric iFCTN-rank matrix R (Def. 2); entries
  *     with k,l < N, k != l must satisfy 1 <= R_{k,l} <= 8; others are ignored.
+ *     Order-3 problems may use ranks up to 64 (the rank grid of Sec. 5.2
+ *     reaches R_{1,2} = 36) as long as every Q_k = prod_{l != k} R_{k,l} is at
+ *     most 4096; such problems always run the per-stage sweep graph (never the
+ *     persistent launch) and are not tuned by ifctn_tune.
  *   - The observation mask holds one byte per tensor entry, nonzero =
  *     observed (the sample set Omega).
  *   - Tensor buffers are FP64 when the problem's precision is IFCTN_FP64 and
@@ -65,7 +69,7 @@ typedef enum {
 typedef struct {
     int32_t order;          /* N, 2..4 */
     int64_t dims[4];        /* I_k >= 1 for k < N */
-    int32_t ranks[16];      /* R[k*4+l], symmetric, 1..8 off the diagonal */
+    int32_t ranks[16];      /* R[k*4+l], symmetric, 1..8 off the diagonal (1..64 at order 3) */
     double rho;             /* proximal weight, > 0 (paper default 0.1) */
     int32_t max_sweeps;     /* t_max >= 0 (paper default 1000) */
     double tol;             /* epsilon of the relative-change test; 0 = run all sweeps */

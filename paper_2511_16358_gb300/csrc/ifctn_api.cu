@@ -94,15 +94,29 @@ ifctn_status build_shape(const ifctn_problem* p, Shape& s) {
             return IFCTN_EINVAL;
         }
     }
+    // Edge ranks up to RMAX for every order; order-3 tensors also take ranks
+    // up to WIDE_RMAX with every Q_k <= WIDE_QMAX (the kernels of ifctn_wide.cu).
+    const int rmax = s.N == 3 ? WIDE_RMAX : RMAX;
     for (int k = 0; k < s.N; ++k)
         for (int l = 0; l < s.N; ++l) {
             if (k == l) continue;
             const int r = p->ranks[k * 4 + l];
-            if (r < 1 || r > RMAX || r != p->ranks[l * 4 + k]) {
-                set_error("ranks must be symmetric and in 1..8");
+            if (r < 1 || r > rmax || r != p->ranks[l * 4 + k]) {
+                set_error(s.N == 3 ? "ranks must be symmetric and in 1..64" : "ranks must be symmetric and in 1..8");
                 return IFCTN_EINVAL;
             }
             s.R[k][l] = r;
+            if (r > RMAX) s.wide = 1;
+        }
+    if (s.wide)
+        for (int k = 0; k < s.N; ++k) {
+            long long q = 1;
+            for (int l = 0; l < s.N; ++l)
+                if (l != k) q *= s.R[k][l];
+            if (q > WIDE_QMAX) {
+                set_error("with ranks above 8, every Q_k (product of a mode's edge ranks) must be <= 4096");
+                return IFCTN_EINVAL;
+            }
         }
     if (!(p->rho > 0.0) || !std::isfinite(p->rho)) {
         set_error("rho must be > 0");
@@ -1048,7 +1062,26 @@ struct Engine : ifctn_ctx {
         std::vector<UnitDesc> all;
         long long maxpart = 1, maxt1 = 1, maxt2 = 1, maxK = 1;
         graph_only = force_path == 1 ? true : force_path == 2 ? false : choose_graph_only(sh, sz);
-        for (int k = 0; k < sh.N; ++k) {
+        if (sh.wide) {
+            // ranks above RMAX: the per-stage kernels of ifctn_wide.cu (t1 holds
+            // the contraction's first link, t2 the Gram's)
+            if (force_path == 2) {
+                set_error("the persistent path needs every edge rank <= 8");
+                return IFCTN_EINVAL;
+            }
+            graph_only = true;
+            for (int k = 0; k < sh.N; ++k) {
+                memset(&plan[k], 0, sizeof(plan[k]));
+                plan[k].Q = mode_q(sh, k);
+                plan[k].nstages = 1;
+                unit_off[k] = 0;
+                const long long Q = plan[k].Q;
+                maxK = std::max(maxK, Q * Q);
+                maxt1 = std::max(maxt1, wide_v_elems(sh, k));
+                maxt2 = std::max(maxt2, wide_t_elems(sh, k));
+            }
+        }
+        for (int k = 0; k < sh.N && !sh.wide; ++k) {
             std::vector<UnitDesc> u;
             plan[k].warp = 0;
             if (graph_only) plan[k] = plan_contract_warp(sh, k, sz, u, default_warp_knobs());
@@ -1090,19 +1123,21 @@ struct Engine : ifctn_ctx {
         for (int k = 0; k < sh.N && ok; ++k)
             ok = alloc(Mk[k], static_cast<size_t>(sh.I[k]) * mode_q(sh, k)) == cudaSuccess;
         std::vector<int> tabs;
-        for (int k = 0; k < sh.N; ++k) {
+        for (int k = 0; k < sh.N && !sh.wide; ++k) {
             stab_off[k] = static_cast<int>(tabs.size());
             const int n = solve_tab_ints(mode_q(sh, k));
             tabs.resize(tabs.size() + (n + 3) / 4 * 4, 0);  // 16-byte aligned blocks
             solve_stage_tables(sh, k, tabs.data() + stab_off[k]);
         }
+        if (tabs.empty()) tabs.resize(4, 0);  // the wide kernels use no index tables
         if (ok) ok = alloc(stab, tabs.size()) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
             set_error("device allocation failed");
             return IFCTN_ENOMEM;
         }
-        CK(cudaMemcpyAsync(units.p, all.data(), all.size() * sizeof(UnitDesc), cudaMemcpyHostToDevice, st));
+        if (!all.empty())
+            CK(cudaMemcpyAsync(units.p, all.data(), all.size() * sizeof(UnitDesc), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(stab.p, tabs.data(), tabs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(ints.p, 0, 4 * sizeof(int), st));
         CK(cudaMemsetAsync(bar.p, 0, 4 * sizeof(unsigned), st));
@@ -1141,7 +1176,7 @@ struct Engine : ifctn_ctx {
         // launch shapes from the tuning cache named by IFCTN_TUNE_CACHE (timed
         // and added to it where the cache has no entry for this shape)
         if (const char* path = getenv("IFCTN_TUNE_CACHE")) {
-            if (*path && graph_only) {
+            if (*path && graph_only && !sh.wide) {
                 rs = tune(path, nullptr, !tune_timing);
                 if (rs != IFCTN_OK) return rs;
                 return IFCTN_OK;  // tune() rebuilt the graph
@@ -1228,6 +1263,10 @@ struct Engine : ifctn_ctx {
     ifctn_status tune(const char* path, int* ntimed, bool lookup_only) {
         NvtxRange nr("ifctn tune");
         int timed = 0;
+        if (sh.wide) {  // the kernels of ifctn_wide.cu have no launch-shape choices
+            if (ntimed) *ntimed = 0;
+            return IFCTN_OK;
+        }
         std::vector<std::string> lines;
         if (path && *path) {
             if (FILE* f = fopen(path, "r")) {
@@ -1335,7 +1374,8 @@ struct Engine : ifctn_ctx {
                 return IFCTN_ENOMEM;
             }
         }
-        CK(cudaMemcpyAsync(units.p, all.data(), all.size() * sizeof(UnitDesc), cudaMemcpyHostToDevice, st));
+        if (!all.empty())
+            CK(cudaMemcpyAsync(units.p, all.data(), all.size() * sizeof(UnitDesc), cudaMemcpyHostToDevice, st));
         for (int k = 0; k < sh.N; ++k) {
             plan[k] = np[k];
             unit_off[k] = noff[k];
@@ -1528,6 +1568,27 @@ struct Engine : ifctn_ctx {
         return IFCTN_OK;
     }
 
+    // The stages of mode k on stream s: the register-resident kernels, or the
+    // kernels of ifctn_wide.cu when some edge rank exceeds RMAX (t1 then holds
+    // the contraction's first link, t2 the Gram's).
+    cudaError_t stage_contract(int k, cudaStream_t s) {
+        if (sh.wide) return launch_wide_contract<T>(sh, k, X.p, Gt.p, W.p, t1.p, done(), s);
+        return launch_contract<T>(cargs(k), s);
+    }
+    cudaError_t stage_finish(int k, cudaStream_t s) {
+        if (sh.wide) return launch_wide_finish<T>(sh, k, Gt.p, t1.p, Mk[k].p, done(), s);
+        return launch_contract_finish<T>(sh, k, plan[k], units.p + unit_off[k], part.p, Gt.p, Mk[k].p, done(), s);
+    }
+    cudaError_t stage_gram(int k, cudaStream_t s) {
+        if (sh.wide) return launch_wide_gram<T>(sh, k, Gt.p, W.p, t2.p, Kk.p, done(), s);
+        return launch_gram<T>(sh, k, Gt.p, W.p, t1.p, t2.p, Kk.p, done(), s);
+    }
+    cudaError_t stage_solve(int k, cudaStream_t s) {
+        if (sh.wide) return launch_wide_solve<T>(sh, k, prob.rho, Mk[k].p, Kk.p, Gd.p, Gt.p, W.p, flags(), done(), s);
+        return launch_solve_cols<T>(pp, k, s);
+    }
+    int mode_system_launches() const { return sh.wide ? 4 : 3; }
+
     ContractArgs<T> cargs(int k) {
         ContractArgs<T> a;
         a.X = X.p;
@@ -1549,12 +1610,10 @@ struct Engine : ifctn_ctx {
         cudaError_t e;
         if ((e = cudaEventRecord(ev_fork[k], st)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(side, ev_fork[k], 0)) != cudaSuccess) return e;
-        if ((e = launch_gram<T>(sh, k, Gt.p, W.p, t1.p, t2.p, Kk.p, done(), side)) != cudaSuccess) return e;
+        if ((e = stage_gram(k, side)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(ev_join[k], side)) != cudaSuccess) return e;
-        if ((e = launch_contract<T>(cargs(k), st)) != cudaSuccess) return e;
-        if ((e = launch_contract_finish<T>(sh, k, plan[k], units.p + unit_off[k], part.p, Gt.p, Mk[k].p,
-                                           done(), st)) != cudaSuccess)
-            return e;
+        if ((e = stage_contract(k, st)) != cudaSuccess) return e;
+        if ((e = stage_finish(k, st)) != cudaSuccess) return e;
         return cudaStreamWaitEvent(st, ev_join[k], 0);
     }
 
@@ -1563,8 +1622,7 @@ struct Engine : ifctn_ctx {
         for (int k = 0; k < sh.N; ++k) {
             if ((e = enqueue_mode_systems(k)) != cudaSuccess) return e;
             NvtxRange r(kModeSolves[k]);
-            if ((e = launch_solve_cols<T>(pp, k, st)) != cudaSuccess)
-                return e;
+            if ((e = stage_solve(k, st)) != cudaSuccess) return e;
         }
         NvtxRange r("ifctn X update");
         pp.Xt = (logm && truth) ? Xt.p : nullptr;
@@ -1803,14 +1861,11 @@ struct Engine : ifctn_ctx {
             return IFCTN_EINVAL;
         }
         switch (stage) {
-            case 0: CK(launch_contract<T>(cargs(k), st)); break;
-            case 1: CK(launch_gram<T>(sh, k, Gt.p, W.p, t1.p, t2.p, Kk.p, done(), st)); break;
-            case 2: CK(launch_solve_cols<T>(pp, k, st)); break;
+            case 0: CK(stage_contract(k, st)); break;
+            case 1: CK(stage_gram(k, st)); break;
+            case 2: CK(stage_solve(k, st)); break;
             case 3: CK(launch_xupdate_slab<T>(pp, xpart.p, slab_xblocks(), st)); break;
-            case 4:
-                CK(launch_contract_finish<T>(sh, k, plan[k], units.p + unit_off[k], part.p, Gt.p, Mk[k].p, done(),
-                                             st));
-                break;
+            case 4: CK(stage_finish(k, st)); break;
             default: set_error("unknown stage"); return IFCTN_EINVAL;
         }
         return IFCTN_OK;
@@ -1845,11 +1900,10 @@ struct Engine : ifctn_ctx {
         for (int s_ = 0; s_ < n; ++s_) {
             for (int k = 0; k < sh.N; ++k) {
                 NvtxRange mr(kModeSystems[k]);
-                CK(launch_contract<T>(cargs(k), st));
-                CK(launch_contract_finish<T>(sh, k, plan[k], units.p + unit_off[k], part.p, Gt.p, Mk[k].p, done(),
-                                             st));
-                CK(launch_gram<T>(sh, k, Gt.p, W.p, t1.p, t2.p, Kk.p, done(), st));
-                launch_count += 3;
+                CK(stage_contract(k, st));
+                CK(stage_finish(k, st));
+                CK(stage_gram(k, st));
+                launch_count += mode_system_launches();
                 if (k > 0) {  // M_k and K_k are sums over the slab's entries: combine them
                     const long long Q = mode_q(sh, k), nm = static_cast<long long>(sh.I[k]) * Q;
                     CK(cudaMemcpyAsync(hb.data(), Mk[k].p, nm * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1872,7 +1926,7 @@ struct Engine : ifctn_ctx {
                     CK(cudaMemcpyAsync(Kk.p, kt.data(), Q * Q * sizeof(T), cudaMemcpyHostToDevice, st));
                     CK(cudaStreamSynchronize(st));  // kt and hb are reused
                 }
-                CK(launch_solve_cols<T>(pp, k, st));
+                CK(stage_solve(k, st));
                 ++launch_count;
             }
             CK(launch_xupdate_slab<T>(pp, xpart.p, slab_xblocks(), st));
@@ -2069,7 +2123,7 @@ ifctn_status create_tuned(const ifctn_problem* prob, const void* obs, const uint
     const int sz = static_cast<int>(sizeof(T));
     const char* cache = getenv("IFCTN_TUNE_CACHE");
     int force = 0;
-    if (!getenv("IFCTN_PATH") && cache && *cache && !choose_graph_only(sh, sz)) {
+    if (!getenv("IFCTN_PATH") && cache && *cache && !sh.wide && !choose_graph_only(sh, sz)) {
         const std::string key = path_key(sh, sz);
         if (FILE* f = fopen(cache, "r")) {
             char buf[1024];

@@ -19,6 +19,11 @@ namespace ifctn {
 
 constexpr int MAXN = 4;
 constexpr int RMAX = 8;
+// Order-3 tensors may have edge ranks above RMAX (the multispectral rank grid
+// of Sec. 5.2 reaches R_{1,2} = 36): their mode systems and column solves run
+// on the kernels of ifctn_wide.cu, up to these limits.
+constexpr int WIDE_RMAX = 64;
+constexpr int WIDE_QMAX = 4096;
 
 enum : int { FLAG_TIMEOUT = 1, FLAG_NOTSPD = 2, FLAG_NONFINITE = 4 };
 
@@ -31,6 +36,7 @@ struct Shape {
     int woff[MAXN][MAXN];  // element offset of W_{p,q} (p<q) in the packed pair array
     int gsize, wsize;
     int nF, IA, IB;        // slab count and slab sizes
+    int wide;              // 1: some R_{k,l} > RMAX (order 3): the kernels of ifctn_wide.cu
 };
 
 // One work unit of a streaming contraction: a list of slabs

@@ -58,6 +58,28 @@ template <typename T>
 cudaError_t launch_gram(const Shape& sh, int k, const T* Gt, const T* W, T* t1, T* t2, T* Kk,
                         const int* done, cudaStream_t st);
 
+// Order-3 tensors with edge ranks above RMAX (Shape::wide): the mode
+// systems as chains of batched products (contraction: modes c1 then c2; Gram:
+// d1 then d2) and the column solves with H in shared memory.
+struct WideChain {
+    int c1, c2, d1, d2;
+};
+WideChain wide_chain(const Shape& s, int k);
+long long wide_v_elems(const Shape& s, int k);  // first contraction link's output (V)
+long long wide_t_elems(const Shape& s, int k);  // first Gram link's output
+template <typename T>
+cudaError_t launch_wide_contract(const Shape& s, int k, const T* X, const T* Gt, const T* W, T* V, const int* done,
+                                 cudaStream_t st);
+template <typename T>
+cudaError_t launch_wide_finish(const Shape& s, int k, const T* Gt, const T* V, double* Mk, const int* done,
+                               cudaStream_t st);
+template <typename T>
+cudaError_t launch_wide_gram(const Shape& s, int k, const T* Gt, const T* W, T* Tg, T* Kk, const int* done,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_wide_solve(const Shape& s, int k, double rho, const double* Mk, const T* Kk, double* Gd, T* Gt,
+                              T* W, int* flags, const int* done, cudaStream_t st);
+
 // eq. (updateX) fused with the reconstruction and the sweep's reductions.
 template <typename T>
 cudaError_t launch_xupdate(const Shape& sh, double rho, T* X, const uint32_t* maskbits, const T* W,

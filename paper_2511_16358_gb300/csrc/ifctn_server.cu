@@ -22,6 +22,7 @@
 
 #include "../../include/ifctn.h"
 #include "ifctn_api_internal.h"
+#include "ifctn_launch.h"
 
 using namespace ifctn;
 using Clock = std::chrono::steady_clock;
@@ -52,7 +53,18 @@ struct Job {
 
 size_t job_bytes_estimate(const Shape& s, size_t esz) {
     // X, the transient observation copy and mask bytes, the bitset, plus slack
-    return static_cast<size_t>(s.P) * (2 * esz + 1) + static_cast<size_t>(s.P) / 8 + (8u << 20);
+    size_t b = static_cast<size_t>(s.P) * (2 * esz + 1) + static_cast<size_t>(s.P) / 8 + (8u << 20);
+    if (s.wide) {  // ranks above 8: K_k (Q_k^2), M_k (FP64) and the chain buffers grow with Q_k
+        size_t kmax = 0, chain = 0;
+        for (int k = 0; k < s.N; ++k) {
+            const size_t Q = static_cast<size_t>(mode_q(s, k));
+            b += static_cast<size_t>(s.I[k]) * Q * 8;
+            kmax = std::max(kmax, Q * Q);
+            chain = std::max(chain, static_cast<size_t>(wide_v_elems(s, k)) + static_cast<size_t>(wide_t_elems(s, k)));
+        }
+        b += (kmax + chain) * esz;
+    }
+    return b;
 }
 
 void free_pinned(Job& j) {

@@ -1,0 +1,556 @@
+// ifctn_wide.cu -- mode systems and column solves of order-3 tensors whose
+// edge ranks exceed the register-resident kernels' limit (R_{k,l} up to
+// WIDE_RMAX, Q_k up to WIDE_QMAX), as in the multispectral rank grid of
+// Sec. 5.2 (R_{1,2} up to 36).
+//
+// For mode k with other modes a < b, the regrouped systems of eq. (updateG)
+// (Prop. 1: M_k = X_(k) Z_k, K_k = Z_k^T Z_k; Q_k index q = r_a R_{k,b} + r_b)
+// are formed as two chains of contractions.  Each link is a batched matrix
+// product whose operands are generated while they are loaded, from X, the pair
+// matrices W and the factors G_{m,k}:
+//
+//   contraction (c1, c2 the other modes; c1 contracted first)
+//     V(j, i_c2, r1)        = sum_{i_c1} X(i) W_{c1,c2}(i_c1, i_c2) G_{c1,k}(r1, i_c1)
+//     M_k(j, (r_c1, r_c2))  = sum_{i_c2} G_{c2,k}(r_c2, i_c2) V(j, i_c2, r_c1)
+//   Gram (d1 summed first)
+//     T(i_d2, r1, r1')      = sum_{i_d1} W_{d1,d2}(i_d1, i_d2)^2 G_{d1,k}(r1, i_d1) G_{d1,k}(r1', i_d1)
+//     K_k((r1,r2),(r1',r2')) = sum_{i_d2} G_{d2,k}(r2, i_d2) G_{d2,k}(r2', i_d2) T(i_d2, r1, r1')
+//
+// X is read once per mode, by the first link, whose contracted mode is the
+// contiguous one (mode 2) unless k is: the loads stay coalesced.  The column
+// solves assemble H = E_j^T K_k E_j + rho I and b = E_j^T M_k(j,:)^T + rho g in
+// the tensor dtype, factorise H by Cholesky in FP64 in shared memory, and
+// refresh W_{k,i}(j, :) with the new columns (Algorithm 1's order: i != k
+// ascending, each stage using the column the previous one produced).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "ifctn_launch.h"
+
+namespace ifctn {
+namespace {
+
+constexpr int WT = 256;  // threads of every kernel in this file
+constexpr int BK = 16;   // reduction depth of one shared-memory tile
+
+// C[b](m, n) = sum_i A[b](m, i) B[b](i, n) for every batch b; Op generates
+// the operands (a, bm), stores the result (store) and names the sizes.  Each
+// CTA computes BM x BN outputs, TM x TN per thread, in the tensor dtype.
+template <typename T, int BM, int BN, int TM, int TN, class Op>
+__global__ void __launch_bounds__(WT) k_wide_gemm(const __grid_constant__ Op op, const int* __restrict__ done) {
+    static_assert((BM / TM) * (BN / TN) == WT, "thread layout");
+    pdl_begin();
+    if (*done) return;
+    __shared__ T As[BK][BM];
+    __shared__ T Bs[BK][BN];
+    const int tid = threadIdx.x;
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    const int mt_n = (op.M + BM - 1) / BM, nt_n = (op.N + BN - 1) / BN;
+    for (int b = blockIdx.z; b < op.batch; b += gridDim.z)
+        for (int mt = blockIdx.y; mt < mt_n; mt += gridDim.y)
+            for (int nt = blockIdx.x; nt < nt_n; nt += gridDim.x) {
+                const int m0 = mt * BM, n0 = nt * BN;
+                T acc[TM][TN];
+#pragma unroll
+                for (int u = 0; u < TM; ++u)
+#pragma unroll
+                    for (int v = 0; v < TN; ++v) acc[u][v] = T(0);
+                for (int k0 = 0; k0 < op.K; k0 += BK) {
+                    for (int e = tid; e < BK * BM; e += WT) {
+                        int kk, mm;
+                        if (op.a_m_fast) {
+                            mm = e % BM;
+                            kk = e / BM;
+                        } else {
+                            kk = e % BK;
+                            mm = e / BK;
+                        }
+                        const int m = m0 + mm, i = k0 + kk;
+                        As[kk][mm] = (m < op.M && i < op.K) ? op.a(b, m, i) : T(0);
+                    }
+                    for (int e = tid; e < BK * BN; e += WT) {
+                        int kk, nn;
+                        if (op.b_n_fast) {
+                            nn = e % BN;
+                            kk = e / BN;
+                        } else {
+                            kk = e % BK;
+                            nn = e / BK;
+                        }
+                        const int n = n0 + nn, i = k0 + kk;
+                        Bs[kk][nn] = (n < op.N && i < op.K) ? op.bm(b, i, n) : T(0);
+                    }
+                    __syncthreads();
+#pragma unroll
+                    for (int kk = 0; kk < BK; ++kk) {
+                        T av[TM], bv[TN];
+#pragma unroll
+                        for (int u = 0; u < TM; ++u) av[u] = As[kk][ty * TM + u];
+#pragma unroll
+                        for (int v = 0; v < TN; ++v) bv[v] = Bs[kk][tx * TN + v];
+#pragma unroll
+                        for (int u = 0; u < TM; ++u)
+#pragma unroll
+                            for (int v = 0; v < TN; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+                    }
+                    __syncthreads();
+                }
+#pragma unroll
+                for (int u = 0; u < TM; ++u)
+#pragma unroll
+                    for (int v = 0; v < TN; ++v) {
+                        const int m = m0 + ty * TM + u, n = n0 + tx * TN + v;
+                        if (m < op.M && n < op.N) op.store(b, m, n, acc[u][v]);
+                    }
+            }
+}
+
+// First link of the contraction: batch b = i_c2, m = j, n = r1, i = i_c1.
+template <typename T>
+struct OpContract1 {
+    const T* X;
+    const T* W;  // W_{c1,c2} or W_{c2,c1}, at its offset
+    const T* G;  // G_{c1,k}
+    T* V;
+    long long sk, sc1, sc2;  // strides of modes k, c1, c2 in X
+    int wsi, wsb;            // W_{c1,c2}(i, b) at W[i * wsi + b * wsb]
+    int Ic1, Ic2, R1;
+    int M, N, K, batch;
+    bool a_m_fast, b_n_fast;
+    __device__ T a(int b, int m, int i) const { return X[m * sk + i * sc1 + b * sc2]; }
+    __device__ T bm(int b, int i, int n) const {
+        return W[static_cast<long long>(i) * wsi + static_cast<long long>(b) * wsb] * G[static_cast<long long>(n) * Ic1 + i];
+    }
+    __device__ void store(int b, int m, int n, T v) const {
+        V[(static_cast<long long>(m) * Ic2 + b) * R1 + n] = v;
+    }
+};
+
+// Second link: batch b = j, m = r_c2, n = r_c1, i = i_c2; M_k in FP64.
+template <typename T>
+struct OpContract2 {
+    const T* G;  // G_{c2,k}
+    const T* V;
+    double* Mk;
+    int Ic2, R1, Q, qsm, qsn;  // q = m * qsm + n * qsn
+    int M, N, K, batch;
+    bool a_m_fast, b_n_fast;
+    __device__ T a(int, int m, int i) const { return G[static_cast<long long>(m) * Ic2 + i]; }
+    __device__ T bm(int b, int i, int n) const { return V[(static_cast<long long>(b) * Ic2 + i) * R1 + n]; }
+    __device__ void store(int b, int m, int n, T v) const {
+        Mk[static_cast<long long>(b) * Q + m * qsm + n * qsn] = static_cast<double>(v);
+    }
+};
+
+// First link of the Gram: m = i_d2, n = (r1, r1'), i = i_d1.
+template <typename T>
+struct OpGram1 {
+    const T* W;  // W_{d1,d2}(i, m) at W[i * wsi + m * wsb]
+    const T* G;  // G_{d1,k}
+    T* Tg;
+    int wsi, wsb, Id1, R1;
+    int M, N, K, batch;
+    bool a_m_fast, b_n_fast;
+    __device__ T a(int, int m, int i) const {
+        const T w = W[static_cast<long long>(i) * wsi + static_cast<long long>(m) * wsb];
+        return w * w;
+    }
+    __device__ T bm(int, int i, int n) const {
+        const int r = n / R1, rp = n - r * R1;
+        return G[static_cast<long long>(r) * Id1 + i] * G[static_cast<long long>(rp) * Id1 + i];
+    }
+    __device__ void store(int, int m, int n, T v) const { Tg[static_cast<long long>(m) * N + n] = v; }
+};
+
+// Second link: m = (r2, r2'), n = (r1, r1'), i = i_d2; K_k(q, q') with
+// q = r1 * s1 + r2 * s2.
+template <typename T>
+struct OpGram2 {
+    const T* G;  // G_{d2,k}
+    const T* Tg;
+    T* Kk;
+    int Id2, R1, R2, Q, s1, s2;
+    int M, N, K, batch;
+    bool a_m_fast, b_n_fast;
+    __device__ T a(int, int m, int i) const {
+        const int r = m / R2, rp = m - r * R2;
+        return G[static_cast<long long>(r) * Id2 + i] * G[static_cast<long long>(rp) * Id2 + i];
+    }
+    __device__ T bm(int, int i, int n) const { return Tg[static_cast<long long>(i) * N + n]; }
+    __device__ void store(int, int m, int n, T v) const {
+        const int r2 = m / R2, r2p = m - r2 * R2;
+        const int r1 = n / R1, r1p = n - r1 * R1;
+        Kk[static_cast<long long>(r1 * s1 + r2 * s2) * Q + r1p * s1 + r2p * s2] = v;
+    }
+};
+
+template <typename T, class Op>
+cudaError_t launch_gemm(const Op& op, const int* done, cudaStream_t st) {
+    if (op.M <= 0 || op.N <= 0 || op.batch <= 0) return cudaSuccess;
+    if (op.N <= 16) {
+        constexpr int BM = 128, BN = 16;
+        dim3 grid(1, std::min((op.M + BM - 1) / BM, 65535), std::min(op.batch, 65535));
+        k_wide_gemm<T, BM, BN, 8, 1, Op><<<grid, WT, 0, st>>>(op, done);
+    } else {
+        constexpr int BM = 64, BN = 64;
+        dim3 grid(std::min((op.N + BN - 1) / BN, 65535), std::min((op.M + BM - 1) / BM, 65535),
+                  std::min(op.batch, 65535));
+        k_wide_gemm<T, BM, BN, 4, 4, Op><<<grid, WT, 0, st>>>(op, done);
+    }
+    return cudaGetLastError();
+}
+
+// W_{p,q}(i_p, i_q) as W[i_p * sp + i_q * sq] from the pointer returned.
+template <typename T>
+const T* pair_view(const Shape& s, const T* W, int p, int q, int& sp, int& sq) {
+    if (p < q) {
+        sp = s.I[q];
+        sq = 1;
+        return W + s.woff[p][q];
+    }
+    sp = 1;
+    sq = s.I[p];
+    return W + s.woff[q][p];
+}
+
+void other_modes(int k, int& a, int& b) {
+    a = k == 0 ? 1 : 0;
+    b = k == 2 ? 1 : 2;
+}
+
+// ---------------------------------------------------------------------------
+// column solves
+// ---------------------------------------------------------------------------
+constexpr int HPART = 4096;  // partial sums of H held in shared memory
+
+__host__ __device__ inline int solve_rx(const Shape& s, int k) {
+    int a, b;
+    a = k == 0 ? 1 : 0;
+    b = k == 2 ? 1 : 2;
+    return s.R[k][a] > s.R[k][b] ? s.R[k][a] : s.R[k][b];
+}
+
+// Row c and column c' <= c of entry e of a lower triangle stored by rows.
+__device__ __forceinline__ void tri_index(int e, int& c, int& cp) {
+    c = static_cast<int>((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+    while (c * (c + 1) / 2 > e) --c;
+    while ((c + 1) * (c + 2) / 2 <= e) ++c;
+    cp = e - c * (c + 1) / 2;
+}
+
+// One CTA per column j of mode k (grid-stride over j).  Shared memory: H
+// (Rx^2, FP64), b (Rx), the two current columns (2 x WIDE_RMAX, FP64), the
+// row M_k(j, :) (Q, FP64), the partial sums of H (HPART, T), a status word.
+template <typename T>
+__global__ void __launch_bounds__(WT) k_wide_solve(const __grid_constant__ Shape s, const int k, const double rho,
+                                                   const double* __restrict__ Mk, const T* __restrict__ Kk,
+                                                   double* __restrict__ Gd, T* __restrict__ Gt, T* __restrict__ W,
+                                                   int* __restrict__ flags, const int* __restrict__ done) {
+    pdl_begin();
+    if (*done) return;
+    extern __shared__ __align__(16) unsigned char wsm[];
+    int m[2];
+    m[0] = k == 0 ? 1 : 0;
+    m[1] = k == 2 ? 1 : 2;
+    const int Rm[2] = {s.R[k][m[0]], s.R[k][m[1]]};
+    const int Q = Rm[0] * Rm[1], Ik = s.I[k];
+    const int Rx = max(Rm[0], Rm[1]);
+    double* H = reinterpret_cast<double*>(wsm);
+    double* bv = H + Rx * Rx;
+    double* gc = bv + Rx;  // [2][WIDE_RMAX]
+    double* Mr = gc + 2 * WIDE_RMAX;
+    T* part = reinterpret_cast<T*>(Mr + Q);
+    int* bad = reinterpret_cast<int*>(part + HPART);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int j = blockIdx.x; j < Ik; j += gridDim.x) {
+        for (int t = 0; t < 2; ++t)
+            for (int r = tid; r < Rm[t]; r += WT) gc[t * WIDE_RMAX + r] = Gd[s.goff[k][m[t]] + r * Ik + j];
+        for (int q = tid; q < Q; q += WT) Mr[q] = Mk[static_cast<long long>(j) * Q + q];
+        __syncthreads();
+        for (int ti = 0; ti < 2; ++ti) {
+            const int Ri = Rm[ti], Ro = Rm[1 - ti];
+            // K index of (o, c): slot 0 is the more significant digit
+            const int sc = ti == 0 ? Ro : 1, so = ti == 0 ? 1 : Ri;
+            const double* go = gc + (1 - ti) * WIDE_RMAX;
+            const int ne = Ri * (Ri + 1) / 2;
+            // o split into ng groups so that the partial sums fit; fixed
+            // ownership keeps the summation order independent of timing
+            const int ng = max(1, min(Ro, HPART / ne));
+            const int og = (Ro + ng - 1) / ng;
+            for (int it = tid; it < ne * ng; it += WT) {
+                const int e = it / ng, g = it - e * ng;
+                int c, cp;
+                tri_index(e, c, cp);
+                T acc = T(0);
+                const int o1 = min(Ro, (g + 1) * og);
+                for (int o = g * og; o < o1; ++o) {
+                    const T* kr = Kk + static_cast<long long>(o * so + c * sc) * Q + cp * sc;
+                    T inner = T(0);
+                    for (int o2 = 0; o2 < Ro; ++o2) inner = fma(static_cast<T>(go[o2]), kr[o2 * so], inner);
+                    acc = fma(static_cast<T>(go[o]), inner, acc);
+                }
+                part[g * ne + e] = acc;
+            }
+            for (int c = tid; c < Ri; c += WT) {
+                T acc = T(0);
+                for (int o = 0; o < Ro; ++o) acc = fma(static_cast<T>(go[o]), static_cast<T>(Mr[o * so + c * sc]), acc);
+                bv[c] = static_cast<double>(acc) + rho * gc[ti * WIDE_RMAX + c];
+            }
+            if (tid == 0) *bad = 0;
+            __syncthreads();
+            for (int e = tid; e < ne; e += WT) {
+                double h = 0.0;
+                for (int g = 0; g < ng; ++g) h += static_cast<double>(part[g * ne + e]);
+                int c, cp;
+                tri_index(e, c, cp);
+                H[c * Ri + cp] = h + (c == cp ? rho : 0.0);
+            }
+            __syncthreads();
+            // Cholesky H = L L^T, lower triangle in place
+            for (int c = 0; c < Ri; ++c) {
+                if (tid == 0) {
+                    double d = H[c * Ri + c];
+                    if (!(d > 0.0) || !isfinite(d)) {
+                        *bad = 1;
+                        d = 1.0;
+                    }
+                    H[c * Ri + c] = sqrt(d);
+                }
+                __syncthreads();
+                const double d = H[c * Ri + c];
+                for (int r = c + 1 + tid; r < Ri; r += WT) H[r * Ri + c] /= d;
+                __syncthreads();
+                const int nt = Ri - c - 1;
+                for (int e = tid; e < nt * (nt + 1) / 2; e += WT) {
+                    int rr, tt;
+                    tri_index(e, rr, tt);
+                    const int r = c + 1 + rr, t = c + 1 + tt;
+                    H[r * Ri + t] -= H[r * Ri + c] * H[t * Ri + c];
+                }
+                __syncthreads();
+            }
+            // L y = b, then L^T g = y, by warp 0
+            if (warp == 0) {
+                for (int r = 0; r < Ri; ++r) {
+                    double v = 0.0;
+                    for (int t = lane; t < r; t += 32) v += H[r * Ri + t] * bv[t];
+                    v = warp_sum(v);
+                    if (lane == 0) bv[r] = (bv[r] - v) / H[r * Ri + r];
+                    __syncwarp();
+                }
+                for (int r = Ri - 1; r >= 0; --r) {
+                    double v = 0.0;
+                    for (int t = r + 1 + lane; t < Ri; t += 32) v += H[t * Ri + r] * bv[t];
+                    v = warp_sum(v);
+                    if (lane == 0) bv[r] = (bv[r] - v) / H[r * Ri + r];
+                    __syncwarp();
+                }
+                bool fin = true;
+                for (int r = lane; r < Ri; r += 32) fin = fin && isfinite(bv[r]);
+                if (!__all_sync(0xffffffffu, fin) && lane == 0) *bad = 1;
+            }
+            __syncthreads();
+            if (*bad) {
+                if (tid == 0) atomicOr(flags, FLAG_NOTSPD);  // the old column stays
+            } else {
+                const int i = m[ti];
+                for (int c = tid; c < Ri; c += WT) {
+                    const double g = bv[c];
+                    gc[ti * WIDE_RMAX + c] = g;
+                    Gd[s.goff[k][i] + c * Ik + j] = g;
+                    Gt[s.goff[k][i] + c * Ik + j] = static_cast<T>(g);
+                }
+            }
+            __syncthreads();
+        }
+        // W_{k,i}(j, :) from the new columns, in the tensor dtype
+        for (int t = 0; t < 2; ++t) {
+            const int i = m[t], Ri = Rm[t], Ii = s.I[i];
+            const T* gik = Gt + s.goff[i][k];
+            for (int b2 = tid; b2 < Ii; b2 += WT) {
+                T w = T(0);
+                for (int r = 0; r < Ri; ++r)
+                    w = fma(static_cast<T>(gc[t * WIDE_RMAX + r]), gik[static_cast<long long>(r) * Ii + b2], w);
+                if (k < i)
+                    W[s.woff[k][i] + static_cast<long long>(j) * Ii + b2] = w;
+                else
+                    W[s.woff[i][k] + static_cast<long long>(b2) * Ik + j] = w;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+int solve_smem(const Shape& s, int k) {
+    const int Rx = solve_rx(s, k);
+    int a, b;
+    other_modes(k, a, b);
+    const int Q = s.R[k][a] * s.R[k][b];
+    return (Rx * Rx + Rx + 2 * WIDE_RMAX + Q) * 8 + HPART * static_cast<int>(sizeof(T)) + 16;
+}
+
+}  // namespace
+
+WideChain wide_chain(const Shape& s, int k) {
+    WideChain c;
+    int a, b;
+    other_modes(k, a, b);
+    // contraction: the contiguous mode first unless it is k (coalesced loads
+    // of X either way); for k = 2 the order with fewer multiply-adds
+    if (k != 2) {
+        c.c1 = 2;
+        c.c2 = k == 0 ? 1 : 0;
+    } else {
+        const int Q = s.R[k][a] * s.R[k][b];
+        const double ca = static_cast<double>(s.P) * s.R[k][a] + static_cast<double>(s.I[k]) * s.I[b] * Q;
+        const double cb = static_cast<double>(s.P) * s.R[k][b] + static_cast<double>(s.I[k]) * s.I[a] * Q;
+        c.c1 = ca <= cb ? a : b;
+        c.c2 = ca <= cb ? b : a;
+    }
+    // Gram: the mode with the cheaper chain summed first
+    const double Ia = s.I[a], Ib = s.I[b], Ra = s.R[k][a], Rb = s.R[k][b];
+    const double Q2 = Ra * Ra * Rb * Rb;
+    const double ga = Ia * Ib * Ra * Ra + Ib * Q2;
+    const double gb = Ia * Ib * Rb * Rb + Ia * Q2;
+    c.d1 = ga <= gb ? a : b;
+    c.d2 = ga <= gb ? b : a;
+    return c;
+}
+
+long long wide_v_elems(const Shape& s, int k) {
+    const WideChain c = wide_chain(s, k);
+    return static_cast<long long>(s.I[k]) * s.I[c.c2] * s.R[k][c.c1];
+}
+
+long long wide_t_elems(const Shape& s, int k) {
+    const WideChain c = wide_chain(s, k);
+    return static_cast<long long>(s.I[c.d2]) * s.R[k][c.d1] * s.R[k][c.d1];
+}
+
+template <typename T>
+cudaError_t launch_wide_contract(const Shape& s, int k, const T* X, const T* Gt, const T* W, T* V, const int* done,
+                                 cudaStream_t st) {
+    const WideChain c = wide_chain(s, k);
+    const long long str[3] = {static_cast<long long>(s.I[1]) * s.I[2], s.I[2], 1};
+    OpContract1<T> op;
+    op.X = X;
+    op.W = pair_view(s, W, c.c1, c.c2, op.wsi, op.wsb);
+    op.G = Gt + s.goff[c.c1][k];
+    op.V = V;
+    op.sk = str[k];
+    op.sc1 = str[c.c1];
+    op.sc2 = str[c.c2];
+    op.Ic1 = s.I[c.c1];
+    op.Ic2 = s.I[c.c2];
+    op.R1 = s.R[k][c.c1];
+    op.M = s.I[k];
+    op.N = op.R1;
+    op.K = op.Ic1;
+    op.batch = op.Ic2;
+    op.a_m_fast = op.sk == 1;
+    op.b_n_fast = false;
+    return launch_gemm<T>(op, done, st);
+}
+
+template <typename T>
+cudaError_t launch_wide_finish(const Shape& s, int k, const T* Gt, const T* V, double* Mk, const int* done,
+                               cudaStream_t st) {
+    const WideChain c = wide_chain(s, k);
+    OpContract2<T> op;
+    op.G = Gt + s.goff[c.c2][k];
+    op.V = V;
+    op.Mk = Mk;
+    op.Ic2 = s.I[c.c2];
+    op.R1 = s.R[k][c.c1];
+    const int R2 = s.R[k][c.c2];
+    op.Q = op.R1 * R2;
+    // q = r_a R_{k,b} + r_b (a < b the other modes)
+    if (c.c2 < c.c1) {
+        op.qsm = op.R1;
+        op.qsn = 1;
+    } else {
+        op.qsm = 1;
+        op.qsn = R2;
+    }
+    op.M = R2;
+    op.N = op.R1;
+    op.K = op.Ic2;
+    op.batch = s.I[k];
+    op.a_m_fast = false;
+    op.b_n_fast = true;
+    return launch_gemm<T>(op, done, st);
+}
+
+template <typename T>
+cudaError_t launch_wide_gram(const Shape& s, int k, const T* Gt, const T* W, T* Tg, T* Kk, const int* done,
+                             cudaStream_t st) {
+    const WideChain c = wide_chain(s, k);
+    const int R1 = s.R[k][c.d1], R2 = s.R[k][c.d2];
+    OpGram1<T> g1;
+    int sp, sq;
+    g1.W = pair_view(s, W, c.d1, c.d2, sp, sq);
+    g1.wsi = sp;
+    g1.wsb = sq;
+    g1.G = Gt + s.goff[c.d1][k];
+    g1.Tg = Tg;
+    g1.Id1 = s.I[c.d1];
+    g1.R1 = R1;
+    g1.M = s.I[c.d2];
+    g1.N = R1 * R1;
+    g1.K = g1.Id1;
+    g1.batch = 1;
+    g1.a_m_fast = sq == 1;
+    g1.b_n_fast = false;
+    cudaError_t e = launch_gemm<T>(g1, done, st);
+    if (e != cudaSuccess) return e;
+    OpGram2<T> g2;
+    g2.G = Gt + s.goff[c.d2][k];
+    g2.Tg = Tg;
+    g2.Kk = Kk;
+    g2.Id2 = s.I[c.d2];
+    g2.R1 = R1;
+    g2.R2 = R2;
+    g2.Q = R1 * R2;
+    // q = r_a R_{k,b} + r_b (a < b the other modes)
+    if (c.d1 < c.d2) {
+        g2.s1 = R2;
+        g2.s2 = 1;
+    } else {
+        g2.s1 = 1;
+        g2.s2 = R1;
+    }
+    g2.M = R2 * R2;
+    g2.N = R1 * R1;
+    g2.K = g2.Id2;
+    g2.batch = 1;
+    g2.a_m_fast = false;
+    g2.b_n_fast = true;
+    return launch_gemm<T>(g2, done, st);
+}
+
+template <typename T>
+cudaError_t launch_wide_solve(const Shape& s, int k, double rho, const double* Mk, const T* Kk, double* Gd, T* Gt,
+                              T* W, int* flags, const int* done, cudaStream_t st) {
+    const int smem = solve_smem<T>(s, k);
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_wide_solve<T>), smem);
+    if (e != cudaSuccess) return e;
+    k_wide_solve<T><<<std::min(s.I[k], 65535), WT, smem, st>>>(s, k, rho, Mk, Kk, Gd, Gt, W, flags, done);
+    return cudaGetLastError();
+}
+
+#define IFCTN_WIDE_INST(T)                                                                                         \
+    template cudaError_t launch_wide_contract<T>(const Shape&, int, const T*, const T*, const T*, T*, const int*, \
+                                                 cudaStream_t);                                                   \
+    template cudaError_t launch_wide_finish<T>(const Shape&, int, const T*, const T*, double*, const int*,        \
+                                               cudaStream_t);                                                     \
+    template cudaError_t launch_wide_gram<T>(const Shape&, int, const T*, const T*, T*, T*, const int*,           \
+                                             cudaStream_t);                                                       \
+    template cudaError_t launch_wide_solve<T>(const Shape&, int, double, const double*, const T*, double*, T*, T*, \
+                                              int*, const int*, cudaStream_t);
+IFCTN_WIDE_INST(float)
+IFCTN_WIDE_INST(double)
+#undef IFCTN_WIDE_INST
+
+}  // namespace ifctn

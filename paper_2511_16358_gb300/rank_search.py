@@ -32,8 +32,26 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-# per-edge rank limit of the library (its stage systems are held in registers)
+# per-edge rank limits of the library: 8 in general (the register-resident
+# stage kernels), 64 for order-3 tensors with every Q_k = prod_{l != k} R_{k,l}
+# at most 4096 (the chain kernels for wide ranks)
 MAX_EDGE_RANK = 8
+MAX_EDGE_RANK_ORDER3 = 64
+MAX_Q_ORDER3 = 4096
+
+
+def check_ranks(N: int, R) -> None:
+    """Raises ValueError when the library would refuse rank matrix R."""
+    lim = MAX_EDGE_RANK_ORDER3 if N == 3 else MAX_EDGE_RANK
+    for k in range(N):
+        for l in range(N):
+            if k != l and not 1 <= int(R[k][l]) <= lim:
+                raise ValueError(f"edge rank R[{k},{l}] = {int(R[k][l])} outside 1..{lim}")
+    if N == 3:
+        for k in range(N):
+            q = int(np.prod([int(R[k][l]) for l in range(N) if l != k]))
+            if q > MAX_Q_ORDER3:
+                raise ValueError(f"Q_{k} = {q} above {MAX_Q_ORDER3}")
 
 
 def rank_matrix(N: int, edges: dict) -> np.ndarray:
@@ -44,9 +62,9 @@ def rank_matrix(N: int, edges: dict) -> np.ndarray:
     return R
 
 
-def msi_grid(max_rank: int = MAX_EDGE_RANK) -> list:
-    """The multispectral grid of Sec. 5.2 for an order-3 tensor, without the
-    points that need an edge rank above ``max_rank``."""
+def msi_grid(max_rank: int = 36) -> list:
+    """The multispectral grid of Sec. 5.2 for an order-3 tensor (18 points),
+    without the points that need an edge rank above ``max_rank``."""
     out = []
     for r12 in (3, 6, 9, 15, 30, 36):
         for r13 in (3, 6, 9):
@@ -111,11 +129,7 @@ def search(obs, mask, grid, *, rho=0.1, max_sweeps=1000, tol=1e-5, precision=Non
     precision = b.FP64 if precision is None else precision
     dims = tuple(int(d) for d in np.shape(obs))
     for R in grid:
-        N = len(dims)
-        for k in range(N):
-            for l in range(N):
-                if k != l and not 1 <= int(R[k][l]) <= MAX_EDGE_RANK:
-                    raise ValueError(f"edge rank R[{k},{l}] = {int(R[k][l])} outside 1..{MAX_EDGE_RANK}")
+        check_ranks(len(dims), R)
     dt = b.tensor_dtype(precision)
     obs_h = np.ascontiguousarray(obs, dtype=dt)
     if xtrue is None:

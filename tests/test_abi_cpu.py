@@ -60,7 +60,10 @@ def _prob(**kw):
 
 @pytest.mark.parametrize("bad", [
     dict(ranks=np.array([[0, 2, 2], [2, 0, 2], [2, 2, 0]]) * 0),
-    dict(ranks=np.array([[0, 9, 2], [9, 0, 2], [2, 2, 0]])),
+    dict(ranks=np.array([[0, 65, 2], [65, 0, 2], [2, 2, 0]])),  # above 64 at order 3
+    dict(ranks=np.array([[0, 64, 65], [64, 0, 1], [65, 1, 0]])),  # Q_0 = 64 * 65 > 4096
+    dict(dims=(4, 5, 6, 3), ranks=np.array([[0, 9, 2, 2], [9, 0, 2, 2], [2, 2, 0, 2], [2, 2, 2, 0]])),  # above 8 at order 4
+    dict(dims=(4, 5), ranks=np.array([[0, 9], [9, 0]])),  # above 8 at order 2
     dict(ranks=np.array([[0, 2, 3], [2, 0, 2], [2, 2, 0]])),  # not symmetric
     dict(rho=0.0),
     dict(rho=-1.0),

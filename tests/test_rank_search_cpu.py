@@ -58,13 +58,25 @@ def _data(shape=(6, 5, 4), p=0.5):
     return xt, mask
 
 
-def test_msi_grid_is_the_papers_grid_capped_at_the_edge_rank_limit():
-    full = rs.msi_grid(max_rank=36)
+def test_msi_grid_is_the_papers_grid():
+    full = rs.msi_grid()
     assert len(full) == 18
     assert all(R[0, 2] == R[1, 2] == R[2, 0] == R[2, 1] for R in full)
     assert sorted({int(R[0, 1]) for R in full}) == [3, 6, 9, 15, 30, 36]
-    capped = rs.msi_grid()
+    for R in full:
+        rs.check_ranks(3, R)  # every point is within the library's order-3 limits
+    capped = rs.msi_grid(max_rank=6)
     assert [(int(R[0, 1]), int(R[0, 2])) for R in capped] == [(3, 3), (3, 6), (6, 3), (6, 6)]
+
+
+def test_rank_limits_follow_the_order():
+    rs.check_ranks(3, rs.rank_matrix(3, {(0, 1): 64, (0, 2): 64, (1, 2): 1}))
+    with pytest.raises(ValueError):
+        rs.check_ranks(3, rs.rank_matrix(3, {(0, 1): 65, (0, 2): 2, (1, 2): 2}))
+    with pytest.raises(ValueError):  # Q_0 = 64 * 65 > 4096
+        rs.check_ranks(3, rs.rank_matrix(3, {(0, 1): 64, (0, 2): 65, (1, 2): 1}))
+    with pytest.raises(ValueError):
+        rs.check_ranks(4, rs.rank_matrix(4, {(0, 1): 9, (0, 2): 2, (0, 3): 2, (1, 2): 2, (1, 3): 2, (2, 3): 2}))
 
 
 def test_edge_grid_enumerates_every_combination():
@@ -133,6 +145,7 @@ def test_server_released_when_a_job_fails_and_bad_grids_refused():
     with pytest.raises(ValueError):
         rs.search(xt * mask, mask, [], xtrue=xt, backend=FakeServer(xt))
     with pytest.raises(ValueError):
-        rs.search(xt * mask, mask, rs.msi_grid(max_rank=36), xtrue=xt, backend=FakeServer(xt))
+        rs.search(xt * mask, mask, [rs.rank_matrix(3, {(0, 1): 65, (0, 2): 3, (1, 2): 3})], xtrue=xt,
+                  backend=FakeServer(xt))
     with pytest.raises(ValueError):
         rs.search(xt * mask, mask, rs.msi_grid(), holdout=0.0, backend=FakeServer(xt))

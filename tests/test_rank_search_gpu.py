@@ -59,3 +59,18 @@ def test_rank_search_holdout_scores_match_oracle():
                           lambda X: float(np.linalg.norm(X[held] - ref) / np.linalg.norm(ref)))
     np.testing.assert_allclose(res.scores, want, rtol=1e-9)
     assert res.best_index == int(np.argmin(want))
+
+
+def test_rank_search_over_ranks_above_eight_matches_oracle():
+    """Points of the multispectral grid with R_{1,2} in {15, 36} (Sec. 5.2) next
+    to small ones, all on one server: each score equals the oracle's."""
+    case = make_case(DIMS, {(0, 1): 3, (0, 2): 2, (1, 2): 2}, 0.4, seed=483, kind="max1", sigma=0.02)
+    xt, mask = case["xt"], case["mask"]
+    grid = [R for R in rs.edge_grid(3, {(0, 1): [3, 15, 36], (0, 2): [3, 9], (1, 2): [3, 9]})
+            if R[0, 2] == R[1, 2]]
+    res = rs.search(xt * mask, mask, grid, rho=0.1, max_sweeps=SWEEPS, tol=0.0, precision=b.FP64, xtrue=xt,
+                    seed=SEED, hbm_budget_bytes=8 << 30, slots=4)
+    den = np.linalg.norm(xt)
+    want = _oracle_scores(case, grid, mask, lambda X: float(np.linalg.norm(xt - X) / den))
+    np.testing.assert_allclose(res.scores, want, rtol=1e-9)
+    assert res.best_index == int(np.argmin(want))
