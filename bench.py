@@ -483,8 +483,11 @@ def tuning_record(path, w):
         for ln in open(path):
             if ln.startswith("ifctn-tune-v1 ") and f" {shape}" in ln:
                 f = dict(kv.split("=", 1) for kv in ln.split() if "=" in kv)
-                k = next(t for t in ln.split() if t.startswith("k") and t[1:].isdigit())
-                out["modes"][k] = f
+                k = next((t for t in ln.split() if t.startswith("k") and t[1:].isdigit()), None)
+                if k is not None:
+                    out["modes"][k] = f
+                elif "path" in f:  # the execution-path choice of the shape
+                    out.setdefault("path", {})[ln.split()[2]] = f
     except OSError:
         pass
     return out

@@ -14,7 +14,7 @@ LIB = os.path.join(HERE, "libifctn.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["ifctn_persistent_f32.cu", "ifctn_persistent_f64.cu", "ifctn_contract_w_f32.cu",
            "ifctn_contract_w_f64.cu", "ifctn_kernels.cu", "ifctn_api.cu", "ifctn_server.cu", "ifctn_noalloc.cu",
-           "ifctn_selftest.cu", "ifctn_xupdate.cu", "ifctn_wide.cu"]
+           "ifctn_selftest.cu", "ifctn_xupdate.cu", "ifctn_wide.cu", "ifctn_plan.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include")]
