@@ -732,6 +732,9 @@ cudaError_t launch_colw_r(const ContractArgs<T>& a, int grid, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_contract_warp(const ContractArgs<T>& a, int grid, cudaStream_t st) {
     const bool col = a.pl.kcase == CASE_COL;
+    // the plan's warps per CTA must be those of the instantiation it selects
+    const int nw_want = a.pl.rpl == 2 ? (col ? 12 : wdev::NWARP) : (a.pl.nwarp == 8 ? 8 : wdev::NWARP);
+    if (a.pl.nwarp != nw_want) return cudaErrorInvalidValue;
     if (!col && a.pl.rpl == 2) {  // two rows per lane: instantiated for equal ranks R_{k,B} = R_{k,l2}
         switch (a.pl.R1) {
             case 2: return wdev::launch_roww_r<T, 2, 2, 2>(a, grid, st);
@@ -746,6 +749,24 @@ cudaError_t launch_contract_warp(const ContractArgs<T>& a, int grid, cudaStream_
 #define IFCTN_CASE(R) \
     case R:           \
         return wdev::launch_colw_r<T, R, 2, 12>(a, grid, st);
+            IFCTN_CASE(1)
+            IFCTN_CASE(2)
+            IFCTN_CASE(3)
+            IFCTN_CASE(4)
+            IFCTN_CASE(5)
+            IFCTN_CASE(6)
+            IFCTN_CASE(7)
+            IFCTN_CASE(8)
+#undef IFCTN_CASE
+            default:
+                return cudaErrorInvalidValue;
+        }
+    }
+    if (a.pl.nwarp == 8) {  // long rows: 8 warps, each with twice the shared memory of the 16-warp plan
+        switch (a.pl.R1) {
+#define IFCTN_CASE(R) \
+    case R:           \
+        return col ? wdev::launch_colw_r<T, R, 1, 8>(a, grid, st) : wdev::launch_roww_r<T, R, 1, 0, 8>(a, grid, st);
             IFCTN_CASE(1)
             IFCTN_CASE(2)
             IFCTN_CASE(3)

@@ -489,10 +489,17 @@ WarpKnobs default_warp_knobs() {
     return kn;
 }
 
-ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitDesc>& units,
-                                const WarpKnobs& kn) {
-    const bool rpl_allowed = kn.rpl != 0;
-    int NW = 16;  // warps of a CTA (12 for the COL kernel with tasks of up to 64 rows)
+namespace {
+
+// The plan with NW0 warps a CTA (12 for the COL kernel with tasks of up to 64
+// rows) and at most XBYTES of X in a one-row-per-lane task; pl.warp = 0 when
+// the rings do not fit.
+ContractPlan plan_contract_warp_at(const Shape& s, int k, int sz, std::vector<UnitDesc>& units,
+                                   const WarpKnobs& kn, int NW0, int XBYTES) {
+    // two rows per lane only with the 16-warp CTA (12 for COL): the kernels
+    // are instantiated for those
+    const bool rpl_allowed = kn.rpl != 0 && NW0 == 16;
+    int NW = NW0;
     ContractPlan pl;
     memset(&pl, 0, sizeof(pl));
     const int N = s.N, Am = N - 2, Bm = N - 1, IA = s.IA, IB = s.IB;
@@ -501,7 +508,6 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
     // work units: enough for balance; where the partials are kept per unit
     // (CASE_A, COL) fewer, since the finisher sums over them
     const int target = (k < N - 2) ? 8 * sms : 4 * sms;
-    const int XBYTES = kn.xbytes;  // at most this many X bytes in a one-row-per-lane task
     // rows per task: at most cap, split evenly
     auto balanced = [](int rows, int cap) {
         cap = std::max(1, std::min(rows, cap));
@@ -794,11 +800,42 @@ ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitD
     if (!pl.warp && pl.rpl == 2) {
         WarpKnobs k1 = kn;
         k1.rpl = 0;
-        return plan_contract_warp(s, k, sz, units, k1);
+        return plan_contract_warp_at(s, k, sz, units, k1, NW0, XBYTES);
     }
     pl.grid = std::max(1, std::min(pl.nunits, sms));
     if (!pl.warp) units.clear();
     return pl;
+}
+
+}  // namespace
+
+// The first plan whose rings fit and whose tasks have at least three quarters
+// of min(IA, 32) rows (or the fitting plan with the most rows a task): 16 warps a CTA,
+// then 8 with twice the shared memory each; the X budget of a task as the knob
+// gives it, doubled, quadrupled (long rows fill fewer lanes).
+ContractPlan plan_contract_warp(const Shape& s, int k, int sz, std::vector<UnitDesc>& units,
+                                const WarpKnobs& kn) {
+    const int rows = s.IA;  // rows of mode A: what a task splits, for both kinds
+    ContractPlan best;
+    memset(&best, 0, sizeof(best));
+    std::vector<UnitDesc> bu;
+    for (int nw : {16, 8})
+        for (int xf = 1; xf <= 4; xf *= 2) {
+            std::vector<UnitDesc> u;
+            const ContractPlan p = plan_contract_warp_at(s, k, sz, u, kn, nw, kn.xbytes * xf);
+            if (!p.warp) continue;
+            const int want = std::min(rows, 32) * 3 / 4;
+            if (p.TAc >= want) {
+                units = u;
+                return p;
+            }
+            if (!best.warp || p.TAc > best.TAc) {
+                best = p;
+                bu = u;
+            }
+        }
+    units = bu;
+    return best;
 }
 
 }  // namespace ifctn

@@ -149,3 +149,30 @@ def test_graph_path_rows_per_lane_two_sweeps_match_oracle(dims, edge, rows_per_l
     assert rel_err(c.factors(), G1) < tol
     assert rel_err(c.x().astype(np.float64), X1) < tol
     c.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(b.FP64, 1e-10), (b.MIXED, 2e-4)])
+@pytest.mark.parametrize("dims,edge", [
+    ((3, 4, 100, 100), 5),                                  # 8 warps a CTA in every mode, 25-row tasks
+    ((2, 3, 33, 128), {(0, 1): 4, (0, 2): 3, (0, 3): 5, (1, 2): 2, (1, 3): 4, (2, 3): 3}),  # 17 + 16 rows
+    ((5, 4, 27, 80), 3),                                    # 8 warps, 80-entry rows
+    ((4, 5, 30, 48), 5),                                    # 16 warps with a doubled task budget
+])
+def test_graph_path_long_rows_two_sweeps_match_oracle(dims, edge, precision, tol):
+    """Rows too long for a well-filled task at the default X budget: the
+    planner doubles or quadruples the budget and, where the rings then do not
+    fit 16 warps, runs 8 warps a CTA with twice the shared memory each
+    (FP64 1e-10; mixed within 2e-4 of the FP64 oracle after two sweeps)."""
+    from tests._cases import make_case
+    case = make_case(dims, edge, 0.3, seed=471, kind="max1", sigma=0.02)
+    dt = b.tensor_dtype(precision)
+    with path("graph"):
+        c = b.Completion(dims, case["R"], case["xt"].astype(dt), case["mask"], rho=0.1, max_sweeps=2, tol=0.0,
+                         precision=precision, init_factors=case["G0"].copy())
+    c.sweep(2)
+    xin = case["xt"].astype(dt).astype(np.float64)
+    G1, X1 = case["G0"].copy(), oracle.init_x(xin, case["mask"])
+    oracle.complete(dims, case["R"], 0.1, G1, X1, case["mask"], max_sweeps=2)
+    assert rel_err(c.factors(), G1) < tol
+    assert rel_err(c.x().astype(np.float64), X1) < tol
+    c.close()
