@@ -23,6 +23,8 @@
 // Partials go to the same per-unit slots as the CTA kernels and are reduced by
 // the same finisher, in a fixed order (deterministic, no atomics).
 #pragma once
+#include <type_traits>
+
 #include "ifctn_contract_dev.cuh"
 
 namespace ifctn {
@@ -113,6 +115,18 @@ __device__ __forceinline__ void load_unit(const UnitDesc* units, int ui, int rbk
     c.fstride = u.fstride;
     c.a0 = u.a0;
     c.a1 = u.a1;
+}
+
+// Slab f -> (i0, i1) with the plan's multiplier instead of a division (N = 4).
+__device__ __forceinline__ void decode_f_fast(const Shape& s, const ContractPlan& pl, long long f, int& i0, int& i1) {
+    const int fi = static_cast<int>(f);
+    if (s.N == 4) {
+        i0 = static_cast<int>((static_cast<unsigned long long>(static_cast<unsigned>(fi)) * pl.fdiv_m) >> pl.fdiv_s);
+        i1 = fi - i0 * s.I[1];
+    } else {
+        i0 = fi;
+        i1 = 0;
+    }
 }
 
 __device__ __forceinline__ Task task_at(const UnitCur& c, int t, int rbk) {
@@ -222,10 +236,10 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
             cp_async_commit();  // empty group: keeps one group per stage
             return;
         }
+        const Task tk = task_at(ic, ct, RBK);
         {
-            const Task tk = task_at(ic, ct, RBK);
             int i0, i1;
-            decode_f(s, tk.f, i0, i1);
+            decode_f_fast(s, pl, tk.f, i0, i1);
             T* ax = auxr + st * AUXW;
             if (p0 >= 0) {
                 const T* r = A.W + s.woff[p0][Bm] + static_cast<long long>(p0 == 0 ? i0 : i1) * IB;
@@ -248,7 +262,6 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
             cp_async_commit();
         }
         if (lane == 0) {
-            const Task tk = task_at(ic, ct, RBK);
             T* buf = tiles + (static_cast<size_t>(warp) * S + st) * TC;
             uint64_t* bar = &bars[warp * S + st];
             uintptr_t xlo, xhi, wlo = 0, whi = 0;
@@ -269,7 +282,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
     settle();
     for (int i = 0; i < S; ++i) issue_next(i);
 
-    int it = 0;  // tasks consumed by this warp
+    int st = 0;        // ring stage of the next task this warp consumes
+    unsigned par = 0;  // and the mbarrier phase parity it waits for
     for (int ui = blockIdx.x; ui < pl.nunits; ui += gridDim.x) {
         UnitCur uc;
         load_unit(A.units, ui, RBK, uc);
@@ -295,9 +309,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
                 for (int r = 0; r < RB; ++r) z[q][r2][r] = T(0);
 
         int zslot = -1;
-        for (int t = warp; t < nt; t += NW, ++it) {
-            const int st = it % S;
-            const unsigned par = static_cast<unsigned>((it / S) & 1);
+        for (int t = warp; t < nt; t += NW) {
             T* buf = tiles + (static_cast<size_t>(warp) * S + st) * TC;
             const T* ax = auxr + st * AUXW;
             cp_async_wait_ring(S);  // this lane's W entries of the task
@@ -305,7 +317,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
             const Task tk = task_at(uc, t, RBK);
             if (ok) {
                 int i0, i1;
-                decode_f(s, tk.f, i0, i1);
+                decode_f_fast(s, pl, tk.f, i0, i1);
                 // coefficient table psi(b, r) = prod_{p in F, p != k} W_{p,B}(i_p, b) G_{B,k}(r, b)
                 for (int b = lane; b < IB; b += 32) {
                     const T om = (p0 >= 0 ? ax[b] : T(1)) * (two_psi ? ax[AUX_W1 + b] : T(1));
@@ -336,20 +348,16 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
 #pragma unroll
                     for (int r = 0; r < RB; ++r) u0[q][r] = u1[q][r] = T(0);
                 if (vec) {
-                    // 16-byte chunks of the row; with pl.skew each lane starts at
-                    // its own chunk so rows that share banks are read apart
-                    const int nch = IB / VN;
-                    int c = pl.skew ? lane % nch : 0;
-#pragma unroll 2
-                    for (int ic2 = 0; ic2 < nch; ++ic2, c = (c + 1 == nch) ? 0 : c + 1) {
-                        const int b = c * VN;
+                    // one 16-byte chunk b..b+VN-1 of the lane's rows; with_w: the
+                    // rows are multiplied by W_{A,B} first
+                    auto chunk = [&](int b, auto with_w) {
                         T p[VN * RB];
                         ld_row<T, VN * RB>(psi + b * RB, p);
 #pragma unroll
                         for (int q = 0; q < RPL; ++q) {
                             T xa[VN];
                             ld_row<T, VN>(xr[q] + b, xa);
-                            if (wr[q]) {
+                            if constexpr (decltype(with_w)::value) {
                                 T wa[VN];
                                 ld_row<T, VN>(wr[q] + b, wa);
 #pragma unroll
@@ -362,6 +370,26 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
                                     if (SPLIT && (j & 1)) u1[q][r] = fma(xa[j], p[j * RB + r], u1[q][r]);
                                     else u0[q][r] = fma(xa[j], p[j * RB + r], u0[q][r]);
                                 }
+                        }
+                    };
+                    const bool hw = wr[0] != nullptr;  // the same for every row of the task
+                    if (!pl.skew) {
+                        if (hw) {
+#pragma unroll 2
+                            for (int b = 0; b < IB; b += VN) chunk(b, std::true_type{});
+                        } else {
+#pragma unroll 2
+                            for (int b = 0; b < IB; b += VN) chunk(b, std::false_type{});
+                        }
+                    } else {
+                        // each lane starts at its own chunk, so that rows that share
+                        // banks are read apart
+                        const int nch = IB / VN;
+                        int c = lane % nch;
+#pragma unroll 2
+                        for (int ic2 = 0; ic2 < nch; ++ic2, c = (c + 1 == nch) ? 0 : c + 1) {
+                            if (hw) chunk(c * VN, std::true_type{});
+                            else chunk(c * VN, std::false_type{});
                         }
                     }
                 } else {
@@ -428,6 +456,10 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
                 issue_next(st);  // the stage is free again
             } else {
                 zslot = st;  // keeps z for the unit reduction; refilled after it
+            }
+            if (++st == S) {
+                st = 0;
+                par ^= 1u;
             }
         }
         // ---- unit end: reduce over warps (fixed order) ----
@@ -565,10 +597,10 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_colw(const __grid_const
             cp_async_commit();
             return;
         }
+        const Task tk = task_at(ic, ct, RBK);
         {
-            const Task tk = task_at(ic, ct, RBK);
             int i0, i1;
-            decode_f(s, tk.f, i0, i1);
+            decode_f_fast(s, pl, tk.f, i0, i1);
             T* ax = auxr + st * AUXW;
 #pragma unroll
             for (int q = 0; q < RPL; ++q) {
@@ -583,7 +615,6 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_colw(const __grid_const
             cp_async_commit();
         }
         if (lane == 0) {
-            const Task tk = task_at(ic, ct, RBK);
             T* buf = tiles + (static_cast<size_t>(warp) * S + st) * TC;
             uint64_t* bar = &bars[warp * S + st];
             uintptr_t lo, hi;
@@ -600,7 +631,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_colw(const __grid_const
     settle();
     for (int i = 0; i < S; ++i) issue_next(i);
 
-    int it = 0;
+    int st = 0;        // ring stage of the next task this warp consumes
+    unsigned par = 0;  // and the mbarrier phase parity it waits for
     for (int ui = blockIdx.x; ui < pl.nunits; ui += gridDim.x) {
         UnitCur uc;
         load_unit(A.units, ui, RBK, uc);
@@ -614,9 +646,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_colw(const __grid_const
 #pragma unroll
             for (int r = 0; r < RA; ++r) z[r2][r] = T(0);
         int zslot = -1;
-        for (int t = warp; t < nt; t += NW, ++it) {
-            const int st = it % S;
-            const unsigned par = static_cast<unsigned>((it / S) & 1);
+        for (int t = warp; t < nt; t += NW) {
             T* buf = tiles + (static_cast<size_t>(warp) * S + st) * TC;
             const T* ax = auxr + st * AUXW;
             cp_async_wait_ring(S);
@@ -624,7 +654,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_colw(const __grid_const
             const Task tk = task_at(uc, t, RBK);
             if (ok) {
                 int i0, i1;
-                decode_f(s, tk.f, i0, i1);
+                decode_f_fast(s, pl, tk.f, i0, i1);
                 // phi rows (lane-owned rows a = lane + 32 q); rows past na are zero
 #pragma unroll
                 for (int q = 0; q < RPL; ++q) {
@@ -643,8 +673,25 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_colw(const __grid_const
                 T u0[RA], u1[RA];
 #pragma unroll
                 for (int r = 0; r < RA; ++r) u0[r] = u1[r] = T(0);
-                const int nav = (tk.na + VN - 1) / VN * VN;
-                for (int a = 0; a < nav; a += VN) {
+                // whole chunks of VN rows, then the ragged last one, whose rows
+                // past na read row na - 1 (their phi rows are zero)
+                const int nfull = tk.na / VN * VN;
+                const T* xa = xt;
+                for (int a = 0; a < nfull; a += VN, xa += static_cast<size_t>(VN) * IB) {
+                    T p[VN * RA];
+                    ld_row<T, VN * RA>(phi + a * RA, p);
+#pragma unroll
+                    for (int j = 0; j < VN; ++j) {
+                        const T x = xa[static_cast<size_t>(j) * IB];
+#pragma unroll
+                        for (int r = 0; r < RA; ++r) {
+                            if (SPLIT && (j & 1)) u1[r] = fma(x, p[j * RA + r], u1[r]);
+                            else u0[r] = fma(x, p[j * RA + r], u0[r]);
+                        }
+                    }
+                }
+                if (nfull < tk.na) {
+                    const int a = nfull;
                     T p[VN * RA];
                     ld_row<T, VN * RA>(phi + a * RA, p);
 #pragma unroll
@@ -682,6 +729,10 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_colw(const __grid_const
                 issue_next(st);
             else
                 zslot = st;
+            if (++st == S) {
+                st = 0;
+                par ^= 1u;
+            }
         }
         const int nwk = min(NW, nt);
         if (zslot >= 0) {

@@ -91,6 +91,8 @@ struct ContractPlan {
     int auxw;        // warp kernels: elements of a warp's per-stage ring slot of W entries
     int rpl;         // warp kernels: rows per lane (1, or 2 for tasks of up to 64 rows)
     int nwarp;       // warp kernels: warps per CTA
+    int fdiv_s;      // warp kernels, N = 4: slab f = i0 I_1 + i1 has i0 = (f * fdiv_m) >> fdiv_s
+    unsigned long long fdiv_m;
     long long part_elems;
 };
 

@@ -803,6 +803,13 @@ ContractPlan plan_contract_warp_at(const Shape& s, int k, int sz, std::vector<Un
         return plan_contract_warp_at(s, k, sz, units, k1, NW0, XBYTES);
     }
     pl.grid = std::max(1, std::min(pl.nunits, sms));
+    if (N == 4) {  // i0 = f / I_1 without a division: exact for f < 2^31 (Granlund-Montgomery, rounded-up multiplier)
+        const unsigned long long d = static_cast<unsigned long long>(s.I[1]);
+        int l = 0;
+        while ((1ULL << l) < d) ++l;
+        pl.fdiv_s = 32 + l;
+        pl.fdiv_m = ((1ULL << pl.fdiv_s) + d - 1) / d;
+    }
     if (!pl.warp) units.clear();
     return pl;
 }
