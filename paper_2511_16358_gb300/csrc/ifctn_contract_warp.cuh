@@ -219,6 +219,21 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
     const int AUX_W1 = IBP, AUX_FW = two_psi ? 2 * IBP : IBP;
     T* auxr = reinterpret_cast<T*>(smem + pl.off_aux) + static_cast<size_t>(warp) * S * AUXW;
 
+    // bases of the W rows a task needs (fixed for the launch), and the element
+    // offsets of X and W_{A,B} within their 16-byte chunk, so that a task's
+    // tile offset needs only 32-bit arithmetic (the offset mod VN is that of
+    // the low 32 bits)
+    const T* Wpsi0 = A.W + s.woff[p0 >= 0 ? p0 : 0][Bm];
+    const T* Wpsi1 = A.W + s.woff[1][Bm];
+    const T* Wfold = (isF && N == 4) ? A.W + s.woff[1 - k][Am] : A.W + s.woff[0][1];
+    const unsigned xmis = static_cast<unsigned>(shift16(A.X));
+    const unsigned wmis = static_cast<unsigned>(shift16(A.W + s.woff[Am][Bm]));
+    auto tile_shift = [&](unsigned mis, long long f, int a0) {
+        return static_cast<int>((mis + (static_cast<unsigned>(f) * static_cast<unsigned>(IA) + static_cast<unsigned>(a0)) *
+                                           static_cast<unsigned>(IB)) &
+                                static_cast<unsigned>(VN - 1));
+    };
+
     // issue path: the task's rows of X (and, N = 3 k = 0, of W_{A,B}) by TMA
     // (lane 0), its W entries by every lane, one cp.async group per issue
     UnitCur ic = {};
@@ -242,22 +257,21 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
             decode_f_fast(s, pl, tk.f, i0, i1);
             T* ax = auxr + st * AUXW;
             if (p0 >= 0) {
-                const T* r = A.W + s.woff[p0][Bm] + static_cast<long long>(p0 == 0 ? i0 : i1) * IB;
+                const T* r = Wpsi0 + static_cast<long long>(p0 == 0 ? i0 : i1) * IB;
                 for (int b = lane; b < IB; b += 32) cp_async_elem(ax + b, r + b);
             }
             if (two_psi) {
-                const T* r = A.W + s.woff[1][Bm] + static_cast<long long>(i1) * IB;
+                const T* r = Wpsi1 + static_cast<long long>(i1) * IB;
                 for (int b = lane; b < IB; b += 32) cp_async_elem(ax + AUX_W1 + b, r + b);
             }
             if (isF && N == 4) {
-                const int o = 1 - k, io = o == 0 ? i0 : i1;
+                const int io = k == 1 ? i0 : i1;  // the other F mode o = 1 - k
+                const T* r = Wfold + static_cast<long long>(io) * IA + tk.a0 + lane;
 #pragma unroll
                 for (int q = 0; q < RPL; ++q)
-                    if (lane + 32 * q < tk.na)
-                        cp_async_elem(ax + AUX_FW + 32 * q + lane,
-                                      A.W + s.woff[o][Am] + static_cast<long long>(io) * IA + tk.a0 + 32 * q + lane);
+                    if (lane + 32 * q < tk.na) cp_async_elem(ax + AUX_FW + 32 * q + lane, r + 32 * q);
             } else if (!isF && N == 4) {
-                cp_async_elem(ax + AUX_FW + lane, A.W + s.woff[0][1] + static_cast<long long>(i0) * s.I[1] + i1);
+                cp_async_elem(ax + AUX_FW + lane, Wfold + static_cast<long long>(i0) * s.I[1] + i1);
             }
             cp_async_commit();
         }
@@ -334,11 +348,9 @@ __global__ void __launch_bounds__(NW * 32, 1) k_contract_roww(const __grid_const
                 for (int q = 0; q < RPL; ++q) {
                     va[q] = lane + 32 * q < tk.na;
                     const int row = va[q] ? lane + 32 * q : 0;
-                    xr[q] = buf + shift16(A.X + (tk.f * IA + tk.a0) * IB) + static_cast<size_t>(row) * IB;
+                    xr[q] = buf + tile_shift(xmis, tk.f, tk.a0) + row * IB;
                     wr[q] = nullptr;
-                    if (foldA)
-                        wr[q] = buf + XR + shift16(A.W + s.woff[Am][Bm] + static_cast<long long>(tk.a0) * IB) +
-                                static_cast<size_t>(row) * IB;
+                    if (foldA) wr[q] = buf + XR + tile_shift(wmis, 0, tk.a0) + row * IB;
                     else if (isF)
                         wr[q] = wab + static_cast<size_t>(tk.a0 - uc.a0 + row) * LDX;
                 }
