@@ -799,8 +799,21 @@ struct Engine : ifctn_ctx {
         return launch_gram<T>(sh, k, Gt.p, W.p, t1.p, t2.p, Kk.p, done(), s);
     }
     cudaError_t stage_solve(int k, cudaStream_t s) {
-        if (sh.wide) return launch_wide_solve<T>(sh, k, prob.rho, Mk[k].p, Kk.p, Gd.p, Gt.p, W.p, flags(), done(), s);
+        if (cta_solve(k))
+            return launch_cta_solve<T>(sh, k, prob.rho, Mk[k].p, Kk.p, Gd.p, Gt.p, W.p, flags(), done(), s);
         return launch_solve_cols<T>(pp, k, s);
+    }
+    // One CTA per column (ranks above RMAX always; on the sweep graph of
+    // order 3 and 4 when a warp per column would give the mode fewer than
+    // about six waves of CTAs: the solves are latency-bound, so spreading a
+    // column's H over a CTA shortens them while the columns still fit in a few
+    // waves of two CTAs a SM).  IFCTN_CTA_SOLVE=0 or 1 forces the choice
+    // (testing, timing).
+    bool cta_solve(int k) const {
+        if (sh.wide) return true;
+        if (!graph_only || sh.N < 3) return false;
+        if (const char* e = getenv("IFCTN_CTA_SOLVE")) return strcmp(e, "0") != 0;
+        return sh.I[k] <= 6 * num_sms();
     }
     int mode_system_launches() const { return sh.wide ? 4 : 3; }
 

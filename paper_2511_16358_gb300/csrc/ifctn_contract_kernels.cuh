@@ -27,6 +27,7 @@
 // order, so results are deterministic (no atomics).
 #pragma once
 #include "ifctn_contract_dev.cuh"
+#include "ifctn_plan.h"
 
 namespace ifctn {
 namespace {
@@ -148,13 +149,14 @@ cudaError_t launch_contract(const ContractArgs<T>& a, cudaStream_t st) {
 // row, times G_{d,k}(rd, key) for every rd of the deferred mode d, and the
 // groups are added in a fixed order (deterministic).
 template <typename T>
-__global__ void __launch_bounds__(256) k_contract_finish_rows(const __grid_constant__ Shape s, const int k, const __grid_constant__ ContractPlan pl,
-                                                              const UnitDesc* __restrict__ units,
-                                                              const T* __restrict__ part, const T* __restrict__ Gt,
-                                                              double* __restrict__ Mk, const int* __restrict__ done) {
+__global__ void __launch_bounds__(1024) k_contract_finish_rows(const __grid_constant__ Shape s, const int k, const __grid_constant__ ContractPlan pl,
+                                                               const UnitDesc* __restrict__ units,
+                                                               const T* __restrict__ part, const T* __restrict__ Gt,
+                                                               double* __restrict__ Mk, const int* __restrict__ done) {
     pdl_begin();
     if (*done) return;
-    __shared__ T red[256 * RMAX];
+    extern __shared__ __align__(16) unsigned char fsm[];
+    T* red = reinterpret_cast<T*>(fsm);  // [blockDim.x][RMAX]
     const int row = blockIdx.x;
     const int Qp = pl.Qp;
     const int ng = blockDim.x / Qp;
@@ -200,7 +202,16 @@ cudaError_t launch_contract_finish(const Shape& sh, int k, const ContractPlan& p
                                    const UnitDesc* units, const T* part, const T* Gt, double* Mk,
                                    const int* done, cudaStream_t st) {
     if (pl.kcase != CASE_F && pl.Qp <= 256) {
-        k_contract_finish_rows<T><<<sh.I[k], 256, 0, st>>>(sh, k, pl, units, part, Gt, Mk, done);
+        // one CTA per output row; with few rows and many units a row gets up to
+        // 1024 threads, so that each sums fewer units (the kernel is latency-bound)
+        const int per_row = pl.nunits / (pl.fin_mod > 0 ? pl.fin_mod : 1);
+        int threads = 256;
+        while (threads < 1024 && sh.I[k] * (threads / 256) < 2 * num_sms() && per_row / (threads / pl.Qp) > 4)
+            threads *= 2;
+        const int smem = threads * RMAX * static_cast<int>(sizeof(T));
+        cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_contract_finish_rows<T>), smem);
+        if (e != cudaSuccess) return e;
+        k_contract_finish_rows<T><<<sh.I[k], threads, smem, st>>>(sh, k, pl, units, part, Gt, Mk, done);
         return cudaGetLastError();
     }
     const long long total = static_cast<long long>(sh.I[k]) * pl.Q;

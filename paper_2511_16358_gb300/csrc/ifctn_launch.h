@@ -76,9 +76,11 @@ cudaError_t launch_wide_finish(const Shape& s, int k, const T* Gt, const T* V, d
 template <typename T>
 cudaError_t launch_wide_gram(const Shape& s, int k, const T* Gt, const T* W, T* Tg, T* Kk, const int* done,
                              cudaStream_t st);
+// Column solves of mode k with one CTA per column (order 3 or 4; ranks up to
+// WIDE_RMAX, Q_k up to WIDE_QMAX): H in shared memory, FP64 Cholesky, W refresh.
 template <typename T>
-cudaError_t launch_wide_solve(const Shape& s, int k, double rho, const double* Mk, const T* Kk, double* Gd, T* Gt,
-                              T* W, int* flags, const int* done, cudaStream_t st);
+cudaError_t launch_cta_solve(const Shape& s, int k, double rho, const double* Mk, const T* Kk, double* Gd, T* Gt,
+                             T* W, int* flags, const int* done, cudaStream_t st);
 
 // eq. (updateX) fused with the reconstruction and the sweep's reductions.
 template <typename T>

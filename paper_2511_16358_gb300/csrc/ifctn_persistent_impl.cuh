@@ -1201,18 +1201,23 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
     for (long long un = VB; un < nunit; un += VG) {
         const long long r0 = un * RU;
         const int nr = static_cast<int>(min(static_cast<long long>(RU), rows_total - r0));
-        const long long f0 = r0 / IA;
+        const long long f0 = rows_total < (1LL << 32)
+                                 ? static_cast<long long>(static_cast<unsigned>(r0) / static_cast<unsigned>(IA))
+                                 : r0 / IA;
         const int a00 = static_cast<int>(r0 - f0 * IA);
         const int nsl = static_cast<int>((r0 + nr - 1) / IA - f0) + 1;
         __syncthreads();  // previous unit done with alpha / beta
+        // slab and row of unit row rl from the unit's first ones (32-bit
+        // divisions of small numbers; the slab count is below 2^31)
         for (int rl = threadIdx.x; rl < nr; rl += PT) {
-            const long long row = r0 + rl;
-            const long long f = row / IA;
-            const int a = static_cast<int>(row - f * IA);
+            const unsigned ar = static_cast<unsigned>(a00 + rl);
+            const unsigned df = ar / static_cast<unsigned>(IA);
+            const int a = static_cast<int>(ar - df * static_cast<unsigned>(IA));
+            const unsigned f = static_cast<unsigned>(f0) + df;
             int i0 = 0, i1 = 0;
             if (N == 4) {
-                i0 = static_cast<int>(f / s.I[1]);
-                i1 = static_cast<int>(f - static_cast<long long>(i0) * s.I[1]);
+                i0 = static_cast<int>(f / static_cast<unsigned>(s.I[1]));
+                i1 = static_cast<int>(f - static_cast<unsigned>(i0) * static_cast<unsigned>(s.I[1]));
             } else {
                 i0 = static_cast<int>(f);
             }
@@ -1223,11 +1228,11 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
         }
         for (int idx = threadIdx.x; idx < nsl * IB; idx += PT) {
             const int sl = idx / IB, b = idx - sl * IB;
-            const long long f = f0 + sl;
+            const unsigned f = static_cast<unsigned>(f0 + sl);
             int i0 = 0, i1 = 0;
             if (N == 4) {
-                i0 = static_cast<int>(f / s.I[1]);
-                i1 = static_cast<int>(f - static_cast<long long>(i0) * s.I[1]);
+                i0 = static_cast<int>(f / static_cast<unsigned>(s.I[1]));
+                i1 = static_cast<int>(f - static_cast<unsigned>(i0) * static_cast<unsigned>(s.I[1]));
             } else {
                 i0 = static_cast<int>(f);
             }

@@ -1,7 +1,9 @@
-// ifctn_wide.cu -- mode systems and column solves of order-3 tensors whose
-// edge ranks exceed the register-resident kernels' limit (R_{k,l} up to
-// WIDE_RMAX, Q_k up to WIDE_QMAX), as in the multispectral rank grid of
-// Sec. 5.2 (R_{1,2} up to 36).
+// ifctn_wide.cu -- mode systems of order-3 tensors whose edge ranks exceed
+// the register-resident kernels' limit (R_{k,l} up to WIDE_RMAX, Q_k up to
+// WIDE_QMAX), as in the multispectral rank grid of Sec. 5.2 (R_{1,2} up to
+// 36), and column solves with one CTA per column: for those tensors, and on
+// the sweep graph of order-3 and order-4 tensors whose modes have few enough
+// columns that a warp per column would leave most SMs idle.
 //
 // For mode k with other modes a < b, the regrouped systems of eq. (updateG)
 // (Prop. 1: M_k = X_(k) Z_k, K_k = Z_k^T Z_k; Q_k index q = r_a R_{k,b} + r_b)
@@ -19,14 +21,16 @@
 // X is read once per mode, by the first link, whose contracted mode is the
 // contiguous one (mode 2) unless k is: the loads stay coalesced.  The column
 // solves assemble H = E_j^T K_k E_j + rho I and b = E_j^T M_k(j,:)^T + rho g in
-// the tensor dtype, factorise H by Cholesky in FP64 in shared memory, and
-// refresh W_{k,i}(j, :) with the new columns (Algorithm 1's order: i != k
-// ascending, each stage using the column the previous one produced).
+// the tensor dtype with all threads of a CTA, factorise H by Cholesky in FP64
+// in shared memory, and refresh W_{k,i}(j, :) with the new columns
+// (Algorithm 1's order: i != k ascending, each stage using the column the
+// previous one produced).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "ifctn_launch.h"
+#include "ifctn_persistent.h"
 
 namespace ifctn {
 namespace {
@@ -220,15 +224,54 @@ void other_modes(int k, int& a, int& b) {
 }
 
 // ---------------------------------------------------------------------------
-// column solves
+// column solves, one CTA per column
 // ---------------------------------------------------------------------------
 constexpr int HPART = 4096;  // partial sums of H held in shared memory
 
-__host__ __device__ inline int solve_rx(const Shape& s, int k) {
-    int a, b;
-    a = k == 0 ? 1 : 0;
-    b = k == 2 ? 1 : 2;
-    return s.R[k][a] > s.R[k][b] ? s.R[k][a] : s.R[k][b];
+// The other modes of k (ascending), their ranks, the Q_k index stride of each
+// slot (slot 0 most significant) and Q_k.
+struct Slots {
+    int nm, Q, Rx;
+    int m[3], R[3], st[3];
+};
+
+__host__ __device__ inline Slots slots_of(const Shape& s, int k) {
+    Slots q;
+    q.nm = 0;
+    for (int t = 0; t < s.N; ++t)
+        if (t != k) q.m[q.nm++] = t;
+    q.Q = 1;
+    q.Rx = 1;
+    for (int t = 0; t < q.nm; ++t) {
+        q.R[t] = s.R[k][q.m[t]];
+        q.Q *= q.R[t];
+        q.Rx = q.R[t] > q.Rx ? q.R[t] : q.Rx;
+    }
+    for (int t = 0; t < 3; ++t) q.st[t] = 1;
+    for (int t = q.nm - 2; t >= 0; --t) q.st[t] = q.st[t + 1] * q.R[t + 1];
+    return q;
+}
+
+// Shared-memory layout of the solve (bytes): H, b, the current columns of the
+// slots, M_k(j, :), the partial sums of H, the weights and K offsets of the
+// other slots' digit combinations, optionally K_k at an odd row stride.
+struct CtaSolveLayout {
+    long long H, bv, gc, Mr, part, om, cbo, K, bad, total;
+};
+
+__host__ __device__ inline CtaSolveLayout cta_solve_layout(const Slots& q, int sz, bool kstage) {
+    CtaSolveLayout L;
+    L.H = 0;
+    L.bv = L.H + 8LL * q.Rx * q.Rx;
+    L.gc = L.bv + 8LL * q.Rx;
+    L.Mr = L.gc + 8LL * 3 * WIDE_RMAX;
+    L.part = L.Mr + 8LL * q.Q;
+    L.om = L.part + static_cast<long long>(sz) * HPART;
+    L.cbo = (L.om + static_cast<long long>(sz) * q.Q + 15) & ~15LL;
+    L.K = (L.cbo + 4LL * q.Q + 15) & ~15LL;
+    L.bad = L.K + (kstage ? static_cast<long long>(sz) * q.Q * k_stride(q.Q) : 0);
+    L.total = L.bad + 16;
+    return L;
 }
 
 // Row c and column c' <= c of entry e of a lower triangle stored by rows.
@@ -239,62 +282,88 @@ __device__ __forceinline__ void tri_index(int e, int& c, int& cp) {
     cp = e - c * (c + 1) / 2;
 }
 
-// One CTA per column j of mode k (grid-stride over j).  Shared memory: H
-// (Rx^2, FP64), b (Rx), the two current columns (2 x WIDE_RMAX, FP64), the
-// row M_k(j, :) (Q, FP64), the partial sums of H (HPART, T), a status word.
+// One CTA per column j of mode k (grid-stride over j), stages i != k in order
+// (each using the columns the previous ones produced).  For stage ti the other
+// slots' digit combinations o get the weight w(o) = prod_t G_{k,m_t}(d_t, j)
+// and the K_k offset cb(o); then
+//   H(c, c') = sum_{o,o'} w(o) w(o') K_k(cb(o) + c sp, cb(o') + c' sp) + rho [c = c']
+//   b(c)     = sum_o w(o) M_k(j, cb(o) + c sp) + rho g_old(c)
+// (sp the stride of slot ti), summed in the tensor dtype by (entry, group of
+// o) work items with fixed owners and added in a fixed order, factorised by
+// Cholesky in FP64 in shared memory, solved by one warp.
 template <typename T>
-__global__ void __launch_bounds__(WT) k_wide_solve(const __grid_constant__ Shape s, const int k, const double rho,
-                                                   const double* __restrict__ Mk, const T* __restrict__ Kk,
-                                                   double* __restrict__ Gd, T* __restrict__ Gt, T* __restrict__ W,
-                                                   int* __restrict__ flags, const int* __restrict__ done) {
+__global__ void __launch_bounds__(WT) k_cta_solve(const __grid_constant__ Shape s, const int k, const double rho,
+                                                  const double* __restrict__ Mk, const T* __restrict__ Kk,
+                                                  double* __restrict__ Gd, T* __restrict__ Gt, T* __restrict__ W,
+                                                  int* __restrict__ flags, const int* __restrict__ done,
+                                                  const int kstage) {
     pdl_begin();
     if (*done) return;
     extern __shared__ __align__(16) unsigned char wsm[];
-    int m[2];
-    m[0] = k == 0 ? 1 : 0;
-    m[1] = k == 2 ? 1 : 2;
-    const int Rm[2] = {s.R[k][m[0]], s.R[k][m[1]]};
-    const int Q = Rm[0] * Rm[1], Ik = s.I[k];
-    const int Rx = max(Rm[0], Rm[1]);
-    double* H = reinterpret_cast<double*>(wsm);
-    double* bv = H + Rx * Rx;
-    double* gc = bv + Rx;  // [2][WIDE_RMAX]
-    double* Mr = gc + 2 * WIDE_RMAX;
-    T* part = reinterpret_cast<T*>(Mr + Q);
-    int* bad = reinterpret_cast<int*>(part + HPART);
+    const Slots q = slots_of(s, k);
+    const int Q = q.Q, Ik = s.I[k], nm = q.nm;
+    const CtaSolveLayout L = cta_solve_layout(q, static_cast<int>(sizeof(T)), kstage != 0);
+    double* H = reinterpret_cast<double*>(wsm + L.H);
+    double* bv = reinterpret_cast<double*>(wsm + L.bv);
+    double* gc = reinterpret_cast<double*>(wsm + L.gc);  // [3][WIDE_RMAX]
+    double* Mr = reinterpret_cast<double*>(wsm + L.Mr);
+    T* part = reinterpret_cast<T*>(wsm + L.part);
+    T* om = reinterpret_cast<T*>(wsm + L.om);
+    int* cbo = reinterpret_cast<int*>(wsm + L.cbo);
+    int* bad = reinterpret_cast<int*>(wsm + L.bad);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const T* K = Kk;
+    int LK = Q;
+    if (kstage) {  // K_k once per CTA, rows at the odd stride k_stride(Q)
+        T* Ks = reinterpret_cast<T*>(wsm + L.K);
+        LK = k_stride(Q);
+        for (int idx = tid; idx < Q * Q; idx += WT) {
+            const int r = idx / Q, c = idx - r * Q;
+            Ks[r * LK + c] = Kk[idx];
+        }
+        K = Ks;
+    }
     for (int j = blockIdx.x; j < Ik; j += gridDim.x) {
-        for (int t = 0; t < 2; ++t)
-            for (int r = tid; r < Rm[t]; r += WT) gc[t * WIDE_RMAX + r] = Gd[s.goff[k][m[t]] + r * Ik + j];
-        for (int q = tid; q < Q; q += WT) Mr[q] = Mk[static_cast<long long>(j) * Q + q];
+        for (int t = 0; t < nm; ++t)
+            for (int r = tid; r < q.R[t]; r += WT) gc[t * WIDE_RMAX + r] = Gd[s.goff[k][q.m[t]] + r * Ik + j];
+        for (int c = tid; c < Q; c += WT) Mr[c] = Mk[static_cast<long long>(j) * Q + c];
         __syncthreads();
-        for (int ti = 0; ti < 2; ++ti) {
-            const int Ri = Rm[ti], Ro = Rm[1 - ti];
-            // K index of (o, c): slot 0 is the more significant digit
-            const int sc = ti == 0 ? Ro : 1, so = ti == 0 ? 1 : Ri;
-            const double* go = gc + (1 - ti) * WIDE_RMAX;
+        for (int ti = 0; ti < nm; ++ti) {
+            const int Ri = q.R[ti], sp = q.st[ti], Qo = Q / Ri;
+            for (int o = tid; o < Qo; o += WT) {  // digits of o over the slots t != ti, last slot fastest
+                int rem = o, cb = 0;
+                double w = 1.0;
+                for (int t = nm - 1; t >= 0; --t) {
+                    if (t == ti) continue;
+                    const int d = rem % q.R[t];
+                    rem /= q.R[t];
+                    w *= gc[t * WIDE_RMAX + d];
+                    cb += d * q.st[t];
+                }
+                om[o] = static_cast<T>(w);
+                cbo[o] = cb;
+            }
+            __syncthreads();
             const int ne = Ri * (Ri + 1) / 2;
-            // o split into ng groups so that the partial sums fit; fixed
-            // ownership keeps the summation order independent of timing
-            const int ng = max(1, min(Ro, HPART / ne));
-            const int og = (Ro + ng - 1) / ng;
+            const int ng = max(1, min(Qo, HPART / ne));
+            const int og = (Qo + ng - 1) / ng;
             for (int it = tid; it < ne * ng; it += WT) {
                 const int e = it / ng, g = it - e * ng;
                 int c, cp;
                 tri_index(e, c, cp);
                 T acc = T(0);
-                const int o1 = min(Ro, (g + 1) * og);
+                const int o1 = min(Qo, (g + 1) * og);
                 for (int o = g * og; o < o1; ++o) {
-                    const T* kr = Kk + static_cast<long long>(o * so + c * sc) * Q + cp * sc;
+                    const T* kr = K + static_cast<long long>(cbo[o] + c * sp) * LK + cp * sp;
                     T inner = T(0);
-                    for (int o2 = 0; o2 < Ro; ++o2) inner = fma(static_cast<T>(go[o2]), kr[o2 * so], inner);
-                    acc = fma(static_cast<T>(go[o]), inner, acc);
+                    for (int o2 = 0; o2 < Qo; ++o2) inner = fma(om[o2], kr[cbo[o2]], inner);
+                    acc = fma(om[o], inner, acc);
                 }
                 part[g * ne + e] = acc;
             }
             for (int c = tid; c < Ri; c += WT) {
                 T acc = T(0);
-                for (int o = 0; o < Ro; ++o) acc = fma(static_cast<T>(go[o]), static_cast<T>(Mr[o * so + c * sc]), acc);
+                for (int o = 0; o < Qo; ++o) acc = fma(om[o], static_cast<T>(Mr[cbo[o] + c * sp]), acc);
                 bv[c] = static_cast<double>(acc) + rho * gc[ti * WIDE_RMAX + c];
             }
             if (tid == 0) *bad = 0;
@@ -354,7 +423,7 @@ __global__ void __launch_bounds__(WT) k_wide_solve(const __grid_constant__ Shape
             if (*bad) {
                 if (tid == 0) atomicOr(flags, FLAG_NOTSPD);  // the old column stays
             } else {
-                const int i = m[ti];
+                const int i = q.m[ti];
                 for (int c = tid; c < Ri; c += WT) {
                     const double g = bv[c];
                     gc[ti * WIDE_RMAX + c] = g;
@@ -365,8 +434,8 @@ __global__ void __launch_bounds__(WT) k_wide_solve(const __grid_constant__ Shape
             __syncthreads();
         }
         // W_{k,i}(j, :) from the new columns, in the tensor dtype
-        for (int t = 0; t < 2; ++t) {
-            const int i = m[t], Ri = Rm[t], Ii = s.I[i];
+        for (int t = 0; t < nm; ++t) {
+            const int i = q.m[t], Ri = q.R[t], Ii = s.I[i];
             const T* gik = Gt + s.goff[i][k];
             for (int b2 = tid; b2 < Ii; b2 += WT) {
                 T w = T(0);
@@ -380,15 +449,6 @@ __global__ void __launch_bounds__(WT) k_wide_solve(const __grid_constant__ Shape
         }
         __syncthreads();
     }
-}
-
-template <typename T>
-int solve_smem(const Shape& s, int k) {
-    const int Rx = solve_rx(s, k);
-    int a, b;
-    other_modes(k, a, b);
-    const int Q = s.R[k][a] * s.R[k][b];
-    return (Rx * Rx + Rx + 2 * WIDE_RMAX + Q) * 8 + HPART * static_cast<int>(sizeof(T)) + 16;
 }
 
 }  // namespace
@@ -531,12 +591,18 @@ cudaError_t launch_wide_gram(const Shape& s, int k, const T* Gt, const T* W, T* 
 }
 
 template <typename T>
-cudaError_t launch_wide_solve(const Shape& s, int k, double rho, const double* Mk, const T* Kk, double* Gd, T* Gt,
-                              T* W, int* flags, const int* done, cudaStream_t st) {
-    const int smem = solve_smem<T>(s, k);
-    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_wide_solve<T>), smem);
+cudaError_t launch_cta_solve(const Shape& s, int k, double rho, const double* Mk, const T* Kk, double* Gd, T* Gt,
+                             T* W, int* flags, const int* done, cudaStream_t st) {
+    const Slots q = slots_of(s, k);
+    if (s.N < 3 || q.Rx > WIDE_RMAX || q.Q > WIDE_QMAX) return cudaErrorInvalidValue;
+    const int sz = static_cast<int>(sizeof(T));
+    // K_k staged in shared memory when the whole layout stays within about
+    // half of an SM's shared memory (two CTAs a SM)
+    int kstage = cta_solve_layout(q, sz, true).total <= 110 * 1024 ? 1 : 0;
+    const int smem = static_cast<int>(cta_solve_layout(q, sz, kstage != 0).total);
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_cta_solve<T>), smem);
     if (e != cudaSuccess) return e;
-    k_wide_solve<T><<<std::min(s.I[k], 65535), WT, smem, st>>>(s, k, rho, Mk, Kk, Gd, Gt, W, flags, done);
+    k_cta_solve<T><<<std::min(s.I[k], 65535), WT, smem, st>>>(s, k, rho, Mk, Kk, Gd, Gt, W, flags, done, kstage);
     return cudaGetLastError();
 }
 
@@ -547,8 +613,8 @@ cudaError_t launch_wide_solve(const Shape& s, int k, double rho, const double* M
                                                cudaStream_t);                                                     \
     template cudaError_t launch_wide_gram<T>(const Shape&, int, const T*, const T*, T*, T*, const int*,           \
                                              cudaStream_t);                                                       \
-    template cudaError_t launch_wide_solve<T>(const Shape&, int, double, const double*, const T*, double*, T*, T*, \
-                                              int*, const int*, cudaStream_t);
+    template cudaError_t launch_cta_solve<T>(const Shape&, int, double, const double*, const T*, double*, T*, T*, \
+                                             int*, const int*, cudaStream_t);
 IFCTN_WIDE_INST(float)
 IFCTN_WIDE_INST(double)
 #undef IFCTN_WIDE_INST

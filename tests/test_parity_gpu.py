@@ -241,3 +241,21 @@ def test_whole_run_is_one_persistent_launch():
     c.sweep(20)
     assert b.launch_count(c.ctx) - n0 == 1
     c.close()
+
+
+@pytest.mark.parametrize("cta", ["0", "1"])
+@pytest.mark.parametrize("dims,edge", [SHAPES[0], SHAPES[2], ((6, 5, 7), 8), ((9, 7, 6, 24), 3)])
+def test_graph_path_both_column_solvers_match_oracle(dims, edge, cta, monkeypatch):
+    """The sweep graph's column solves with a warp per column and with a CTA
+    per column (FP64 Cholesky of the assembled systems): one FP64 sweep each,
+    within 1e-10 of the oracle."""
+    monkeypatch.setenv("IFCTN_CTA_SOLVE", cta)
+    case = make_case(dims, edge, 0.4, seed=sum(dims) + 3)
+    with path("graph"):
+        c = _ctx(case)
+    c.sweep(1)
+    G, X = case["G0"].copy(), case["X0"].copy()
+    oracle.sweep(dims, case["R"], 0.1, G, X, case["mask"])
+    assert rel_err(c.factors(), G) < TOL64
+    assert rel_err(c.x(), X) < TOL64
+    c.close()

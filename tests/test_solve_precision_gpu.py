@@ -47,16 +47,22 @@ def _host_solves(dims, R, G, Mk, Kk, k, rho):
     return G
 
 
+@pytest.mark.parametrize("solver", ["warp", "cta"])
 @pytest.mark.parametrize("precision,tol", [(b.FP64, 1e-12), (b.MIXED, 2e-6)])
 @pytest.mark.parametrize("dims,edge", [
     ((40, 36, 30), 4),
     ((14, 12, 10, 9), {(0, 1): 3, (0, 2): 4, (0, 3): 2, (1, 2): 3, (1, 3): 4, (2, 3): 2}),
 ])
-def test_mode_solves_match_fp64_solves_of_the_same_systems(dims, edge, precision, tol):
+def test_mode_solves_match_fp64_solves_of_the_same_systems(dims, edge, precision, tol, solver, monkeypatch):
+    """solver "warp": one warp per column (the persistent path's solve phase);
+    "cta": one CTA per column (the sweep graph's solve for modes with few
+    columns; FP64 Cholesky of the assembled system)."""
     case = make_case(dims, edge, 0.3, seed=311, kind="max1", sigma=0.02)
     R, rho = case["R"], 0.1
     N = len(dims)
     dt = b.tensor_dtype(precision)
+    monkeypatch.setenv("IFCTN_PATH", "persistent" if solver == "warp" else "graph")
+    monkeypatch.setenv("IFCTN_CTA_SOLVE", "0" if solver == "warp" else "1")
     c = b.Completion(dims, R, case["xt"].astype(dt), case["mask"], rho=rho, max_sweeps=1, tol=0.0,
                      precision=precision, init_factors=case["G0"].copy())
     worst = 0.0
@@ -84,4 +90,4 @@ def test_mode_solves_match_fp64_solves_of_the_same_systems(dims, edge, precision
                         np.testing.assert_array_equal(got[(m, l)], inp.unpack_factors(G, dims, R)[(m, l)])
     c.close()
     print(f"solve error vs FP64 solves of the same systems ({'fp64' if precision == b.FP64 else 'mixed'}, "
-          f"{dims}): {worst:.3e}")
+          f"{solver}, {dims}): {worst:.3e}")
