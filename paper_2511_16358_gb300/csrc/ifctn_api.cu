@@ -803,17 +803,17 @@ struct Engine : ifctn_ctx {
             return launch_cta_solve<T>(sh, k, prob.rho, Mk[k].p, Kk.p, Gd.p, Gt.p, W.p, flags(), done(), s);
         return launch_solve_cols<T>(pp, k, s);
     }
-    // One CTA per column (ranks above RMAX always; on the sweep graph of
-    // order 3 and 4 when a warp per column would give the mode fewer than
-    // about six waves of CTAs: the solves are latency-bound, so spreading a
-    // column's H over a CTA shortens them while the columns still fit in a few
-    // waves of two CTAs a SM).  IFCTN_CTA_SOLVE=0 or 1 forces the choice
-    // (testing, timing).
+    // One CTA per column for ranks above RMAX; otherwise a warp per column,
+    // whose mixed-precision solve runs no FP64 instruction (the CTA solve's
+    // FP64 Cholesky and sums measured 3-5x slower on GB300 for the 288x400x60x24
+    // shape's modes).  IFCTN_CTA_SOLVE=1 selects the CTA solve on the sweep
+    // graph of order 3 and 4 (testing).
     bool cta_solve(int k) const {
+        (void)k;
         if (sh.wide) return true;
         if (!graph_only || sh.N < 3) return false;
-        if (const char* e = getenv("IFCTN_CTA_SOLVE")) return strcmp(e, "0") != 0;
-        return sh.I[k] <= 6 * num_sms();
+        const char* e = getenv("IFCTN_CTA_SOLVE");
+        return e && strcmp(e, "1") == 0;
     }
     int mode_system_launches() const { return sh.wide ? 4 : 3; }
 

@@ -1,9 +1,9 @@
 // ifctn_wide.cu -- mode systems of order-3 tensors whose edge ranks exceed
 // the register-resident kernels' limit (R_{k,l} up to WIDE_RMAX, Q_k up to
 // WIDE_QMAX), as in the multispectral rank grid of Sec. 5.2 (R_{1,2} up to
-// 36), and column solves with one CTA per column: for those tensors, and on
-// the sweep graph of order-3 and order-4 tensors whose modes have few enough
-// columns that a warp per column would leave most SMs idle.
+// 36), and column solves with one CTA per column: for those tensors (and,
+// when selected for testing, on the sweep graph of order-3 and order-4
+// tensors; the warp-per-column solve is faster there on GB300).
 //
 // For mode k with other modes a < b, the regrouped systems of eq. (updateG)
 // (Prop. 1: M_k = X_(k) Z_k, K_k = Z_k^T Z_k; Q_k index q = r_a R_{k,b} + r_b)
@@ -276,7 +276,9 @@ __host__ __device__ inline CtaSolveLayout cta_solve_layout(const Slots& q, int s
 
 // Row c and column c' <= c of entry e of a lower triangle stored by rows.
 __device__ __forceinline__ void tri_index(int e, int& c, int& cp) {
-    c = static_cast<int>((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+    // FP32 estimate (e < 2^12 here), corrected exactly below: no FP64 on a
+    // pipe that GB300 keeps narrow
+    c = static_cast<int>((sqrtf(8.0f * static_cast<float>(e) + 1.0f) - 1.0f) * 0.5f);
     while (c * (c + 1) / 2 > e) --c;
     while ((c + 1) * (c + 2) / 2 <= e) ++c;
     cp = e - c * (c + 1) / 2;

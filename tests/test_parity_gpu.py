@@ -246,9 +246,9 @@ def test_whole_run_is_one_persistent_launch():
 @pytest.mark.parametrize("cta", ["0", "1"])
 @pytest.mark.parametrize("dims,edge", [SHAPES[0], SHAPES[2], ((6, 5, 7), 8), ((9, 7, 6, 24), 3)])
 def test_graph_path_both_column_solvers_match_oracle(dims, edge, cta, monkeypatch):
-    """The sweep graph's column solves with a warp per column and with a CTA
-    per column (FP64 Cholesky of the assembled systems): one FP64 sweep each,
-    within 1e-10 of the oracle."""
+    """The sweep graph's column solves with a warp per column (the default) and
+    with a CTA per column (the solve of ranks above 8, selected here): one FP64
+    sweep each, within 1e-10 of the oracle."""
     monkeypatch.setenv("IFCTN_CTA_SOLVE", cta)
     case = make_case(dims, edge, 0.4, seed=sum(dims) + 3)
     with path("graph"):

@@ -54,9 +54,9 @@ def _host_solves(dims, R, G, Mk, Kk, k, rho):
     ((14, 12, 10, 9), {(0, 1): 3, (0, 2): 4, (0, 3): 2, (1, 2): 3, (1, 3): 4, (2, 3): 2}),
 ])
 def test_mode_solves_match_fp64_solves_of_the_same_systems(dims, edge, precision, tol, solver, monkeypatch):
-    """solver "warp": one warp per column (the persistent path's solve phase);
-    "cta": one CTA per column (the sweep graph's solve for modes with few
-    columns; FP64 Cholesky of the assembled system)."""
+    """solver "warp": one warp per column (both paths' default); "cta": one
+    CTA per column (the solve of ranks above 8, selected here on the sweep
+    graph; FP64 Cholesky of the assembled system)."""
     case = make_case(dims, edge, 0.3, seed=311, kind="max1", sigma=0.02)
     R, rho = case["R"], 0.1
     N = len(dims)
