@@ -52,6 +52,7 @@ struct SweepParams {
     int xu_rows;                 // X update: rows of a slab per work unit
     int xu_wab_smem;             // X update: W_{A,B} kept in shared memory
     int xu_variant;              // X update (per-stage path): batch / residency variant
+    int solve_nw;                // warps of a CTA that take columns in the solve (0: all); the rest help stage and refresh
     int cta0, ncta;              // the job's slice of the launch's grid (first CTA, CTA count)
 };
 

@@ -829,7 +829,8 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
     // what the first column needs (its data, K, the index tables) in one
     // cp.async group; the tables G_{i,k}, read only by the W refresh, in a
     // second group that is waited for before the refresh
-    const int j0 = warp * VG + VB;
+    const int NWc = p.solve_nw > 0 ? p.solve_nw : PW;  // warps that take columns (the others help stage and refresh)
+    const int j0 = warp < NWc ? warp * VG + VB : Ik;
     if (j0 < Ik) fetch_column(j0);
     if (ksm) {  // rows at the odd stride k_stride(Q)
         const int LKs = k_stride(Q);
@@ -863,12 +864,12 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
     const float rhi = static_cast<float>(rho);
     const float rlo = static_cast<float>(rho - static_cast<double>(rhi));
     // W refresh by the whole CTA when every warp has at most one column
-    const bool cta_refresh = static_cast<long long>(VG) * PW >= Ik;
+    const bool cta_refresh = static_cast<long long>(VG) * NWc >= Ik;
     if (!cta_refresh) {  // every warp refreshes its columns: the tables first
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
     }
-    for (int j = j0; j < Ik; j += VG * PW) {
+    for (int j = j0; j < Ik; j += VG * NWc) {
         if (j != j0) {
             fetch_column(j);
             asm volatile("cp.async.wait_all;" ::: "memory");
@@ -989,12 +990,11 @@ __device__ void solve_phase(const SweepParams<T>& p, int k, unsigned char* smem,
     if (cta_refresh) {
         // columns of this CTA: j = w * VG + VB, their new
         // G_{k,i}(:, j) in warp w's scratch (same arithmetic as per warp)
-        const int ncol = min(PW, (Ik - VB + VG - 1) /
-                                     VG);
+        const int ncol = min(NWc, (Ik - VB + VG - 1) / VG);
         for (int t = 0; t < nm; ++t) {
             const int i = m[t], Ri = Rm[t], Ii = s.I[i];
             const T* gk = gik + gko[t];
-            for (int idx = tid; idx < ncol * Ii; idx += PT) {
+            for (int idx = tid; idx < ncol * Ii; idx += blockDim.x) {
                 const int w = idx / Ii, b = idx - w * Ii;
                 const int j = w * VG + VB;
                 const T* vtw = warp_scratch_t<T>(smem, w) + SC_VT + t * RMAX;
@@ -1714,8 +1714,19 @@ cudaError_t launch_solve_cols(const SweepParams<T>& p0, int k, cudaStream_t st) 
     const int smem = static_cast<int>(solve_layout(Q, tot, sz, p.solve_k_in_smem != 0).total + 64);
     cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(k_solve_cols<T>), smem);
     if (e != cudaSuccess) return e;
+    // Warps of a CTA that take columns: as few as spread the columns over
+    // every SM, so that columns do not queue on one SM's shared-memory pipe
+    // while others idle (the assembly of H reads K_k from shared memory); all
+    // PT threads still stage K_k and the tables and refresh W.  With nw warps
+    // and ncta = ceil(I_k / nw) CTAs, column j = w ncta + CTA is taken by warp
+    // w < nw, and every CTA refreshes its own columns.
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int nw = std::max(1, std::min(PW, (s.I[k] + sms - 1) / std::max(1, sms)));
+    p.solve_nw = nw;
     p.cta0 = 0;
-    p.ncta = (s.I[k] + PW - 1) / PW;
+    p.ncta = (s.I[k] + nw - 1) / nw;
     k_solve_cols<T><<<p.ncta, PT, smem, st>>>(p, k);
     return cudaGetLastError();
 }
