@@ -718,6 +718,8 @@ struct Engine : ifctn_ctx {
         if (psmem > 227 * 1024) return;
         int g = persistent_max_grid<T>(psmem);
         if (grid_cap > 0) g = std::min(g, grid_cap);
+        if (const char* e = getenv("IFCTN_GRID_CAP"))  // timing of the grid size
+            if (atoi(e) > 0) g = std::min(g, atoi(e));
         if (g < 1 || 16LL * g > static_cast<long long>(xpart.n)) return;
         pgrid = g;
         persistent = true;
