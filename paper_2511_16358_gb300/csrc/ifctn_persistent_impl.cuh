@@ -1299,16 +1299,22 @@ __device__ void xupdate_phase(const SweepParams<T>& p, double* out6, unsigned ch
                     const int o = ob + t * PT + threadIdx.x;
                     if (o < n4) {
                         const long long e = e0 + static_cast<long long>(o) * VN;
+                        // the vector's VN mask bits (a whole chunk lies in one 32-bit word)
+                        const uint32_t ob4 = wd[t] >> (static_cast<unsigned>(e) & 31u);
                         T xn[VN];
 #pragma unroll
                         for (int j = 0; j < VN; ++j) {
-                            const bool obs = (wd[t] >> ((e + j) & 31)) & 1u;
+                            const bool obs = (ob4 >> j) & 1u;
                             xn[j] = obs ? xo[t][j] : (rec[t][j] + rho * xo[t][j]) * inv1p;
                             const T d = xn[j] - xo[t][j], r = xn[j] - rec[t][j];
                             fa[0] = fma(d, d, fa[0]);
                             fa[1] = fma(xo[t][j], xo[t][j], fa[1]);
                             fa[2] = fma(r, r, fa[2]);
-                            if (met) {
+                        }
+                        if (met) {
+#pragma unroll
+                            for (int j = 0; j < VN; ++j) {
+                                const bool obs = (ob4 >> j) & 1u;
                                 const T xt = p.Xt[e + j];
                                 const T de = xt - xn[j];
                                 fa[3] = fma(de, de, fa[3]);
