@@ -1,4 +1,7 @@
 // ifctn_kernels.cu -- Gram chain, proximal solves, fused X update and helpers.
+#include <cstdlib>
+#include <cstring>
+
 #include "ifctn_launch.h"
 
 namespace ifctn {
@@ -770,7 +773,14 @@ cudaError_t launch_gram(const Shape& sh, int k, const T* Gt, const T* W, T* t1, 
     int m[3], nm = 0;
     for (int q = 0; q < sh.N; ++q)
         if (q != k) m[nm++] = q;
-    if (nm == 3) {
+    // a middle mode of 128 or more entries: one CTA per i_o is latency-bound, the
+    // batched products over i_o are not (IFCTN_GRAM_GEMM=0 or 1 forces the choice)
+    bool gemm = nm == 3 && sh.I[m[1]] >= 128;
+    if (const char* e = getenv("IFCTN_GRAM_GEMM")) gemm = nm == 3 && strcmp(e, "0") != 0;
+    if (gemm) {
+        cudaError_t e = launch_gram4_gemm<T>(sh, k, Gt, W, t1, t2, done, st);
+        if (e != cudaSuccess) return e;
+    } else if (nm == 3) {
         const int RL = sh.R[k][m[2]];
         const long long smem = gram_io_smem<T>(RL, sh.I[m[2]], sh.I[m[1]], sh.R[k][m[1]]);
         if (smem <= 200 * 1024) {

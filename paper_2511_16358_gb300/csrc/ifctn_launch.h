@@ -76,6 +76,13 @@ cudaError_t launch_wide_finish(const Shape& s, int k, const T* Gt, const T* V, d
 template <typename T>
 cudaError_t launch_wide_gram(const Shape& s, int k, const T* Gt, const T* W, T* Tg, T* Kk, const int* done,
                              cudaStream_t st);
+// The first two steps of the order-4 Gram chain (T2 of k_gram_io: t1 scratch of
+// I_o I_c R_{k,l}(R_{k,l}+1)/2 entries) as two batched products over i_o; used
+// when the middle mode is long enough that one CTA per i_o is latency-bound.
+template <typename T>
+cudaError_t launch_gram4_gemm(const Shape& s, int k, const T* Gt, const T* W, T* t1, T* t2, const int* done,
+                              cudaStream_t st);
+
 // Column solves of mode k with one CTA per column (order 3 or 4; ranks up to
 // WIDE_RMAX, Q_k up to WIDE_QMAX): H in shared memory, FP64 Cholesky, W refresh.
 template <typename T>

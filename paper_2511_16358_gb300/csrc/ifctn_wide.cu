@@ -189,6 +189,71 @@ struct OpGram2 {
     }
 };
 
+// Order-4 Gram, other modes o < c < l of k (o the batch): pairs p = (x, y),
+// x <= y, of the l-slot rank run over NP = R_l (R_l + 1) / 2 in row order.
+__device__ __forceinline__ void pair_of(int p, int R, int& x, int& y) {
+    x = 0;
+    while (p >= R - x) {
+        p -= R - x;
+        ++x;
+    }
+    y = x + p;
+}
+
+// First link: t1[o][ic][p] = W_{o,c}(o, ic)^2 sum_{il} W_{c,l}(ic, il)^2 W_{o,l}(o, il)^2 G_{l,k}(x_p, il) G_{l,k}(y_p, il);
+// batch b = i_o, m = i_c, n = p, i = i_l.
+template <typename T>
+struct OpGram4a {
+    const T* Wcl;  // W_{c,l}(ic, il) at Wcl[ic * cs_c + il * cs_l]
+    const T* Wol;  // W_{o,l}(io, il) at Wol[io * os_o + il * os_l]
+    const T* Woc;  // W_{o,c}(io, ic) at Woc[io * ws_o + ic * ws_c]
+    const T* Gl;   // G_{l,k}
+    T* t1;
+    int cs_c, cs_l, os_o, os_l, ws_o, ws_c, Il, RL;
+    int M, N, K, batch;
+    bool a_m_fast, b_n_fast;
+    __device__ T a(int, int m, int i) const {
+        const T w = Wcl[static_cast<long long>(m) * cs_c + static_cast<long long>(i) * cs_l];
+        return w * w;
+    }
+    __device__ T bm(int b, int i, int n) const {
+        int x, y;
+        pair_of(n, RL, x, y);
+        const T w = Wol[static_cast<long long>(b) * os_o + static_cast<long long>(i) * os_l];
+        return w * w * Gl[static_cast<long long>(x) * Il + i] * Gl[static_cast<long long>(y) * Il + i];
+    }
+    __device__ void store(int b, int m, int n, T v) const {
+        const T w = Woc[static_cast<long long>(b) * ws_o + static_cast<long long>(m) * ws_c];
+        t1[(static_cast<long long>(b) * M + m) * N + n] = v * w * w;
+    }
+};
+
+// Second link: T2[o][(xc, xl), (yc, yl)] = sum_{ic} G_{c,k}(xc, ic) G_{c,k}(yc, ic) t1[o][ic][p(xl, yl)],
+// both (xl, yl) and (yl, xl); batch b = i_o, m = (xc, yc), n = p, i = i_c.
+template <typename T>
+struct OpGram4b {
+    const T* Gc;  // G_{c,k}
+    const T* t1;
+    T* T2;
+    int Ic, Rc, RL, NP;
+    int M, N, K, batch;
+    bool a_m_fast, b_n_fast;
+    __device__ T a(int, int m, int i) const {
+        const int xc = m / Rc, yc = m - xc * Rc;
+        return Gc[static_cast<long long>(xc) * Ic + i] * Gc[static_cast<long long>(yc) * Ic + i];
+    }
+    __device__ T bm(int b, int i, int n) const { return t1[(static_cast<long long>(b) * Ic + i) * NP + n]; }
+    __device__ void store(int b, int m, int n, T v) const {
+        const int xc = m / Rc, yc = m - xc * Rc;
+        int xl, yl;
+        pair_of(n, RL, xl, yl);
+        const int Q2 = Rc * RL;
+        T* out = T2 + static_cast<long long>(b) * Q2 * Q2;
+        out[(xc * RL + xl) * Q2 + yc * RL + yl] = v;
+        if (xl != yl) out[(xc * RL + yl) * Q2 + yc * RL + xl] = v;
+    }
+};
+
 template <typename T, class Op>
 cudaError_t launch_gemm(const Op& op, const int* done, cudaStream_t st) {
     if (op.M <= 0 || op.N <= 0 || op.batch <= 0) return cudaSuccess;
@@ -593,6 +658,48 @@ cudaError_t launch_wide_gram(const Shape& s, int k, const T* Gt, const T* W, T* 
 }
 
 template <typename T>
+cudaError_t launch_gram4_gemm(const Shape& s, int k, const T* Gt, const T* W, T* t1, T* t2, const int* done,
+                              cudaStream_t st) {
+    int m[3], nm = 0;
+    for (int q = 0; q < s.N; ++q)
+        if (q != k) m[nm++] = q;
+    if (nm != 3) return cudaErrorInvalidValue;
+    const int o = m[0], c = m[1], l = m[2];
+    const int RL = s.R[k][l], Rc = s.R[k][c], NP = RL * (RL + 1) / 2;
+    OpGram4a<T> a;
+    a.Wcl = pair_view(s, W, c, l, a.cs_c, a.cs_l);
+    a.Wol = pair_view(s, W, o, l, a.os_o, a.os_l);
+    a.Woc = pair_view(s, W, o, c, a.ws_o, a.ws_c);
+    a.Gl = Gt + s.goff[l][k];
+    a.t1 = t1;
+    a.Il = s.I[l];
+    a.RL = RL;
+    a.M = s.I[c];
+    a.N = NP;
+    a.K = s.I[l];
+    a.batch = s.I[o];
+    a.a_m_fast = a.cs_c == 1;
+    a.b_n_fast = false;
+    cudaError_t e = launch_gemm<T>(a, done, st);
+    if (e != cudaSuccess) return e;
+    OpGram4b<T> b;
+    b.Gc = Gt + s.goff[c][k];
+    b.t1 = t1;
+    b.T2 = t2;
+    b.Ic = s.I[c];
+    b.Rc = Rc;
+    b.RL = RL;
+    b.NP = NP;
+    b.M = Rc * Rc;
+    b.N = NP;
+    b.K = s.I[c];
+    b.batch = s.I[o];
+    b.a_m_fast = false;
+    b.b_n_fast = true;
+    return launch_gemm<T>(b, done, st);
+}
+
+template <typename T>
 cudaError_t launch_cta_solve(const Shape& s, int k, double rho, const double* Mk, const T* Kk, double* Gd, T* Gt,
                              T* W, int* flags, const int* done, cudaStream_t st) {
     const Slots q = slots_of(s, k);
@@ -616,7 +723,9 @@ cudaError_t launch_cta_solve(const Shape& s, int k, double rho, const double* Mk
     template cudaError_t launch_wide_gram<T>(const Shape&, int, const T*, const T*, T*, T*, const int*,           \
                                              cudaStream_t);                                                       \
     template cudaError_t launch_cta_solve<T>(const Shape&, int, double, const double*, const T*, double*, T*, T*, \
-                                             int*, const int*, cudaStream_t);
+                                             int*, const int*, cudaStream_t);                                     \
+    template cudaError_t launch_gram4_gemm<T>(const Shape&, int, const T*, const T*, T*, T*, const int*,         \
+                                              cudaStream_t);
 IFCTN_WIDE_INST(float)
 IFCTN_WIDE_INST(double)
 #undef IFCTN_WIDE_INST

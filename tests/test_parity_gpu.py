@@ -259,3 +259,34 @@ def test_graph_path_both_column_solvers_match_oracle(dims, edge, cta, monkeypatc
     assert rel_err(c.factors(), G) < TOL64
     assert rel_err(c.x(), X) < TOL64
     c.close()
+
+
+@pytest.mark.parametrize("gemm", ["0", "1"])
+@pytest.mark.parametrize("dims,edge", [((5, 130, 7, 6), 3), ((6, 9, 5, 4), {(0, 1): 2, (0, 2): 3, (0, 3): 4,
+                                                                               (1, 2): 2, (1, 3): 3, (2, 3): 2})])
+def test_order4_gram_chain_both_forms_match_oracle_block_systems(dims, edge, gemm, monkeypatch):
+    """The order-4 Gram K_k of the sweep graph by one CTA per i_o and by two
+    batched products over i_o (IFCTN_GRAM_GEMM): E_j^T K_k E_j equals the
+    oracle's A_j^T A_j for every block and column (1e-11)."""
+    monkeypatch.setenv("IFCTN_GRAM_GEMM", gemm)
+    case = make_case(dims, edge, 0.5, seed=13)
+    with path("graph"):
+        c = _ctx(case)
+    N = len(dims)
+    R = case["R"]
+    F = inp.unpack_factors(case["G0"], dims, R)
+    for k in range(N):
+        others = [m for m in range(N) if m != k]
+        Q = int(np.prod([R[k][m] for m in others]))
+        Mk = np.zeros((dims[k], Q))
+        Kk = np.zeros((Q, Q))
+        b.mode_system(c.ctx, k, Mk, Kk)
+        for i in others:
+            for j in range(0, dims[k], max(1, dims[k] // 7)):
+                vecs = [np.eye(R[k][m]) if m == i else F[(k, m)][:, j][:, None] for m in others]
+                E = vecs[0]
+                for v in vecs[1:]:
+                    E = np.kron(E, v)
+                Ho, _ = oracle.block_system(dims, R, case["G0"], case["X0"], k, i, j)
+                assert rel_err(E.T @ Kk @ E, Ho) < 1e-11
+    c.close()
