@@ -77,8 +77,8 @@ template <typename T>
 cudaError_t launch_wide_gram(const Shape& s, int k, const T* Gt, const T* W, T* Tg, T* Kk, const int* done,
                              cudaStream_t st);
 // The first two steps of the order-4 Gram chain (T2 of k_gram_io: t1 scratch of
-// I_o I_c R_{k,l}(R_{k,l}+1)/2 entries) as two batched products over i_o; used
-// when the middle mode is long enough that one CTA per i_o is latency-bound.
+// I_o I_c R_{k,l}(R_{k,l}+1)/2 entries) as two batched products over i_o, the
+// alternative to one CTA per i_o (selected by IFCTN_GRAM_GEMM=1).
 template <typename T>
 cudaError_t launch_gram4_gemm(const Shape& s, int k, const T* Gt, const T* W, T* t1, T* t2, const int* done,
                               cudaStream_t st);

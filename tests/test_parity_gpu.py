@@ -265,9 +265,9 @@ def test_graph_path_both_column_solvers_match_oracle(dims, edge, cta, monkeypatc
 @pytest.mark.parametrize("dims,edge", [((5, 130, 7, 6), 3), ((6, 9, 5, 4), {(0, 1): 2, (0, 2): 3, (0, 3): 4,
                                                                                (1, 2): 2, (1, 3): 3, (2, 3): 2})])
 def test_order4_gram_chain_both_forms_match_oracle_block_systems(dims, edge, gemm, monkeypatch):
-    """The order-4 Gram K_k of the sweep graph by one CTA per i_o and by two
-    batched products over i_o (IFCTN_GRAM_GEMM): E_j^T K_k E_j equals the
-    oracle's A_j^T A_j for every block and column (1e-11)."""
+    """The order-4 Gram K_k of the sweep graph by one CTA per i_o (the default)
+    and by two batched products over i_o (IFCTN_GRAM_GEMM=1): E_j^T K_k E_j
+    equals the oracle's A_j^T A_j for every block and column (1e-11)."""
     monkeypatch.setenv("IFCTN_GRAM_GEMM", gemm)
     case = make_case(dims, edge, 0.5, seed=13)
     with path("graph"):
